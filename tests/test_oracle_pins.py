@@ -1,0 +1,431 @@
+"""Pins for the CPU oracle: each check compares it with something other than
+itself (closed forms, brute force, exact low rank, dense SVD, the identities
+of Sec. III-A).  CPU only."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import h2_oracle as O
+from paper_2506_16759_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+KNAMES = {"exp": O.K_EXP, "matern32": O.K_MATERN32, "gauss": O.K_GAUSS,
+          "laplace_ie": O.K_LAPLACE_IE, "poly": O.K_POLY}
+
+
+def _golden_kernel_rows():
+    rows = []
+    with open(os.path.join(GOLDEN, "kernel_values.txt")) as f:
+        for line in f:
+            if not line.strip() or line.startswith("#"):
+                continue
+            fields = [x.strip() for x in line.split("|")]
+            kname, params = fields[0].split()
+            rows.append((KNAMES[kname], tuple(float(v) for v in params.split(",")),
+                         [float(v) for v in fields[1].split(",")],
+                         [float(v) for v in fields[2].split(",")],
+                         fields[3] == "1", float(fields[4])))
+    return rows
+
+
+@pytest.mark.parametrize("row", _golden_kernel_rows())
+def test_kernel_closed_forms(row):
+    kernel, params, xa, xb, same, expected = row
+    if kernel == O.K_POLY:
+        params = (params[0], int(params[1]))
+    ia = np.array([0])
+    ib = np.array([0 if same else 1])
+    val = O.kernel_block(kernel, params, np.array([xa]), np.array([xb]), ia, ib)[0, 0]
+    assert val == pytest.approx(expected, rel=1e-14, abs=1e-15)
+
+
+# --- cluster tree ----------------------------------------------------------------
+
+
+@pytest.mark.parametrize("n,dim,leaf", [(1000, 2, 64), (777, 3, 16), (64, 2, 64), (65, 3, 64),
+                                        (5, 2, 2), (1, 3, 4)])
+def test_tree_structure(n, dim, leaf):
+    X = W.uniform_points(n, dim, 11)
+    t = O.build_cluster_tree(X, leaf)
+    # uniform depth: smallest L with ceil(n / 2^L) <= leaf
+    L = t.depth
+    assert math.ceil(n / 2 ** L) <= leaf and (L == 0 or math.ceil(n / 2 ** (L - 1)) > leaf)
+    assert sorted(t.perm.tolist()) == list(range(n))
+    for v in range(t.n_nodes):
+        P = t.perm[t.begin[v]:t.end[v]]
+        assert len(P) >= 1
+        # tight box
+        assert np.array_equal(t.lo[v], X[P].min(0)) and np.array_equal(t.hi[v], X[P].max(0))
+        if 2 * v + 1 < t.n_nodes:
+            a, b = 2 * v + 1, 2 * v + 2
+            na, nb = t.end[a] - t.begin[a], t.end[b] - t.begin[b]
+            assert na == (len(P) + 1) // 2 and na + nb == len(P)
+            ext = t.hi[v] - t.lo[v]
+            s = t.split_dim[v]
+            assert ext[s] == ext.max() and all(ext[q] < ext[s] for q in range(s))
+            # every left point precedes every right point in (coordinate, index) order
+            left = [(X[p, s], p) for p in t.perm[t.begin[a]:t.end[a]]]
+            right = [(X[p, s], p) for p in t.perm[t.begin[b]:t.end[b]]]
+            assert max(left) < min(right)
+    # leaf members are ordered by the parent's split key
+    if L > 0:
+        for v in t.nodes_at_depth(L):
+            s = t.split_dim[(v - 1) // 2]
+            keys = [(X[p, s], p) for p in t.perm[t.begin[v]:t.end[v]]]
+            assert keys == sorted(keys)
+
+
+def test_tree_duplicate_points():
+    # all points identical: every extent is 0, so dimension 0 is used and the
+    # point index alone orders the split
+    X = np.full((100, 3), 0.25)
+    t = O.build_cluster_tree(X, 8)
+    assert t.perm.tolist() == list(range(100))
+    lists = O.dual_traversal(t, 0.7)
+    assert O.top_level(t, lists) == 0
+
+
+def test_admissibility_hand_cases():
+    # unit squares: D = sqrt 2 each.  Gap 2 -> (sqrt2 + sqrt2)/2 = 1.414 > 0.7*2
+    t = O.ClusterTree(np.zeros((1, 2)), 2, 0, np.zeros(1, int), np.zeros(3, int), np.zeros(3, int),
+                      np.array([[0, 0], [3, 0], [4, 0.]]), np.array([[1, 1], [4, 1], [5, 1.]]),
+                      np.zeros(3, int))
+    assert O.box_diameter(t.lo[0], t.hi[0]) == pytest.approx(math.sqrt(2))
+    assert O.box_distance(t.lo[0], t.hi[0], t.lo[1], t.hi[1]) == 2.0
+    assert not O.admissible(t, 0, 1, 0.7)
+    assert O.box_distance(t.lo[0], t.hi[0], t.lo[2], t.hi[2]) == 3.0
+    assert O.admissible(t, 0, 2, 0.7)           # 1.414 <= 2.1
+    assert O.admissible(t, 2, 0, 0.7)
+    assert not O.admissible(t, 0, 2, 0.47)      # 1.414 > 1.41
+    # touching or overlapping boxes are never admissible (Dist = 0)
+    assert not O.admissible(t, 1, 2, 1e9)
+    # diagonal gap: boxes [0,1]^2 and [2,3]^2 -> Dist = sqrt(2)
+    t.lo[1], t.hi[1] = [2, 2], [3, 3]
+    assert O.box_distance(t.lo[0], t.hi[0], t.lo[1], t.hi[1]) == pytest.approx(math.sqrt(2))
+
+
+@pytest.mark.parametrize("eta", [0.7, 1.5, 0.3])
+def test_block_partition_brute_force(eta):
+    n = 300
+    X = W.uniform_points(n, 2, 3)
+    t = O.build_cluster_tree(X, 8)
+    lists = O.dual_traversal(t, eta)
+    cover = np.zeros((n, n), dtype=int)
+    for s, partners in lists.near.items():
+        for b in partners:
+            cover[t.begin[s]:t.end[s], t.begin[b]:t.end[b]] += 1
+    for k in range(t.depth + 1):
+        for s, partners in lists.far[k].items():
+            for b in partners:
+                cover[t.begin[s]:t.end[s], t.begin[b]:t.end[b]] += 1
+                assert O.admissible(t, s, b, eta)
+                # F_s: the parents must form an inadmissible pair
+                if k > 0:
+                    assert not O.admissible(t, (s - 1) // 2, (b - 1) // 2, eta)
+    assert (cover == 1).all()
+    # symmetry of both lists
+    for s, partners in lists.near.items():
+        for b in partners:
+            assert s in lists.near[b]
+    for k in range(t.depth + 1):
+        for s, partners in lists.far[k].items():
+            assert partners == sorted(partners)
+            for b in partners:
+                assert s in lists.far[k][b]
+
+
+# --- dense kernels of the construction ---------------------------------------------
+
+
+def test_qr_min_diag_known_factor():
+    rng = np.random.default_rng(0)
+    Q, _ = np.linalg.qr(rng.standard_normal((40, 12)))
+    R0 = np.triu(rng.standard_normal((12, 12)))
+    diag = np.array([3.0, -2.0, 1.5, 1e-3, 7.0, 0.5, -0.25, 2.0, 1.0, 4.0, -9.0, 0.75])
+    R0[np.arange(12), np.arange(12)] = diag
+    assert O.qr_min_abs_diag(Q @ R0) == pytest.approx(1e-3, rel=1e-9)
+    assert O.node_converged(Q @ R0, 2e-3) and not O.node_converged(Q @ R0, 5e-4)
+    assert O.node_converged(rng.standard_normal((8, 12)), 0.0)   # m <= d
+
+
+def test_cpqr_exact_rank_and_interpolation():
+    rng = np.random.default_rng(1)
+    for rows, cols, k in [(30, 50, 7), (20, 20, 20), (12, 40, 1)]:
+        A = rng.standard_normal((rows, k)) @ rng.standard_normal((k, cols))
+        kk, piv, T = O.cpqr_column_id(A, 1e-10 * np.linalg.norm(A))
+        assert kk == k
+        S, R = piv[:kk], piv[kk:]
+        assert np.linalg.norm(A[:, R] - A[:, S] @ T) <= 1e-12 * np.linalg.norm(A)
+        if len(R):
+            Tls = np.linalg.lstsq(A[:, S], A[:, R], rcond=None)[0]
+            assert np.allclose(T, Tls, atol=1e-8)
+
+
+def test_cpqr_pivots_follow_norms():
+    # orthogonal columns: pivots in decreasing norm order, lowest index on ties
+    norms = np.array([1.0, 5.0, 3.0, 5.0, 0.5])
+    Q, _ = np.linalg.qr(np.random.default_rng(2).standard_normal((8, 5)))
+    A = Q * norms
+    k, piv, T = O.cpqr_column_id(A, 0.0)
+    assert piv.tolist() == [1, 3, 2, 0, 4] and k == 5
+    k, piv, T = O.cpqr_column_id(A, math.sqrt(1.0 + 0.25) + 1e-12)
+    assert k == 3
+
+
+def test_row_id_basis_identity_rows():
+    rng = np.random.default_rng(3)
+    Y = rng.standard_normal((30, 6)) @ rng.standard_normal((6, 40))
+    rid = O.row_id(Y, 1e-9)
+    assert rid.k == 6
+    assert np.array_equal(rid.J, np.sort(rid.J))
+    assert np.array_equal(rid.U[rid.J], np.eye(6))
+    assert np.linalg.norm(Y - rid.U @ Y[rid.J]) <= 1e-11 * np.linalg.norm(Y)
+
+
+# --- whole construction ------------------------------------------------------------
+
+
+def _build(n, dim, kernel, params, tol, leaf=64, eta=0.7, seed=1, d0=32, d_inc=16, d_max=256):
+    X = W.uniform_points(n, dim, seed)
+    om = W.gaussian_omega(n, d_max, seed + 1)
+    t = O.build_cluster_tree(X, leaf)
+    lists = O.dual_traversal(t, eta)
+    A = O.dense_matrix(X, kernel, params)
+    h = O.build_h2(t, lists, kernel, params, tol, om, O.dense_sampler(A), d0, d_inc, d_max)
+    return X, om, t, lists, A, h
+
+
+def test_c1_dense_error_within_tolerance():
+    w = W.config("c1")
+    X, om = w.points(), w.omega()
+    t = O.build_cluster_tree(X, w.leaf_size)
+    lists = O.dual_traversal(t, w.eta)
+    A = O.dense_matrix(X, w.kernel, w.params)
+    h = O.build_h2(t, lists, w.kernel, w.params, w.tol, om, O.dense_sampler(A),
+                   w.d0, w.d_inc, w.d_max)
+    assert h.converged and h.l_top >= 2
+    err = O.dense_rel_error(h, A)
+    assert err <= 10 * w.tol
+    # the tree-walk matvec agrees with the dense expansion of the representation
+    G = W.gaussian_probe(w.n, 4, 0)
+    Ad = O.h2_dense(h)
+    assert np.linalg.norm(O.h2_matvec(h, G) - Ad @ G) <= 1e-13 * np.linalg.norm(Ad @ G)
+    # randomized Frobenius estimate agrees with the dense error to a factor ~2
+    est = O.sampled_rel_error(h, X, w.kernel, w.params, W.gaussian_probe(w.n, 16, 1))
+    assert 0.3 * err <= est <= 3 * err
+
+
+def test_polynomial_kernel_exact_rank():
+    # (1 + x.y)^3 in 2D has rank C(2+3, 3) = 10: every compressed node whose
+    # admissible block row has rank 10 gets k = 10 and the result is exact.
+    X, om, t, lists, A, h = _build(2048, 2, O.K_POLY, (1.0, 3), 1e-10, leaf=32)
+    assert h.l_top >= 2
+    for level in range(1, h.l_top + 1):
+        for tau in t.nodes_at_depth(t.level_depth(level)):
+            nd = h.nodes[tau]
+            assert nd.k <= 10
+            if nd.m >= 10 and _far_columns(t, lists, h.l_top, tau, level).size >= 10:
+                assert nd.k == 10
+    assert O.dense_rel_error(h, A) <= 1e-12
+
+
+def _far_columns(t, lists, l_top, tau, level):
+    """Tree positions of every column block admissible to tau or an ancestor at
+    levels >= level."""
+    cols = []
+    node, lv = tau, level
+    while lv <= l_top:
+        for b in lists.far[t.level_depth(lv)].get(node, []):
+            cols.extend(range(t.begin[b], t.end[b]))
+        node, lv = (node - 1) // 2, lv + 1
+    return np.array(sorted(cols), dtype=int)
+
+
+def _frobenius_rank(s, eps):
+    tail = np.sqrt(np.cumsum((s ** 2)[::-1])[::-1])
+    for r in range(len(s)):
+        if tail[r] <= eps:
+            return r
+    return len(s)
+
+
+def _svd_rank_violations(t, lists, h, kernel, params, slack=3):
+    Xt = t.Xt()
+    bad = []
+    for level in range(1, h.l_top + 1):
+        eps = h.eps_level[level]
+        for tau in t.nodes_at_depth(t.level_depth(level)):
+            nd = h.nodes[tau]
+            cols = _far_columns(t, lists, h.l_top, tau, level)
+            if cols.size == 0 or nd.m == 0:
+                continue
+            M = O.kernel_block(kernel, params, Xt[nd.Ibar], Xt[cols], nd.Ibar, cols)
+            s = np.linalg.svd(M, compute_uv=False)
+            if not (_frobenius_rank(s, 2 * eps) <= nd.k <= _frobenius_rank(s, eps) + slack):
+                bad.append((level, tau, nd.k, _frobenius_rank(s, eps)))
+    return bad
+
+
+@pytest.mark.parametrize("tol", [1e-4, 1e-6, 1e-8])
+def test_ranks_match_dense_svd(tol):
+    # The ID rank of each node sits between the Frobenius eps_l-ranks of its
+    # true admissible block row (rows: the node's candidate skeletons; columns:
+    # everything admissible to it or its ancestors).
+    X, om, t, lists, A, h = _build(1024, 2, O.K_EXP, (0.2, 1e-4), tol, leaf=16, seed=5)
+    assert h.l_top >= 3
+    assert _svd_rank_violations(t, lists, h, O.K_EXP, (0.2, 1e-4)) == []
+    assert O.dense_rel_error(h, A) <= 10 * tol
+
+
+def test_sample_recurrence_exact_low_rank():
+    # Y^l = W^l Y^{l-1} (Sec. III-A): with exact IDs (rank-10 kernel) the local
+    # samples of child nu inside its parent equal the samples of the blocks
+    # admissible to nu's ancestors only, restricted to nu's skeleton rows.
+    X, om, t, lists, A, h = _build(2048, 2, O.K_POLY, (1.0, 3), 1e-10, leaf=32)
+    Xt = t.Xt()
+    omt = om[t.perm]
+    d = h.d_level[2]
+    checked = 0
+    for tau in t.nodes_at_depth(t.level_depth(2)):
+        nd = h.nodes[tau]
+        row0 = 0
+        cols = _far_columns(t, lists, h.l_top, tau, 2)
+        for nu in (2 * tau + 1, 2 * tau + 2):
+            Itil = h.nodes[nu].Itil
+            expect = O.kernel_block(O.K_POLY, (1.0, 3), Xt[Itil], Xt[cols], Itil, cols) @ omt[cols, :d]
+            got = nd.Yloc[row0:row0 + len(Itil)]
+            assert np.linalg.norm(got - expect) <= 1e-9 * max(1.0, np.linalg.norm(expect))
+            checked += int(cols.size > 0)
+            row0 += len(Itil)
+    assert checked > 0
+
+
+def test_full_sampling_is_exact():
+    # tol = 0: no node converges until d >= m, so every ID keeps all rows.
+    X, om, t, lists, A, h = _build(512, 2, O.K_EXP, (0.2, 1e-4), 0.0, leaf=16, d0=8, d_inc=8,
+                                   d_max=64)
+    assert h.converged
+    assert h.d_level[1] >= 16
+    assert O.dense_rel_error(h, A) <= 1e-13
+
+
+def test_nothing_admissible_is_exact():
+    X, om, t, lists, A, h = _build(600, 3, O.K_MATERN32, (0.1, 1e-4), 1e-6, leaf=16, eta=1e-12)
+    assert h.l_top == 0 and not h.B
+    assert O.dense_rel_error(h, A) == 0.0
+
+
+def test_adaptive_rounds_and_budget():
+    X, om, t, lists, A, h = _build(4096, 2, O.K_EXP, (0.2, 1e-4), 1e-9, leaf=64)
+    assert h.converged and max(h.d_level.values()) > 32
+    assert O.dense_rel_error(h, A) <= 10 * 1e-9
+    # the same problem with the sample budget capped at the first block
+    X, om, t, lists, A, h2 = _build(4096, 2, O.K_EXP, (0.2, 1e-4), 1e-9, leaf=64, d_max=32)
+    assert not h2.converged
+
+
+def test_power_method_matches_dense_two_norm():
+    X, om, t, lists, A, h = _build(1024, 2, O.K_EXP, (0.2, 1e-4), 1e-5, leaf=16)
+    Ad = O.h2_dense(h)
+    exact = np.linalg.norm(A - Ad, 2) / np.linalg.norm(A, 2)
+    est = O.power_rel_error(h, O.dense_sampler(A), 1024, iters=30)
+    assert est == pytest.approx(exact, rel=0.05)
+
+
+def test_sparsity_constant_bounded():
+    # C_sp (Sec. II-A): the longest block row of any level's list does not grow
+    # with N (uniform points, eta 0.7).
+    csp = []
+    for n in (4096, 16384, 65536):
+        t = O.build_cluster_tree(W.uniform_points(n, 2, 4), 16)
+        lists = O.dual_traversal(t, 0.7)
+        m = max(len(v) for v in lists.near.values())
+        for k in range(t.depth + 1):
+            if lists.far[k]:
+                m = max(m, max(len(v) for v in lists.far[k].values()))
+        csp.append(m)
+    assert max(csp) <= 1.25 * csp[0]
+
+
+def test_storage_per_point_levels_off():
+    # O(N) memory (Sec. III-A, Sec. V-B): stored entries per point change by
+    # less than 15% from N=4096 to N=8192 (the growth comes from the boundary
+    # layer of the domain and shrinks with N).
+    per_point = []
+    for n in (4096, 8192):
+        X = W.uniform_points(n, 2, 9)
+        om = W.gaussian_omega(n, 256, 10)
+        t = O.build_cluster_tree(X, 32)
+        lists = O.dual_traversal(t, 0.7)
+        h = O.build_h2(t, lists, O.K_EXP, (0.2, 1e-4), 1e-6, om,
+                       O.ksum_sampler(X, O.K_EXP, (0.2, 1e-4), chunk=1024))
+        per_point.append(O.storage_entries(h)["total"] / n)
+    assert per_point[1] <= 1.15 * per_point[0]
+
+
+# --- sensitivity: mistakes planted in the oracle must trip a pin -------------------
+
+
+def test_planted_mistake_dropped_inner_subtraction(monkeypatch):
+    orig = O._Builder.local_samples
+
+    def no_far_subtraction(self, level, Yt, Ot, below):
+        saved = self.B
+        if level > 1:
+            self.B = {k: np.zeros_like(v) for k, v in saved.items()}
+        try:
+            return orig(self, level, Yt, Ot, below)
+        finally:
+            self.B = saved
+
+    monkeypatch.setattr(O._Builder, "local_samples", no_far_subtraction)
+    with pytest.raises(AssertionError):
+        test_sample_recurrence_exact_low_rank()
+    with pytest.raises(AssertionError):
+        test_ranks_match_dense_svd(1e-6)
+
+
+def test_planted_mistake_skeleton_indices(monkeypatch):
+    # local skeleton positions used where tree positions are needed
+    monkeypatch.setattr(O._Builder, "skeleton_rows", lambda self, nd: nd.J)
+    with pytest.raises(AssertionError):
+        test_c1_dense_error_within_tolerance()
+
+
+def test_planted_mistake_wrong_threshold(monkeypatch):
+    # eps_l without the per-level split of the budget
+    orig = O.row_id
+    monkeypatch.setattr(O, "row_id", lambda Y, eps: orig(Y, eps * 30.0))
+    with pytest.raises(AssertionError):
+        test_ranks_match_dense_svd(1e-6)
+
+
+def test_planted_mistake_omega_upsweep(monkeypatch):
+    # Omega^{l+1} taken as the skeleton rows of Omega^l instead of U^T Omega^l
+    def bad(self, level, local):
+        return {tau: (Y[self.nodes[tau].J, :], O_[self.nodes[tau].J, :])
+                for tau, (Y, O_) in local.items()}
+
+    monkeypatch.setattr(O._Builder, "upsweep", bad)
+    with pytest.raises(AssertionError):
+        test_sample_recurrence_exact_low_rank()
+
+
+def test_planted_mistake_near_field_sign(monkeypatch):
+    orig = O._Builder.local_samples
+
+    def flipped(self, level, Yt, Ot, below):
+        if level == 1:
+            saved = self.D
+            self.D = {k: -v for k, v in saved.items()}
+            try:
+                return orig(self, level, Yt, Ot, below)
+            finally:
+                self.D = saved
+        return orig(self, level, Yt, Ot, below)
+
+    monkeypatch.setattr(O._Builder, "local_samples", flipped)
+    with pytest.raises(AssertionError):
+        test_ranks_match_dense_svd(1e-6)
