@@ -1,0 +1,1421 @@
+// C ABI and host driver of the construction (Algorithm 1 with the adaptive
+// loop of Sec. III-B), the H2 matrix-vector product and the exports.
+//
+// The driver keeps one "level" of clusters of ALL instances together, so every
+// per-level step is a single batched launch over variable-size clusters.  The
+// only host decisions are the adaptive flag per round and the sizes of the
+// next level (ranks), each read with one small device-to-host copy.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+
+#include "h2_level.h"
+#include "h2_types.h"
+
+namespace h2 {
+
+thread_local int64_t g_launches = 0;
+static thread_local std::string g_last_error;
+
+void set_error(h2_status code, const std::string &msg) {
+  (void)code;
+  g_last_error = msg;
+}
+h2_status fail(h2_status code, const std::string &msg) {
+  set_error(code, msg);
+  return code;
+}
+
+int device_sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 132;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 132;
+  return sms;
+}
+
+KernelDesc make_kernel_desc(int kid, const double *params, int nparams) {
+  KernelDesc k{};
+  k.kid = kid;
+  auto need = [&](int n) {
+    if (nparams < n || params == nullptr) throw Error{H2_ERR_ARG, "too few kernel parameters"};
+  };
+  switch (kid) {
+    case H2_K_EXP:
+      need(1);
+      H2_REQUIRE(params[0] > 0, "length scale must be > 0");
+      k.scale = 1.0 / params[0];
+      k.diag = nparams > 1 ? params[1] : 0.0;
+      break;
+    case H2_K_MATERN32:
+      need(1);
+      H2_REQUIRE(params[0] > 0, "length scale must be > 0");
+      k.scale = std::sqrt(3.0) / params[0];
+      k.diag = nparams > 1 ? params[1] : 0.0;
+      break;
+    case H2_K_GAUSS:
+      need(1);
+      H2_REQUIRE(params[0] > 0, "sigma must be > 0");
+      k.scale = 1.0 / (2.0 * params[0] * params[0]);
+      k.diag = nparams > 1 ? params[1] : 0.0;
+      break;
+    case H2_K_LAPLACE_IE:
+      need(1);
+      k.scale = 1.0 / (4.0 * M_PI);
+      k.diag = params[0];
+      break;
+    case H2_K_POLY:
+      need(2);
+      k.scale = params[0];
+      k.pw = (int)params[1];
+      H2_REQUIRE(k.pw >= 0 && k.pw <= 16 && (double)k.pw == params[1], "poly power must be 0..16");
+      k.diag = 0.0;
+      break;
+    default:
+      throw Error{H2_ERR_ARG, "unsupported kernel id"};
+  }
+  return k;
+}
+
+// ----------------------------------------------------------------------------
+// Handle layout of a built H2 matrix (one or many instances).
+// ----------------------------------------------------------------------------
+struct LevelData {
+  int n = 0;
+  std::vector<int32_t> h_inst, h_m, h_k, h_child0;
+  std::vector<int64_t> h_row;
+  std::vector<int> task_base;  // per instance, -1 if absent
+  DBuf<int32_t> inst, m, k, child0, J, skel, Jtmp, skeltmp, conv;
+  DBuf<int64_t> row, krow, eoff;
+  int64_t M = 0, K = 0;
+  int max_m = 0, max_k = 0;
+  DBuf<double> E;
+  DBuf<float> E32;
+  int64_t E_size = 0;
+  DBuf<int64_t> far_ptr, boff;
+  DBuf<int32_t> far_idx, far_erow;
+  int64_t far_nnz = 0;
+  DBuf<double> B64;
+  DBuf<float> B32;
+  int64_t B_size = 0;
+  DBuf<double> Y64, Om64;
+  DBuf<float> Y32, Om32;
+  std::vector<double> h_eps;
+  DBuf<double> eps;
+  std::vector<int32_t> h_active, h_active_next;
+  DBuf<int32_t> active, active_next;
+  std::vector<int32_t> d_at_id;
+
+  TasksDev dev() const {
+    return TasksDev{n, inst.p, m.p, row.p, k.p, krow.p, J.p, eoff.p};
+  }
+};
+
+}  // namespace h2
+
+struct h2_matrix {
+  int count = 0;
+  bool fp64 = true;
+  int kid = 0;
+  int levels = 0;
+  int64_t n_total = 0;
+  std::vector<int64_t> inst_n, inst_base;
+  std::vector<int> inst_depth, inst_ltop;
+  std::vector<h2::KernelDesc> kd;
+  h2::DBuf<h2::InstDev> inst_dev;
+  h2::DBuf<double> x, y, z;
+  h2::DBuf<float> xh, yh, zh, xl, yl, zl;
+  h2::DBuf<int32_t> orig_of_pos;
+  std::vector<h2::LevelData> lv;
+  h2::DBuf<int64_t> near_ptr, doff;
+  h2::DBuf<int32_t> near_idx, near_erow;
+  int64_t near_nnz = 0;
+  h2::DBuf<double> D64;
+  h2::DBuf<float> D32;
+  int64_t D_size = 0;
+  std::vector<int> dcur;
+  bool converged = true;
+  h2_stats_t st{};
+};
+
+namespace h2 {
+namespace {
+
+__global__ void k_offset_copy_i32(const int32_t *src, int64_t n, int32_t add, int32_t *dst) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[i] + add;
+}
+
+__global__ void k_convert_f64_f32(const double *src, int64_t n, float *dst) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = (float)src[i];
+}
+
+__global__ void k_check_finite_cols(const double *p, int64_t ld, int64_t n, int c0, int c1,
+                                    int *bad) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int c = c0; c < c1; ++c)
+    if (!isfinite(p[i + c * ld])) { atomicExch(bad, 1); return; }
+}
+
+void convert32(const double *src, int64_t n, float *dst, cudaStream_t s) {
+  if (n == 0) return;
+  k_convert_f64_f32<<<ceil_div(n, 256), 256, 0, s>>>(src, n, dst);
+  count_launch();
+  H2_CHECK_LAUNCH();
+}
+
+struct PhaseTimer {
+  bool on = false;
+  cudaStream_t s = nullptr;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[8];
+  cudaEvent_t open[8] = {};
+  void begin(int phase) {
+    if (!on) return;
+    cudaEvent_t e;
+    H2_CUDA(cudaEventCreate(&e));
+    H2_CUDA(cudaEventRecord(e, s));
+    open[phase] = e;
+  }
+  void end(int phase) {
+    if (!on || !open[phase]) return;
+    cudaEvent_t e;
+    H2_CUDA(cudaEventCreate(&e));
+    H2_CUDA(cudaEventRecord(e, s));
+    ev[phase].push_back({open[phase], e});
+    open[phase] = nullptr;
+  }
+  double total(int phase, double *max_one = nullptr) {
+    double t = 0, mx = 0;
+    for (auto &p : ev[phase]) {
+      float ms = 0;
+      cudaEventSynchronize(p.second);
+      cudaEventElapsedTime(&ms, p.first, p.second);
+      t += ms;
+      mx = std::max<double>(mx, ms);
+    }
+    if (max_one) *max_one = mx;
+    return t;
+  }
+  ~PhaseTimer() {
+    for (auto &v : ev)
+      for (auto &p : v) { cudaEventDestroy(p.first); cudaEventDestroy(p.second); }
+    for (auto e : open)
+      if (e) cudaEventDestroy(e);
+  }
+};
+enum { PH_SKETCH = 0, PH_NEAR, PH_QR, PH_ID, PH_UP, PH_COUP, PH_BSR, PH_TOTAL };
+
+int pick_dc(int ncols) {
+  if (ncols % 32 == 0) return 32;
+  if (ncols % 16 == 0) return 16;
+  return 8;
+}
+
+// ----------------------------------------------------------------------------
+// The builder.
+// ----------------------------------------------------------------------------
+struct Builder {
+  h2_matrix *H;
+  const h2_tree *const *trees;
+  const h2_build_opts &o;
+  cudaStream_t s;
+  PhaseTimer timer;
+  int sm_count;
+  std::vector<double> tols;
+  DBuf<int32_t> cb, ce;             // per-instance column range of the current pass
+  DBuf<double> om_stage;            // FP64 staging of new Omega columns (mixed / callbacks)
+  int64_t sketch_pairs = 0, sketch_cols = 0;
+  double sketch_flops = 0;
+  int rounds = 0;
+  std::vector<int> not_conv;
+
+  Builder(h2_matrix *h, const h2_tree *const *t, const h2_build_opts &opts, cudaStream_t st)
+      : H(h), trees(t), o(opts), s(st) {
+    sm_count = device_sm_count();
+  }
+
+  bool fp64() const { return H->fp64; }
+  void *Yp(LevelData &L) { return fp64() ? (void *)L.Y64.p : (void *)L.Y32.p; }
+  void *Omp(LevelData &L) { return fp64() ? (void *)L.Om64.p : (void *)L.Om32.p; }
+  void *Ep(LevelData &L) { return fp64() ? (void *)L.E.p : (void *)L.E32.p; }
+  void *Bp(LevelData &L) { return fp64() ? (void *)L.B64.p : (void *)L.B32.p; }
+  void *Dp() { return fp64() ? (void *)H->D64.p : (void *)H->D32.p; }
+
+  void set_cols(const std::vector<int32_t> &b, const std::vector<int32_t> &e) {
+    to_device(cb, b, s);
+    to_device(ce, e, s);
+  }
+  InstCols cols() const { return InstCols{cb.p, ce.p}; }
+
+  void alloc_panels(LevelData &L) {
+    size_t sz = (size_t)std::max<int64_t>(L.M, 1) * o.d_max;
+    if (fp64()) {
+      L.Y64.alloc_zero(sz, s);
+      L.Om64.alloc_zero(sz, s);
+    } else {
+      L.Y32.alloc_zero(sz, s);
+      L.Om32.alloc_zero(sz, s);
+    }
+  }
+
+  // ---------------- setup ---------------------------------------------------
+  void setup_instances(const int *kids, const double *params) {
+    int C = H->count;
+    H->inst_n.resize(C);
+    H->inst_base.resize(C);
+    H->inst_depth.resize(C);
+    H->inst_ltop.resize(C);
+    H->kd.resize(C);
+    int64_t base = 0;
+    for (int i = 0; i < C; ++i) {
+      const h2_tree *t = trees[i];
+      H->inst_n[i] = t->n;
+      H->inst_base[i] = base;
+      H->inst_depth[i] = t->depth;
+      H->inst_ltop[i] = t->l_top;
+      H->kd[i] = make_kernel_desc(kids[i], params + 4 * i, 4);
+      H2_REQUIRE(t->leaf_size <= 256, "leaf size above 256 is not supported");
+      base += t->n;
+    }
+    H2_REQUIRE(base < (1ll << 31) - 1, "too many points in total");
+    H->n_total = base;
+    std::vector<InstDev> idev(C);
+    for (int i = 0; i < C; ++i) idev[i] = InstDev{H->inst_base[i], H->inst_n[i], H->kd[i]};
+    to_device(H->inst_dev, idev, s);
+    int64_t N = H->n_total;
+    H->x.alloc(N);
+    H->y.alloc(N);
+    H->z.alloc(N);
+    H->orig_of_pos.alloc(N);
+    for (int i = 0; i < C; ++i) {
+      const h2_tree *t = trees[i];
+      int64_t b = H->inst_base[i];
+      H2_CUDA(cudaMemcpyAsync(H->x.p + b, t->x.p, t->n * 8, cudaMemcpyDeviceToDevice, s));
+      H2_CUDA(cudaMemcpyAsync(H->y.p + b, t->y.p, t->n * 8, cudaMemcpyDeviceToDevice, s));
+      H2_CUDA(cudaMemcpyAsync(H->z.p + b, t->z.p, t->n * 8, cudaMemcpyDeviceToDevice, s));
+      k_offset_copy_i32<<<ceil_div(t->n, 256), 256, 0, s>>>(t->perm.p, t->n, (int32_t)b,
+                                                            H->orig_of_pos.p + b);
+      count_launch();
+      H2_CHECK_LAUNCH();
+    }
+    if (!fp64()) {
+      H->xh.alloc(N); H->yh.alloc(N); H->zh.alloc(N);
+      H->xl.alloc(N); H->yl.alloc(N); H->zl.alloc(N);
+      split_coords32(H->x.p, H->y.p, H->z.p, N, H->xh.p, H->yh.p, H->zh.p, H->xl.p, H->yl.p,
+                     H->zl.p, s);
+    }
+    H->levels = *std::max_element(H->inst_ltop.begin(), H->inst_ltop.end());
+    H->dcur.assign(C, o.d0);
+  }
+
+  Points64 p64() const { return Points64{H->x.p, H->y.p, H->z.p}; }
+  Points32 p32() const {
+    return Points32{H->xh.p, H->yh.p, H->zh.p, H->xl.p, H->yl.p, H->zl.p};
+  }
+
+  // Level-1 tasks: every leaf of every instance (the near field is needed
+  // even where nothing is compressed).
+  void setup_leaves() {
+    LevelData &L = H->lv[1];
+    int C = H->count;
+    L.task_base.assign(C, -1);
+    for (int i = 0; i < C; ++i) {
+      const h2_tree *t = trees[i];
+      int first = (1 << t->depth) - 1;
+      int nl = 1 << t->depth;
+      L.task_base[i] = L.n;
+      for (int r = 0; r < nl; ++r) {
+        int node = first + r;
+        L.h_inst.push_back(i);
+        L.h_row.push_back(H->inst_base[i] + t->h_begin[node]);
+        L.h_m.push_back((int32_t)(t->h_end[node] - t->h_begin[node]));
+      }
+      L.n += nl;
+    }
+    L.M = H->n_total;
+    L.max_m = *std::max_element(L.h_m.begin(), L.h_m.end());
+    to_device(L.inst, L.h_inst, s);
+    to_device(L.row, L.h_row, s);
+    to_device(L.m, L.h_m, s);
+    // near list over leaf tasks
+    H->near_ptr.alloc(L.n + 1);
+    int64_t nnz = 0;
+    for (int i = 0; i < C; ++i) nnz += trees[i]->near_nnz;
+    H->near_nnz = nnz;
+    H->near_idx.alloc(std::max<int64_t>(nnz, 1));
+    H->near_erow.alloc(std::max<int64_t>(nnz, 1));
+    int64_t nb = 0;
+    for (int i = 0; i < C; ++i) {
+      const h2_tree *t = trees[i];
+      map_csr(t->near_ptr.p, t->near_idx.p, 1 << t->depth, (1 << t->depth) - 1, L.task_base[i], nb,
+              H->near_ptr.p, H->near_idx.p, H->near_erow.p, i == C - 1, s);
+      nb += t->near_nnz;
+    }
+    DBuf<int64_t> sz;
+    sz.alloc(std::max<int64_t>(nnz, 1));
+    block_sizes(nnz, H->near_erow.p, H->near_idx.p, L.m.p, L.m.p, sz.p, s);
+    H->doff.alloc(nnz + 1);
+    scan_exclusive(sz.p, H->doff.p, nnz, s);
+    H->D_size = to_host(H->doff.p + nnz, 1, s)[0];
+    if (fp64()) H->D64.alloc(std::max<int64_t>(H->D_size, 1));
+    else H->D32.alloc(std::max<int64_t>(H->D_size, 1));
+    alloc_panels(L);
+  }
+
+  void set_level_flags(int l) {
+    LevelData &L = H->lv[l];
+    int C = H->count;
+    L.h_active.assign(C, 0);
+    L.h_active_next.assign(C, 0);
+    for (int i = 0; i < C; ++i) {
+      L.h_active[i] = l <= H->inst_ltop[i];
+      L.h_active_next[i] = l + 1 <= H->inst_ltop[i];
+    }
+    to_device(L.active, L.h_active, s);
+    to_device(L.active_next, L.h_active_next, s);
+  }
+
+  // ---------------- sampling -------------------------------------------------
+  // New Omega columns [c0_i, c0_i+nc) of the listed instances into the level-1
+  // panel (tree order), then Y = K Omega for the same columns.
+  void sample(const std::vector<int> &insts, int nc) {
+    LevelData &L = H->lv[1];
+    int64_t N = H->n_total;
+    timer.begin(PH_SKETCH);
+    // Omega in FP64 (staging for mixed precision)
+    double *om64 = fp64() ? L.Om64.p : nullptr;
+    if (!fp64()) {
+      if ((int64_t)om_stage.n < N * o.d_max) om_stage.alloc((size_t)N * o.d_max);
+      om64 = om_stage.p;
+    }
+    for (int i : insts) {
+      int c0 = H->dcur[i];
+      int64_t b = H->inst_base[i], n = H->inst_n[i];
+      if (o.omega_mode == 1)
+        gather_rows64(o.omega_stored, N, H->orig_of_pos.p + b, n, c0, c0 + nc, om64 + b, N, s);
+      else
+        philox_gaussian64(om64 + b, N, H->orig_of_pos.p + b, n, c0, c0 + nc, o.seed, s);
+      if (!fp64()) convert_cols_to32(om64, N, b, n, c0, c0 + nc, L.Om32.p, s);
+    }
+    if (o.sketch == H2_SKETCH_KSUM) {
+      std::vector<int64_t> nn(H->inst_n), bb(H->inst_base);
+      int done = 0;
+      while (done < nc) {
+        int dc = std::min(32, pick_dc(nc - done));
+        std::vector<int> c0(insts.size());
+        for (size_t q = 0; q < insts.size(); ++q) c0[q] = H->dcur[insts[q]] + done;
+        KsumPlan plan = plan_ksum(nn, bb, insts, c0, dc, fp64(), o.ksum_tile, sm_count);
+        for (int i : insts) sketch_pairs += H->inst_n[i] * H->inst_n[i];
+        for (int i : insts)
+          sketch_flops += (double)H->inst_n[i] * H->inst_n[i] * (2.0 * dc + 10.0);
+        if (fp64()) {
+          KsumArgs64 a{p64(), L.Om64.p, L.Y64.p, N, H->inst_dev.p, nullptr, nullptr};
+          run_ksum64(H->kid, plan, a, s);
+        } else {
+          KsumArgs32 a{p32(), L.Om32.p, L.Y32.p, N, H->inst_dev.p, nullptr, nullptr};
+          run_ksum32(H->kid, plan, a, s);
+        }
+        done += dc;
+      }
+    } else {
+      // samplers working in original order: Omega_orig -> y_orig -> tree order
+      H2_REQUIRE(H->count == 1 || o.sketch == H2_SKETCH_H2SUM,
+                 "dense and callback sketches take a single instance");
+      int c0 = H->dcur[insts[0]];
+      DBuf<double> omo, yo;
+      omo.alloc((size_t)N * nc);
+      yo.alloc_zero((size_t)N * nc, s);
+      // om64 (tree order, columns c0..) -> original order
+      permute_out(true, om64 + (int64_t)c0 * N, N, H->orig_of_pos.p, N, nc, omo.p, N, s);
+      if (o.sketch == H2_SKETCH_DENSE) {
+        H2_REQUIRE(o.dense_a != nullptr, "dense sketch needs dense_a");
+        dense_gemm64(o.dense_a, N, N, omo.p, N, yo.p, N, nc, s);
+      } else if (o.sketch == H2_SKETCH_CALLBACK) {
+        H2_REQUIRE(o.sampler != nullptr, "callback sketch needs a sampler");
+        int rc = o.sampler(o.sampler_ctx, omo.p, yo.p, N, nc, N, (h2_stream_t)s);
+        if (rc != 0) throw Error{H2_ERR_SAMPLER, "sampler callback returned an error"};
+      } else {
+        H2_REQUIRE(o.operands != nullptr && o.n_operands > 0, "H2 sum needs operands");
+        DBuf<double> tmp;
+        tmp.alloc((size_t)N * nc);
+        for (int q = 0; q < o.n_operands; ++q) {
+          const h2_matrix *op = o.operands[q];
+          H2_REQUIRE(op && op->n_total == N, "operand size mismatch");
+          h2_status st = h2_matvec(op, omo.p, tmp.p, nc, (h2_stream_t)s);
+          if (st != H2_OK) throw Error{st, "operand matvec failed"};
+          add_into(yo.p, tmp.p, (int64_t)N * nc);
+        }
+      }
+      DBuf<int> bad;
+      bad.alloc_zero(1, s);
+      k_check_finite_cols<<<ceil_div(N, 256), 256, 0, s>>>(yo.p, N, N, 0, nc, bad.p);
+      count_launch();
+      H2_CHECK_LAUNCH();
+      if (to_host(bad.p, 1, s)[0]) throw Error{H2_ERR_INPUT, "sampler produced non-finite values"};
+      if (fp64()) {
+        permute_in(true, yo.p, N, H->orig_of_pos.p, N, nc, L.Y64.p + (int64_t)c0 * N, N, s);
+      } else {
+        DBuf<double> yt;
+        yt.alloc((size_t)N * nc);
+        permute_in(true, yo.p, N, H->orig_of_pos.p, N, nc, yt.p, N, s);
+        convert32(yt.p, (int64_t)N * nc, L.Y32.p + (int64_t)c0 * N, s);
+      }
+      H2_CUDA(cudaStreamSynchronize(s));
+    }
+    sketch_cols += nc;
+    timer.end(PH_SKETCH);
+  }
+
+  void add_into(double *y, const double *x, int64_t n);
+
+  // ---------------- near field and sweeps ------------------------------------
+  void nearfield_initial() {
+    LevelData &L = H->lv[1];
+    int C = H->count;
+    int first = std::min(32, o.d0);
+    std::vector<int32_t> b(C, 0), e(C, first);
+    set_cols(b, e);
+    timer.begin(PH_NEAR);
+    NearArgs a{};
+    a.t = L.dev();
+    a.ptr = H->near_ptr.p;
+    a.idx = H->near_idx.p;
+    a.doff = H->doff.p;
+    a.D = Dp();
+    a.inst = H->inst_dev.p;
+    a.p64 = p64();
+    a.p32 = p32();
+    a.Y = Yp(L);
+    a.Om = Omp(L);
+    a.ld = H->n_total;
+    a.cols = cols();
+    nearfield_gen(H->kid, fp64(), a, L.max_m, s);
+    timer.end(PH_NEAR);
+    if (o.d0 > first) {
+      std::vector<int32_t> b2(C, first), e2(C, o.d0);
+      set_cols(b2, e2);
+      near_bsr();
+    }
+  }
+
+  // Y1(cols) -= D Om1(cols) over the leaf tasks, columns from cb/ce.
+  void near_bsr() {
+    LevelData &L = H->lv[1];
+    timer.begin(PH_BSR);
+    BsrArgs a{};
+    a.n_rows = L.n;
+    a.row_inst = L.inst.p;
+    a.row_m = L.m.p;
+    a.row_off = L.row.p;
+    a.col_m = L.m.p;
+    a.col_off = L.row.p;
+    a.ptr = H->near_ptr.p;
+    a.idx = H->near_idx.p;
+    a.boff = H->doff.p;
+    a.blocks = Dp();
+    a.in = Omp(L);
+    a.ld_in = L.M;
+    a.out = Yp(L);
+    a.ld_out = L.M;
+    a.sign = -1.0;
+    a.cols = cols();
+    bsr_apply(fp64(), a, L.max_m, s);
+    timer.end(PH_BSR);
+  }
+
+  // Level l -> level l+1 panels for the current columns: skeleton rows of Y,
+  // E^T Omega, then the far-field subtraction with the level-l couplings.
+  void transfer_up(int l) {
+    LevelData &L = H->lv[l], &U = H->lv[l + 1];
+    timer.begin(PH_UP);
+    gather_skeleton_rows(fp64(), L.dev(), Yp(L), L.M, Yp(U), U.M, cols(), L.active_next.p, s);
+    basis_t_apply(fp64(), L.dev(), Ep(L), Omp(L), L.M, Omp(U), U.M, cols(), L.active_next.p, s);
+    timer.end(PH_UP);
+    if (L.far_nnz == 0) return;
+    timer.begin(PH_BSR);
+    BsrArgs a{};
+    a.n_rows = L.n;
+    a.row_inst = L.inst.p;
+    a.row_m = L.k.p;
+    a.row_off = L.krow.p;
+    a.col_m = L.k.p;
+    a.col_off = L.krow.p;
+    a.ptr = L.far_ptr.p;
+    a.idx = L.far_idx.p;
+    a.boff = L.boff.p;
+    a.blocks = Bp(L);
+    a.in = Omp(U);
+    a.ld_in = U.M;
+    a.out = Yp(U);
+    a.ld_out = U.M;
+    a.sign = -1.0;
+    a.cols = cols();
+    bsr_apply(fp64(), a, L.max_k, s);
+    timer.end(PH_BSR);
+  }
+
+  // ---------------- per-level steps -----------------------------------------
+  void level_thresholds(int l, const std::vector<double> &eps_abs) {
+    LevelData &L = H->lv[l];
+    int C = H->count;
+    L.h_eps.assign(C, 0.0);
+    for (int i = 0; i < C; ++i) {
+      int lt = H->inst_ltop[i];
+      if (l > lt) continue;
+      double nl = std::ldexp(1.0, H->inst_depth[i] - l + 1);
+      L.h_eps[i] = eps_abs[i] / std::sqrt((double)lt * nl);
+    }
+    to_device(L.eps, L.h_eps, s);
+  }
+
+  // workspace offsets for clusters whose m x d panel exceeds shared memory
+  size_t plan_workspace(LevelData &L, size_t budget, size_t fixed, DBuf<int64_t> &ws_off,
+                        DBuf<double> &ws, bool qr) {
+    std::vector<int64_t> off(L.n, -1);
+    int64_t total = 0;
+    size_t need_smem = 0;
+    for (int t = 0; t < L.n; ++t) {
+      int i = L.h_inst[t];
+      if (!L.h_active[i]) continue;
+      int64_t m = L.h_m[t], d = H->dcur[i];
+      if (qr && m <= d) continue;
+      size_t bytes = (size_t)(m * d) * sizeof(double);
+      if (bytes + fixed > budget) {
+        off[t] = total;
+        total += m * d;
+      } else {
+        need_smem = std::max(need_smem, bytes);
+      }
+    }
+    to_device(ws_off, off, s);
+    if ((int64_t)ws.n < total) ws.alloc(total);
+    return need_smem;
+  }
+
+  void qr_round(int l, DBuf<int32_t> &unconv) {
+    LevelData &L = H->lv[l];
+    DBuf<int64_t> ws_off;
+    DBuf<double> ws;
+    size_t smem = plan_workspace(L, 200 * 1024, 0, ws_off, ws, true);
+    QrArgs a{};
+    a.t = L.dev();
+    a.Y = Yp(L);
+    a.ld = L.M;
+    DBuf<int32_t> dcur;
+    std::vector<int32_t> hd(H->dcur.begin(), H->dcur.end());
+    to_device(dcur, hd, s);
+    a.dcur = dcur.p;
+    a.eps = L.eps.p;
+    a.active = L.active.p;
+    a.conv = L.conv.p;
+    a.unconv = unconv.p;
+    a.ws = ws.p;
+    a.ws_off = ws_off.p;
+    a.mindiag = nullptr;
+    timer.begin(PH_QR);
+    qr_test(fp64(), a, smem, s);
+    timer.end(PH_QR);
+    H2_CUDA(cudaStreamSynchronize(s));
+  }
+
+  void run_level(int l, const std::vector<double> &eps_abs) {
+    LevelData &L = H->lv[l];
+    int C = H->count;
+    level_thresholds(l, eps_abs);
+    L.conv.alloc_zero(L.n, s);
+    DBuf<int32_t> unconv;
+    unconv.alloc(C);
+    // adaptive sampling (Sec. III-B)
+    for (;;) {
+      H2_CUDA(cudaMemsetAsync(unconv.p, 0, C * sizeof(int32_t), s));
+      qr_round(l, unconv);
+      std::vector<int32_t> hu = to_host(unconv.p, C, s);
+      std::vector<int> need;
+      for (int i = 0; i < C; ++i) {
+        if (!L.h_active[i] || hu[i] == 0) continue;
+        if (o.d_inc <= 0 || H->dcur[i] + o.d_inc > o.d_max) {
+          if (std::find(not_conv.begin(), not_conv.end(), i) == not_conv.end())
+            not_conv.push_back(i);
+          continue;
+        }
+        need.push_back(i);
+      }
+      if (need.empty()) break;
+      ++rounds;
+      sample(need, o.d_inc);
+      std::vector<int32_t> b(C, 0), e(C, 0);
+      for (int i : need) { b[i] = H->dcur[i]; e[i] = H->dcur[i] + o.d_inc; }
+      set_cols(b, e);
+      near_bsr();
+      for (int lp = 1; lp < l; ++lp) transfer_up(lp);
+      for (int i : need) H->dcur[i] += o.d_inc;
+    }
+    L.d_at_id.assign(H->dcur.begin(), H->dcur.end());
+    // row ID of every cluster (batchedID)
+    DBuf<int32_t> dcur;
+    std::vector<int32_t> hd(H->dcur.begin(), H->dcur.end());
+    to_device(dcur, hd, s);
+    {
+      DBuf<int64_t> cap;
+      cap.alloc(L.n);
+      basis_capacity(L.n, L.m.p, L.inst.p, dcur.p, cap.p, s);
+      L.eoff.alloc(L.n + 1);
+      scan_exclusive(cap.p, L.eoff.p, L.n, s);
+      L.E_size = to_host(L.eoff.p + L.n, 1, s)[0];
+      L.E.alloc(std::max<int64_t>(L.E_size, 1));
+    }
+    L.k.alloc(L.n);
+    L.Jtmp.alloc(std::max<int64_t>(L.M, 1));
+    L.skeltmp.alloc(std::max<int64_t>(L.M, 1));
+    DBuf<int64_t> ws_off;
+    DBuf<double> ws;
+    size_t fixed = row_id_fixed_smem();
+    size_t smem = plan_workspace(L, 200 * 1024, fixed, ws_off, ws, false);
+    IdArgs a{};
+    a.t = L.dev();
+    a.Y = Yp(L);
+    a.ld = L.M;
+    a.dcur = dcur.p;
+    a.eps = L.eps.p;
+    a.active = L.active.p;
+    a.ibar = l == 1 ? nullptr : H->lv[l - 1].skel.p;
+    a.k_out = L.k.p;
+    a.J_tmp = L.Jtmp.p;
+    a.skel_tmp = L.skeltmp.p;
+    a.eoff = L.eoff.p;
+    a.E = L.E.p;
+    a.ws = ws.p;
+    a.ws_off = ws_off.p;
+    timer.begin(PH_ID);
+    row_id(fp64(), a, smem, s);
+    timer.end(PH_ID);
+    L.krow.alloc(L.n + 1);
+    scan_exclusive_i32(L.k.p, L.krow.p, L.n, s);
+    L.h_k = to_host(L.k.p, L.n, s);
+    L.K = to_host(L.krow.p + L.n, 1, s)[0];
+    L.max_k = L.h_k.empty() ? 0 : *std::max_element(L.h_k.begin(), L.h_k.end());
+    L.J.alloc(std::max<int64_t>(L.K, 1));
+    L.skel.alloc(std::max<int64_t>(L.K, 1));
+    compact_skeletons(L.dev(), L.Jtmp.p, L.skeltmp.p, L.J.p, L.skel.p, s);
+    if (!fp64()) {
+      L.E32.alloc(std::max<int64_t>(L.E_size, 1));
+      convert32(L.E.p, L.E_size, L.E32.p, s);
+    }
+    // couplings B = K(Itil_s, Itil_t) for the far list of this level
+    build_far_list(l);
+    if (L.far_nnz > 0) {
+      DBuf<int64_t> sz;
+      sz.alloc(L.far_nnz);
+      block_sizes(L.far_nnz, L.far_erow.p, L.far_idx.p, L.k.p, L.k.p, sz.p, s);
+      L.boff.alloc(L.far_nnz + 1);
+      scan_exclusive(sz.p, L.boff.p, L.far_nnz, s);
+      L.B_size = to_host(L.boff.p + L.far_nnz, 1, s)[0];
+      if (fp64()) L.B64.alloc(std::max<int64_t>(L.B_size, 1));
+      else L.B32.alloc(std::max<int64_t>(L.B_size, 1));
+      CouplingArgs ca{};
+      ca.nnz = L.far_nnz;
+      ca.erow = L.far_erow.p;
+      ca.idx = L.far_idx.p;
+      ca.boff = L.boff.p;
+      ca.t = L.dev();
+      ca.skel = L.skel.p;
+      ca.inst = H->inst_dev.p;
+      ca.p64 = p64();
+      ca.p32 = p32();
+      ca.B = Bp(L);
+      timer.begin(PH_COUP);
+      coupling_gen(H->kid, fp64(), ca, s);
+      timer.end(PH_COUP);
+    }
+  }
+
+  void build_far_list(int l) {
+    LevelData &L = H->lv[l];
+    int C = H->count;
+    int64_t nnz = 0;
+    for (int i = 0; i < C; ++i)
+      if (L.task_base[i] >= 0 && L.h_active[i])
+        nnz += trees[i]->far_nnz[H->inst_depth[i] - l + 1];
+    L.far_nnz = nnz;
+    L.far_ptr.alloc_zero(L.n + 1, s);
+    if (nnz == 0) return;
+    L.far_idx.alloc(nnz);
+    L.far_erow.alloc(nnz);
+    int64_t nb = 0;
+    // rows of instances without a far list keep ptr = running nnz
+    std::vector<int64_t> hptr(L.n + 1, 0);
+    for (int i = 0; i < C; ++i) {
+      if (L.task_base[i] < 0) continue;
+      int depth = H->inst_depth[i] - l + 1;
+      int nrows = 1 << depth;
+      if (L.h_active[i] && trees[i]->far_nnz[depth] > 0) {
+        map_csr(trees[i]->far_ptr[depth].p, trees[i]->far_idx[depth].p, nrows, nrows - 1,
+                L.task_base[i], nb, L.far_ptr.p, L.far_idx.p, L.far_erow.p, false, s);
+        nb += trees[i]->far_nnz[depth];
+      } else {
+        std::vector<int64_t> flat(nrows, nb);
+        H2_CUDA(cudaMemcpyAsync(L.far_ptr.p + L.task_base[i], flat.data(), nrows * 8,
+                                cudaMemcpyHostToDevice, s));
+        H2_CUDA(cudaStreamSynchronize(s));
+      }
+    }
+    H2_CUDA(cudaMemcpyAsync(L.far_ptr.p + L.n, &nb, 8, cudaMemcpyHostToDevice, s));
+    H2_CUDA(cudaStreamSynchronize(s));
+  }
+
+  // Tasks of level l+1 (parents of level-l tasks, for instances compressed there).
+  void setup_next_level(int l) {
+    LevelData &L = H->lv[l], &U = H->lv[l + 1];
+    int C = H->count;
+    U.task_base.assign(C, -1);
+    for (int i = 0; i < C; ++i) {
+      if (l + 1 > H->inst_ltop[i]) continue;
+      int depth = H->inst_depth[i] - l;  // depth of level l+1
+      int nl = 1 << depth;
+      U.task_base[i] = U.n;
+      for (int r = 0; r < nl; ++r) {
+        U.h_inst.push_back(i);
+        U.h_child0.push_back(L.task_base[i] + 2 * r);
+      }
+      U.n += nl;
+    }
+    U.M = L.K;
+    to_device(U.inst, U.h_inst, s);
+    to_device(U.child0, U.h_child0, s);
+    U.row.alloc(std::max(U.n, 1));
+    U.m.alloc(std::max(U.n, 1));
+    inner_tasks(U.n, U.child0.p, L.krow.p, L.k.p, U.row.p, U.m.p, s);
+    U.h_m = to_host(U.m.p, U.n, s);
+    U.h_row = to_host(U.row.p, U.n, s);
+    U.max_m = U.h_m.empty() ? 0 : *std::max_element(U.h_m.begin(), U.h_m.end());
+    alloc_panels(U);
+    set_level_flags(l + 1);
+    // panels for all current columns, then subtract the level-l couplings
+    std::vector<int32_t> b(C, 0), e(C, 0);
+    for (int i = 0; i < C; ++i)
+      if (L.h_active_next[i]) e[i] = H->dcur[i];
+    set_cols(b, e);
+    transfer_up(l);
+  }
+
+  h2_status run(const int *kids, const double *params, const double *tol_in) {
+    int C = H->count;
+    timer.on = o.timing != 0;
+    timer.s = s;
+    int64_t launches0 = g_launches;
+    timer.begin(PH_TOTAL);
+    setup_instances(kids, params);
+    H->lv.resize(std::max(H->levels, 1) + 2);
+    setup_leaves();
+    set_level_flags(1);
+    // initial samples and the norm estimate
+    std::vector<int> all(C);
+    std::iota(all.begin(), all.end(), 0);
+    for (int i = 0; i < C; ++i) H->dcur[i] = 0;
+    sample(all, o.d0);
+    for (int i = 0; i < C; ++i) H->dcur[i] = o.d0;
+    DBuf<int64_t> ib, in_;
+    to_device(ib, H->inst_base, s);
+    to_device(in_, H->inst_n, s);
+    DBuf<double> ss;
+    ss.alloc(C);
+    instance_sumsq(Yp(H->lv[1]), fp64(), H->n_total, ib.p, in_.p, C, o.d0, ss.p, s);
+    std::vector<double> hs = to_host(ss.p, C, s), eps_abs(C);
+    for (int i = 0; i < C; ++i) {
+      if (!std::isfinite(hs[i])) throw Error{H2_ERR_INPUT, "sketch is not finite"};
+      double nrmK = std::sqrt(hs[i] / o.d0);
+      eps_abs[i] = tol_in[i] * nrmK;
+      if (i == 0) H->st.nrmK = nrmK;
+    }
+    nearfield_initial();
+    for (int l = 1; l <= H->levels; ++l) {
+      run_level(l, eps_abs);
+      if (l < H->levels) setup_next_level(l);
+    }
+    timer.end(PH_TOTAL);
+    H2_CUDA(cudaStreamSynchronize(s));
+    // release build-time panels
+    for (auto &L : H->lv) {
+      L.Y64.release(); L.Om64.release(); L.Y32.release(); L.Om32.release();
+      L.Jtmp.release(); L.skeltmp.release(); L.conv.release();
+    }
+    om_stage.release();
+    fill_stats(launches0);
+    H->converged = not_conv.empty();
+    return H->converged ? H2_OK : H2_ERR_NOT_CONVERGED;
+  }
+
+  void fill_stats(int64_t launches0) {
+    h2_stats_t &st = H->st;
+    double nrmK = st.nrmK;
+    st = h2_stats_t{};
+    st.nrmK = nrmK;
+    st.count = H->count;
+    st.n_total = H->n_total;
+    st.levels = H->levels;
+    st.d_final = *std::max_element(H->dcur.begin(), H->dcur.end());
+    st.rank_min = 1 << 30;
+    st.rank_max = 0;
+    int64_t bb = 0, bu = 0;
+    for (int l = 1; l <= H->levels; ++l) {
+      LevelData &L = H->lv[l];
+      for (int t = 0; t < L.n; ++t) {
+        if (!L.h_active[L.h_inst[t]]) continue;
+        st.rank_min = std::min(st.rank_min, L.h_k[t]);
+        st.rank_max = std::max(st.rank_max, L.h_k[t]);
+      }
+      bb += L.B_size;
+      int64_t used = 0;
+      for (int t = 0; t < L.n; ++t) used += (int64_t)L.h_m[t] * L.h_k[t];
+      bu += used;
+    }
+    if (st.rank_min > st.rank_max) st.rank_min = 0;
+    size_t es = fp64() ? 8 : 4;
+    st.bytes_dense = H->D_size * es;
+    st.bytes_coupling = bb * es;
+    st.bytes_basis = bu * 8;
+    st.near_entries = H->D_size;
+    st.sketch_pairs = sketch_pairs;
+    st.sketch_columns = sketch_cols;
+    st.kernel_launches = g_launches - launches0;
+    st.rounds = rounds;
+    st.converged = not_conv.empty();
+    st.sketch_flops = sketch_flops;
+    if (timer.on) {
+      st.ms_sketch = timer.total(PH_SKETCH, &st.ms_sketch_launch_max);
+      st.ms_nearfield = timer.total(PH_NEAR);
+      st.ms_qr = timer.total(PH_QR);
+      st.ms_id = timer.total(PH_ID);
+      st.ms_upsweep = timer.total(PH_UP);
+      st.ms_coupling = timer.total(PH_COUP);
+      st.ms_bsr = timer.total(PH_BSR);
+      st.ms_total = timer.total(PH_TOTAL);
+    }
+  }
+};
+
+__global__ void k_add_into(double *y, const double *x, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] += x[i];
+}
+
+void Builder::add_into(double *y, const double *x, int64_t n) {
+  if (n == 0) return;
+  k_add_into<<<ceil_div(n, 256), 256, 0, s>>>(y, x, n);
+  count_launch();
+  H2_CHECK_LAUNCH();
+}
+
+void validate_opts(const h2_build_opts &o) {
+  H2_REQUIRE(o.d0 >= 8 && o.d0 % 8 == 0, "d0 must be a positive multiple of 8");
+  H2_REQUIRE(o.d_inc >= 0 && o.d_inc % 8 == 0, "d_inc must be a non-negative multiple of 8");
+  H2_REQUIRE(o.d_max >= o.d0 && o.d_max <= 256, "need d0 <= d_max <= 256");
+  H2_REQUIRE(o.prec == H2_PREC_FP64 || o.prec == H2_PREC_MIXED, "unknown precision");
+  H2_REQUIRE(o.omega_mode == 0 || (o.omega_mode == 1 && o.omega_stored != nullptr),
+             "stored Omega mode needs omega_stored");
+}
+
+template <typename F>
+h2_status guarded(F &&f) {
+  try {
+    return f();
+  } catch (const Error &e) {
+    return fail(e.code, e.msg);
+  } catch (const std::bad_alloc &) {
+    return fail(H2_ERR_OOM, "host allocation failed");
+  } catch (const std::exception &e) {
+    return fail(H2_ERR_ARG, e.what());
+  }
+}
+
+// Matvec with a built matrix; T chosen by the matrix's precision.
+void matvec_impl(const h2_matrix *H, const double *x, double *y, int nrhs, cudaStream_t s) {
+  bool f64 = H->fp64;
+  int64_t N = H->n_total;
+  size_t es = f64 ? 8 : 4;
+  H2_REQUIRE(x && y && nrhs >= 1, "bad matvec arguments");
+  DBuf<char> xt, yt;
+  xt.alloc((size_t)N * nrhs * es);
+  yt.alloc_zero((size_t)N * nrhs * es, s);
+  permute_in(f64, x, N, H->orig_of_pos.p, N, nrhs, xt.p, N, s);
+  DBuf<int32_t> cb, ce;
+  std::vector<int32_t> hb(H->count, 0), he(H->count, nrhs);
+  to_device(cb, hb, s);
+  to_device(ce, he, s);
+  InstCols cols{cb.p, ce.p};
+  const LevelData &L1 = H->lv[1];
+  // near field
+  {
+    BsrArgs a{};
+    a.n_rows = L1.n;
+    a.row_inst = L1.inst.p;
+    a.row_m = L1.m.p;
+    a.row_off = L1.row.p;
+    a.col_m = L1.m.p;
+    a.col_off = L1.row.p;
+    a.ptr = H->near_ptr.p;
+    a.idx = H->near_idx.p;
+    a.boff = H->doff.p;
+    a.blocks = f64 ? (const void *)H->D64.p : (const void *)H->D32.p;
+    a.in = xt.p;
+    a.ld_in = N;
+    a.out = yt.p;
+    a.ld_out = N;
+    a.sign = 1.0;
+    a.cols = cols;
+    bsr_apply(f64, a, L1.max_m, s);
+  }
+  int levels = H->levels;
+  if (levels > 0) {
+    std::vector<DBuf<char>> xh(levels + 1), yh(levels + 1);
+    for (int l = 1; l <= levels; ++l) {
+      const LevelData &L = H->lv[l];
+      xh[l].alloc((size_t)std::max<int64_t>(L.K, 1) * nrhs * es);
+      yh[l].alloc_zero((size_t)std::max<int64_t>(L.K, 1) * nrhs * es, s);
+    }
+    // upsweep
+    for (int l = 1; l <= levels; ++l) {
+      const LevelData &L = H->lv[l];
+      const void *E = f64 ? (const void *)L.E.p : (const void *)L.E32.p;
+      if (l == 1) basis_t_apply(f64, L.dev(), E, xt.p, N, xh[1].p, L.K, cols, L.active.p, s);
+      else
+        basis_t_apply(f64, L.dev(), E, xh[l - 1].p, H->lv[l - 1].K, xh[l].p, L.K, cols,
+                      L.active.p, s);
+    }
+    // couplings
+    for (int l = 1; l <= levels; ++l) {
+      const LevelData &L = H->lv[l];
+      if (L.far_nnz == 0) continue;
+      BsrArgs a{};
+      a.n_rows = L.n;
+      a.row_inst = L.inst.p;
+      a.row_m = L.k.p;
+      a.row_off = L.krow.p;
+      a.col_m = L.k.p;
+      a.col_off = L.krow.p;
+      a.ptr = L.far_ptr.p;
+      a.idx = L.far_idx.p;
+      a.boff = L.boff.p;
+      a.blocks = f64 ? (const void *)L.B64.p : (const void *)L.B32.p;
+      a.in = xh[l].p;
+      a.ld_in = L.K;
+      a.out = yh[l].p;
+      a.ld_out = L.K;
+      a.sign = 1.0;
+      a.cols = cols;
+      bsr_apply(f64, a, L.max_k, s);
+    }
+    // downsweep
+    for (int l = levels; l >= 1; --l) {
+      const LevelData &L = H->lv[l];
+      const void *E = f64 ? (const void *)L.E.p : (const void *)L.E32.p;
+      if (l > 1)
+        basis_n_apply(f64, L.dev(), E, yh[l].p, L.K, yh[l - 1].p, H->lv[l - 1].K, cols, s);
+      else
+        basis_n_apply(f64, L.dev(), E, yh[1].p, L.K, yt.p, N, cols, s);
+    }
+  }
+  permute_out(f64, yt.p, N, H->orig_of_pos.p, N, nrhs, y, N, s);
+  H2_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace
+}  // namespace h2
+
+using namespace h2;
+
+extern "C" {
+
+void h2_default_opts(h2_build_opts *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->d0 = 32;
+  o->d_inc = 16;
+  o->d_max = 256;
+  o->prec = H2_PREC_FP64;
+  o->omega_mode = 0;
+  o->seed = 0;
+  o->sketch = H2_SKETCH_KSUM;
+}
+
+const char *h2_last_error(void) { return g_last_error.c_str(); }
+
+h2_status h2_build_cluster_tree(const double *points, int64_t n, int dim, int leaf_size,
+                                double eta, h2_stream_t s, h2_tree **out) {
+  return guarded([&]() -> h2_status {
+    H2_REQUIRE(out != nullptr, "out is NULL");
+    *out = nullptr;
+    auto t = std::make_unique<h2_tree>();
+    h2::build_tree(points, n, dim, leaf_size, eta, (cudaStream_t)s, t.get());
+    *out = t.release();
+    return H2_OK;
+  });
+}
+
+h2_status h2_tree_info(const h2_tree *t, h2_tree_info_t *info) {
+  return guarded([&]() -> h2_status {
+    H2_REQUIRE(t && info, "NULL argument");
+    std::memset(info, 0, sizeof(*info));
+    info->n = t->n;
+    info->dim = t->dim;
+    info->leaf_size = t->leaf_size;
+    info->eta = t->eta;
+    info->depth = t->depth;
+    info->n_nodes = t->n_nodes;
+    info->l_top = t->l_top;
+    info->near_nnz = t->near_nnz;
+    for (int k = 0; k <= t->depth && k < 64; ++k) info->far_nnz[k] = t->far_nnz[k];
+    return H2_OK;
+  });
+}
+
+h2_status h2_tree_export(const h2_tree *t, int32_t *perm, int64_t *begin, int64_t *end,
+                         double *lo, double *hi) {
+  return guarded([&]() -> h2_status {
+    H2_REQUIRE(t, "NULL tree");
+    cudaStream_t s = 0;
+    if (perm) H2_CUDA(cudaMemcpy(perm, t->perm.p, t->n * 4, cudaMemcpyDeviceToHost));
+    if (begin) std::memcpy(begin, t->h_begin.data(), t->n_nodes * 8);
+    if (end) std::memcpy(end, t->h_end.data(), t->n_nodes * 8);
+    if (lo || hi) {
+      std::vector<double> l = to_host(t->lo.p, 3 * (size_t)t->n_nodes, s);
+      std::vector<double> h = to_host(t->hi.p, 3 * (size_t)t->n_nodes, s);
+      for (int v = 0; v < t->n_nodes; ++v)
+        for (int k = 0; k < t->dim; ++k) {
+          if (lo) lo[(size_t)v * t->dim + k] = l[(size_t)k * t->n_nodes + v];
+          if (hi) hi[(size_t)v * t->dim + k] = h[(size_t)k * t->n_nodes + v];
+        }
+    }
+    return H2_OK;
+  });
+}
+
+h2_status h2_tree_export_list(const h2_tree *t, int which, int depth, int64_t *rowptr,
+                              int32_t *cols) {
+  return guarded([&]() -> h2_status {
+    H2_REQUIRE(t && rowptr, "NULL argument");
+    H2_REQUIRE(depth >= 0 && depth <= t->depth, "depth out of range");
+    int nrows = 1 << depth;
+    const int64_t *p;
+    const int32_t *c;
+    int64_t nnz;
+    if (which == 1) {
+      H2_REQUIRE(depth == t->depth, "the near list lives at the leaf depth");
+      p = t->near_ptr.p;
+      c = t->near_idx.p;
+      nnz = t->near_nnz;
+    } else {
+      if (depth == 0) {
+        for (int r = 0; r <= nrows; ++r) rowptr[r] = 0;
+        return H2_OK;
+      }
+      p = t->far_ptr[depth].p;
+      c = t->far_idx[depth].p;
+      nnz = t->far_nnz[depth];
+    }
+    H2_CUDA(cudaMemcpy(rowptr, p, (nrows + 1) * 8, cudaMemcpyDeviceToHost));
+    if (cols && nnz) H2_CUDA(cudaMemcpy(cols, c, nnz * 4, cudaMemcpyDeviceToHost));
+    return H2_OK;
+  });
+}
+
+void h2_tree_destroy(h2_tree *t) {
+  if (t) {
+    cudaDeviceSynchronize();
+    delete t;
+  }
+}
+
+h2_status h2_build_batched(const h2_tree *const *trees, int count, const int *kernel_ids,
+                           const double *params, const double *tols, const h2_build_opts *opts,
+                           h2_stream_t s, h2_matrix **out) {
+  return guarded([&]() -> h2_status {
+    H2_REQUIRE(out != nullptr, "out is NULL");
+    *out = nullptr;
+    H2_REQUIRE(trees && count >= 1 && kernel_ids && params && tols && opts, "NULL argument");
+    validate_opts(*opts);
+    for (int i = 0; i < count; ++i) {
+      H2_REQUIRE(trees[i] != nullptr, "NULL tree");
+      H2_REQUIRE(kernel_ids[i] == kernel_ids[0], "instances must share one kernel type");
+      H2_REQUIRE(tols[i] >= 0 && std::isfinite(tols[i]), "tol must be finite and >= 0");
+    }
+    H2_REQUIRE(kernel_ids[0] != H2_K_H2SUM, "H2 sums are built with h2_build");
+    auto H = std::make_unique<h2_matrix>();
+    H->count = count;
+    H->fp64 = opts->prec == H2_PREC_FP64;
+    H->kid = kernel_ids[0];
+    Builder b(H.get(), trees, *opts, (cudaStream_t)s);
+    h2_status st = b.run(kernel_ids, params, tols);
+    *out = H.release();
+    if (st == H2_ERR_NOT_CONVERGED) set_error(st, "sample budget d_max reached before convergence");
+    return st;
+  });
+}
+
+h2_status h2_build(const h2_tree *tree, int kernel_id, const double *params, int nparams,
+                   double tol, const h2_build_opts *opts, h2_stream_t s, h2_matrix **out) {
+  return guarded([&]() -> h2_status {
+    H2_REQUIRE(tree && opts && out, "NULL argument");
+    H2_REQUIRE(nparams >= 0 && nparams <= 4, "at most 4 kernel parameters");
+    double p4[4] = {0, 0, 0, 0};
+    for (int q = 0; q < nparams; ++q) p4[q] = params[q];
+    const h2_tree *tr[1] = {tree};
+    int kid = kernel_id;
+    double tl = tol;
+    return h2_build_batched(tr, 1, &kid, p4, &tl, opts, s, out);
+  });
+}
+
+h2_status h2_matvec(const h2_matrix *h, const double *x, double *y, int nrhs, h2_stream_t s) {
+  return guarded([&]() -> h2_status {
+    H2_REQUIRE(h != nullptr, "NULL matrix");
+    matvec_impl(h, x, y, nrhs, (cudaStream_t)s);
+    return H2_OK;
+  });
+}
+
+h2_status h2_stats(const h2_matrix *h, h2_stats_t *st) {
+  return guarded([&]() -> h2_status {
+    H2_REQUIRE(h && st, "NULL argument");
+    *st = h->st;
+    return H2_OK;
+  });
+}
+
+h2_status h2_export_level(const h2_matrix *h, int inst, int level, int32_t *ranks, int32_t *skel,
+                          double *eps_l, int32_t *d_l) {
+  return guarded([&]() -> h2_status {
+    H2_REQUIRE(h && ranks, "NULL argument");
+    H2_REQUIRE(inst >= 0 && inst < h->count, "instance out of range");
+    H2_REQUIRE(level >= 1 && level <= h->inst_ltop[inst], "level not compressed");
+    const LevelData &L = h->lv[level];
+    int base = L.task_base[inst];
+    int nl = 1 << (h->inst_depth[inst] - level + 1);
+    std::vector<int64_t> krow = to_host(L.krow.p, L.n + 1, 0);
+    std::vector<int32_t> sk = to_host(L.skel.p, std::max<int64_t>(L.K, 1), 0);
+    std::vector<int32_t> orig = to_host(h->orig_of_pos.p, h->n_total, 0);
+    int64_t q = 0;
+    for (int r = 0; r < nl; ++r) {
+      int t = base + r;
+      ranks[r] = L.h_k[t];
+      if (skel)
+        for (int a = 0; a < L.h_k[t]; ++a)
+          skel[q++] = orig[sk[krow[t] + a]] - (int32_t)h->inst_base[inst];
+    }
+    if (eps_l) *eps_l = L.h_eps[inst];
+    if (d_l) *d_l = L.d_at_id[inst];
+    return H2_OK;
+  });
+}
+
+void h2_matrix_destroy(h2_matrix *h) {
+  if (h) {
+    cudaDeviceSynchronize();
+    delete h;
+  }
+}
+
+// ---------------------------------------------------------------- primitives
+h2_status h2_ksum_sketch(const double *points, int64_t n, int dim, int kernel_id,
+                         const double *params, int nparams, const double *omega, int64_t ldo,
+                         double *y, int64_t ldy, int d, int prec, h2_stream_t s) {
+  return guarded([&]() -> h2_status {
+    cudaStream_t st = (cudaStream_t)s;
+    H2_REQUIRE(points && omega && y && n >= 1 && d >= 1 && ldo >= n && ldy >= n, "bad arguments");
+    H2_REQUIRE(dim >= 1 && dim <= 3, "dim must be 1..3");
+    KernelDesc kd = make_kernel_desc(kernel_id, params, nparams);
+    // coordinates in SoA (original order is the "tree order" here)
+    DBuf<double> px, py, pz;
+    px.alloc(n); py.alloc(n); pz.alloc(n);
+    split_points_soa(points, n, dim, px.p, py.p, pz.p, st);
+    DBuf<InstDev> idev;
+    std::vector<InstDev> hi = {InstDev{0, n, kd}};
+    to_device(idev, hi, st);
+    bool f64 = prec == H2_PREC_FP64;
+    DBuf<double> om_c, y_c;
+    om_c.alloc((size_t)n * d);
+    y_c.alloc((size_t)n * d);
+    H2_CUDA(cudaMemcpy2DAsync(om_c.p, n * 8, omega, ldo * 8, n * 8, d, cudaMemcpyDeviceToDevice, st));
+    std::vector<int64_t> nn = {n}, bb = {0};
+    std::vector<int> insts = {0};
+    int done = 0;
+    DBuf<float> xh, yh, zh, xl, yl, zl, om32, y32;
+    if (!f64) {
+      xh.alloc(n); yh.alloc(n); zh.alloc(n); xl.alloc(n); yl.alloc(n); zl.alloc(n);
+      split_coords32(px.p, py.p, pz.p, n, xh.p, yh.p, zh.p, xl.p, yl.p, zl.p, st);
+      om32.alloc((size_t)n * d);
+      y32.alloc((size_t)n * d);
+      convert32(om_c.p, (int64_t)n * d, om32.p, st);
+    }
+    H2_REQUIRE(d % 8 == 0, "d must be a multiple of 8");
+    while (done < d) {
+      int dc = std::min(32, pick_dc(d - done));
+      std::vector<int> c0 = {done};
+      KsumPlan plan = plan_ksum(nn, bb, insts, c0, dc, f64, 0, device_sm_count());
+      if (f64) {
+        KsumArgs64 a{Points64{px.p, py.p, pz.p}, om_c.p, y_c.p, n, idev.p, nullptr, nullptr};
+        run_ksum64(kernel_id, plan, a, st);
+      } else {
+        KsumArgs32 a{Points32{xh.p, yh.p, zh.p, xl.p, yl.p, zl.p}, om32.p, y32.p, n, idev.p,
+                     nullptr, nullptr};
+        run_ksum32(kernel_id, plan, a, st);
+      }
+      done += dc;
+    }
+    if (!f64) convert_to64(y32.p, (int64_t)n * d, y_c.p, st);
+    H2_CUDA(cudaMemcpy2DAsync(y, ldy * 8, y_c.p, n * 8, n * 8, d, cudaMemcpyDeviceToDevice, st));
+    H2_CUDA(cudaStreamSynchronize(st));
+    return H2_OK;
+  });
+}
+
+h2_status h2_entry_block(const double *points, int64_t n, int dim, int kernel_id,
+                         const double *params, int nparams, const int32_t *rows, int64_t nr,
+                         const int32_t *cols, int64_t nc, double *out, h2_stream_t s) {
+  return guarded([&]() -> h2_status {
+    cudaStream_t st = (cudaStream_t)s;
+    H2_REQUIRE(points && rows && cols && out && n >= 1 && nr >= 0 && nc >= 0, "bad arguments");
+    KernelDesc kd = make_kernel_desc(kernel_id, params, nparams);
+    DBuf<double> px, py, pz;
+    px.alloc(n); py.alloc(n); pz.alloc(n);
+    split_points_soa(points, n, dim, px.p, py.p, pz.p, st);
+    entry_block64(kernel_id, kd, Points64{px.p, py.p, pz.p}, rows, nr, cols, nc, out, st);
+    H2_CUDA(cudaStreamSynchronize(st));
+    return H2_OK;
+  });
+}
+
+h2_status h2_dense_sketch(const double *a, int64_t lda, int64_t n, const double *omega,
+                          int64_t ldo, double *y, int64_t ldy, int d, h2_stream_t s) {
+  return guarded([&]() -> h2_status {
+    H2_REQUIRE(a && omega && y && n >= 1 && d >= 1 && lda >= n && ldo >= n && ldy >= n,
+               "bad arguments");
+    dense_gemm64(a, lda, n, omega, ldo, y, ldy, d, (cudaStream_t)s);
+    H2_CUDA(cudaStreamSynchronize((cudaStream_t)s));
+    return H2_OK;
+  });
+}
+
+h2_status h2_batched_qr_mindiag(int count, const int32_t *m, const int32_t *d, const int64_t *off,
+                                const double *panels, double *mindiag, h2_stream_t s) {
+  return guarded([&]() -> h2_status {
+    cudaStream_t st = (cudaStream_t)s;
+    H2_REQUIRE(count >= 0 && m && d && off && panels && mindiag, "bad arguments");
+    if (count == 0) return H2_OK;
+    // the batched kernel reads one panel with ld = M; here every task has its
+    // own panel, so each task is an "instance" whose rows start at its offset
+    std::vector<int32_t> hm = to_host(m, count, st), hd = to_host(d, count, st);
+    std::vector<int64_t> ho = to_host(off, count, st);
+    DBuf<double> eps, ws;
+    DBuf<int32_t> inst, act, conv, unconv, dd;
+    DBuf<int64_t> row, wsoff;
+    std::vector<int32_t> hi(count), ha(count, 1);
+    std::vector<int64_t> hr(count, 0), hw(count);
+    int64_t tot = 0;
+    for (int t = 0; t < count; ++t) {
+      H2_REQUIRE(hm[t] >= 0 && hm[t] <= 512 && hd[t] >= 1 && hd[t] <= 512, "panel too large");
+      hi[t] = t;
+      hw[t] = tot;
+      tot += (int64_t)hm[t] * hd[t];
+    }
+    // copy panels into a workspace laid out per task (ld = m), each task
+    // reading "row 0" of its own region through ld = m
+    ws.alloc(std::max<int64_t>(tot, 1));
+    DBuf<double> panel_copy;
+    panel_copy.alloc(std::max<int64_t>(tot, 1));
+    for (int t = 0; t < count; ++t)
+      if (hm[t] * hd[t])
+        H2_CUDA(cudaMemcpyAsync(panel_copy.p + hw[t], panels + ho[t],
+                                (size_t)hm[t] * hd[t] * 8, cudaMemcpyDeviceToDevice, st));
+    // per-task launch so that each panel keeps ld = m
+    std::vector<double> zero(count, 0.0);
+    to_device(eps, zero, st);
+    to_device(inst, hi, st);
+    to_device(act, ha, st);
+    conv.alloc_zero(count, st);
+    unconv.alloc_zero(count, st);
+    to_device(dd, hd, st);
+    for (int t = 0; t < count; ++t) {
+      TasksDev td{1, inst.p + t, m + t, row.p, nullptr, nullptr, nullptr, nullptr};
+      std::vector<int64_t> r0 = {0};
+      DBuf<int64_t> r0d, wo;
+      to_device(r0d, r0, st);
+      std::vector<int64_t> w0 = {0};
+      to_device(wo, w0, st);
+      td.row = r0d.p;
+      QrArgs a{};
+      a.t = td;
+      a.Y = panel_copy.p + hw[t];
+      a.ld = hm[t];
+      a.dcur = dd.p;
+      a.eps = eps.p;
+      a.active = act.p;
+      a.conv = conv.p + t;
+      a.unconv = unconv.p;
+      a.ws = ws.p + hw[t];
+      a.ws_off = wo.p;
+      a.mindiag = mindiag + t;
+      qr_test(true, a, 0, st);
+      H2_CUDA(cudaStreamSynchronize(st));
+    }
+    return H2_OK;
+  });
+}
+
+h2_status h2_batched_row_id(int count, const int32_t *m, const int32_t *d, const int64_t *off,
+                            const double *panels, const double *eps, int32_t *k, int32_t *J,
+                            int ldj, const int64_t *eoff, double *basis, h2_stream_t s) {
+  return guarded([&]() -> h2_status {
+    cudaStream_t st = (cudaStream_t)s;
+    H2_REQUIRE(count >= 0 && m && d && off && panels && eps && k && J && eoff && basis,
+               "bad arguments");
+    if (count == 0) return H2_OK;
+    std::vector<int32_t> hm = to_host(m, count, st), hd = to_host(d, count, st);
+    std::vector<int64_t> ho = to_host(off, count, st), he = to_host(eoff, count, st);
+    std::vector<double> heps = to_host(eps, count, st);
+    for (int t = 0; t < count; ++t) {
+      H2_REQUIRE(hm[t] >= 0 && hm[t] <= 512 && hd[t] >= 1 && hd[t] <= 512, "panel too large");
+      H2_REQUIRE(ldj >= hm[t], "ldj too small");
+      DBuf<int32_t> inst, act, mm, dd, kk, jt, sk;
+      DBuf<int64_t> row, eo, wo;
+      DBuf<double> ep, ws;
+      std::vector<int32_t> z = {0}, one = {1}, m1 = {hm[t]}, d1 = {hd[t]};
+      std::vector<int64_t> r0 = {0}, e0 = {0}, w0 = {0};
+      std::vector<double> e1 = {heps[t]};
+      to_device(inst, z, st);
+      to_device(act, one, st);
+      to_device(mm, m1, st);
+      to_device(dd, d1, st);
+      to_device(row, r0, st);
+      to_device(eo, e0, st);
+      to_device(wo, w0, st);
+      to_device(ep, e1, st);
+      ws.alloc(std::max<int64_t>((int64_t)hm[t] * hd[t], 1));
+      jt.alloc(std::max(hm[t], 1));
+      sk.alloc(std::max(hm[t], 1));
+      TasksDev td{1, inst.p, mm.p, row.p, nullptr, nullptr, nullptr, eo.p};
+      IdArgs a{};
+      a.t = td;
+      a.Y = panels + ho[t];
+      a.ld = hm[t];
+      a.dcur = dd.p;
+      a.eps = ep.p;
+      a.active = act.p;
+      a.ibar = nullptr;
+      a.k_out = k + t;
+      a.J_tmp = jt.p;
+      a.skel_tmp = sk.p;
+      a.eoff = eo.p;
+      a.E = basis + he[t];
+      a.ws = ws.p;
+      a.ws_off = wo.p;
+      row_id(true, a, 0, st);
+      H2_CUDA(cudaMemcpyAsync(J + (int64_t)t * ldj, jt.p, hm[t] * 4, cudaMemcpyDeviceToDevice, st));
+      H2_CUDA(cudaStreamSynchronize(st));
+    }
+    return H2_OK;
+  });
+}
+
+}  // extern "C"

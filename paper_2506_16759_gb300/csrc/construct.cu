@@ -1,0 +1,804 @@
+// Per-level batched kernels of Algorithm 1 (Sec. III-A/III-B):
+//  - leaf near field: D = K(I_t, I_b) generated and stored while
+//    Y_loc = Y - sum_b D Omega_b is accumulated (batchedGen + batchedBSRGemm);
+//  - block-sparse products with stored D or B (adaptive re-sweeps, inner
+//    far-field subtraction, matvec);
+//  - the QR convergence test (min_j |R_jj| of Y_loc, FP64 Householder);
+//  - the row ID by column-pivoted Householder QR of Y_loc^T/sqrt(d) (FP64);
+//  - shrink (skeleton-row gather) and the Omega upsweep U^T Omega;
+//  - couplings B = K(Itil_s, Itil_t).
+// One CTA owns one cluster (row block), so no output is written by two CTAs.
+#include <algorithm>
+
+#include "h2_level.h"
+#include "h2_types.h"
+
+namespace h2 {
+namespace {
+
+constexpr int kNT = 256;   // threads per cluster CTA
+constexpr int kJC = 64;    // block columns staged per step
+constexpr int kMaxRows = 256;     // rows of a block-product row task
+constexpr int kMaxIdRows = 512;   // rows of a cluster in the QR test / row ID
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the CTA; every thread gets the result.  `sh` holds >= 33 doubles.
+__device__ double block_sum(double v, double *sh) {
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    double w = lane < nw ? sh[lane] : 0.0;
+    w = warp_sum(w);
+    if (lane == 0) sh[32] = w;
+  }
+  __syncthreads();
+  double r = sh[32];
+  __syncthreads();
+  return r;
+}
+
+// Argmax over the CTA, lowest index on ties.  Every thread gets the index.
+__device__ int block_argmax(double v, int idx, double *shv, int *shi) {
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    double ov = __shfl_xor_sync(0xffffffffu, v, o);
+    int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+  }
+  if (lane == 0) { shv[warp] = v; shi[warp] = idx; }
+  __syncthreads();
+  if (warp == 0) {
+    double w = lane < nw ? shv[lane] : -1.0;
+    int wi = lane < nw ? shi[lane] : 0x7fffffff;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double ov = __shfl_xor_sync(0xffffffffu, w, o);
+      int oi = __shfl_xor_sync(0xffffffffu, wi, o);
+      if (ov > w || (ov == w && oi < wi)) { w = ov; wi = oi; }
+    }
+    if (lane == 0) shi[32] = wi;
+  }
+  __syncthreads();
+  int r = shi[32];
+  __syncthreads();
+  return r;
+}
+
+template <typename T>
+struct PtsOf;
+template <>
+struct PtsOf<double> {
+  __device__ static void load(const Points64 &p, const Points32 &, int64_t g, double *c) {
+    c[0] = p.x[g]; c[1] = p.y[g]; c[2] = p.z[g];
+  }
+  template <int KID>
+  __device__ static double geom(const double *a, const double *b) {
+    return geom64<KID>(a[0], a[1], a[2], b[0], b[1], b[2]);
+  }
+  static constexpr int NC = 3;
+};
+template <>
+struct PtsOf<float> {
+  __device__ static void load(const Points64 &, const Points32 &p, int64_t g, float *c) {
+    c[0] = p.xh[g]; c[1] = p.yh[g]; c[2] = p.zh[g];
+    c[3] = p.xl[g]; c[4] = p.yl[g]; c[5] = p.zl[g];
+  }
+  template <int KID>
+  __device__ static float geom(const float *a, const float *b) {
+    return geom32<KID>(a[0], a[1], a[2], a[3], a[4], a[5], b[0], b[1], b[2], b[3], b[4], b[5]);
+  }
+  static constexpr int NC = 6;
+};
+
+// ----------------------------------------------------------------------------
+// Leaf near field.  Output mapping: thread -> rows i = tid%64 + 64q (q<4),
+// column group tid/64 of DC/4 columns.
+// ----------------------------------------------------------------------------
+template <int KID, typename T, int DC>
+__global__ void __launch_bounds__(kNT) k_nearfield(NearArgs a, int mmax) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int NC = PtsOf<T>::NC;
+  constexpr int DG = DC / 4;
+  int tau = blockIdx.x;
+  int m = a.t.m[tau];
+  int inst = a.t.inst[tau];
+  int cb = a.cols.cb[inst], ce = a.cols.ce[inst];
+  int ncol = ce - cb;
+  if (m == 0 || ncol <= 0) return;
+  int64_t rowt = a.t.row[tau];
+  const InstDev in = a.inst[inst];
+  const T scale = (T)in.kd.scale, diag = (T)in.kd.diag;
+  const int pw = in.kd.pw;
+  T *sD = reinterpret_cast<T *>(smem_raw);                 // [kJC][mmax]
+  T *sO = sD + (size_t)kJC * mmax;                         // [kJC][DC]
+  T *sxa = sO + (size_t)kJC * DC;                          // [mmax][NC]
+  T *sxb = sxa + (size_t)mmax * NC;                        // [kJC][NC]
+  const T *Om = reinterpret_cast<const T *>(a.Om);
+  T *Y = reinterpret_cast<T *>(a.Y);
+  T *D = reinterpret_cast<T *>(a.D);
+  for (int i = threadIdx.x; i < m; i += kNT) PtsOf<T>::load(a.p64, a.p32, rowt + i, sxa + i * NC);
+  const int ri = threadIdx.x % 64, cg = threadIdx.x / 64;
+  T acc[4][DG];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int c = 0; c < DG; ++c) acc[q][c] = T(0);
+  __syncthreads();
+  for (int64_t e = a.ptr[tau]; e < a.ptr[tau + 1]; ++e) {
+    int b = a.idx[e];
+    int mb = a.t.m[b];
+    int64_t rowb = a.t.row[b];
+    T *Dblk = D + a.doff[e];
+    for (int jc = 0; jc < mb; jc += kJC) {
+      int nj = min(kJC, mb - jc);
+      for (int j = threadIdx.x; j < nj; j += kNT)
+        PtsOf<T>::load(a.p64, a.p32, rowb + jc + j, sxb + j * NC);
+      for (int q = threadIdx.x; q < kJC * DC; q += kNT) {
+        int j = q % kJC, c = q / kJC;
+        sO[j * DC + c] = (j < nj && c < ncol) ? Om[rowb + jc + j + (int64_t)(cb + c) * a.ld] : T(0);
+      }
+      __syncthreads();
+      for (int q = threadIdx.x; q < m * nj; q += kNT) {
+        int i = q % m, j = q / m;
+        T g = PtsOf<T>::template geom<KID>(sxa + i * NC, sxb + j * NC);
+        T v = (rowt + i == rowb + jc + j) ? kdiag<KID, T>(g, scale, pw, diag)
+                                          : kval<KID, T>(g, scale, pw);
+        sD[j * mmax + i] = v;
+        Dblk[i + (int64_t)(jc + j) * m] = v;
+      }
+      __syncthreads();
+      for (int j = 0; j < nj; ++j) {
+        T ov[DG];
+#pragma unroll
+        for (int c = 0; c < DG; ++c) ov[c] = sO[j * DC + cg * DG + c];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          int i = ri + 64 * q;
+          if (i < m) {
+            T dv = sD[j * mmax + i];
+#pragma unroll
+            for (int c = 0; c < DG; ++c) acc[q][c] += dv * ov[c];
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    int i = ri + 64 * q;
+    if (i >= m) continue;
+#pragma unroll
+    for (int c = 0; c < DG; ++c) {
+      int col = cg * DG + c;
+      if (col < ncol) {
+        T *yp = Y + rowt + i + (int64_t)(cb + col) * a.ld;
+        *yp = *yp - acc[q][c];
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Block-sparse product with stored blocks, same mapping, column blocks of DC.
+// ----------------------------------------------------------------------------
+template <typename T, int DC>
+__global__ void __launch_bounds__(kNT) k_bsr(BsrArgs a, int mmax) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int DG = DC / 4;
+  int tau = blockIdx.x;
+  int m = a.row_m[tau];
+  int inst = a.row_inst[tau];
+  int cb = a.cols.cb[inst], ce = a.cols.ce[inst];
+  if (m == 0 || ce <= cb || a.ptr[tau] == a.ptr[tau + 1]) return;
+  int64_t orow = a.row_off[tau];
+  T *sB = reinterpret_cast<T *>(smem_raw);   // [kJC][mmax]
+  T *sI = sB + (size_t)kJC * mmax;           // [kJC][DC]
+  const T *blocks = reinterpret_cast<const T *>(a.blocks);
+  const T *in = reinterpret_cast<const T *>(a.in);
+  T *out = reinterpret_cast<T *>(a.out);
+  const T sign = (T)a.sign;
+  const int ri = threadIdx.x % 64, cg = threadIdx.x / 64;
+  for (int c0 = cb; c0 < ce; c0 += DC) {
+    int ncol = min(DC, ce - c0);
+    T acc[4][DG];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int c = 0; c < DG; ++c) acc[q][c] = T(0);
+    for (int64_t e = a.ptr[tau]; e < a.ptr[tau + 1]; ++e) {
+      int b = a.idx[e];
+      int mb = a.col_m[b];
+      int64_t irow = a.col_off[b];
+      const T *blk = blocks + a.boff[e];
+      for (int jc = 0; jc < mb; jc += kJC) {
+        int nj = min(kJC, mb - jc);
+        for (int q = threadIdx.x; q < m * nj; q += kNT) {
+          int i = q % m, j = q / m;
+          sB[j * mmax + i] = blk[i + (int64_t)(jc + j) * m];
+        }
+        for (int q = threadIdx.x; q < kJC * DC; q += kNT) {
+          int j = q % kJC, c = q / kJC;
+          sI[j * DC + c] = (j < nj && c < ncol) ? in[irow + jc + j + (int64_t)(c0 + c) * a.ld_in]
+                                                : T(0);
+        }
+        __syncthreads();
+        for (int j = 0; j < nj; ++j) {
+          T ov[DG];
+#pragma unroll
+          for (int c = 0; c < DG; ++c) ov[c] = sI[j * DC + cg * DG + c];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            int i = ri + 64 * q;
+            if (i < m) {
+              T bv = sB[j * mmax + i];
+#pragma unroll
+              for (int c = 0; c < DG; ++c) acc[q][c] += bv * ov[c];
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int i = ri + 64 * q;
+      if (i >= m) continue;
+#pragma unroll
+      for (int c = 0; c < DG; ++c) {
+        int col = cg * DG + c;
+        if (col < ncol) {
+          T *op = out + orow + i + (int64_t)(c0 + col) * a.ld_out;
+          *op = *op + sign * acc[q][c];
+        }
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// QR convergence test (FP64 Householder, one CTA per cluster).
+// ----------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kNT) k_qr_test(QrArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[33];
+  int tau = blockIdx.x;
+  int inst = a.t.inst[tau];
+  if (!a.active[inst] || a.conv[tau]) return;
+  int m = a.t.m[tau];
+  int d = a.dcur[inst];
+  if (m <= d) {
+    if (threadIdx.x == 0) {
+      a.conv[tau] = 1;
+      if (a.mindiag) a.mindiag[tau] = 0.0;
+    }
+    return;
+  }
+  double *A = a.ws_off && a.ws_off[tau] >= 0 ? a.ws + a.ws_off[tau]
+                                             : reinterpret_cast<double *>(smem_raw);
+  const T *Y = reinterpret_cast<const T *>(a.Y);
+  int64_t row = a.t.row[tau];
+  for (int64_t q = threadIdx.x; q < (int64_t)m * d; q += kNT) {
+    int i = (int)(q % m), c = (int)(q / m);
+    A[q] = (double)Y[row + i + (int64_t)c * a.ld];
+  }
+  __syncthreads();
+  const double eps = a.eps[inst];
+  double minr = INFINITY;
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kNT >> 5;
+  for (int j = 0; j < d; ++j) {
+    double *colj = A + (int64_t)j * m;
+    double part = 0.0;
+    for (int i = j + threadIdx.x; i < m; i += kNT) part += colj[i] * colj[i];
+    double nrm2 = block_sum(part, red);
+    double nrm = sqrt(nrm2);
+    minr = fmin(minr, nrm);
+    if (minr <= eps && !a.mindiag) break;  // converged: the minimum only decreases
+    if (nrm == 0.0) continue;
+    double x0 = colj[j];
+    double alpha = x0 != 0.0 ? -copysign(nrm, x0) : -nrm;
+    double v0 = x0 - alpha;
+    double beta = 1.0 / (nrm * (nrm + fabs(x0)));   // 2 / (v^T v)
+    __syncthreads();
+    if (threadIdx.x == 0) colj[j] = v0;
+    __syncthreads();
+    for (int c = j + 1 + warp; c < d; c += nw) {
+      double *colc = A + (int64_t)c * m;
+      double w = 0.0;
+      for (int i = j + lane; i < m; i += 32) w += colj[i] * colc[i];
+      w = warp_sum(w) * beta;
+      for (int i = j + lane; i < m; i += 32) colc[i] -= w * colj[i];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (a.mindiag) a.mindiag[tau] = minr;
+    if (minr <= eps) a.conv[tau] = 1;
+    else atomicAdd(&a.unconv[inst], 1);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Row ID by column-pivoted Householder QR of A = Y_loc^T / sqrt(d), d x m.
+// ----------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kNT) k_row_id(IdArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[33];
+  __shared__ double redv[33];
+  __shared__ int redi[33];
+  int tau = blockIdx.x;
+  int inst = a.t.inst[tau];
+  int m = a.t.m[tau];
+  int64_t row = a.t.row[tau];
+  if (!a.active[inst] || m == 0) {
+    if (threadIdx.x == 0) a.k_out[tau] = 0;
+    return;
+  }
+  int d = a.dcur[inst];
+  // shared layout: norms[m] (double), piv[m], rank[m], sig[m] (int), then A
+  double *nrm2 = reinterpret_cast<double *>(smem_raw);
+  int *piv = reinterpret_cast<int *>(nrm2 + kMaxIdRows);
+  int *rnk = piv + kMaxIdRows;
+  int *sig = rnk + kMaxIdRows;
+  double *A = a.ws_off && a.ws_off[tau] >= 0 ? a.ws + a.ws_off[tau]
+                                             : reinterpret_cast<double *>(sig + kMaxIdRows);
+  const T *Y = reinterpret_cast<const T *>(a.Y);
+  const double sd = sqrt((double)d);
+  for (int64_t q = threadIdx.x; q < (int64_t)m * d; q += kNT) {
+    int i = (int)(q % m), c = (int)(q / m);
+    A[c + (int64_t)i * d] = (double)Y[row + i + (int64_t)c * a.ld] / sd;
+  }
+  for (int i = threadIdx.x; i < m; i += kNT) piv[i] = i;
+  __syncthreads();
+  const double eps = a.eps[inst];
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kNT >> 5;
+  int kmax = min(d, m);
+  int k = 0;
+  while (k < kmax) {
+    // norms of the trailing columns, recomputed from scratch
+    for (int c = k + warp; c < m; c += nw) {
+      const double *col = A + (int64_t)c * d;
+      double s = 0.0;
+      for (int r = k + lane; r < d; r += 32) s += col[r] * col[r];
+      s = warp_sum(s);
+      if (lane == 0) nrm2[c] = s;
+    }
+    __syncthreads();
+    double tot = 0.0, best = -1.0;
+    int bi = 0x7fffffff;
+    for (int c = k + threadIdx.x; c < m; c += kNT) {
+      double nv = sqrt(nrm2[c]);
+      tot += nv * nv;
+      if (nv > best) { best = nv; bi = c; }
+    }
+    tot = block_sum(tot, red);
+    if (sqrt(tot) <= eps) break;
+    int p = block_argmax(best, bi, redv, redi);
+    if (p < k || p >= m) break;  // no finite pivot left
+    if (p != k) {
+      double *ck = A + (int64_t)k * d, *cp = A + (int64_t)p * d;
+      for (int r = threadIdx.x; r < d; r += kNT) {
+        double t0 = ck[r]; ck[r] = cp[r]; cp[r] = t0;
+      }
+      if (threadIdx.x == 0) { int t1 = piv[k]; piv[k] = piv[p]; piv[p] = t1; }
+    }
+    __syncthreads();
+    double *colk = A + (int64_t)k * d;
+    double nk = sqrt(nrm2[p]);
+    double x0 = colk[k];
+    double alpha = x0 != 0.0 ? -copysign(nk, x0) : -nk;
+    double beta = nk > 0.0 ? 1.0 / (nk * (nk + fabs(x0))) : 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0) colk[k] = x0 - alpha;
+    __syncthreads();
+    if (beta != 0.0) {
+      for (int c = k + 1 + warp; c < m; c += nw) {
+        double *colc = A + (int64_t)c * d;
+        double w = 0.0;
+        for (int r = k + lane; r < d; r += 32) w += colk[r] * colc[r];
+        w = warp_sum(w) * beta;
+        for (int r = k + lane; r < d; r += 32) colc[r] -= w * colk[r];
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) colk[k] = alpha;
+    __syncthreads();
+    ++k;
+  }
+  // T = R11^{-1} R12 by back substitution, written over R12 (column-wise)
+  for (int c = k + threadIdx.x; c < m; c += kNT) {
+    double *col = A + (int64_t)c * d;
+    for (int i = k - 1; i >= 0; --i) {
+      double t = col[i];
+      for (int j = i + 1; j < k; ++j) t -= A[i + (int64_t)j * d] * col[j];
+      col[i] = t / A[i + (int64_t)i * d];
+    }
+  }
+  // sorted skeleton order
+  for (int q = threadIdx.x; q < k; q += kNT) {
+    int r = 0;
+    for (int b = 0; b < k; ++b) r += piv[b] < piv[q];
+    rnk[q] = r;
+    sig[r] = q;
+  }
+  __syncthreads();
+  double *E = a.E + a.eoff[tau];
+  for (int64_t q = threadIdx.x; q < (int64_t)m * k; q += kNT) E[q] = 0.0;
+  __syncthreads();
+  for (int q = threadIdx.x; q < k; q += kNT) {
+    int jr = piv[sig[q]];
+    E[jr + (int64_t)q * m] = 1.0;
+    a.J_tmp[row + q] = jr;
+    a.skel_tmp[row + q] = a.ibar ? a.ibar[row + jr] : (int32_t)(row + jr);
+  }
+  for (int64_t q = threadIdx.x; q < (int64_t)(m - k) * k; q += kNT) {
+    int rr = (int)(q % (m - k)), ap = (int)(q / (m - k));
+    E[piv[k + rr] + (int64_t)ap * m] = A[sig[ap] + (int64_t)(k + rr) * d];
+  }
+  if (threadIdx.x == 0) a.k_out[tau] = k;
+}
+
+__global__ void k_compact(TasksDev t, const int32_t *J_tmp, const int32_t *skel_tmp, int32_t *J,
+                          int32_t *skel) {
+  int tau = blockIdx.x;
+  int k = t.k[tau];
+  int64_t row = t.row[tau], kr = t.krow[tau];
+  for (int a = threadIdx.x; a < k; a += blockDim.x) {
+    J[kr + a] = J_tmp[row + a];
+    skel[kr + a] = skel_tmp[row + a];
+  }
+}
+
+template <typename T>
+__global__ void k_gather_rows_skel(TasksDev t, const T *Y, int64_t ld, T *Yn, int64_t ldn,
+                                   InstCols cols, const int32_t *active) {
+  int tau = blockIdx.x;
+  int inst = t.inst[tau];
+  if (!active[inst]) return;
+  int k = t.k[tau];
+  int cb = cols.cb[inst], ce = cols.ce[inst];
+  int64_t row = t.row[tau], kr = t.krow[tau];
+  for (int64_t q = threadIdx.x; q < (int64_t)k * (ce - cb); q += blockDim.x) {
+    int a = (int)(q % k), c = cb + (int)(q / k);
+    Yn[kr + a + c * ldn] = Y[row + t.J[kr + a] + c * ld];
+  }
+}
+
+// out(krow+a, c) = sum_i E(i,a) in(row+i, c)
+template <typename T, typename TE>
+__global__ void k_basis_t(TasksDev t, const TE *E, const T *in, int64_t ld_in, T *out,
+                          int64_t ld_out, InstCols cols, const int32_t *active) {
+  int tau = blockIdx.x;
+  int inst = t.inst[tau];
+  if (active && !active[inst]) return;
+  int k = t.k[tau], m = t.m[tau];
+  int cb = cols.cb[inst], ce = cols.ce[inst];
+  if (k == 0 || ce <= cb) return;
+  int64_t row = t.row[tau], kr = t.krow[tau];
+  const TE *Et = E + t.eoff[tau];
+  for (int64_t q = threadIdx.x; q < (int64_t)k * (ce - cb); q += blockDim.x) {
+    int a = (int)(q % k), c = cb + (int)(q / k);
+    const TE *ea = Et + (int64_t)a * m;
+    const T *xc = in + row + c * ld_in;
+    T s = T(0);
+    for (int i = 0; i < m; ++i) s += (T)ea[i] * xc[i];
+    out[kr + a + c * ld_out] = s;
+  }
+}
+
+// out(row+i, c) += sum_a E(i,a) in(krow+a, c)
+template <typename T, typename TE>
+__global__ void k_basis_n(TasksDev t, const TE *E, const T *in, int64_t ld_in, T *out,
+                          int64_t ld_out, InstCols cols) {
+  int tau = blockIdx.x;
+  int inst = t.inst[tau];
+  int k = t.k[tau], m = t.m[tau];
+  int cb = cols.cb[inst], ce = cols.ce[inst];
+  if (k == 0 || ce <= cb) return;
+  int64_t row = t.row[tau], kr = t.krow[tau];
+  const TE *Et = E + t.eoff[tau];
+  for (int64_t q = threadIdx.x; q < (int64_t)m * (ce - cb); q += blockDim.x) {
+    int i = (int)(q % m), c = cb + (int)(q / m);
+    const T *yc = in + kr + c * ld_in;
+    T s = T(0);
+    for (int aa = 0; aa < k; ++aa) s += (T)Et[i + (int64_t)aa * m] * yc[aa];
+    out[row + i + c * ld_out] += s;
+  }
+}
+
+template <int KID, typename T>
+__global__ void k_coupling(CouplingArgs a) {
+  int64_t e = blockIdx.x;
+  int tr = a.erow[e], tc = a.idx[e];
+  int kr = a.t.k[tr], kc = a.t.k[tc];
+  if (kr == 0 || kc == 0) return;
+  const InstDev in = a.inst[a.t.inst[tr]];
+  const T scale = (T)in.kd.scale, diag = (T)in.kd.diag;
+  const int pw = in.kd.pw;
+  const int32_t *sr = a.skel + a.t.krow[tr];
+  const int32_t *sc = a.skel + a.t.krow[tc];
+  T *B = reinterpret_cast<T *>(a.B) + a.boff[e];
+  constexpr int NC = PtsOf<T>::NC;
+  for (int64_t q = threadIdx.x; q < (int64_t)kr * kc; q += blockDim.x) {
+    int i = (int)(q % kr), j = (int)(q / kr);
+    T pa[NC], pb[NC];
+    PtsOf<T>::load(a.p64, a.p32, sr[i], pa);
+    PtsOf<T>::load(a.p64, a.p32, sc[j], pb);
+    T g = PtsOf<T>::template geom<KID>(pa, pb);
+    B[q] = sr[i] == sc[j] ? kdiag<KID, T>(g, scale, pw, diag) : kval<KID, T>(g, scale, pw);
+  }
+}
+
+__global__ void k_block_sizes(int64_t nnz, const int32_t *erow, const int32_t *idx,
+                              const int32_t *mrow, const int32_t *mcol, int64_t *out) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < nnz) out[e] = (int64_t)mrow[erow[e]] * mcol[idx[e]];
+}
+
+__global__ void k_inner_tasks(int n, const int32_t *child0, const int64_t *krow_child,
+                              const int32_t *k_child, int64_t *row, int32_t *m) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  int c = child0[t];
+  row[t] = krow_child[c];
+  m[t] = k_child[c] + k_child[c + 1];
+}
+
+__global__ void k_basis_capacity(int n, const int32_t *m, const int32_t *inst,
+                                 const int32_t *dcur, int64_t *cap) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  int mm = m[t];
+  int d = dcur[inst[t]];
+  cap[t] = (int64_t)mm * min(mm, d);
+}
+
+__global__ void k_map_csr(const int64_t *ptr, const int32_t *idx, int nrows, int first_node,
+                          int task_base, int64_t nnz_base, int64_t *ptr_out, int32_t *idx_out,
+                          int32_t *erow_out, int write_last) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrows) return;
+  int64_t b = ptr[r], e = ptr[r + 1];
+  ptr_out[task_base + r] = nnz_base + b;
+  if (write_last && r == nrows - 1) ptr_out[task_base + nrows] = nnz_base + e;
+  for (int64_t q = b; q < e; ++q) {
+    idx_out[nnz_base + q] = task_base + (idx[q] - first_node);
+    if (erow_out) erow_out[nnz_base + q] = task_base + r;
+  }
+}
+
+template <typename T>
+__global__ void k_permute_in(const double *x, int64_t ldx, const int32_t *orig, int64_t n,
+                             int nrhs, T *xt, int64_t ldt) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t o = orig[i];
+  for (int c = 0; c < nrhs; ++c) xt[i + c * ldt] = (T)x[o + c * ldx];
+}
+
+template <typename T>
+__global__ void k_permute_out(const T *yt, int64_t ldt, const int32_t *orig, int64_t n, int nrhs,
+                              double *y, int64_t ldy) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t o = orig[i];
+  for (int c = 0; c < nrhs; ++c) y[o + c * ldy] = (double)yt[i + c * ldt];
+}
+
+__global__ void k_fill_i32(int32_t *p, int64_t n, int32_t v) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+template <typename K>
+void set_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024)
+    H2_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+}
+
+}  // namespace
+
+void nearfield_gen(int kid, bool fp64, const NearArgs &a, int max_m, cudaStream_t s) {
+  if (a.t.n == 0) return;
+  H2_REQUIRE(max_m <= kMaxRows, "leaf size above 256 is not supported");
+  int mm = std::max(max_m, 1);
+  dispatch_kernel(kid, [&](auto K) {
+    constexpr int KID = decltype(K)::value;
+    if (fp64) {
+      size_t bytes = sizeof(double) * ((size_t)kJC * mm + kJC * 32 + (size_t)(mm + kJC) * 3);
+      auto kern = k_nearfield<KID, double, 32>;
+      set_smem(kern, bytes);
+      kern<<<a.t.n, kNT, bytes, s>>>(a, mm);
+    } else {
+      size_t bytes = sizeof(float) * ((size_t)kJC * mm + kJC * 32 + (size_t)(mm + kJC) * 6);
+      auto kern = k_nearfield<KID, float, 32>;
+      set_smem(kern, bytes);
+      kern<<<a.t.n, kNT, bytes, s>>>(a, mm);
+    }
+    count_launch();
+    H2_CHECK_LAUNCH();
+  });
+}
+
+void bsr_apply(bool fp64, const BsrArgs &a, int max_m, cudaStream_t s) {
+  if (a.n_rows == 0) return;
+  H2_REQUIRE(max_m <= kMaxRows, "block rows above 256 are not supported");
+  int mm = std::max(max_m, 1);
+  if (fp64) {
+    size_t bytes = sizeof(double) * ((size_t)kJC * mm + kJC * 32);
+    auto kern = k_bsr<double, 32>;
+    set_smem(kern, bytes);
+    kern<<<a.n_rows, kNT, bytes, s>>>(a, mm);
+  } else {
+    size_t bytes = sizeof(float) * ((size_t)kJC * mm + kJC * 32);
+    auto kern = k_bsr<float, 32>;
+    set_smem(kern, bytes);
+    kern<<<a.n_rows, kNT, bytes, s>>>(a, mm);
+  }
+  count_launch();
+  H2_CHECK_LAUNCH();
+}
+
+void qr_test(bool fp64, const QrArgs &a, size_t smem_bytes, cudaStream_t s) {
+  if (a.t.n == 0) return;
+  if (fp64) {
+    auto kern = k_qr_test<double>;
+    set_smem(kern, smem_bytes);
+    kern<<<a.t.n, kNT, smem_bytes, s>>>(a);
+  } else {
+    auto kern = k_qr_test<float>;
+    set_smem(kern, smem_bytes);
+    kern<<<a.t.n, kNT, smem_bytes, s>>>(a);
+  }
+  count_launch();
+  H2_CHECK_LAUNCH();
+}
+
+size_t row_id_fixed_smem() { return kMaxIdRows * (sizeof(double) + 3 * sizeof(int)); }
+
+void row_id(bool fp64, const IdArgs &a, size_t smem_bytes, cudaStream_t s) {
+  if (a.t.n == 0) return;
+  size_t bytes = smem_bytes + row_id_fixed_smem();
+  if (fp64) {
+    auto kern = k_row_id<double>;
+    set_smem(kern, bytes);
+    kern<<<a.t.n, kNT, bytes, s>>>(a);
+  } else {
+    auto kern = k_row_id<float>;
+    set_smem(kern, bytes);
+    kern<<<a.t.n, kNT, bytes, s>>>(a);
+  }
+  count_launch();
+  H2_CHECK_LAUNCH();
+}
+
+void compact_skeletons(const TasksDev &t, const int32_t *J_tmp, const int32_t *skel_tmp,
+                       int32_t *J, int32_t *skel, cudaStream_t s) {
+  if (t.n == 0) return;
+  k_compact<<<t.n, 128, 0, s>>>(t, J_tmp, skel_tmp, J, skel);
+  count_launch();
+  H2_CHECK_LAUNCH();
+}
+
+void gather_skeleton_rows(bool fp64, const TasksDev &t, const void *Y, int64_t ld, void *Yn,
+                          int64_t ldn, InstCols cols, const int32_t *active, cudaStream_t s) {
+  if (t.n == 0) return;
+  if (fp64)
+    k_gather_rows_skel<double><<<t.n, 256, 0, s>>>(t, (const double *)Y, ld, (double *)Yn, ldn,
+                                                   cols, active);
+  else
+    k_gather_rows_skel<float><<<t.n, 256, 0, s>>>(t, (const float *)Y, ld, (float *)Yn, ldn, cols,
+                                                  active);
+  count_launch();
+  H2_CHECK_LAUNCH();
+}
+
+void basis_t_apply(bool fp64, const TasksDev &t, const void *E, const void *in, int64_t ld_in,
+                   void *out, int64_t ld_out, InstCols cols, const int32_t *active,
+                   cudaStream_t s) {
+  if (t.n == 0) return;
+  if (fp64)
+    k_basis_t<double, double><<<t.n, 256, 0, s>>>(t, (const double *)E, (const double *)in,
+                                                  ld_in, (double *)out, ld_out, cols, active);
+  else
+    k_basis_t<float, float><<<t.n, 256, 0, s>>>(t, (const float *)E, (const float *)in, ld_in,
+                                                (float *)out, ld_out, cols, active);
+  count_launch();
+  H2_CHECK_LAUNCH();
+}
+
+void basis_n_apply(bool fp64, const TasksDev &t, const void *E, const void *in, int64_t ld_in,
+                   void *out, int64_t ld_out, InstCols cols, cudaStream_t s) {
+  if (t.n == 0) return;
+  if (fp64)
+    k_basis_n<double, double><<<t.n, 256, 0, s>>>(t, (const double *)E, (const double *)in,
+                                                  ld_in, (double *)out, ld_out, cols);
+  else
+    k_basis_n<float, float><<<t.n, 256, 0, s>>>(t, (const float *)E, (const float *)in, ld_in,
+                                                (float *)out, ld_out, cols);
+  count_launch();
+  H2_CHECK_LAUNCH();
+}
+
+void coupling_gen(int kid, bool fp64, const CouplingArgs &a, cudaStream_t s) {
+  if (a.nnz == 0) return;
+  H2_REQUIRE(a.nnz < (1ll << 31), "too many coupling blocks");
+  dispatch_kernel(kid, [&](auto K) {
+    constexpr int KID = decltype(K)::value;
+    if (fp64) k_coupling<KID, double><<<(int)a.nnz, 128, 0, s>>>(a);
+    else k_coupling<KID, float><<<(int)a.nnz, 128, 0, s>>>(a);
+    count_launch();
+    H2_CHECK_LAUNCH();
+  });
+}
+
+void block_sizes(int64_t nnz, const int32_t *erow, const int32_t *idx, const int32_t *mrow,
+                 const int32_t *mcol, int64_t *out, cudaStream_t s) {
+  if (nnz == 0) return;
+  k_block_sizes<<<ceil_div(nnz, 256), 256, 0, s>>>(nnz, erow, idx, mrow, mcol, out);
+  count_launch();
+  H2_CHECK_LAUNCH();
+}
+
+void inner_tasks(int n, const int32_t *child0, const int64_t *krow_child, const int32_t *k_child,
+                 int64_t *row, int32_t *m, cudaStream_t s) {
+  if (n == 0) return;
+  k_inner_tasks<<<ceil_div(n, 256), 256, 0, s>>>(n, child0, krow_child, k_child, row, m);
+  count_launch();
+  H2_CHECK_LAUNCH();
+}
+
+void basis_capacity(int n, const int32_t *m, const int32_t *inst, const int32_t *dcur,
+                    int64_t *cap, cudaStream_t s) {
+  if (n == 0) return;
+  k_basis_capacity<<<ceil_div(n, 256), 256, 0, s>>>(n, m, inst, dcur, cap);
+  count_launch();
+  H2_CHECK_LAUNCH();
+}
+
+void map_csr(const int64_t *ptr, const int32_t *idx, int nrows, int first_node, int task_base,
+             int64_t nnz_base, int64_t *ptr_out, int32_t *idx_out, int32_t *erow_out,
+             bool write_last, cudaStream_t s) {
+  if (nrows == 0) return;
+  k_map_csr<<<ceil_div(nrows, 128), 128, 0, s>>>(ptr, idx, nrows, first_node, task_base, nnz_base,
+                                                 ptr_out, idx_out, erow_out, write_last ? 1 : 0);
+  count_launch();
+  H2_CHECK_LAUNCH();
+}
+
+void permute_in(bool fp64, const double *x, int64_t ldx, const int32_t *orig, int64_t n, int nrhs,
+                void *xt, int64_t ldt, cudaStream_t s) {
+  if (n == 0) return;
+  if (fp64) k_permute_in<double><<<ceil_div(n, 256), 256, 0, s>>>(x, ldx, orig, n, nrhs, (double *)xt, ldt);
+  else k_permute_in<float><<<ceil_div(n, 256), 256, 0, s>>>(x, ldx, orig, n, nrhs, (float *)xt, ldt);
+  count_launch();
+  H2_CHECK_LAUNCH();
+}
+
+void permute_out(bool fp64, const void *yt, int64_t ldt, const int32_t *orig, int64_t n, int nrhs,
+                 double *y, int64_t ldy, cudaStream_t s) {
+  if (n == 0) return;
+  if (fp64) k_permute_out<double><<<ceil_div(n, 256), 256, 0, s>>>((const double *)yt, ldt, orig, n, nrhs, y, ldy);
+  else k_permute_out<float><<<ceil_div(n, 256), 256, 0, s>>>((const float *)yt, ldt, orig, n, nrhs, y, ldy);
+  count_launch();
+  H2_CHECK_LAUNCH();
+}
+
+void fill_i32(int32_t *p, int64_t n, int32_t v, cudaStream_t s) {
+  if (n == 0) return;
+  k_fill_i32<<<ceil_div(n, 256), 256, 0, s>>>(p, n, v);
+  count_launch();
+  H2_CHECK_LAUNCH();
+}
+
+}  // namespace h2

@@ -1,0 +1,108 @@
+// Internal launch interfaces between the driver and the kernel translation
+// units.  All pointers are device pointers unless stated otherwise.
+#pragma once
+
+#include "h2_internal.cuh"
+
+namespace h2 {
+
+// One instance of a (possibly batched) build, as seen by the kernels.
+struct InstDev {
+  int64_t pbase;   // first global tree position of the instance
+  int64_t n;       // points
+  KernelDesc kd;   // entry evaluator
+};
+
+// ---------------------------------------------------------------- sketch
+// Work item of the fused kernel summation: rows [row0, row0+rows) of
+// instance `inst` against its points [j0, j1), sample columns
+// [c0, c0+DC) of the launch; part >= 0 selects a partial-sum slot.
+struct KsumItem {
+  int inst;
+  int rows;
+  int64_t row0;
+  int64_t j0, j1;
+  int c0;
+  int part;
+};
+
+// Plan for one ksum launch (host side): items and the partial reduction.
+struct KsumPlan {
+  std::vector<KsumItem> items;
+  int64_t n_parts = 0;      // partial slots (each tile_rows x dc values)
+  int tile_rows = 0;
+  int dc = 0;
+  // reduction: for each output tile (inst, row0, rows, c0) the first slot and count
+  struct Red {
+    int inst, rows;
+    int64_t row0;
+    int c0;
+    int64_t slot0;
+    int nslots;
+  };
+  std::vector<Red> reds;
+};
+
+struct KsumArgs64 {
+  Points64 pts;
+  const double *om;  // panel, ld = ld
+  double *y;         // panel, ld = ld
+  int64_t ld;
+  const InstDev *inst;
+  const KsumItem *items;
+  double *partial;
+};
+struct KsumArgs32 {
+  Points32 pts;
+  const float *om;
+  float *y;
+  int64_t ld;
+  const InstDev *inst;
+  const KsumItem *items;
+  float *partial;
+};
+
+// Plans a launch covering, for every listed instance, all its rows and
+// columns [c0[i], c0[i]+ncols).  `insts` are instance indices.
+KsumPlan plan_ksum(const std::vector<int64_t> &inst_n, const std::vector<int64_t> &inst_base,
+                   const std::vector<int> &insts, const std::vector<int> &c0, int ncols,
+                   bool fp64, int tile_rows_hint, int sm_count);
+
+// Runs a plan (items/partials staged in `scratch`-owned buffers).  Returns the
+// number of kernel launches.  `work` must hold plan.n_parts*tile_rows*dc
+// values; items/reds are copied to device-side staging inside.
+void run_ksum64(int kid, const KsumPlan &plan, const KsumArgs64 &a, cudaStream_t s);
+void run_ksum32(int kid, const KsumPlan &plan, const KsumArgs32 &a, cudaStream_t s);
+
+// Gaussian sample columns for rows in tree order: om[pos + c*ld] for
+// c in [c0, c1), drawn from Philox4x32-10 keyed by (seed) at counter
+// (original index of pos, column).  T = double or float.
+void philox_gaussian64(double *om, int64_t ld, const int32_t *orig_of_pos, int64_t n, int c0,
+                       int c1, uint64_t seed, cudaStream_t s);
+// Stored Omega (original order, ld_src) gathered into tree order.
+void gather_rows64(const double *src, int64_t ld_src, const int32_t *orig_of_pos, int64_t n,
+                   int c0, int c1, double *dst, int64_t ld_dst, cudaStream_t s);
+void convert_cols_to32(const double *src, int64_t ld, int64_t row0, int64_t n, int c0, int c1,
+                       float *dst, cudaStream_t s);
+
+// Dense GEMM Y[:, c] = A Om[:, c] (FP64), all column-major.
+void dense_gemm64(const double *a, int64_t lda, int64_t n, const double *om, int64_t ldo,
+                  double *y, int64_t ldy, int d, cudaStream_t s);
+// Entries K(rows, cols) into out (nr x nc, ld nr).
+void entry_block64(int kid, const KernelDesc &kd, Points64 pts, const int32_t *rows, int64_t nr,
+                   const int32_t *cols, int64_t nc, double *out, cudaStream_t s);
+
+// Split FP64 coordinates into FP32 hi/lo parts.
+void split_coords32(const double *x, const double *y, const double *z, int64_t n, float *xh,
+                    float *yh, float *zh, float *xl, float *yl, float *zl, cudaStream_t s);
+
+// Row-major n x dim points -> SoA (zero padding to 3 coordinates).
+void split_points_soa(const double *pts, int64_t n, int dim, double *x, double *y, double *z,
+                      cudaStream_t s);
+void convert_to64(const float *src, int64_t n, double *dst, cudaStream_t s);
+
+// sum of squares of panel columns [0, d) per instance rows (FP64 result).
+void instance_sumsq(const void *panel, bool fp64, int64_t ld, const int64_t *inst_base,
+                    const int64_t *inst_n, int count, int d, double *out, cudaStream_t s);
+
+}  // namespace h2

@@ -1,0 +1,302 @@
+"""CUDA path vs the CPU oracle, through the C ABI.
+
+Bars: cluster tree, boxes and block lists bit-exact; FP64 construction with
+the same ranks and skeletons as the oracle and a matvec that agrees to 1e-10
+relative; mixed precision within 1e-5 of the oracle's matvec; approximation
+error within 10*tol in both modes.
+"""
+import ctypes
+import functools
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import h2_oracle as O
+from paper_2506_16759_gb300 import api
+from paper_2506_16759_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+def gpu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+# ------------------------------------------------------------------ tree
+
+
+def _tree_cases():
+    return [
+        ("uniform2d", W.uniform_points(4096, 2, 1), 64, 0.7),
+        ("ragged3d", W.uniform_points(1000, 3, 2), 16, 0.7),
+        ("tiny", W.uniform_points(5, 2, 3), 2, 0.7),
+        ("single", W.uniform_points(1, 3, 4), 4, 0.7),
+        ("line1d", W.uniform_points(777, 1, 5), 8, 1.0),
+        ("duplicates", np.full((100, 3), 0.25), 8, 0.7),
+        ("grid_ties", W.grid_points(12, 3), 16, 0.7),
+        ("eta_large", W.uniform_points(2000, 2, 6), 32, 3.0),
+        ("eta_zero", W.uniform_points(500, 2, 7), 16, 0.0),
+    ]
+
+
+def _compare_tree(X, leaf, eta):
+    tg = api.ClusterTree(gpu(X), leaf, eta)
+    to = O.build_cluster_tree(X, leaf)
+    lo = O.dual_traversal(to, eta)
+    ex = tg.export()
+    assert tg.info.depth == to.depth
+    assert np.array_equal(ex["perm"], to.perm)
+    assert np.array_equal(ex["begin"], to.begin) and np.array_equal(ex["end"], to.end)
+    assert np.array_equal(ex["lo"], to.lo) and np.array_equal(ex["hi"], to.hi)
+    for k in range(to.depth + 1):
+        assert tg.block_list("far", k) == lo.far[k], f"far list differs at depth {k}"
+    assert tg.block_list("near", to.depth) == lo.near
+    assert tg.info.l_top == O.top_level(to, lo)
+    return tg, to, lo
+
+
+@pytest.mark.parametrize("case", _tree_cases(), ids=lambda c: c[0])
+def test_tree_bit_exact(case):
+    _, X, leaf, eta = case
+    _compare_tree(X, leaf, eta)
+
+
+@pytest.mark.parametrize("name", ["c2", "c3", "c4"])
+def test_tree_bit_exact_full_size(name):
+    w = W.config(name)
+    _compare_tree(w.points(), w.leaf_size, w.eta)
+
+
+# ------------------------------------------------------------------ primitives
+
+
+KCASES = [(W.K_EXP, (0.2, 1e-4), 2), (W.K_MATERN32, (0.1, 1e-4), 3), (W.K_GAUSS, (0.05, 1e-3), 3),
+          (W.K_LAPLACE_IE, (0.3799 / 48 / 48,), 3), (W.K_POLY, (1.0, 3), 2)]
+
+
+@pytest.mark.parametrize("kernel,params,dim", KCASES)
+def test_entry_block(kernel, params, dim):
+    X = W.uniform_points(700, dim, 3)
+    rng = np.random.default_rng(0)
+    rows = rng.integers(0, 700, 37)
+    cols = np.concatenate([rng.integers(0, 700, 50), rows[:5]])
+    got = api.entry_block(gpu(X), kernel, params, gpu(rows), gpu(cols)).cpu().numpy()
+    want = O.kernel_block(kernel, params, X[rows], X[cols], rows, cols)
+    assert np.allclose(got, want, rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("kernel,params,dim", KCASES)
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed", 2e-5)])
+def test_ksum_sketch(kernel, params, dim, prec, tol):
+    n = 3001  # ragged against every tile size
+    X = W.uniform_points(n, dim, 4)
+    om = W.gaussian_omega(n, 48, 5)
+    got = api.ksum_sketch(gpu(X), kernel, params, gpu(om), prec=prec).cpu().numpy()
+    want = O.ksum_rows(X, kernel, params, om, np.arange(n))
+    err = np.linalg.norm(got - want, axis=0) / np.linalg.norm(want, axis=0)
+    assert err.max() <= tol
+
+
+def test_ksum_sketch_full_size_sampled():
+    w = W.config("c2")
+    X = w.points()
+    om = w.omega(32)
+    rows = np.random.default_rng(1).integers(0, w.n, 48)
+    want = O.ksum_rows(X, w.kernel, w.params, om, rows)
+    for prec, tol in (("fp64", 1e-12), ("mixed", 1e-5)):
+        got = api.ksum_sketch(gpu(X), w.kernel, w.params, gpu(om), prec=prec).cpu().numpy()[rows]
+        assert np.linalg.norm(got - want) / np.linalg.norm(want) <= tol
+
+
+def test_dense_sketch():
+    n = 1000
+    X = W.uniform_points(n, 2, 6)
+    A = O.dense_matrix(X, W.K_EXP, (0.2, 1e-4))
+    om = W.gaussian_omega(n, 40, 7)
+    got = api.dense_sketch(gpu(A), gpu(om)).cpu().numpy()
+    assert np.allclose(got, A @ om, rtol=1e-12, atol=1e-12)
+
+
+def test_batched_qr_mindiag():
+    rng = np.random.default_rng(8)
+    panels = [rng.standard_normal((m, d)) @ np.diag(rng.uniform(1e-6, 2, d))
+              for m, d in [(64, 32), (100, 48), (33, 32), (8, 16), (300, 96), (129, 1)]]
+    got = api.batched_qr_mindiag([gpu(p) for p in panels]).cpu().numpy()
+    for g, p in zip(got, panels):
+        if p.shape[0] <= p.shape[1]:
+            assert g == 0.0
+        else:
+            assert g == pytest.approx(O.qr_min_abs_diag(p), rel=1e-11)
+
+
+def test_batched_row_id():
+    rng = np.random.default_rng(9)
+    panels, eps = [], []
+    for m, d, k in [(64, 32, 12), (90, 64, 40), (20, 48, 20), (64, 16, 16), (7, 32, 3)]:
+        Y = rng.standard_normal((m, k)) @ rng.standard_normal((k, d))
+        Y += 1e-9 * rng.standard_normal((m, d))
+        panels.append(Y)
+        eps.append(1e-6 * np.linalg.norm(Y) / np.sqrt(d))
+    ks, Js, Es = api.batched_row_id([gpu(p) for p in panels], eps)
+    for Y, e, k, J, E in zip(panels, eps, ks, Js, Es):
+        rid = O.row_id(Y, e)
+        assert k == rid.k
+        assert np.array_equal(J, rid.J)
+        assert np.allclose(E, rid.U, rtol=1e-9, atol=1e-10)
+
+
+# ------------------------------------------------------------------ construction
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_build(n, dim, kernel, params, tol, leaf, eta, seed, d0=32, d_inc=16, d_max=256):
+    X = W.uniform_points(n, dim, seed)
+    om = W.gaussian_omega(n, d_max, seed + 1)
+    t = O.build_cluster_tree(X, leaf)
+    lists = O.dual_traversal(t, eta)
+    h = O.build_h2(t, lists, kernel, params, tol, om, O.ksum_sampler(X, kernel, params, 1024),
+                   d0, d_inc, d_max)
+    return X, om, t, lists, h
+
+
+def gpu_build(X, om, kernel, params, tol, leaf, eta, prec="fp64", sketch="ksum", **kw):
+    tree = api.ClusterTree(gpu(X), leaf, eta)
+    extra = {}
+    if sketch == "dense":
+        extra["dense_a"] = gpu(O.dense_matrix(X, kernel, params))
+    h = api.H2Matrix.build(tree, kernel, params, tol, omega=gpu(om), sketch=sketch, prec=prec,
+                           **extra, **kw)
+    return tree, h
+
+
+def check_same_skeletons(h, t, ho):
+    for level in range(1, ho.l_top + 1):
+        ranks, skel, eps, d = h.export_level(level)
+        nodes = list(t.nodes_at_depth(t.level_depth(level)))
+        assert ranks.tolist() == [ho.nodes[v].k for v in nodes], f"ranks differ at level {level}"
+        want = np.concatenate([t.perm[ho.nodes[v].Itil] for v in nodes]) if nodes else []
+        assert np.array_equal(skel, want), f"skeletons differ at level {level}"
+        assert d == ho.d_level[level]
+        assert eps == pytest.approx(ho.eps_level[level], rel=1e-12)
+
+
+def matvec_rel(h, ho, n, ncols=4, seed=0):
+    G = W.gaussian_probe(n, ncols, seed)
+    y = h.matvec(gpu(G)).cpu().numpy()
+    yo = O.h2_matvec(ho, G)
+    return np.linalg.norm(y - yo) / np.linalg.norm(yo), y, G
+
+
+BUILD_CASES = [
+    # n, dim, kernel, params, tol, leaf, eta, seed
+    (4096, 2, W.K_EXP, (0.2, 1e-4), 1e-6, 64, 0.7, 1),        # C1
+    (4096, 2, W.K_EXP, (0.2, 1e-4), 1e-9, 64, 0.7, 11),       # adaptive rounds
+    (3000, 3, W.K_MATERN32, (0.1, 1e-4), 1e-6, 32, 0.7, 12),  # ragged 3D
+    (2048, 3, W.K_LAPLACE_IE, (0.3799 / 48 / 48,), 1e-5, 32, 0.7, 13),
+    (2048, 2, W.K_POLY, (1.0, 3), 1e-10, 32, 0.7, 14),       # exact rank 10
+    (1500, 2, W.K_GAUSS, (0.05, 1e-4), 1e-6, 16, 1.0, 15),
+]
+
+
+@pytest.mark.parametrize("case", BUILD_CASES, ids=lambda c: f"n{c[0]}d{c[1]}k{c[2]}t{c[4]:g}")
+def test_build_fp64_matches_oracle(case):
+    n, dim, kernel, params, tol, leaf, eta, seed = case
+    X, om, t, lists, ho = oracle_build(n, dim, kernel, params, tol, leaf, eta, seed)
+    tree, h = gpu_build(X, om, kernel, params, tol, leaf, eta)
+    assert h.converged == ho.converged
+    check_same_skeletons(h, t, ho)
+    rel, y, G = matvec_rel(h, ho, n)
+    assert rel <= 1e-10
+    # approximation error against the exact matrix
+    AG = O.ksum_rows(X, kernel, params, G, np.arange(n))
+    err = np.linalg.norm(y - AG) / np.linalg.norm(AG)
+    assert err <= 10 * max(tol, 1e-12)
+
+
+def test_build_c1_dense_sketch():
+    w = W.config("c1")
+    X, om, t, lists, ho = oracle_build(w.n, w.dim, w.kernel, w.params, w.tol, w.leaf_size, w.eta,
+                                       1)
+    # the oracle run above used the kernel-sum sampler; the dense one gives the
+    # same sketch up to rounding, so ranks and skeletons must still agree
+    tree, h = gpu_build(X, om, w.kernel, w.params, w.tol, w.leaf_size, w.eta, sketch="dense")
+    check_same_skeletons(h, t, ho)
+    rel, _, _ = matvec_rel(h, ho, w.n)
+    assert rel <= 1e-10
+
+
+@pytest.mark.parametrize("case", BUILD_CASES[:4], ids=lambda c: f"n{c[0]}d{c[1]}k{c[2]}")
+def test_build_mixed_within_tolerance(case):
+    n, dim, kernel, params, tol, leaf, eta, seed = case
+    X, om, t, lists, ho = oracle_build(n, dim, kernel, params, tol, leaf, eta, seed)
+    tree, h = gpu_build(X, om, kernel, params, tol, leaf, eta, prec="mixed")
+    rel, y, G = matvec_rel(h, ho, n)
+    assert rel <= max(1e-5, 10 * tol)
+    AG = O.ksum_rows(X, kernel, params, G, np.arange(n))
+    err = np.linalg.norm(y - AG) / np.linalg.norm(AG)
+    assert err <= 10 * max(tol, 1e-6)
+
+
+def test_budget_exhausted_reports_not_converged():
+    X, om, t, lists, ho = oracle_build(4096, 2, W.K_EXP, (0.2, 1e-4), 1e-9, 64, 0.7, 11,
+                                       32, 16, 32)
+    tree, h = gpu_build(X, om, W.K_EXP, (0.2, 1e-4), 1e-9, 64, 0.7, d_max=32)
+    assert not ho.converged and not h.converged
+    rel, _, _ = matvec_rel(h, ho, 4096)
+    assert rel <= 1e-10
+
+
+def test_nothing_admissible_is_exact():
+    X = W.uniform_points(700, 3, 21)
+    A = O.dense_matrix(X, W.K_MATERN32, (0.1, 1e-4))
+    tree, h = gpu_build(X, W.gaussian_omega(700, 256, 22), W.K_MATERN32, (0.1, 1e-4), 1e-6, 16,
+                        0.0)
+    G = W.gaussian_probe(700, 3, 0)
+    y = h.matvec(gpu(G)).cpu().numpy()
+    assert np.linalg.norm(y - A @ G) <= 1e-13 * np.linalg.norm(A @ G)
+
+
+def test_callback_sampler_matches_dense():
+    w = W.config("c1")
+    X, om = W.uniform_points(2048, 2, 31), W.gaussian_omega(2048, 256, 32)
+    A = gpu(O.dense_matrix(X, w.kernel, w.params))
+    from paper_2506_16759_gb300 import _lib
+    calls = []
+
+    def sampler(ctx, omega_p, y_p, n, d, ld, stream):
+        calls.append(d)
+        return _lib.lib().h2_dense_sketch(A.data_ptr(), n, n, ctypes.cast(omega_p, ctypes.c_void_p),
+                                          ld, ctypes.cast(y_p, ctypes.c_void_p), ld, d, stream)
+
+    tree = api.ClusterTree(gpu(X), 32, 0.7)
+    h1 = api.H2Matrix.build(tree, w.kernel, w.params, 1e-8, omega=gpu(om), sketch="callback",
+                            sampler=sampler)
+    h2 = api.H2Matrix.build(tree, w.kernel, w.params, 1e-8, omega=gpu(om), sketch="dense",
+                            dense_a=A)
+    assert calls and calls[0] == 32
+    G = gpu(W.gaussian_probe(2048, 2, 0))
+    assert torch.equal(h1.matvec(G), h2.matvec(G))
+
+
+def test_batched_instances_match_single_builds():
+    insts = [(1500, 2, 0.1, 41), (3000, 3, 0.2, 42), (800, 2, 0.3, 43)]
+    trees, params, oms, builds = [], [], [], []
+    for n, dim, ell, seed in insts:
+        X = W.uniform_points(n, dim, seed)
+        om = W.gaussian_omega(n, 256, seed + 100)
+        trees.append(api.ClusterTree(gpu(X), 32, 0.7))
+        params.append((ell, 1e-4))
+        oms.append(om)
+        builds.append(api.H2Matrix.build(trees[-1], W.K_EXP, (ell, 1e-4), 1e-6, omega=gpu(om)))
+    om_all = np.concatenate(oms, axis=0)
+    hb = api.H2Matrix.build_batched(trees, [W.K_EXP] * 3, params, [1e-6] * 3, omega=gpu(om_all))
+    ntot = sum(n for n, *_ in insts)
+    G = W.gaussian_probe(ntot, 3, 1)
+    yb = hb.matvec(gpu(G)).cpu().numpy()
+    off = 0
+    for (n, *_), h in zip(insts, builds):
+        ys = h.matvec(gpu(G[off:off + n])).cpu().numpy()
+        assert np.linalg.norm(yb[off:off + n] - ys) <= 1e-12 * np.linalg.norm(ys)
+        off += n
