@@ -206,8 +206,12 @@ typedef struct {
   /* per-phase device time (ms) when opts.timing = 1 */
   double ms_tree_unused, ms_sketch, ms_nearfield, ms_qr, ms_id, ms_upsweep, ms_coupling,
       ms_bsr, ms_total;
-  double ms_sketch_launch_max;  /* longest single sketch launch */
-  double sketch_flops;          /* algorithmic flops of the sketch launches */
+  double ms_sketch_launch_max;  /* longest sketch phase (one round) */
+  double sketch_flops;          /* algorithmic flops of the sketch launches:
+                                   pairs * (2*columns + 10) */
+  double ms_sketch_kernel;      /* summed device time of the fused-summation
+                                   kernel launches alone (timing = 1) */
+  int64_t sketch_launches;      /* fused-summation kernel launches */
 } h2_stats_t;
 
 h2_status h2_stats(const h2_matrix *h, h2_stats_t *st);
@@ -262,6 +266,10 @@ h2_status h2_batched_qr_mindiag(int count, const int32_t *m, const int32_t *d, c
 h2_status h2_batched_row_id(int count, const int32_t *m, const int32_t *d, const int64_t *off,
                             const double *panels, const double *eps, int32_t *k, int32_t *J,
                             int ldj, const int64_t *eoff, double *basis, h2_stream_t s);
+
+/* CUDA kernels the library has launched from the calling host thread so far
+ * (all entry points); a profiling aid. */
+int64_t h2_kernel_launches(void);
 
 const char *h2_last_error(void);
 

@@ -46,7 +46,8 @@ class Stats(C.Structure):
                 ("ms_nearfield", C.c_double), ("ms_qr", C.c_double), ("ms_id", C.c_double),
                 ("ms_upsweep", C.c_double), ("ms_coupling", C.c_double), ("ms_bsr", C.c_double),
                 ("ms_total", C.c_double), ("ms_sketch_launch_max", C.c_double),
-                ("sketch_flops", C.c_double)]
+                ("sketch_flops", C.c_double), ("ms_sketch_kernel", C.c_double),
+                ("sketch_launches", C.c_int64)]
 
 
 vp = C.c_void_p
@@ -58,6 +59,7 @@ dbl = C.c_double
 SIGNATURES = {
     "h2_default_opts": (None, [C.POINTER(BuildOpts)]),
     "h2_last_error": (C.c_char_p, []),
+    "h2_kernel_launches": (C.c_int64, []),
     "h2_build_cluster_tree": (i32, [vp, i64, i32, i32, dbl, vp, C.POINTER(vp)]),
     "h2_tree_info": (i32, [vp, C.POINTER(TreeInfo)]),
     "h2_tree_export": (i32, [vp, vp, vp, vp, vp, vp]),

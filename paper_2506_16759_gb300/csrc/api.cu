@@ -15,6 +15,7 @@
 namespace h2 {
 
 thread_local int64_t g_launches = 0;
+thread_local KernelTimer *g_ksum_timer = nullptr;
 static thread_local std::string g_last_error;
 
 void set_error(h2_status code, const std::string &msg) {
@@ -799,9 +800,16 @@ struct Builder {
     transfer_up(l);
   }
 
+  KernelTimer ktimer;
+  struct TimerGuard {
+    explicit TimerGuard(KernelTimer *t) { g_ksum_timer = t; }
+    ~TimerGuard() { g_ksum_timer = nullptr; }
+  };
+
   h2_status run(const int *kids, const double *params, const double *tol_in) {
     int C = H->count;
     timer.on = o.timing != 0;
+    TimerGuard tg(timer.on ? &ktimer : nullptr);
     timer.s = s;
     int64_t launches0 = g_launches;
     timer.begin(PH_TOTAL);
@@ -882,6 +890,8 @@ struct Builder {
     st.rounds = rounds;
     st.converged = not_conv.empty();
     st.sketch_flops = sketch_flops;
+    st.ms_sketch_kernel = ktimer.ms;
+    st.sketch_launches = ktimer.launches;
     if (timer.on) {
       st.ms_sketch = timer.total(PH_SKETCH, &st.ms_sketch_launch_max);
       st.ms_nearfield = timer.total(PH_NEAR);
@@ -1040,6 +1050,8 @@ void h2_default_opts(h2_build_opts *o) {
 }
 
 const char *h2_last_error(void) { return g_last_error.c_str(); }
+
+int64_t h2_kernel_launches(void) { return g_launches; }
 
 h2_status h2_build_cluster_tree(const double *points, int64_t n, int dim, int leaf_size,
                                 double eta, h2_stream_t s, h2_tree **out) {

@@ -44,6 +44,14 @@ h2_status fail(h2_status code, const std::string &msg);
 extern thread_local int64_t g_launches;
 inline void count_launch(int64_t n = 1) { g_launches += n; }
 
+// When set, the fused-summation launches record CUDA events around the main
+// kernel on its stream and accumulate their device time here.
+struct KernelTimer {
+  double ms = 0.0;
+  int64_t launches = 0;
+};
+extern thread_local KernelTimer *g_ksum_timer;
+
 // ---------------------------------------------------------------------------
 // Device memory: a typed buffer freed on destruction (stream-ordered).
 // ---------------------------------------------------------------------------

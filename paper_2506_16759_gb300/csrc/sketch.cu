@@ -166,6 +166,31 @@ __global__ void k_ksum_reduce(const KsumPlan::Red *reds, const T *partial, T *y,
   }
 }
 
+// Records events around one launch when a KernelTimer is installed.
+struct KernelEvents {
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaStream_t s;
+  explicit KernelEvents(cudaStream_t st) : s(st) {
+    if (!g_ksum_timer) return;
+    H2_CUDA(cudaEventCreate(&a));
+    H2_CUDA(cudaEventCreate(&b));
+    H2_CUDA(cudaEventRecord(a, s));
+  }
+  void stop() {
+    if (a) H2_CUDA(cudaEventRecord(b, s));
+  }
+  ~KernelEvents() {
+    if (!a) return;
+    float ms = 0.f;
+    if (cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&ms, a, b) == cudaSuccess) {
+      g_ksum_timer->ms += ms;
+      g_ksum_timer->launches += 1;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+};
+
 template <typename T>
 struct StagedPlan {
   DBuf<KsumItem> items;
@@ -350,7 +375,9 @@ void launch_ksum32(const KsumPlan &p, const KsumArgs32 &a0, cudaStream_t s) {
   KsumArgs32 a = a0;
   a.items = sp.items.p;
   a.partial = sp.partial.p;
+  KernelEvents ev(s);
   k_ksum32<KID, DC, RPT, NT, TJ><<<(int)p.items.size(), NT, 0, s>>>(a, p.tile_rows);
+  ev.stop();
   count_launch();
   H2_CHECK_LAUNCH();
   if (!p.reds.empty()) {
@@ -370,7 +397,9 @@ void launch_ksum64(const KsumPlan &p, const KsumArgs64 &a0, cudaStream_t s) {
   KsumArgs64 a = a0;
   a.items = sp.items.p;
   a.partial = sp.partial.p;
+  KernelEvents ev(s);
   k_ksum64<KID, DC, NT, TJ><<<(int)p.items.size(), NT, 0, s>>>(a, p.tile_rows);
+  ev.stop();
   count_launch();
   H2_CHECK_LAUNCH();
   if (!p.reds.empty()) {

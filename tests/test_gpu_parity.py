@@ -171,13 +171,14 @@ def gpu_build(X, om, kernel, params, tol, leaf, eta, prec="fp64", sketch="ksum",
     return tree, h
 
 
-def check_same_skeletons(h, t, ho):
+def check_same_skeletons(h, t, ho, unique=True):
     for level in range(1, ho.l_top + 1):
         ranks, skel, eps, d = h.export_level(level)
         nodes = list(t.nodes_at_depth(t.level_depth(level)))
         assert ranks.tolist() == [ho.nodes[v].k for v in nodes], f"ranks differ at level {level}"
         want = np.concatenate([t.perm[ho.nodes[v].Itil] for v in nodes]) if nodes else []
-        assert np.array_equal(skel, want), f"skeletons differ at level {level}"
+        if unique:
+            assert np.array_equal(skel, want), f"skeletons differ at level {level}"
         assert d == ho.d_level[level]
         assert eps == pytest.approx(ho.eps_level[level], rel=1e-12)
 
@@ -206,7 +207,9 @@ def test_build_fp64_matches_oracle(case):
     X, om, t, lists, ho = oracle_build(n, dim, kernel, params, tol, leaf, eta, seed)
     tree, h = gpu_build(X, om, kernel, params, tol, leaf, eta)
     assert h.converged == ho.converged
-    check_same_skeletons(h, t, ho)
+    # an exactly low-rank kernel leaves pivots tied once its rank is used up:
+    # only the ranks are unique there, and any skeleton set is exact
+    check_same_skeletons(h, t, ho, unique=kernel != W.K_POLY)
     rel, y, G = matvec_rel(h, ho, n)
     assert rel <= 1e-10
     # approximation error against the exact matrix
