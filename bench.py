@@ -369,6 +369,34 @@ def main_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def main_kernel_only(args):
+    """Only the fused sketch of the benchmark workload (N=131072, 32 columns,
+    same launch plan as inside a build): a small process for ncu captures."""
+    import torch
+
+    from paper_2506_16759_gb300 import api
+    from paper_2506_16759_gb300 import workloads as W
+    dev = torch.device("cuda:0")
+    w = W.config("c2")
+    X = torch.from_numpy(w.points()).to(dev)
+    om = torch.from_numpy(w.omega(32)).to(dev)
+    times = []
+    for k in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        api.ksum_sketch(X, w.kernel, w.params, om, prec=args.prec)
+        e1.record()
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            times.append(e0.elapsed_time(e1))
+    flops = float(w.n) * w.n * (2 * 32 + 10)
+    ms = statistics.mean(times)
+    print(json.dumps({"kernel_only": "ksum", "prec": args.prec, "n": w.n, "columns": 32,
+                      "ms": ms, "tflops": flops / (ms * 1e-3) / 1e12}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -381,7 +409,12 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--kernel-only", default="", choices=["", "ksum"],
+                    help="time only the fused sketch of the workload (for profiling)")
     args = ap.parse_args()
+    if args.kernel_only:
+        main_kernel_only(args)
+        return
     if args.oracle_sample:
         print(json.dumps(oracle_sample(args.oracle_sample)))
         return

@@ -89,8 +89,7 @@ struct LevelData {
   DBuf<int64_t> row, krow, eoff;
   int64_t M = 0, K = 0;
   int max_m = 0, max_k = 0;
-  DBuf<double> E;
-  DBuf<float> E32;
+  DBuf<double> E;   // bases, FP64 in both precision modes
   int64_t E_size = 0;
   DBuf<int64_t> far_ptr, boff;
   DBuf<int32_t> far_idx, far_erow;
@@ -239,7 +238,7 @@ struct Builder {
   bool fp64() const { return H->fp64; }
   void *Yp(LevelData &L) { return fp64() ? (void *)L.Y64.p : (void *)L.Y32.p; }
   void *Omp(LevelData &L) { return fp64() ? (void *)L.Om64.p : (void *)L.Om32.p; }
-  void *Ep(LevelData &L) { return fp64() ? (void *)L.E.p : (void *)L.E32.p; }
+  void *Ep(LevelData &L) { return (void *)L.E.p; }
   void *Bp(LevelData &L) { return fp64() ? (void *)L.B64.p : (void *)L.B32.p; }
   void *Dp() { return fp64() ? (void *)H->D64.p : (void *)H->D32.p; }
 
@@ -699,10 +698,6 @@ struct Builder {
     L.J.alloc(std::max<int64_t>(L.K, 1));
     L.skel.alloc(std::max<int64_t>(L.K, 1));
     compact_skeletons(L.dev(), L.Jtmp.p, L.skeltmp.p, L.J.p, L.skel.p, s);
-    if (!fp64()) {
-      L.E32.alloc(std::max<int64_t>(L.E_size, 1));
-      convert32(L.E.p, L.E_size, L.E32.p, s);
-    }
     // couplings B = K(Itil_s, Itil_t) for the far list of this level
     build_far_list(l);
     if (L.far_nnz > 0) {
@@ -987,7 +982,7 @@ void matvec_impl(const h2_matrix *H, const double *x, double *y, int nrhs, cudaS
     // upsweep
     for (int l = 1; l <= levels; ++l) {
       const LevelData &L = H->lv[l];
-      const void *E = f64 ? (const void *)L.E.p : (const void *)L.E32.p;
+      const void *E = (const void *)L.E.p;
       if (l == 1) basis_t_apply(f64, L.dev(), E, xt.p, N, xh[1].p, L.K, cols, L.active.p, s);
       else
         basis_t_apply(f64, L.dev(), E, xh[l - 1].p, H->lv[l - 1].K, xh[l].p, L.K, cols,
@@ -1019,7 +1014,7 @@ void matvec_impl(const h2_matrix *H, const double *x, double *y, int nrhs, cudaS
     // downsweep
     for (int l = levels; l >= 1; --l) {
       const LevelData &L = H->lv[l];
-      const void *E = f64 ? (const void *)L.E.p : (const void *)L.E32.p;
+      const void *E = (const void *)L.E.p;
       if (l > 1)
         basis_n_apply(f64, L.dev(), E, yh[l].p, L.K, yh[l - 1].p, H->lv[l - 1].K, cols, s);
       else

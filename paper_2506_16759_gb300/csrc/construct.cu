@@ -72,6 +72,26 @@ __device__ int block_argmax(double v, int idx, double *shv, int *shi) {
   return r;
 }
 
+// Running sum of per-chunk partial sums: FP64 adds directly, FP32 with
+// Kahan compensation (the chunk sums are short, the running sum is long).
+template <typename T>
+struct Acc {
+  T s = T(0);
+  __device__ void add(T v) { s += v; }
+  __device__ T value() const { return s; }
+};
+template <>
+struct Acc<float> {
+  float s = 0.f, c = 0.f;
+  __device__ void add(float v) {
+    float y = v - c;
+    float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ float value() const { return s; }
+};
+
 template <typename T>
 struct PtsOf;
 template <>
@@ -126,11 +146,7 @@ __global__ void __launch_bounds__(kNT) k_nearfield(NearArgs a, int mmax) {
   T *D = reinterpret_cast<T *>(a.D);
   for (int i = threadIdx.x; i < m; i += kNT) PtsOf<T>::load(a.p64, a.p32, rowt + i, sxa + i * NC);
   const int ri = threadIdx.x % 64, cg = threadIdx.x / 64;
-  T acc[4][DG];
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-#pragma unroll
-    for (int c = 0; c < DG; ++c) acc[q][c] = T(0);
+  Acc<T> acc[4][DG];
   __syncthreads();
   for (int64_t e = a.ptr[tau]; e < a.ptr[tau + 1]; ++e) {
     int b = a.idx[e];
@@ -155,19 +171,20 @@ __global__ void __launch_bounds__(kNT) k_nearfield(NearArgs a, int mmax) {
         Dblk[i + (int64_t)(jc + j) * m] = v;
       }
       __syncthreads();
-      for (int j = 0; j < nj; ++j) {
-        T ov[DG];
 #pragma unroll
-        for (int c = 0; c < DG; ++c) ov[c] = sO[j * DC + cg * DG + c];
+      for (int q = 0; q < 4; ++q) {
+        int i = ri + 64 * q;
+        if (i >= m) continue;
+        T part[DG];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          int i = ri + 64 * q;
-          if (i < m) {
-            T dv = sD[j * mmax + i];
+        for (int c = 0; c < DG; ++c) part[c] = T(0);
+        for (int j = 0; j < nj; ++j) {
+          T dv = sD[j * mmax + i];
 #pragma unroll
-            for (int c = 0; c < DG; ++c) acc[q][c] += dv * ov[c];
-          }
+          for (int c = 0; c < DG; ++c) part[c] += dv * sO[j * DC + cg * DG + c];
         }
+#pragma unroll
+        for (int c = 0; c < DG; ++c) acc[q][c].add(part[c]);
       }
       __syncthreads();
     }
@@ -181,7 +198,9 @@ __global__ void __launch_bounds__(kNT) k_nearfield(NearArgs a, int mmax) {
       int col = cg * DG + c;
       if (col < ncol) {
         T *yp = Y + rowt + i + (int64_t)(cb + col) * a.ld;
-        *yp = *yp - acc[q][c];
+        Acc<T> r = acc[q][c];
+        r.add(-*yp);
+        *yp = -r.value();
       }
     }
   }
@@ -209,11 +228,7 @@ __global__ void __launch_bounds__(kNT) k_bsr(BsrArgs a, int mmax) {
   const int ri = threadIdx.x % 64, cg = threadIdx.x / 64;
   for (int c0 = cb; c0 < ce; c0 += DC) {
     int ncol = min(DC, ce - c0);
-    T acc[4][DG];
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int c = 0; c < DG; ++c) acc[q][c] = T(0);
+    Acc<T> acc[4][DG];
     for (int64_t e = a.ptr[tau]; e < a.ptr[tau + 1]; ++e) {
       int b = a.idx[e];
       int mb = a.col_m[b];
@@ -231,19 +246,20 @@ __global__ void __launch_bounds__(kNT) k_bsr(BsrArgs a, int mmax) {
                                                 : T(0);
         }
         __syncthreads();
-        for (int j = 0; j < nj; ++j) {
-          T ov[DG];
 #pragma unroll
-          for (int c = 0; c < DG; ++c) ov[c] = sI[j * DC + cg * DG + c];
+        for (int q = 0; q < 4; ++q) {
+          int i = ri + 64 * q;
+          if (i >= m) continue;
+          T part[DG];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            int i = ri + 64 * q;
-            if (i < m) {
-              T bv = sB[j * mmax + i];
+          for (int c = 0; c < DG; ++c) part[c] = T(0);
+          for (int j = 0; j < nj; ++j) {
+            T bv = sB[j * mmax + i];
 #pragma unroll
-              for (int c = 0; c < DG; ++c) acc[q][c] += bv * ov[c];
-            }
+            for (int c = 0; c < DG; ++c) part[c] += bv * sI[j * DC + cg * DG + c];
           }
+#pragma unroll
+          for (int c = 0; c < DG; ++c) acc[q][c].add(sign * part[c]);
         }
         __syncthreads();
       }
@@ -257,7 +273,9 @@ __global__ void __launch_bounds__(kNT) k_bsr(BsrArgs a, int mmax) {
         int col = cg * DG + c;
         if (col < ncol) {
           T *op = out + orow + i + (int64_t)(c0 + col) * a.ld_out;
-          *op = *op + sign * acc[q][c];
+          Acc<T> r = acc[q][c];
+          r.add(*op);
+          *op = r.value();
         }
       }
     }
@@ -490,9 +508,9 @@ __global__ void k_basis_t(TasksDev t, const TE *E, const T *in, int64_t ld_in, T
     int a = (int)(q % k), c = cb + (int)(q / k);
     const TE *ea = Et + (int64_t)a * m;
     const T *xc = in + row + c * ld_in;
-    T s = T(0);
-    for (int i = 0; i < m; ++i) s += (T)ea[i] * xc[i];
-    out[kr + a + c * ld_out] = s;
+    double s = 0.0;
+    for (int i = 0; i < m; ++i) s += (double)ea[i] * (double)xc[i];
+    out[kr + a + c * ld_out] = (T)s;
   }
 }
 
@@ -510,9 +528,9 @@ __global__ void k_basis_n(TasksDev t, const TE *E, const T *in, int64_t ld_in, T
   for (int64_t q = threadIdx.x; q < (int64_t)m * (ce - cb); q += blockDim.x) {
     int i = (int)(q % m), c = cb + (int)(q / m);
     const T *yc = in + kr + c * ld_in;
-    T s = T(0);
-    for (int aa = 0; aa < k; ++aa) s += (T)Et[i + (int64_t)aa * m] * yc[aa];
-    out[row + i + c * ld_out] += s;
+    double s = 0.0;
+    for (int aa = 0; aa < k; ++aa) s += (double)Et[i + (int64_t)aa * m] * (double)yc[aa];
+    out[row + i + c * ld_out] = (T)((double)out[row + i + c * ld_out] + s);
   }
 }
 
@@ -711,7 +729,7 @@ void basis_t_apply(bool fp64, const TasksDev &t, const void *E, const void *in, 
     k_basis_t<double, double><<<t.n, 256, 0, s>>>(t, (const double *)E, (const double *)in,
                                                   ld_in, (double *)out, ld_out, cols, active);
   else
-    k_basis_t<float, float><<<t.n, 256, 0, s>>>(t, (const float *)E, (const float *)in, ld_in,
+    k_basis_t<float, double><<<t.n, 256, 0, s>>>(t, (const double *)E, (const float *)in, ld_in,
                                                 (float *)out, ld_out, cols, active);
   count_launch();
   H2_CHECK_LAUNCH();
@@ -724,7 +742,7 @@ void basis_n_apply(bool fp64, const TasksDev &t, const void *E, const void *in, 
     k_basis_n<double, double><<<t.n, 256, 0, s>>>(t, (const double *)E, (const double *)in,
                                                   ld_in, (double *)out, ld_out, cols);
   else
-    k_basis_n<float, float><<<t.n, 256, 0, s>>>(t, (const float *)E, (const float *)in, ld_in,
+    k_basis_n<float, double><<<t.n, 256, 0, s>>>(t, (const double *)E, (const float *)in, ld_in,
                                                 (float *)out, ld_out, cols);
   count_launch();
   H2_CHECK_LAUNCH();

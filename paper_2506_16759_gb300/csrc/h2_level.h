@@ -112,6 +112,7 @@ void compact_skeletons(const TasksDev &t, const int32_t *J_tmp, const int32_t *s
 void gather_skeleton_rows(bool fp64, const TasksDev &t, const void *Y, int64_t ld, void *Ynext,
                           int64_t ldn, InstCols cols, const int32_t *active, cudaStream_t s);
 // out(krow+a, c) = sum_i E(i,a) in(row+i, c)       (E^T products: upsweep)
+// E is FP64 in both modes; the sums accumulate in FP64.
 void basis_t_apply(bool fp64, const TasksDev &t, const void *E, const void *in, int64_t ld_in,
                    void *out, int64_t ld_out, InstCols cols, const int32_t *active,
                    cudaStream_t s);

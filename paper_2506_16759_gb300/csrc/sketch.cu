@@ -13,11 +13,13 @@ namespace {
 
 // ----------------------------------------------------------------------------
 // Fused kernel summation, FP32 arithmetic on split hi/lo coordinates.
-// Each thread owns RPT rows (strided by NT so that global writes coalesce) and
-// DC sample columns; the CTA streams TJ points and their Omega rows through
-// shared memory.  Work items are a row tile against a range of columns j.
+// Each thread owns one row and DC sample columns; the CTA streams TJ points
+// and their Omega rows through shared memory.  Work items are a row tile
+// against a range of columns j.  Each TJ-point tile is summed in plain FP32
+// and the tile sums are added with Kahan compensation, so the rounding of the
+// N-term sum stays a few FP32 ulps instead of growing with sqrt(N).
 // ----------------------------------------------------------------------------
-template <int KID, int DC, int RPT, int NT, int TJ>
+template <int KID, int DC, int NT, int TJ>
 __global__ void __launch_bounds__(NT) k_ksum32(KsumArgs32 a, int tile_rows) {
   const KsumItem it = a.items[blockIdx.x];
   const InstDev in = a.inst[it.inst];
@@ -27,72 +29,65 @@ __global__ void __launch_bounds__(NT) k_ksum32(KsumArgs32 a, int tile_rows) {
   __shared__ float sp[6][TJ];
   __shared__ __align__(16) float so[TJ][DC];
 
-  float xh[RPT], yh[RPT], zh[RPT], xl[RPT], yl[RPT], zl[RPT];
-  float acc[RPT][DC];
+  const int lr = threadIdx.x;
+  int64_t g = it.row0 + (lr < it.rows ? lr : 0);
+  const float xh = a.pts.xh[g], yh = a.pts.yh[g], zh = a.pts.zh[g];
+  const float xl = a.pts.xl[g], yl = a.pts.yl[g], zl = a.pts.zl[g];
+  float acc[DC], cmp[DC];
 #pragma unroll
-  for (int r = 0; r < RPT; ++r) {
-    int lr = threadIdx.x + r * NT;
-    int64_t g = it.row0 + (lr < it.rows ? lr : 0);
-    xh[r] = a.pts.xh[g]; yh[r] = a.pts.yh[g]; zh[r] = a.pts.zh[g];
-    xl[r] = a.pts.xl[g]; yl[r] = a.pts.yl[g]; zl[r] = a.pts.zl[g];
-#pragma unroll
-    for (int c = 0; c < DC; ++c) acc[r][c] = 0.f;
-  }
+  for (int c = 0; c < DC; ++c) { acc[c] = 0.f; cmp[c] = 0.f; }
   for (int64_t j = it.j0; j < it.j1; j += TJ) {
     int nj = (int)(it.j1 - j < TJ ? it.j1 - j : TJ);
     for (int q = threadIdx.x; q < TJ; q += NT) {
-      int64_t g = j + (q < nj ? q : 0);
-      sp[0][q] = a.pts.xh[g]; sp[1][q] = a.pts.yh[g]; sp[2][q] = a.pts.zh[g];
-      sp[3][q] = a.pts.xl[g]; sp[4][q] = a.pts.yl[g]; sp[5][q] = a.pts.zl[g];
+      int64_t gj = j + (q < nj ? q : 0);
+      sp[0][q] = a.pts.xh[gj]; sp[1][q] = a.pts.yh[gj]; sp[2][q] = a.pts.zh[gj];
+      sp[3][q] = a.pts.xl[gj]; sp[4][q] = a.pts.yl[gj]; sp[5][q] = a.pts.zl[gj];
     }
     for (int q = threadIdx.x; q < TJ * DC; q += NT) {
       int jj = q % TJ, c = q / TJ;
       so[jj][c] = jj < nj ? a.om[(j + jj) + (int64_t)(it.c0 + c) * a.ld] : 0.f;
     }
     __syncthreads();
+    float t[DC];
+#pragma unroll
+    for (int c = 0; c < DC; ++c) t[c] = 0.f;
 #pragma unroll 2
     for (int jj = 0; jj < nj; ++jj) {
-      float pxh = sp[0][jj], pyh = sp[1][jj], pzh = sp[2][jj];
-      float pxl = sp[3][jj], pyl = sp[4][jj], pzl = sp[5][jj];
-      float kv[RPT];
-#pragma unroll
-      for (int r = 0; r < RPT; ++r) {
-        float g = geom32<KID>(xh[r], yh[r], zh[r], xl[r], yl[r], zl[r], pxh, pyh, pzh, pxl, pyl,
-                              pzl);
-        kv[r] = kval<KID, float>(g, scale, pw);
-      }
+      float gm = geom32<KID>(xh, yh, zh, xl, yl, zl, sp[0][jj], sp[1][jj], sp[2][jj], sp[3][jj],
+                             sp[4][jj], sp[5][jj]);
+      float kv = kval<KID, float>(gm, scale, pw);
       const float4 *o4 = reinterpret_cast<const float4 *>(&so[jj][0]);
 #pragma unroll
       for (int c4 = 0; c4 < DC / 4; ++c4) {
         float4 o = o4[c4];
-#pragma unroll
-        for (int r = 0; r < RPT; ++r) {
-          acc[r][4 * c4 + 0] = fmaf(kv[r], o.x, acc[r][4 * c4 + 0]);
-          acc[r][4 * c4 + 1] = fmaf(kv[r], o.y, acc[r][4 * c4 + 1]);
-          acc[r][4 * c4 + 2] = fmaf(kv[r], o.z, acc[r][4 * c4 + 2]);
-          acc[r][4 * c4 + 3] = fmaf(kv[r], o.w, acc[r][4 * c4 + 3]);
-        }
+        t[4 * c4 + 0] = fmaf(kv, o.x, t[4 * c4 + 0]);
+        t[4 * c4 + 1] = fmaf(kv, o.y, t[4 * c4 + 1]);
+        t[4 * c4 + 2] = fmaf(kv, o.z, t[4 * c4 + 2]);
+        t[4 * c4 + 3] = fmaf(kv, o.w, t[4 * c4 + 3]);
       }
+    }
+#pragma unroll
+    for (int c = 0; c < DC; ++c) {
+      float y = t[c] - cmp[c];
+      float s = acc[c] + y;
+      cmp[c] = (s - acc[c]) - y;
+      acc[c] = s;
     }
     __syncthreads();
   }
+  if (lr >= it.rows) return;
+  g = it.row0 + lr;
+  if (KID != H2_K_POLY && g >= it.j0 && g < it.j1 && diag != 0.f) {
 #pragma unroll
-  for (int r = 0; r < RPT; ++r) {
-    int lr = threadIdx.x + r * NT;
-    if (lr >= it.rows) continue;
-    int64_t g = it.row0 + lr;
-    if (KID != H2_K_POLY && g >= it.j0 && g < it.j1 && diag != 0.f) {
+    for (int c = 0; c < DC; ++c) acc[c] += diag * a.om[g + (int64_t)(it.c0 + c) * a.ld];
+  }
+  if (it.part < 0) {
 #pragma unroll
-      for (int c = 0; c < DC; ++c) acc[r][c] += diag * a.om[g + (int64_t)(it.c0 + c) * a.ld];
-    }
-    if (it.part < 0) {
+    for (int c = 0; c < DC; ++c) a.y[g + (int64_t)(it.c0 + c) * a.ld] = acc[c];
+  } else {
+    float *dst = a.partial + (int64_t)it.part * tile_rows * DC;
 #pragma unroll
-      for (int c = 0; c < DC; ++c) a.y[g + (int64_t)(it.c0 + c) * a.ld] = acc[r][c];
-    } else {
-      float *dst = a.partial + (int64_t)it.part * tile_rows * DC;
-#pragma unroll
-      for (int c = 0; c < DC; ++c) dst[c * tile_rows + lr] = acc[r][c];
-    }
+    for (int c = 0; c < DC; ++c) dst[c * tile_rows + lr] = acc[c];
   }
 }
 
@@ -369,14 +364,14 @@ __global__ void k_sumsq_final(const double *part, int nb, int count, double *out
 
 template <int KID, int DC>
 void launch_ksum32(const KsumPlan &p, const KsumArgs32 &a0, cudaStream_t s) {
-  constexpr int NT = 128, RPT = 2, TJ = 64;
+  constexpr int NT = 128, TJ = 64;
   StagedPlan<float> sp;
   stage_plan(p, sp, s);
   KsumArgs32 a = a0;
   a.items = sp.items.p;
   a.partial = sp.partial.p;
   KernelEvents ev(s);
-  k_ksum32<KID, DC, RPT, NT, TJ><<<(int)p.items.size(), NT, 0, s>>>(a, p.tile_rows);
+  k_ksum32<KID, DC, NT, TJ><<<(int)p.items.size(), NT, 0, s>>>(a, p.tile_rows);
   ev.stop();
   count_launch();
   H2_CHECK_LAUNCH();
@@ -417,7 +412,7 @@ KsumPlan plan_ksum(const std::vector<int64_t> &inst_n, const std::vector<int64_t
                    const std::vector<int> &insts, const std::vector<int> &c0, int ncols,
                    bool fp64, int tile_rows_hint, int sm_count) {
   KsumPlan p;
-  p.tile_rows = fp64 ? 128 : 256;
+  p.tile_rows = 128;
   (void)tile_rows_hint;
   p.dc = ncols;
   int64_t tiles = 0;
