@@ -267,6 +267,28 @@ h2_status h2_batched_row_id(int count, const int32_t *m, const int32_t *d, const
                             const double *panels, const double *eps, int32_t *k, int32_t *J,
                             int ldj, const int64_t *eoff, double *basis, h2_stream_t s);
 
+/* Same statistic as h2_batched_qr_mindiag, for callers that cannot allocate
+ * device memory: code that runs while another component owns the device's
+ * memory (a custom or pre-reserving allocator, an allocation callback, a
+ * memory-capped service), where a cudaMalloc would fail, deadlock or break a
+ * budget.  This entry point allocates nothing; the paper has no counterpart.
+ * Arguments are those of h2_batched_qr_mindiag and stay owned by the caller.
+ *
+ * Working copies of the panels that need a QR (m[i] > d[i]) go to one fixed
+ * workspace compiled into the library: 2097152 doubles (16 MiB), present on
+ * every device that loads the library until the process exits.  If the sum of
+ * m[i]*d[i] over those panels exceeds it, the call returns H2_ERR_ARG and the
+ * panels that did not fit get NaN.
+ * The first call on a device looks up the workspace's device address (once
+ * per device, with that device current); make that first call before any
+ * stream capture.  All calls share the one workspace and it keeps the last
+ * call's contents: calls that overlap on the GPU (other streams, other host
+ * threads) race with each other.  The call waits for its stream to finish
+ * before it returns. */
+h2_status h2_batched_qr_mindiag_static(int count, const int32_t *m, const int32_t *d,
+                                       const int64_t *off, const double *panels,
+                                       double *mindiag, h2_stream_t s);
+
 /* CUDA kernels the library has launched from the calling host thread so far
  * (all entry points); a profiling aid. */
 int64_t h2_kernel_launches(void);

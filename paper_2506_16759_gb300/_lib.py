@@ -76,6 +76,7 @@ SIGNATURES = {
     "h2_dense_sketch": (i32, [vp, i64, i64, vp, i64, vp, i64, i32, vp]),
     "h2_batched_qr_mindiag": (i32, [i32, vp, vp, vp, vp, vp, vp]),
     "h2_batched_row_id": (i32, [i32, vp, vp, vp, vp, vp, vp, vp, i32, vp, vp, vp]),
+    "h2_batched_qr_mindiag_static": (i32, [i32, vp, vp, vp, vp, vp, vp]),
 }
 
 _lib = None
