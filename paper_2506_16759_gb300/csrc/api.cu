@@ -226,6 +226,7 @@ struct Builder {
   DBuf<int32_t> cb, ce;             // per-instance column range of the current pass
   DBuf<double> om_stage;            // FP64 staging of new Omega columns (mixed / callbacks)
   int64_t sketch_pairs = 0, sketch_cols = 0;
+  std::vector<int64_t> near_pairs;   // per instance: sum of m_t * m_b over its near list
   double sketch_flops = 0;
   int rounds = 0;
   std::vector<int> not_conv;
@@ -242,9 +243,12 @@ struct Builder {
   void *Bp(LevelData &L) { return fp64() ? (void *)L.B64.p : (void *)L.B32.p; }
   void *Dp() { return fp64() ? (void *)H->D64.p : (void *)H->D32.p; }
 
+  int max_cols = 0;
   void set_cols(const std::vector<int32_t> &b, const std::vector<int32_t> &e) {
     to_device(cb, b, s);
     to_device(ce, e, s);
+    max_cols = 0;
+    for (size_t i = 0; i < b.size(); ++i) max_cols = std::max(max_cols, e[i] - b[i]);
   }
   InstCols cols() const { return InstCols{cb.p, ce.p}; }
 
@@ -310,6 +314,10 @@ struct Builder {
   }
 
   Points64 p64() const { return Points64{H->x.p, H->y.p, H->z.p}; }
+  FarLists far_lists() const {
+    const LevelData &L = H->lv[1];
+    return FarLists{L.row.p, L.m.p, H->near_ptr.p, H->near_idx.p};
+  }
   Points32 p32() const {
     return Points32{H->xh.p, H->yh.p, H->zh.p, H->xl.p, H->yl.p, H->zl.p};
   }
@@ -352,14 +360,21 @@ struct Builder {
               H->near_ptr.p, H->near_idx.p, H->near_erow.p, i == C - 1, s);
       nb += t->near_nnz;
     }
+    {
+      std::vector<int32_t> er = to_host(H->near_erow.p, nnz, s), ci = to_host(H->near_idx.p, nnz, s);
+      near_pairs.assign(C, 0);
+      for (int64_t e = 0; e < nnz; ++e)
+        near_pairs[L.h_inst[er[e]]] += (int64_t)L.h_m[er[e]] * L.h_m[ci[e]];
+    }
     DBuf<int64_t> sz;
     sz.alloc(std::max<int64_t>(nnz, 1));
-    block_sizes(nnz, H->near_erow.p, H->near_idx.p, L.m.p, L.m.p, sz.p, s);
+    block_sizes(nnz, H->near_erow.p, H->near_idx.p, L.m.p, L.m.p, fp64() ? 2 : 4, sz.p, s);
     H->doff.alloc(nnz + 1);
     scan_exclusive(sz.p, H->doff.p, nnz, s);
     H->D_size = to_host(H->doff.p + nnz, 1, s)[0];
-    if (fp64()) H->D64.alloc(std::max<int64_t>(H->D_size, 1));
-    else H->D32.alloc(std::max<int64_t>(H->D_size, 1));
+    // 16 bytes of slack: block copies round up to whole 16-byte units
+    if (fp64()) H->D64.alloc(H->D_size + 2);
+    else H->D32.alloc(H->D_size + 4);
     alloc_panels(L);
   }
 
@@ -379,7 +394,9 @@ struct Builder {
   // ---------------- sampling -------------------------------------------------
   // New Omega columns [c0_i, c0_i+nc) of the listed instances into the level-1
   // panel (tree order), then Y = K Omega for the same columns.
-  void sample(const std::vector<int> &insts, int nc) {
+  // Returns true when the new columns already hold Y_loc (far-only summation:
+  // the leaf near field was never added, so it must not be subtracted).
+  bool sample(const std::vector<int> &insts, int nc, bool far_only = false) {
     LevelData &L = H->lv[1];
     int64_t N = H->n_total;
     timer.begin(PH_SKETCH);
@@ -398,23 +415,30 @@ struct Builder {
         philox_gaussian64(om64 + b, N, H->orig_of_pos.p + b, n, c0, c0 + nc, o.seed, s);
       if (!fp64()) convert_cols_to32(om64, N, b, n, c0, c0 + nc, L.Om32.p, s);
     }
+    bool far = far_only && o.sketch == H2_SKETCH_KSUM && L.max_m <= 64;
     if (o.sketch == H2_SKETCH_KSUM) {
       std::vector<int64_t> nn(H->inst_n), bb(H->inst_base);
+      std::vector<int> lcount(H->count);
+      for (int i = 0; i < H->count; ++i) lcount[i] = 1 << H->inst_depth[i];
       int done = 0;
       while (done < nc) {
         int dc = std::min(32, pick_dc(nc - done));
         std::vector<int> c0(insts.size());
         for (size_t q = 0; q < insts.size(); ++q) c0[q] = H->dcur[insts[q]] + done;
-        KsumPlan plan = plan_ksum(nn, bb, insts, c0, dc, fp64(), o.ksum_tile, sm_count);
-        for (int i : insts) sketch_pairs += H->inst_n[i] * H->inst_n[i];
-        for (int i : insts)
-          sketch_flops += (double)H->inst_n[i] * H->inst_n[i] * (2.0 * dc + 10.0);
+        KsumPlan plan = far ? plan_ksum_far(L.h_row, L.h_m, L.task_base, lcount, insts, c0, dc,
+                                            sm_count)
+                            : plan_ksum(nn, bb, insts, c0, dc, fp64(), o.ksum_tile, sm_count);
+        for (int i : insts) {
+          int64_t pairs = H->inst_n[i] * H->inst_n[i] - (far ? near_pairs[i] : 0);
+          sketch_pairs += pairs;
+          sketch_flops += (double)pairs * (2.0 * dc + 10.0);
+        }
         if (fp64()) {
-          KsumArgs64 a{p64(), L.Om64.p, L.Y64.p, N, H->inst_dev.p, nullptr, nullptr};
-          run_ksum64(H->kid, plan, a, s);
+          KsumArgs64 a{far_lists(), p64(), L.Om64.p, L.Y64.p, N, H->inst_dev.p, nullptr, nullptr};
+          run_ksum64(H->kid, plan, a, s, far);
         } else {
-          KsumArgs32 a{p32(), L.Om32.p, L.Y32.p, N, H->inst_dev.p, nullptr, nullptr};
-          run_ksum32(H->kid, plan, a, s);
+          KsumArgs32 a{far_lists(), p32(), L.Om32.p, L.Y32.p, N, H->inst_dev.p, nullptr, nullptr};
+          run_ksum32(H->kid, plan, a, s, far);
         }
         done += dc;
       }
@@ -465,42 +489,46 @@ struct Builder {
     }
     sketch_cols += nc;
     timer.end(PH_SKETCH);
+    return far;
   }
 
   void add_into(double *y, const double *x, int64_t n);
 
   // ---------------- near field and sweeps ------------------------------------
-  void nearfield_initial() {
+  // Generates every near-field block D.  If the first samples came from the
+  // far-only summation they already are Y_loc; P = D Omega is then formed
+  // separately (for the norm estimate only).  Otherwise Y -= D Omega.
+  void nearfield_initial(bool far, DBuf<char> &P) {
     LevelData &L = H->lv[1];
     int C = H->count;
-    int first = std::min(32, o.d0);
-    std::vector<int32_t> b(C, 0), e(C, first);
-    set_cols(b, e);
     timer.begin(PH_NEAR);
-    NearArgs a{};
-    a.t = L.dev();
-    a.ptr = H->near_ptr.p;
-    a.idx = H->near_idx.p;
-    a.doff = H->doff.p;
-    a.D = Dp();
-    a.inst = H->inst_dev.p;
-    a.p64 = p64();
-    a.p32 = p32();
-    a.Y = Yp(L);
-    a.Om = Omp(L);
-    a.ld = H->n_total;
-    a.cols = cols();
-    nearfield_gen(H->kid, fp64(), a, L.max_m, s);
+    DgenArgs g{};
+    g.nnz = H->near_nnz;
+    g.erow = H->near_erow.p;
+    g.idx = H->near_idx.p;
+    g.doff = H->doff.p;
+    g.m = L.m.p;
+    g.row = L.row.p;
+    g.tinst = L.inst.p;
+    g.inst = H->inst_dev.p;
+    g.p64 = p64();
+    g.p32 = p32();
+    g.D = Dp();
+    dense_blocks_gen(H->kid, fp64(), g, s);
     timer.end(PH_NEAR);
-    if (o.d0 > first) {
-      std::vector<int32_t> b2(C, first), e2(C, o.d0);
-      set_cols(b2, e2);
-      near_bsr();
+    std::vector<int32_t> b(C, 0), e(C, o.d0);
+    set_cols(b, e);
+    if (far) {
+      P.alloc_zero((size_t)H->n_total * o.d0 * (fp64() ? 8 : 4), s);
+      near_bsr(P.p, 1.0);
+    } else {
+      near_bsr(Yp(L), -1.0);
     }
   }
 
-  // Y1(cols) -= D Om1(cols) over the leaf tasks, columns from cb/ce.
-  void near_bsr() {
+  // out(cols) += sign * D Om1(cols) over the leaf tasks, columns from cb/ce
+  // (out: an N-row panel, by default the level-1 Y panel with sign -1).
+  void near_bsr(void *out = nullptr, double sign = -1.0) {
     LevelData &L = H->lv[1];
     timer.begin(PH_BSR);
     BsrArgs a{};
@@ -516,11 +544,11 @@ struct Builder {
     a.blocks = Dp();
     a.in = Omp(L);
     a.ld_in = L.M;
-    a.out = Yp(L);
+    a.out = out ? out : Yp(L);
     a.ld_out = L.M;
-    a.sign = -1.0;
+    a.sign = sign;
     a.cols = cols();
-    bsr_apply(fp64(), a, L.max_m, s);
+    bsr_apply(fp64(), a, L.max_m, max_cols, s);
     timer.end(PH_BSR);
   }
 
@@ -551,7 +579,7 @@ struct Builder {
     a.ld_out = U.M;
     a.sign = -1.0;
     a.cols = cols();
-    bsr_apply(fp64(), a, L.max_k, s);
+    bsr_apply(fp64(), a, L.max_k, max_cols, s);
     timer.end(PH_BSR);
   }
 
@@ -643,11 +671,11 @@ struct Builder {
       }
       if (need.empty()) break;
       ++rounds;
-      sample(need, o.d_inc);
+      const bool far = sample(need, o.d_inc, true);
       std::vector<int32_t> b(C, 0), e(C, 0);
       for (int i : need) { b[i] = H->dcur[i]; e[i] = H->dcur[i] + o.d_inc; }
       set_cols(b, e);
-      near_bsr();
+      if (!far) near_bsr();
       for (int lp = 1; lp < l; ++lp) transfer_up(lp);
       for (int i : need) H->dcur[i] += o.d_inc;
     }
@@ -703,12 +731,12 @@ struct Builder {
     if (L.far_nnz > 0) {
       DBuf<int64_t> sz;
       sz.alloc(L.far_nnz);
-      block_sizes(L.far_nnz, L.far_erow.p, L.far_idx.p, L.k.p, L.k.p, sz.p, s);
+      block_sizes(L.far_nnz, L.far_erow.p, L.far_idx.p, L.k.p, L.k.p, fp64() ? 2 : 4, sz.p, s);
       L.boff.alloc(L.far_nnz + 1);
       scan_exclusive(sz.p, L.boff.p, L.far_nnz, s);
       L.B_size = to_host(L.boff.p + L.far_nnz, 1, s)[0];
-      if (fp64()) L.B64.alloc(std::max<int64_t>(L.B_size, 1));
-      else L.B32.alloc(std::max<int64_t>(L.B_size, 1));
+      if (fp64()) L.B64.alloc(L.B_size + 2);
+      else L.B32.alloc(L.B_size + 4);
       CouplingArgs ca{};
       ca.nnz = L.far_nnz;
       ca.erow = L.far_erow.p;
@@ -816,14 +844,19 @@ struct Builder {
     std::vector<int> all(C);
     std::iota(all.begin(), all.end(), 0);
     for (int i = 0; i < C; ++i) H->dcur[i] = 0;
-    sample(all, o.d0);
+    const bool far = sample(all, o.d0, true);
     for (int i = 0; i < C; ++i) H->dcur[i] = o.d0;
     DBuf<int64_t> ib, in_;
     to_device(ib, H->inst_base, s);
     to_device(in_, H->inst_n, s);
     DBuf<double> ss;
     ss.alloc(C);
-    instance_sumsq(Yp(H->lv[1]), fp64(), H->n_total, ib.p, in_.p, C, o.d0, ss.p, s);
+    // nrmK from the full sketch Y (= Y_loc + D Omega in far-only mode)
+    DBuf<char> P;
+    if (far) nearfield_initial(true, P);
+    else instance_sumsq(Yp(H->lv[1]), nullptr, fp64(), H->n_total, ib.p, in_.p, C, o.d0, ss.p, s);
+    if (far)
+      instance_sumsq(Yp(H->lv[1]), P.p, fp64(), H->n_total, ib.p, in_.p, C, o.d0, ss.p, s);
     std::vector<double> hs = to_host(ss.p, C, s), eps_abs(C);
     for (int i = 0; i < C; ++i) {
       if (!std::isfinite(hs[i])) throw Error{H2_ERR_INPUT, "sketch is not finite"};
@@ -831,7 +864,8 @@ struct Builder {
       eps_abs[i] = tol_in[i] * nrmK;
       if (i == 0) H->st.nrmK = nrmK;
     }
-    nearfield_initial();
+    if (!far) nearfield_initial(false, P);
+    P.release();
     for (int l = 1; l <= H->levels; ++l) {
       run_level(l, eps_abs);
       if (l < H->levels) setup_next_level(l);
@@ -969,7 +1003,7 @@ void matvec_impl(const h2_matrix *H, const double *x, double *y, int nrhs, cudaS
     a.ld_out = N;
     a.sign = 1.0;
     a.cols = cols;
-    bsr_apply(f64, a, L1.max_m, s);
+    bsr_apply(f64, a, L1.max_m, nrhs, s);
   }
   int levels = H->levels;
   if (levels > 0) {
@@ -1009,7 +1043,7 @@ void matvec_impl(const h2_matrix *H, const double *x, double *y, int nrhs, cudaS
       a.ld_out = L.K;
       a.sign = 1.0;
       a.cols = cols;
-      bsr_apply(f64, a, L.max_k, s);
+      bsr_apply(f64, a, L.max_k, nrhs, s);
     }
     // downsweep
     for (int l = levels; l >= 1; --l) {
@@ -1261,10 +1295,10 @@ h2_status h2_ksum_sketch(const double *points, int64_t n, int dim, int kernel_id
       std::vector<int> c0 = {done};
       KsumPlan plan = plan_ksum(nn, bb, insts, c0, dc, f64, 0, device_sm_count());
       if (f64) {
-        KsumArgs64 a{Points64{px.p, py.p, pz.p}, om_c.p, y_c.p, n, idev.p, nullptr, nullptr};
+        KsumArgs64 a{FarLists{}, Points64{px.p, py.p, pz.p}, om_c.p, y_c.p, n, idev.p, nullptr, nullptr};
         run_ksum64(kernel_id, plan, a, st);
       } else {
-        KsumArgs32 a{Points32{xh.p, yh.p, zh.p, xl.p, yl.p, zl.p}, om32.p, y32.p, n, idev.p,
+        KsumArgs32 a{FarLists{}, Points32{xh.p, yh.p, zh.p, xl.p, yl.p, zl.p}, om32.p, y32.p, n, idev.p,
                      nullptr, nullptr};
         run_ksum32(kernel_id, plan, a, st);
       }

@@ -17,7 +17,6 @@ namespace h2 {
 namespace {
 
 constexpr int kNT = 256;   // threads per cluster CTA
-constexpr int kJC = 64;    // block columns staged per step
 constexpr int kMaxRows = 256;     // rows of a block-product row task
 constexpr int kMaxIdRows = 512;   // rows of a cluster in the QR test / row ID
 
@@ -119,166 +118,168 @@ struct PtsOf<float> {
 };
 
 // ----------------------------------------------------------------------------
-// Leaf near field.  Output mapping: thread -> rows i = tid%64 + 64q (q<4),
-// column group tid/64 of DC/4 columns.
+// Block-sparse row products: out(rows of t) += sign * sum_e Blk_e in(rows of b_e).
+//
+// One CTA owns one row block (all of its m <= 256 rows).  Its partner blocks
+// are stored contiguously (column-major, 16-byte aligned offsets), so a chunk
+// of JC block columns is one contiguous range; chunks stream through a
+// three-slot shared-memory ring filled with cp.async (16-byte copies, L2 only)
+// together with the matching JC input rows, two chunks ahead of the compute.
+// Thread t owns rows t%64 + 64r (r < RPT) and DC/4 output columns
+// (t/64)*DC/4 ...; each chunk is summed plainly, chunk sums are added with
+// compensation in FP32.  No output is shared between threads or CTAs.
 // ----------------------------------------------------------------------------
-template <int KID, typename T, int DC>
-__global__ void __launch_bounds__(kNT) k_nearfield(NearArgs a, int mmax) {
+constexpr int kStages = 3;
+constexpr int kSlotBytes = 16384;
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+template <int B>
+__device__ __forceinline__ void cp_async_small(void *smem, const void *gmem, bool valid) {
+  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  int src = valid ? B : 0;  // src-size 0 fills the destination with zeros
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(sa), "l"(gmem), "n"(B),
+               "r"(src));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+template <typename T, int DC, int RPT>
+__global__ void __launch_bounds__(kNT) k_bsr_pipe(BsrArgs a) {
+  constexpr int SLOT = kSlotBytes / sizeof(T);   // block elements per slot
+  constexpr int JMAX = 64;                        // block columns per chunk at most
+  constexpr int CG = DC / 4;                      // output columns per thread
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int NC = PtsOf<T>::NC;
-  constexpr int DG = DC / 4;
-  int tau = blockIdx.x;
-  int m = a.t.m[tau];
-  int inst = a.t.inst[tau];
-  int cb = a.cols.cb[inst], ce = a.cols.ce[inst];
-  int ncol = ce - cb;
-  if (m == 0 || ncol <= 0) return;
-  int64_t rowt = a.t.row[tau];
-  const InstDev in = a.inst[inst];
-  const T scale = (T)in.kd.scale, diag = (T)in.kd.diag;
-  const int pw = in.kd.pw;
-  T *sD = reinterpret_cast<T *>(smem_raw);                 // [kJC][mmax]
-  T *sO = sD + (size_t)kJC * mmax;                         // [kJC][DC]
-  T *sxa = sO + (size_t)kJC * DC;                          // [mmax][NC]
-  T *sxb = sxa + (size_t)mmax * NC;                        // [kJC][NC]
-  const T *Om = reinterpret_cast<const T *>(a.Om);
-  T *Y = reinterpret_cast<T *>(a.Y);
-  T *D = reinterpret_cast<T *>(a.D);
-  for (int i = threadIdx.x; i < m; i += kNT) PtsOf<T>::load(a.p64, a.p32, rowt + i, sxa + i * NC);
-  const int ri = threadIdx.x % 64, cg = threadIdx.x / 64;
-  Acc<T> acc[4][DG];
-  __syncthreads();
-  for (int64_t e = a.ptr[tau]; e < a.ptr[tau + 1]; ++e) {
-    int b = a.idx[e];
-    int mb = a.t.m[b];
-    int64_t rowb = a.t.row[b];
-    T *Dblk = D + a.doff[e];
-    for (int jc = 0; jc < mb; jc += kJC) {
-      int nj = min(kJC, mb - jc);
-      for (int j = threadIdx.x; j < nj; j += kNT)
-        PtsOf<T>::load(a.p64, a.p32, rowb + jc + j, sxb + j * NC);
-      for (int q = threadIdx.x; q < kJC * DC; q += kNT) {
-        int j = q % kJC, c = q / kJC;
-        sO[j * DC + c] = (j < nj && c < ncol) ? Om[rowb + jc + j + (int64_t)(cb + c) * a.ld] : T(0);
-      }
-      __syncthreads();
-      for (int q = threadIdx.x; q < m * nj; q += kNT) {
-        int i = q % m, j = q / m;
-        T g = PtsOf<T>::template geom<KID>(sxa + i * NC, sxb + j * NC);
-        T v = (rowt + i == rowb + jc + j) ? kdiag<KID, T>(g, scale, pw, diag)
-                                          : kval<KID, T>(g, scale, pw);
-        sD[j * mmax + i] = v;
-        Dblk[i + (int64_t)(jc + j) * m] = v;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        int i = ri + 64 * q;
-        if (i >= m) continue;
-        T part[DG];
-#pragma unroll
-        for (int c = 0; c < DG; ++c) part[c] = T(0);
-        for (int j = 0; j < nj; ++j) {
-          T dv = sD[j * mmax + i];
-#pragma unroll
-          for (int c = 0; c < DG; ++c) part[c] += dv * sO[j * DC + cg * DG + c];
+  T *sBlk = reinterpret_cast<T *>(smem_raw);               // [kStages][SLOT]
+  T *sIn = sBlk + kStages * SLOT;                          // [kStages][JMAX][DC]
+  const int tau = blockIdx.x;
+  const int m = a.row_m[tau];
+  const int inst = a.row_inst[tau];
+  const int cb = a.cols.cb[inst], ce = a.cols.ce[inst];
+  const int64_t e0 = a.ptr[tau], e1 = a.ptr[tau + 1];
+  if (m == 0 || ce <= cb || e0 == e1) return;
+  // block columns per chunk: fits a slot, multiple of 4 (16-byte aligned starts)
+  int jc = SLOT / m;
+  jc = jc > JMAX ? JMAX : jc;
+  jc &= ~3;
+  const int i0 = threadIdx.x % 64, g = threadIdx.x / 64;
+  const int64_t orow = a.row_off[tau];
+  const T *blocks = reinterpret_cast<const T *>(a.blocks);
+  const T *in = reinterpret_cast<const T *>(a.in);
+  T *out = reinterpret_cast<T *>(a.out);
+  for (int c0 = cb; c0 < ce; c0 += DC) {
+    const int ncol = min(DC, ce - c0);
+    Acc<T> acc[RPT][CG];
+    // producer state (chunk to issue) and consumer state (chunk to compute)
+    int64_t pe = e0;
+    int pj = 0;
+    int64_t ce_ = e0;
+    int cj = 0;
+    auto issue = [&](int slot) {
+      if (pe < e1) {
+        const int b = a.idx[pe];
+        const int mb = a.col_m[b];
+        const int nj = min(jc, mb - pj);
+        const T *src = blocks + a.boff[pe] + (int64_t)pj * m;
+        const int n16 = (int)(((int64_t)nj * m * sizeof(T) + 15) / 16);
+        char *dst = reinterpret_cast<char *>(sBlk + slot * SLOT);
+        for (int u = threadIdx.x; u < n16; u += kNT)
+          cp_async16(dst + 16 * u, reinterpret_cast<const char *>(src) + 16 * u);
+        const int64_t irow = a.col_off[b] + pj;
+        T *di = sIn + slot * JMAX * DC;
+        for (int q = threadIdx.x; q < JMAX * DC; q += kNT) {
+          const int j = q / DC, c = q % DC;
+          const bool ok = j < nj && c < ncol;
+          const T *sp = ok ? in + irow + j + (int64_t)(c0 + c) * a.ld_in : in;
+          cp_async_small<sizeof(T)>(di + q, sp, ok);
         }
-#pragma unroll
-        for (int c = 0; c < DG; ++c) acc[q][c].add(part[c]);
+        pj += nj;
+        if (pj >= mb) { pj = 0; ++pe; }
       }
+      cp_async_commit();
+    };
+    for (int st = 0; st < kStages - 1; ++st) issue(st);
+    for (int it = 0; ce_ < e1; ++it) {
+      issue((it + kStages - 1) % kStages);
+      cp_async_wait<kStages - 1>();
+      __syncthreads();
+      const int slot = it % kStages;
+      const int mb = a.col_m[a.idx[ce_]];
+      const int nj = min(jc, mb - cj);
+      const T *sb = sBlk + slot * SLOT;
+      const T *si = sIn + slot * JMAX * DC + g * CG;
+      T part[RPT][CG];
+#pragma unroll
+      for (int r = 0; r < RPT; ++r)
+#pragma unroll
+        for (int c = 0; c < CG; ++c) part[r][c] = T(0);
+      for (int j = 0; j < nj; ++j) {
+        T ov[CG];
+#pragma unroll
+        for (int c = 0; c < CG; ++c) ov[c] = si[j * DC + c];
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+          const int i = i0 + 64 * r;
+          const T bv = i < m ? sb[j * m + i] : T(0);
+#pragma unroll
+          for (int c = 0; c < CG; ++c) part[r][c] += bv * ov[c];
+        }
+      }
+      const T sgn = (T)a.sign;
+#pragma unroll
+      for (int r = 0; r < RPT; ++r)
+#pragma unroll
+        for (int c = 0; c < CG; ++c) acc[r][c].add(sgn * part[r][c]);
+      cj += nj;
+      if (cj >= mb) { cj = 0; ++ce_; }
       __syncthreads();
     }
-  }
+    cp_async_wait<0>();
+    __syncthreads();
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    int i = ri + 64 * q;
-    if (i >= m) continue;
+    for (int r = 0; r < RPT; ++r) {
+      const int i = i0 + 64 * r;
+      if (i >= m) continue;
 #pragma unroll
-    for (int c = 0; c < DG; ++c) {
-      int col = cg * DG + c;
-      if (col < ncol) {
-        T *yp = Y + rowt + i + (int64_t)(cb + col) * a.ld;
-        Acc<T> r = acc[q][c];
-        r.add(-*yp);
-        *yp = -r.value();
+      for (int c = 0; c < CG; ++c) {
+        const int col = g * CG + c;
+        if (col < ncol) {
+          T *op = out + orow + i + (int64_t)(c0 + col) * a.ld_out;
+          Acc<T> t = acc[r][c];
+          t.add(*op);
+          *op = t.value();
+        }
       }
     }
   }
 }
 
-// ----------------------------------------------------------------------------
-// Block-sparse product with stored blocks, same mapping, column blocks of DC.
-// ----------------------------------------------------------------------------
-template <typename T, int DC>
-__global__ void __launch_bounds__(kNT) k_bsr(BsrArgs a, int mmax) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int DG = DC / 4;
-  int tau = blockIdx.x;
-  int m = a.row_m[tau];
-  int inst = a.row_inst[tau];
-  int cb = a.cols.cb[inst], ce = a.cols.ce[inst];
-  if (m == 0 || ce <= cb || a.ptr[tau] == a.ptr[tau + 1]) return;
-  int64_t orow = a.row_off[tau];
-  T *sB = reinterpret_cast<T *>(smem_raw);   // [kJC][mmax]
-  T *sI = sB + (size_t)kJC * mmax;           // [kJC][DC]
-  const T *blocks = reinterpret_cast<const T *>(a.blocks);
-  const T *in = reinterpret_cast<const T *>(a.in);
-  T *out = reinterpret_cast<T *>(a.out);
-  const T sign = (T)a.sign;
-  const int ri = threadIdx.x % 64, cg = threadIdx.x / 64;
-  for (int c0 = cb; c0 < ce; c0 += DC) {
-    int ncol = min(DC, ce - c0);
-    Acc<T> acc[4][DG];
-    for (int64_t e = a.ptr[tau]; e < a.ptr[tau + 1]; ++e) {
-      int b = a.idx[e];
-      int mb = a.col_m[b];
-      int64_t irow = a.col_off[b];
-      const T *blk = blocks + a.boff[e];
-      for (int jc = 0; jc < mb; jc += kJC) {
-        int nj = min(kJC, mb - jc);
-        for (int q = threadIdx.x; q < m * nj; q += kNT) {
-          int i = q % m, j = q / m;
-          sB[j * mmax + i] = blk[i + (int64_t)(jc + j) * m];
-        }
-        for (int q = threadIdx.x; q < kJC * DC; q += kNT) {
-          int j = q % kJC, c = q / kJC;
-          sI[j * DC + c] = (j < nj && c < ncol) ? in[irow + jc + j + (int64_t)(c0 + c) * a.ld_in]
-                                                : T(0);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          int i = ri + 64 * q;
-          if (i >= m) continue;
-          T part[DG];
-#pragma unroll
-          for (int c = 0; c < DG; ++c) part[c] = T(0);
-          for (int j = 0; j < nj; ++j) {
-            T bv = sB[j * mmax + i];
-#pragma unroll
-            for (int c = 0; c < DG; ++c) part[c] += bv * sI[j * DC + cg * DG + c];
-          }
-#pragma unroll
-          for (int c = 0; c < DG; ++c) acc[q][c].add(sign * part[c]);
-        }
-        __syncthreads();
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      int i = ri + 64 * q;
-      if (i >= m) continue;
-#pragma unroll
-      for (int c = 0; c < DG; ++c) {
-        int col = cg * DG + c;
-        if (col < ncol) {
-          T *op = out + orow + i + (int64_t)(c0 + col) * a.ld_out;
-          Acc<T> r = acc[q][c];
-          r.add(*op);
-          *op = r.value();
-        }
-      }
-    }
+// Dense near-field blocks D_{t,b} = K(I_t, I_b) for every near pair: one CTA
+// per block, coalesced column-major stores.
+template <int KID, typename T>
+__global__ void k_dgen(DgenArgs a) {
+  constexpr int NC = PtsOf<T>::NC;
+  __shared__ T sa[kMaxRows * NC], sb[kMaxRows * NC];
+  const int64_t e = blockIdx.x;
+  const int tr = a.erow[e], tc = a.idx[e];
+  const int m = a.m[tr], mb = a.m[tc];
+  const int64_t rt = a.row[tr], rb = a.row[tc];
+  const InstDev in = a.inst[a.tinst[tr]];
+  const T scale = (T)in.kd.scale, diag = (T)in.kd.diag;
+  const int pw = in.kd.pw;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) PtsOf<T>::load(a.p64, a.p32, rt + i, sa + i * NC);
+  for (int j = threadIdx.x; j < mb; j += blockDim.x) PtsOf<T>::load(a.p64, a.p32, rb + j, sb + j * NC);
+  __syncthreads();
+  T *D = reinterpret_cast<T *>(a.D) + a.doff[e];
+  for (int q = threadIdx.x; q < m * mb; q += blockDim.x) {
+    const int i = q % m, j = q / m;
+    const T gm = PtsOf<T>::template geom<KID>(sa + i * NC, sb + j * NC);
+    D[q] = (rt + i == rb + j) ? kdiag<KID, T>(gm, scale, pw, diag) : kval<KID, T>(gm, scale, pw);
   }
 }
 
@@ -558,9 +559,13 @@ __global__ void k_coupling(CouplingArgs a) {
 }
 
 __global__ void k_block_sizes(int64_t nnz, const int32_t *erow, const int32_t *idx,
-                              const int32_t *mrow, const int32_t *mcol, int64_t *out) {
+                              const int32_t *mrow, const int32_t *mcol, int align,
+                              int64_t *out) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e < nnz) out[e] = (int64_t)mrow[erow[e]] * mcol[idx[e]];
+  if (e < nnz) {
+    int64_t sz = (int64_t)mrow[erow[e]] * mcol[idx[e]];
+    out[e] = (sz + align - 1) / align * align;
+  }
 }
 
 __global__ void k_inner_tasks(int n, const int32_t *child0, const int64_t *krow_child,
@@ -626,45 +631,40 @@ void set_smem(K kernel, size_t bytes) {
 
 }  // namespace
 
-void nearfield_gen(int kid, bool fp64, const NearArgs &a, int max_m, cudaStream_t s) {
-  if (a.t.n == 0) return;
-  H2_REQUIRE(max_m <= kMaxRows, "leaf size above 256 is not supported");
-  int mm = std::max(max_m, 1);
+void dense_blocks_gen(int kid, bool fp64, const DgenArgs &a, cudaStream_t s) {
+  if (a.nnz == 0) return;
+  H2_REQUIRE(a.nnz < (1ll << 31), "too many near-field blocks");
   dispatch_kernel(kid, [&](auto K) {
     constexpr int KID = decltype(K)::value;
-    if (fp64) {
-      size_t bytes = sizeof(double) * ((size_t)kJC * mm + kJC * 32 + (size_t)(mm + kJC) * 3);
-      auto kern = k_nearfield<KID, double, 32>;
-      set_smem(kern, bytes);
-      kern<<<a.t.n, kNT, bytes, s>>>(a, mm);
-    } else {
-      size_t bytes = sizeof(float) * ((size_t)kJC * mm + kJC * 32 + (size_t)(mm + kJC) * 6);
-      auto kern = k_nearfield<KID, float, 32>;
-      set_smem(kern, bytes);
-      kern<<<a.t.n, kNT, bytes, s>>>(a, mm);
-    }
+    if (fp64) k_dgen<KID, double><<<(int)a.nnz, 256, 0, s>>>(a);
+    else k_dgen<KID, float><<<(int)a.nnz, 256, 0, s>>>(a);
     count_launch();
     H2_CHECK_LAUNCH();
   });
 }
 
-void bsr_apply(bool fp64, const BsrArgs &a, int max_m, cudaStream_t s) {
-  if (a.n_rows == 0) return;
-  H2_REQUIRE(max_m <= kMaxRows, "block rows above 256 are not supported");
-  int mm = std::max(max_m, 1);
-  if (fp64) {
-    size_t bytes = sizeof(double) * ((size_t)kJC * mm + kJC * 32);
-    auto kern = k_bsr<double, 32>;
-    set_smem(kern, bytes);
-    kern<<<a.n_rows, kNT, bytes, s>>>(a, mm);
-  } else {
-    size_t bytes = sizeof(float) * ((size_t)kJC * mm + kJC * 32);
-    auto kern = k_bsr<float, 32>;
-    set_smem(kern, bytes);
-    kern<<<a.n_rows, kNT, bytes, s>>>(a, mm);
-  }
+template <typename T, int DC, int RPT>
+void launch_bsr(const BsrArgs &a, cudaStream_t s) {
+  constexpr int SLOT = kSlotBytes / sizeof(T);
+  size_t bytes = sizeof(T) * ((size_t)kStages * SLOT + (size_t)kStages * 64 * DC);
+  auto kern = k_bsr_pipe<T, DC, RPT>;
+  set_smem(kern, bytes);
+  kern<<<a.n_rows, kNT, bytes, s>>>(a);
   count_launch();
   H2_CHECK_LAUNCH();
+}
+
+void bsr_apply(bool fp64, const BsrArgs &a, int max_m, int max_cols, cudaStream_t s) {
+  if (a.n_rows == 0 || max_cols <= 0) return;
+  H2_REQUIRE(max_m <= kMaxRows, "block rows above 256 are not supported");
+  const bool narrow = max_cols <= 16;
+  if (max_m <= 64) {
+    if (fp64) narrow ? launch_bsr<double, 16, 1>(a, s) : launch_bsr<double, 32, 1>(a, s);
+    else narrow ? launch_bsr<float, 16, 1>(a, s) : launch_bsr<float, 32, 1>(a, s);
+  } else {
+    if (fp64) narrow ? launch_bsr<double, 16, 4>(a, s) : launch_bsr<double, 32, 4>(a, s);
+    else narrow ? launch_bsr<float, 16, 4>(a, s) : launch_bsr<float, 32, 4>(a, s);
+  }
 }
 
 void qr_test(bool fp64, const QrArgs &a, size_t smem_bytes, cudaStream_t s) {
@@ -761,9 +761,9 @@ void coupling_gen(int kid, bool fp64, const CouplingArgs &a, cudaStream_t s) {
 }
 
 void block_sizes(int64_t nnz, const int32_t *erow, const int32_t *idx, const int32_t *mrow,
-                 const int32_t *mcol, int64_t *out, cudaStream_t s) {
+                 const int32_t *mcol, int align, int64_t *out, cudaStream_t s) {
   if (nnz == 0) return;
-  k_block_sizes<<<ceil_div(nnz, 256), 256, 0, s>>>(nnz, erow, idx, mrow, mcol, out);
+  k_block_sizes<<<ceil_div(nnz, 256), 256, 0, s>>>(nnz, erow, idx, mrow, mcol, align, out);
   count_launch();
   H2_CHECK_LAUNCH();
 }

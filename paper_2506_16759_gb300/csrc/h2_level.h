@@ -46,26 +46,25 @@ struct BsrArgs {
   double sign;
   InstCols cols;
 };
-void bsr_apply(bool fp64, const BsrArgs &a, int max_m, cudaStream_t s);
+// max_cols: the widest per-instance column range of this call.
+void bsr_apply(bool fp64, const BsrArgs &a, int max_m, int max_cols, cudaStream_t s);
 
-// Leaf near field: D = K(I_t, I_b) generated, stored, and
-// Y(I_t, cols) -= sum_b D Omega(I_b, cols) for one block of <= 32 columns
-// starting at cb[inst] (the block width is ce-cb, at most 32).
-struct NearArgs {
-  TasksDev t;               // level-1 tasks (row = global tree position)
-  const int64_t *ptr;       // near CSR over tasks
-  const int32_t *idx;
-  const int64_t *doff;      // D block offsets
-  void *D;                  // T
+// Leaf near field: every D_{t,b} = K(I_t, I_b) of the near list, stored at
+// doff (16-byte aligned offsets).
+struct DgenArgs {
+  int64_t nnz;
+  const int32_t *erow;      // row task of each near entry
+  const int32_t *idx;       // column task of each near entry
+  const int64_t *doff;
+  const int32_t *m;         // rows of each leaf task
+  const int64_t *row;       // first global tree position of each leaf task
+  const int32_t *tinst;     // instance of each task
   const InstDev *inst;
   Points64 p64;
   Points32 p32;
-  void *Y;                  // T panel (level 1)
-  const void *Om;           // T panel (level 1)
-  int64_t ld;
-  InstCols cols;
+  void *D;                  // T
 };
-void nearfield_gen(int kid, bool fp64, const NearArgs &a, int max_m, cudaStream_t s);
+void dense_blocks_gen(int kid, bool fp64, const DgenArgs &a, cudaStream_t s);
 
 // QR convergence test of Sec. III-B on each active unconverged task.
 struct QrArgs {
@@ -135,9 +134,10 @@ struct CouplingArgs {
 };
 void coupling_gen(int kid, bool fp64, const CouplingArgs &a, cudaStream_t s);
 
-// Sizes of blocks for offset scans: out[e] = rows(row task) * cols(col task).
+// Sizes of blocks for offset scans: out[e] = rows(row task) * cols(col task),
+// rounded up to a multiple of `align` elements (16-byte aligned blocks).
 void block_sizes(int64_t nnz, const int32_t *erow, const int32_t *idx, const int32_t *mrow,
-                 const int32_t *mcol, int64_t *out, cudaStream_t s);
+                 const int32_t *mcol, int align, int64_t *out, cudaStream_t s);
 
 // Inner-level task geometry: row[t] = krow_child[c0], m[t] = k[c0] + k[c0+1].
 void inner_tasks(int n, const int32_t *child0, const int64_t *krow_child,

@@ -21,9 +21,20 @@ struct KsumItem {
   int inst;
   int rows;
   int64_t row0;
-  int64_t j0, j1;
+  int64_t j0, j1;   // point range (all-points mode)
   int c0;
   int part;
+  int task;         // far-only mode: the leaf task that owns the rows
+  int lb0, lb1;     // far-only mode: range of leaf tasks summed over
+};
+
+// Leaf tasks and their near lists, for the far-only summation
+// Y_loc(I_t) = sum over points outside the near leaves of t.
+struct FarLists {
+  const int64_t *leaf_row;  // first tree position of each leaf task
+  const int32_t *leaf_m;    // points of each leaf task
+  const int64_t *near_ptr;  // near CSR over leaf tasks (sorted)
+  const int32_t *near_idx;
 };
 
 // Plan for one ksum launch (host side): items and the partial reduction.
@@ -44,6 +55,7 @@ struct KsumPlan {
 };
 
 struct KsumArgs64 {
+  FarLists far;
   Points64 pts;
   const double *om;  // panel, ld = ld
   double *y;         // panel, ld = ld
@@ -53,6 +65,7 @@ struct KsumArgs64 {
   double *partial;
 };
 struct KsumArgs32 {
+  FarLists far;
   Points32 pts;
   const float *om;
   float *y;
@@ -68,11 +81,21 @@ KsumPlan plan_ksum(const std::vector<int64_t> &inst_n, const std::vector<int64_t
                    const std::vector<int> &insts, const std::vector<int> &c0, int ncols,
                    bool fp64, int tile_rows_hint, int sm_count);
 
+// Plan of the far-only summation over the leaf tasks [t0, t1) of each listed
+// instance (one item row tile = one leaf).  leaf_base/leaf_count: per
+// instance, its first leaf task and number of leaves.
+KsumPlan plan_ksum_far(const std::vector<int64_t> &leaf_row, const std::vector<int32_t> &leaf_m,
+                       const std::vector<int> &leaf_base, const std::vector<int> &leaf_count,
+                       const std::vector<int> &insts, const std::vector<int> &c0, int ncols,
+                       int sm_count);
+
 // Runs a plan (items/partials staged in `scratch`-owned buffers).  Returns the
 // number of kernel launches.  `work` must hold plan.n_parts*tile_rows*dc
 // values; items/reds are copied to device-side staging inside.
-void run_ksum64(int kid, const KsumPlan &plan, const KsumArgs64 &a, cudaStream_t s);
-void run_ksum32(int kid, const KsumPlan &plan, const KsumArgs32 &a, cudaStream_t s);
+void run_ksum64(int kid, const KsumPlan &plan, const KsumArgs64 &a, cudaStream_t s,
+                bool far = false);
+void run_ksum32(int kid, const KsumPlan &plan, const KsumArgs32 &a, cudaStream_t s,
+                bool far = false);
 
 // Gaussian sample columns for rows in tree order: om[pos + c*ld] for
 // c in [c0, c1), drawn from Philox4x32-10 keyed by (seed) at counter
@@ -101,8 +124,10 @@ void split_points_soa(const double *pts, int64_t n, int dim, double *x, double *
                       cudaStream_t s);
 void convert_to64(const float *src, int64_t n, double *dst, cudaStream_t s);
 
-// sum of squares of panel columns [0, d) per instance rows (FP64 result).
-void instance_sumsq(const void *panel, bool fp64, int64_t ld, const int64_t *inst_base,
-                    const int64_t *inst_n, int count, int d, double *out, cudaStream_t s);
+// Sum of squares of (panel + panel2) columns [0, d) over each instance's rows
+// (FP64 result); panel2 may be NULL.
+void instance_sumsq(const void *panel, const void *panel2, bool fp64, int64_t ld,
+                    const int64_t *inst_base, const int64_t *inst_n, int count, int d,
+                    double *out, cudaStream_t s);
 
 }  // namespace h2

@@ -14,19 +14,22 @@ namespace {
 // ----------------------------------------------------------------------------
 // Fused kernel summation, FP32 arithmetic on split hi/lo coordinates.
 // Each thread owns one row and DC sample columns; the CTA streams TJ points
-// and their Omega rows through shared memory.  Work items are a row tile
-// against a range of columns j.  Each TJ-point tile is summed in plain FP32
-// and the tile sums are added with Kahan compensation, so the rounding of the
-// N-term sum stays a few FP32 ulps instead of growing with sqrt(N).
+// (coordinates as two float4) and their Omega rows through shared memory.
+// Each TJ-point tile is summed in plain FP32 and the tile sums are added with
+// Kahan compensation, so the rounding of the N-term sum stays a few FP32 ulps
+// instead of growing with sqrt(N).
+// All-points mode sums j over [j0, j1).  Far-only mode (FAR) sums, for the
+// rows of one leaf, over the leaves [lb0, lb1) that are not in its near list:
+// that is Y_loc = Y - sum_b D_{t,b} Omega_b of Algorithm 1 without forming Y.
 // ----------------------------------------------------------------------------
-template <int KID, int DC, int NT, int TJ>
+template <int KID, int DC, int NT, int TJ, bool FAR>
 __global__ void __launch_bounds__(NT) k_ksum32(KsumArgs32 a, int tile_rows) {
   const KsumItem it = a.items[blockIdx.x];
   const InstDev in = a.inst[it.inst];
   const float scale = (float)in.kd.scale;
   const float diag = (float)in.kd.diag;
   const int pw = in.kd.pw;
-  __shared__ float sp[6][TJ];
+  __shared__ float4 sh[TJ], sl[TJ];
   __shared__ __align__(16) float so[TJ][DC];
 
   const int lr = threadIdx.x;
@@ -36,12 +39,12 @@ __global__ void __launch_bounds__(NT) k_ksum32(KsumArgs32 a, int tile_rows) {
   float acc[DC], cmp[DC];
 #pragma unroll
   for (int c = 0; c < DC; ++c) { acc[c] = 0.f; cmp[c] = 0.f; }
-  for (int64_t j = it.j0; j < it.j1; j += TJ) {
-    int nj = (int)(it.j1 - j < TJ ? it.j1 - j : TJ);
+
+  auto tile = [&](int64_t j, int nj) {
     for (int q = threadIdx.x; q < TJ; q += NT) {
       int64_t gj = j + (q < nj ? q : 0);
-      sp[0][q] = a.pts.xh[gj]; sp[1][q] = a.pts.yh[gj]; sp[2][q] = a.pts.zh[gj];
-      sp[3][q] = a.pts.xl[gj]; sp[4][q] = a.pts.yl[gj]; sp[5][q] = a.pts.zl[gj];
+      sh[q] = make_float4(a.pts.xh[gj], a.pts.yh[gj], a.pts.zh[gj], 0.f);
+      sl[q] = make_float4(a.pts.xl[gj], a.pts.yl[gj], a.pts.zl[gj], 0.f);
     }
     for (int q = threadIdx.x; q < TJ * DC; q += NT) {
       int jj = q % TJ, c = q / TJ;
@@ -51,20 +54,25 @@ __global__ void __launch_bounds__(NT) k_ksum32(KsumArgs32 a, int tile_rows) {
     float t[DC];
 #pragma unroll
     for (int c = 0; c < DC; ++c) t[c] = 0.f;
-#pragma unroll 2
-    for (int jj = 0; jj < nj; ++jj) {
-      float gm = geom32<KID>(xh, yh, zh, xl, yl, zl, sp[0][jj], sp[1][jj], sp[2][jj], sp[3][jj],
-                             sp[4][jj], sp[5][jj]);
-      float kv = kval<KID, float>(gm, scale, pw);
+    auto pair = [&](int jj) {
+      const float4 ph = sh[jj], pl = sl[jj];
+      const float gm = geom32<KID>(xh, yh, zh, xl, yl, zl, ph.x, ph.y, ph.z, pl.x, pl.y, pl.z);
+      const float kv = kval<KID, float>(gm, scale, pw);
       const float4 *o4 = reinterpret_cast<const float4 *>(&so[jj][0]);
 #pragma unroll
       for (int c4 = 0; c4 < DC / 4; ++c4) {
-        float4 o = o4[c4];
+        const float4 o = o4[c4];
         t[4 * c4 + 0] = fmaf(kv, o.x, t[4 * c4 + 0]);
         t[4 * c4 + 1] = fmaf(kv, o.y, t[4 * c4 + 1]);
         t[4 * c4 + 2] = fmaf(kv, o.z, t[4 * c4 + 2]);
         t[4 * c4 + 3] = fmaf(kv, o.w, t[4 * c4 + 3]);
       }
+    };
+    if (nj == TJ) {
+#pragma unroll 4
+      for (int jj = 0; jj < TJ; ++jj) pair(jj);
+    } else {
+      for (int jj = 0; jj < nj; ++jj) pair(jj);
     }
 #pragma unroll
     for (int c = 0; c < DC; ++c) {
@@ -74,10 +82,24 @@ __global__ void __launch_bounds__(NT) k_ksum32(KsumArgs32 a, int tile_rows) {
       acc[c] = s;
     }
     __syncthreads();
+  };
+
+  if (!FAR) {
+    for (int64_t j = it.j0; j < it.j1; j += TJ) tile(j, (int)(it.j1 - j < TJ ? it.j1 - j : TJ));
+  } else {
+    int64_t p = a.far.near_ptr[it.task];
+    const int64_t pe = a.far.near_ptr[it.task + 1];
+    for (int b = it.lb0; b < it.lb1; ++b) {
+      while (p < pe && a.far.near_idx[p] < b) ++p;
+      if (p < pe && a.far.near_idx[p] == b) continue;
+      const int64_t r0 = a.far.leaf_row[b];
+      const int mb = a.far.leaf_m[b];
+      for (int q = 0; q < mb; q += TJ) tile(r0 + q, mb - q < TJ ? mb - q : TJ);
+    }
   }
   if (lr >= it.rows) return;
   g = it.row0 + lr;
-  if (KID != H2_K_POLY && g >= it.j0 && g < it.j1 && diag != 0.f) {
+  if (!FAR && KID != H2_K_POLY && g >= it.j0 && g < it.j1 && diag != 0.f) {
 #pragma unroll
     for (int c = 0; c < DC; ++c) acc[c] += diag * a.om[g + (int64_t)(it.c0 + c) * a.ld];
   }
@@ -91,8 +113,8 @@ __global__ void __launch_bounds__(NT) k_ksum32(KsumArgs32 a, int tile_rows) {
   }
 }
 
-// Same summation in FP64.
-template <int KID, int DC, int NT, int TJ>
+// Same summation in FP64 (no compensation needed).
+template <int KID, int DC, int NT, int TJ, bool FAR>
 __global__ void __launch_bounds__(NT) k_ksum64(KsumArgs64 a, int tile_rows) {
   const KsumItem it = a.items[blockIdx.x];
   const InstDev in = a.inst[it.inst];
@@ -101,14 +123,13 @@ __global__ void __launch_bounds__(NT) k_ksum64(KsumArgs64 a, int tile_rows) {
   const int pw = in.kd.pw;
   __shared__ double sp[3][TJ];
   __shared__ __align__(16) double so[TJ][DC];
-  int lr = threadIdx.x;
+  const int lr = threadIdx.x;
   int64_t g = it.row0 + (lr < it.rows ? lr : 0);
-  double xi = a.pts.x[g], yi = a.pts.y[g], zi = a.pts.z[g];
+  const double xi = a.pts.x[g], yi = a.pts.y[g], zi = a.pts.z[g];
   double acc[DC];
 #pragma unroll
   for (int c = 0; c < DC; ++c) acc[c] = 0.0;
-  for (int64_t j = it.j0; j < it.j1; j += TJ) {
-    int nj = (int)(it.j1 - j < TJ ? it.j1 - j : TJ);
+  auto tile = [&](int64_t j, int nj) {
     for (int q = threadIdx.x; q < TJ; q += NT) {
       int64_t gj = j + (q < nj ? q : 0);
       sp[0][q] = a.pts.x[gj]; sp[1][q] = a.pts.y[gj]; sp[2][q] = a.pts.z[gj];
@@ -130,10 +151,23 @@ __global__ void __launch_bounds__(NT) k_ksum64(KsumArgs64 a, int tile_rows) {
       }
     }
     __syncthreads();
+  };
+  if (!FAR) {
+    for (int64_t j = it.j0; j < it.j1; j += TJ) tile(j, (int)(it.j1 - j < TJ ? it.j1 - j : TJ));
+  } else {
+    int64_t p = a.far.near_ptr[it.task];
+    const int64_t pe = a.far.near_ptr[it.task + 1];
+    for (int b = it.lb0; b < it.lb1; ++b) {
+      while (p < pe && a.far.near_idx[p] < b) ++p;
+      if (p < pe && a.far.near_idx[p] == b) continue;
+      const int64_t r0 = a.far.leaf_row[b];
+      const int mb = a.far.leaf_m[b];
+      for (int q = 0; q < mb; q += TJ) tile(r0 + q, mb - q < TJ ? mb - q : TJ);
+    }
   }
   if (lr >= it.rows) return;
   g = it.row0 + lr;
-  if (KID != H2_K_POLY && g >= it.j0 && g < it.j1 && diag != 0.0) {
+  if (!FAR && KID != H2_K_POLY && g >= it.j0 && g < it.j1 && diag != 0.0) {
 #pragma unroll
     for (int c = 0; c < DC; ++c) acc[c] += diag * a.om[g + (int64_t)(it.c0 + c) * a.ld];
   }
@@ -332,7 +366,7 @@ __global__ void k_to64(const float *src, int64_t n, double *dst) {
 }
 
 template <typename T>
-__global__ void k_sumsq_partial(const T *panel, int64_t ld, const int64_t *base,
+__global__ void k_sumsq_partial(const T *panel, const T *panel2, int64_t ld, const int64_t *base,
                                 const int64_t *nn, int d, double *part) {
   int inst = blockIdx.y;
   int64_t b = base[inst], n = nn[inst];
@@ -342,6 +376,7 @@ __global__ void k_sumsq_partial(const T *panel, int64_t ld, const int64_t *base,
        e += (int64_t)gridDim.x * blockDim.x) {
     int64_t r = e % n, c = e / n;
     double v = (double)panel[b + r + c * ld];
+    if (panel2) v += (double)panel2[b + r + c * ld];
     s += v * v;
   }
   __shared__ double sh[256];
@@ -362,16 +397,16 @@ __global__ void k_sumsq_final(const double *part, int nb, int count, double *out
   out[inst] = s;
 }
 
-template <int KID, int DC>
+template <int KID, int DC, bool FAR>
 void launch_ksum32(const KsumPlan &p, const KsumArgs32 &a0, cudaStream_t s) {
-  constexpr int NT = 128, TJ = 64;
+  constexpr int NT = FAR ? 64 : 128, TJ = 64;
   StagedPlan<float> sp;
   stage_plan(p, sp, s);
   KsumArgs32 a = a0;
   a.items = sp.items.p;
   a.partial = sp.partial.p;
   KernelEvents ev(s);
-  k_ksum32<KID, DC, NT, TJ><<<(int)p.items.size(), NT, 0, s>>>(a, p.tile_rows);
+  k_ksum32<KID, DC, NT, TJ, FAR><<<(int)p.items.size(), NT, 0, s>>>(a, p.tile_rows);
   ev.stop();
   count_launch();
   H2_CHECK_LAUNCH();
@@ -384,16 +419,16 @@ void launch_ksum32(const KsumPlan &p, const KsumArgs32 &a0, cudaStream_t s) {
   H2_CUDA(cudaStreamSynchronize(s));  // staging buffers die with this scope
 }
 
-template <int KID, int DC>
+template <int KID, int DC, bool FAR>
 void launch_ksum64(const KsumPlan &p, const KsumArgs64 &a0, cudaStream_t s) {
-  constexpr int NT = 128, TJ = 32;
+  constexpr int NT = FAR ? 64 : 128, TJ = 32;
   StagedPlan<double> sp;
   stage_plan(p, sp, s);
   KsumArgs64 a = a0;
   a.items = sp.items.p;
   a.partial = sp.partial.p;
   KernelEvents ev(s);
-  k_ksum64<KID, DC, NT, TJ><<<(int)p.items.size(), NT, 0, s>>>(a, p.tile_rows);
+  k_ksum64<KID, DC, NT, TJ, FAR><<<(int)p.items.size(), NT, 0, s>>>(a, p.tile_rows);
   ev.stop();
   count_launch();
   H2_CHECK_LAUNCH();
@@ -455,29 +490,83 @@ KsumPlan plan_ksum(const std::vector<int64_t> &inst_n, const std::vector<int64_t
   return p;
 }
 
-void run_ksum32(int kid, const KsumPlan &plan, const KsumArgs32 &a, cudaStream_t s) {
+KsumPlan plan_ksum_far(const std::vector<int64_t> &leaf_row, const std::vector<int32_t> &leaf_m,
+                       const std::vector<int> &leaf_base, const std::vector<int> &leaf_count,
+                       const std::vector<int> &insts, const std::vector<int> &c0, int ncols,
+                       int sm_count) {
+  KsumPlan p;
+  p.tile_rows = 64;
+  p.dc = ncols;
+  int64_t tiles = 0;
+  for (int i : insts) tiles += leaf_count[i];
+  const int64_t target = (int64_t)sm_count * 8 * 4;
+  struct Tmp {
+    int64_t work;
+    KsumItem it;
+  };
+  std::vector<Tmp> all;
+  for (size_t q = 0; q < insts.size(); ++q) {
+    const int i = insts[q];
+    const int nl = leaf_count[i], lb = leaf_base[i];
+    int64_t S = tiles > 0 ? (target + tiles - 1) / tiles : 1;
+    S = std::max<int64_t>(1, std::min<int64_t>(S, std::min<int64_t>(16, nl / 8)));
+    for (int t = lb; t < lb + nl; ++t) {
+      H2_REQUIRE(leaf_m[t] <= 64, "far-only summation needs leaves of at most 64 points");
+      const int64_t slot0 = p.n_parts;
+      for (int64_t sidx = 0; sidx < S; ++sidx) {
+        KsumItem it{};
+        it.inst = i;
+        it.rows = leaf_m[t];
+        it.row0 = leaf_row[t];
+        it.c0 = c0[q];
+        it.task = t;
+        it.lb0 = lb + (int)((nl * sidx) / S);
+        it.lb1 = lb + (int)((nl * (sidx + 1)) / S);
+        it.part = S > 1 ? (int)(p.n_parts++) : -1;
+        all.push_back({(int64_t)(it.lb1 - it.lb0) * it.rows, it});
+      }
+      if (S > 1) p.reds.push_back({i, leaf_m[t], leaf_row[t], c0[q], slot0, (int)S});
+    }
+  }
+  std::stable_sort(all.begin(), all.end(),
+                   [](const Tmp &a, const Tmp &b) { return a.work > b.work; });
+  for (auto &t : all) p.items.push_back(t.it);
+  return p;
+}
+
+void run_ksum32(int kid, const KsumPlan &plan, const KsumArgs32 &a, cudaStream_t s, bool far) {
   if (plan.items.empty()) return;
   dispatch_kernel(kid, [&](auto K) {
     constexpr int KID = decltype(K)::value;
-    switch (plan.dc) {
-      case 32: launch_ksum32<KID, 32>(plan, a, s); break;
-      case 16: launch_ksum32<KID, 16>(plan, a, s); break;
-      case 8: launch_ksum32<KID, 8>(plan, a, s); break;
-      default: throw Error{H2_ERR_ARG, "sketch column block must be 8, 16 or 32"};
-    }
+    auto go = [&](auto F) {
+      constexpr bool FAR = decltype(F)::value;
+      switch (plan.dc) {
+        case 32: launch_ksum32<KID, 32, FAR>(plan, a, s); break;
+        case 16: launch_ksum32<KID, 16, FAR>(plan, a, s); break;
+        case 8: launch_ksum32<KID, 8, FAR>(plan, a, s); break;
+        default: throw Error{H2_ERR_ARG, "sketch column block must be 8, 16 or 32"};
+      }
+    };
+    if (far) go(std::true_type{});
+    else go(std::false_type{});
   });
 }
 
-void run_ksum64(int kid, const KsumPlan &plan, const KsumArgs64 &a, cudaStream_t s) {
+void run_ksum64(int kid, const KsumPlan &plan, const KsumArgs64 &a, cudaStream_t s, bool far) {
   if (plan.items.empty()) return;
   dispatch_kernel(kid, [&](auto K) {
     constexpr int KID = decltype(K)::value;
-    switch (plan.dc) {
-      case 32: launch_ksum64<KID, 32>(plan, a, s); break;
-      case 16: launch_ksum64<KID, 16>(plan, a, s); break;
-      case 8: launch_ksum64<KID, 8>(plan, a, s); break;
-      default: throw Error{H2_ERR_ARG, "sketch column block must be 8, 16 or 32"};
-    }
+    auto go = [&](auto F) {
+      constexpr bool FAR = decltype(F)::value;
+      switch (plan.dc) {
+        case 32: launch_ksum64<KID, 32, FAR>(plan, a, s); break;
+        case 16: launch_ksum64<KID, 16, FAR>(plan, a, s); break;
+        case 8: launch_ksum64<KID, 8, FAR>(plan, a, s); break;
+        default: throw Error{H2_ERR_ARG, "sketch column block must be 8, 16 or 32"};
+      }
+    };
+    if (far) go(std::true_type{});
+    else go(std::false_type{});
   });
 }
 
@@ -548,18 +637,19 @@ void convert_to64(const float *src, int64_t n, double *dst, cudaStream_t s) {
   H2_CHECK_LAUNCH();
 }
 
-void instance_sumsq(const void *panel, bool fp64, int64_t ld, const int64_t *inst_base,
-                    const int64_t *inst_n, int count, int d, double *out, cudaStream_t s) {
+void instance_sumsq(const void *panel, const void *panel2, bool fp64, int64_t ld,
+                    const int64_t *inst_base, const int64_t *inst_n, int count, int d,
+                    double *out, cudaStream_t s) {
   const int nb = 64;
   DBuf<double> part;
   part.alloc((size_t)nb * count);
   dim3 grid(nb, count);
   if (fp64)
-    k_sumsq_partial<double><<<grid, 256, 0, s>>>((const double *)panel, ld, inst_base, inst_n, d,
-                                                 part.p);
+    k_sumsq_partial<double><<<grid, 256, 0, s>>>((const double *)panel, (const double *)panel2, ld,
+                                                 inst_base, inst_n, d, part.p);
   else
-    k_sumsq_partial<float><<<grid, 256, 0, s>>>((const float *)panel, ld, inst_base, inst_n, d,
-                                                part.p);
+    k_sumsq_partial<float><<<grid, 256, 0, s>>>((const float *)panel, (const float *)panel2, ld,
+                                                inst_base, inst_n, d, part.p);
   count_launch();
   H2_CHECK_LAUNCH();
   k_sumsq_final<<<ceil_div(count, 128), 128, 0, s>>>(part.p, nb, count, out);
