@@ -65,9 +65,13 @@ typedef enum {
 } h2_kernel;
 
 typedef enum {
-  H2_PREC_FP64 = 0,  /* every step in FP64 */
-  H2_PREC_MIXED = 1  /* sketch, entries and block products in FP32; QR
-                        convergence test and pivoted-QR ID in FP64 */
+  H2_PREC_FP64 = 0,       /* every step in FP64 */
+  H2_PREC_MIXED = 1,      /* entries and block products in FP32, the fused
+                             sketch on the tensor cores (TF32 hi/lo split,
+                             FP32 accumulation); QR convergence test and
+                             pivoted-QR ID in FP64 */
+  H2_PREC_MIXED_SIMT = 2  /* as H2_PREC_MIXED with the sketch in FP32 on the
+                             CUDA cores */
 } h2_prec;
 
 typedef enum {

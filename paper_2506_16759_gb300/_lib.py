@@ -8,7 +8,10 @@ from __future__ import annotations
 import ctypes as C
 import os
 
-LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libh2gb.so")
+# H2GB_LIB may point at another build of the library (e.g. a variant with
+# different compile-time options).
+LIB_PATH = os.environ.get("H2GB_LIB") or os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                                                      "libh2gb.so")
 
 H2_OK = 0
 H2_ERR_NOT_CONVERGED = -4

@@ -115,6 +115,7 @@ struct LevelData {
 struct h2_matrix {
   int count = 0;
   bool fp64 = true;
+  bool tensor_sketch = false;   // mixed precision with the tcgen05 sketch
   int kid = 0;
   int levels = 0;
   int64_t n_total = 0;
@@ -425,8 +426,9 @@ struct Builder {
         int dc = std::min(32, pick_dc(nc - done));
         std::vector<int> c0(insts.size());
         for (size_t q = 0; q < insts.size(); ++q) c0[q] = H->dcur[insts[q]] + done;
+        const bool tc = H->tensor_sketch && tc_sketch_supported(dc);
         KsumPlan plan = far ? plan_ksum_far(L.h_row, L.h_m, L.task_base, lcount, insts, c0, dc,
-                                            sm_count)
+                                            sm_count, tc)
                             : plan_ksum(nn, bb, insts, c0, dc, fp64(), o.ksum_tile, sm_count);
         for (int i : insts) {
           int64_t pairs = H->inst_n[i] * H->inst_n[i] - (far ? near_pairs[i] : 0);
@@ -437,8 +439,9 @@ struct Builder {
           KsumArgs64 a{far_lists(), p64(), L.Om64.p, L.Y64.p, N, H->inst_dev.p, nullptr, nullptr};
           run_ksum64(H->kid, plan, a, s, far);
         } else {
-          KsumArgs32 a{far_lists(), p32(), L.Om32.p, L.Y32.p, N, H->inst_dev.p, nullptr, nullptr};
-          run_ksum32(H->kid, plan, a, s, far);
+          KsumArgs32 a{far_lists(), p32(), L.Om32.p, L.Y32.p, N, H->inst_dev.p, nullptr, nullptr,
+                       nullptr};
+          run_ksum32(H->kid, plan, a, s, far, tc);
         }
         done += dc;
       }
@@ -950,7 +953,8 @@ void validate_opts(const h2_build_opts &o) {
   H2_REQUIRE(o.d0 >= 8 && o.d0 % 8 == 0, "d0 must be a positive multiple of 8");
   H2_REQUIRE(o.d_inc >= 0 && o.d_inc % 8 == 0, "d_inc must be a non-negative multiple of 8");
   H2_REQUIRE(o.d_max >= o.d0 && o.d_max <= 256, "need d0 <= d_max <= 256");
-  H2_REQUIRE(o.prec == H2_PREC_FP64 || o.prec == H2_PREC_MIXED, "unknown precision");
+  H2_REQUIRE(o.prec == H2_PREC_FP64 || o.prec == H2_PREC_MIXED || o.prec == H2_PREC_MIXED_SIMT,
+             "unknown precision");
   H2_REQUIRE(o.omega_mode == 0 || (o.omega_mode == 1 && o.omega_stored != nullptr),
              "stored Omega mode needs omega_stored");
 }
@@ -1185,6 +1189,7 @@ h2_status h2_build_batched(const h2_tree *const *trees, int count, const int *ke
     auto H = std::make_unique<h2_matrix>();
     H->count = count;
     H->fp64 = opts->prec == H2_PREC_FP64;
+    H->tensor_sketch = opts->prec == H2_PREC_MIXED;
     H->kid = kernel_ids[0];
     Builder b(H.get(), trees, *opts, (cudaStream_t)s);
     h2_status st = b.run(kernel_ids, params, tols);
@@ -1299,8 +1304,8 @@ h2_status h2_ksum_sketch(const double *points, int64_t n, int dim, int kernel_id
         run_ksum64(kernel_id, plan, a, st);
       } else {
         KsumArgs32 a{FarLists{}, Points32{xh.p, yh.p, zh.p, xl.p, yl.p, zl.p}, om32.p, y32.p, n, idev.p,
-                     nullptr, nullptr};
-        run_ksum32(kernel_id, plan, a, st);
+                     nullptr, nullptr, nullptr};
+        run_ksum32(kernel_id, plan, a, st, false, prec == H2_PREC_MIXED && tc_sketch_supported(dc));
       }
       done += dc;
     }

@@ -73,6 +73,7 @@ struct KsumArgs32 {
   const InstDev *inst;
   const KsumItem *items;
   float *partial;
+  int *err;          // set by the tensor-core kernel if a wait timed out
 };
 
 // Plans a launch covering, for every listed instance, all its rows and
@@ -84,18 +85,23 @@ KsumPlan plan_ksum(const std::vector<int64_t> &inst_n, const std::vector<int64_t
 // Plan of the far-only summation over the leaf tasks [t0, t1) of each listed
 // instance (one item row tile = one leaf).  leaf_base/leaf_count: per
 // instance, its first leaf task and number of leaves.
+// pair_leaves: row tiles of two consecutive leaves (128 rows, tensor-core path).
 KsumPlan plan_ksum_far(const std::vector<int64_t> &leaf_row, const std::vector<int32_t> &leaf_m,
                        const std::vector<int> &leaf_base, const std::vector<int> &leaf_count,
                        const std::vector<int> &insts, const std::vector<int> &c0, int ncols,
-                       int sm_count);
+                       int sm_count, bool pair_leaves = false);
 
 // Runs a plan (items/partials staged in `scratch`-owned buffers).  Returns the
 // number of kernel launches.  `work` must hold plan.n_parts*tile_rows*dc
 // values; items/reds are copied to device-side staging inside.
 void run_ksum64(int kid, const KsumPlan &plan, const KsumArgs64 &a, cudaStream_t s,
                 bool far = false);
+// tensor_cores: use the tcgen05 kernel (16 or 32 columns, 128-row tiles).
 void run_ksum32(int kid, const KsumPlan &plan, const KsumArgs32 &a, cudaStream_t s,
-                bool far = false);
+                bool far = false, bool tensor_cores = false);
+// tcgen05 launch of a staged plan (sketch_tc.cu).
+bool tc_sketch_supported(int ncols);
+void launch_ksum_tc(int kid, const KsumPlan &plan, const KsumArgs32 &a, bool far, cudaStream_t s);
 
 // Gaussian sample columns for rows in tree order: om[pos + c*ld] for
 // c in [c0, c1), drawn from Philox4x32-10 keyed by (seed) at counter

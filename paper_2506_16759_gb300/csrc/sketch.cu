@@ -493,12 +493,13 @@ KsumPlan plan_ksum(const std::vector<int64_t> &inst_n, const std::vector<int64_t
 KsumPlan plan_ksum_far(const std::vector<int64_t> &leaf_row, const std::vector<int32_t> &leaf_m,
                        const std::vector<int> &leaf_base, const std::vector<int> &leaf_count,
                        const std::vector<int> &insts, const std::vector<int> &c0, int ncols,
-                       int sm_count) {
+                       int sm_count, bool pair_leaves) {
   KsumPlan p;
-  p.tile_rows = 64;
+  const int per = pair_leaves ? 2 : 1;
+  p.tile_rows = 64 * per;
   p.dc = ncols;
   int64_t tiles = 0;
-  for (int i : insts) tiles += leaf_count[i];
+  for (int i : insts) tiles += (leaf_count[i] + per - 1) / per;
   const int64_t target = (int64_t)sm_count * 8 * 4;
   struct Tmp {
     int64_t work;
@@ -510,22 +511,27 @@ KsumPlan plan_ksum_far(const std::vector<int64_t> &leaf_row, const std::vector<i
     const int nl = leaf_count[i], lb = leaf_base[i];
     int64_t S = tiles > 0 ? (target + tiles - 1) / tiles : 1;
     S = std::max<int64_t>(1, std::min<int64_t>(S, std::min<int64_t>(16, nl / 8)));
-    for (int t = lb; t < lb + nl; ++t) {
-      H2_REQUIRE(leaf_m[t] <= 64, "far-only summation needs leaves of at most 64 points");
+    for (int t = lb; t < lb + nl; t += per) {
+      const int nt = std::min(per, lb + nl - t);
+      int rows = 0;
+      for (int u = 0; u < nt; ++u) {
+        H2_REQUIRE(leaf_m[t + u] <= 64, "far-only summation needs leaves of at most 64 points");
+        rows += leaf_m[t + u];
+      }
       const int64_t slot0 = p.n_parts;
       for (int64_t sidx = 0; sidx < S; ++sidx) {
         KsumItem it{};
         it.inst = i;
-        it.rows = leaf_m[t];
+        it.rows = rows;
         it.row0 = leaf_row[t];
         it.c0 = c0[q];
         it.task = t;
         it.lb0 = lb + (int)((nl * sidx) / S);
         it.lb1 = lb + (int)((nl * (sidx + 1)) / S);
         it.part = S > 1 ? (int)(p.n_parts++) : -1;
-        all.push_back({(int64_t)(it.lb1 - it.lb0) * it.rows, it});
+        all.push_back({(int64_t)(it.lb1 - it.lb0) * rows, it});
       }
-      if (S > 1) p.reds.push_back({i, leaf_m[t], leaf_row[t], c0[q], slot0, (int)S});
+      if (S > 1) p.reds.push_back({i, rows, leaf_row[t], c0[q], slot0, (int)S});
     }
   }
   std::stable_sort(all.begin(), all.end(),
@@ -534,8 +540,35 @@ KsumPlan plan_ksum_far(const std::vector<int64_t> &leaf_row, const std::vector<i
   return p;
 }
 
-void run_ksum32(int kid, const KsumPlan &plan, const KsumArgs32 &a, cudaStream_t s, bool far) {
+void run_ksum32(int kid, const KsumPlan &plan, const KsumArgs32 &a, cudaStream_t s, bool far,
+                bool tensor_cores) {
   if (plan.items.empty()) return;
+  if (tensor_cores) {
+    H2_REQUIRE(tc_sketch_supported(plan.dc) && plan.tile_rows == 128,
+               "tensor-core sketch needs 16/32 columns and 128-row tiles");
+    StagedPlan<float> sp;
+    stage_plan(plan, sp, s);
+    DBuf<int> err;
+    err.alloc_zero(1, s);
+    KsumArgs32 b = a;
+    b.items = sp.items.p;
+    b.partial = sp.partial.p;
+    b.err = err.p;
+    {
+      KernelEvents ev(s);
+      launch_ksum_tc(kid, plan, b, far, s);
+      ev.stop();
+    }
+    if (!plan.reds.empty()) {
+      k_ksum_reduce<float><<<(int)plan.reds.size(), 256, 0, s>>>(sp.reds.p, sp.partial.p, b.y, b.ld,
+                                                                plan.tile_rows, plan.dc);
+      count_launch();
+      H2_CHECK_LAUNCH();
+    }
+    if (to_host(err.p, 1, s)[0])
+      throw Error{H2_ERR_CUDA, "tensor-core sketch: an mbarrier wait timed out"};
+    return;
+  }
   dispatch_kernel(kid, [&](auto K) {
     constexpr int KID = decltype(K)::value;
     auto go = [&](auto F) {

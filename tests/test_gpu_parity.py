@@ -88,7 +88,7 @@ def test_entry_block(kernel, params, dim):
 
 
 @pytest.mark.parametrize("kernel,params,dim", KCASES)
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed", 2e-5)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed", 2e-5), ("mixed_simt", 2e-5)])
 def test_ksum_sketch(kernel, params, dim, prec, tol):
     n = 3001  # ragged against every tile size
     X = W.uniform_points(n, dim, 4)
@@ -105,7 +105,7 @@ def test_ksum_sketch_full_size_sampled():
     om = w.omega(32)
     rows = np.random.default_rng(1).integers(0, w.n, 48)
     want = O.ksum_rows(X, w.kernel, w.params, om, rows)
-    for prec, tol in (("fp64", 1e-12), ("mixed", 1e-5)):
+    for prec, tol in (("fp64", 1e-12), ("mixed", 1e-5), ("mixed_simt", 1e-5)):
         got = api.ksum_sketch(gpu(X), w.kernel, w.params, gpu(om), prec=prec).cpu().numpy()[rows]
         assert np.linalg.norm(got - want) / np.linalg.norm(want) <= tol
 
