@@ -226,6 +226,7 @@ struct Builder {
   std::vector<double> tols;
   DBuf<int32_t> cb, ce;             // per-instance column range of the current pass
   DBuf<double> om_stage;            // FP64 staging of new Omega columns (mixed / callbacks)
+  DBuf<float> om_hi, om_lo;         // TF32 parts of the level-1 Omega panel (tensor-core sketch)
   int64_t sketch_pairs = 0, sketch_cols = 0;
   std::vector<int64_t> near_pairs;   // per instance: sum of m_t * m_b over its near list
   double sketch_flops = 0;
@@ -415,6 +416,13 @@ struct Builder {
       else
         philox_gaussian64(om64 + b, N, H->orig_of_pos.p + b, n, c0, c0 + nc, o.seed, s);
       if (!fp64()) convert_cols_to32(om64, N, b, n, c0, c0 + nc, L.Om32.p, s);
+      if (H->tensor_sketch) {
+        if (!om_hi.p) {
+          om_hi.alloc((size_t)N * o.d_max);
+          om_lo.alloc((size_t)N * o.d_max);
+        }
+        split_tf32(L.Om32.p, N, b, n, c0, c0 + nc, om_hi.p, om_lo.p, s);
+      }
     }
     bool far = far_only && o.sketch == H2_SKETCH_KSUM && L.max_m <= 64;
     if (o.sketch == H2_SKETCH_KSUM) {
@@ -440,7 +448,7 @@ struct Builder {
           run_ksum64(H->kid, plan, a, s, far);
         } else {
           KsumArgs32 a{far_lists(), p32(), L.Om32.p, L.Y32.p, N, H->inst_dev.p, nullptr, nullptr,
-                       nullptr};
+                       nullptr, om_hi.p, om_lo.p};
           run_ksum32(H->kid, plan, a, s, far, tc);
         }
         done += dc;
@@ -881,6 +889,8 @@ struct Builder {
       L.Jtmp.release(); L.skeltmp.release(); L.conv.release();
     }
     om_stage.release();
+    om_hi.release();
+    om_lo.release();
     fill_stats(launches0);
     H->converged = not_conv.empty();
     return H->converged ? H2_OK : H2_ERR_NOT_CONVERGED;
@@ -1286,13 +1296,18 @@ h2_status h2_ksum_sketch(const double *points, int64_t n, int dim, int kernel_id
     std::vector<int64_t> nn = {n}, bb = {0};
     std::vector<int> insts = {0};
     int done = 0;
-    DBuf<float> xh, yh, zh, xl, yl, zl, om32, y32;
+    DBuf<float> xh, yh, zh, xl, yl, zl, om32, y32, omh, oml;
     if (!f64) {
       xh.alloc(n); yh.alloc(n); zh.alloc(n); xl.alloc(n); yl.alloc(n); zl.alloc(n);
       split_coords32(px.p, py.p, pz.p, n, xh.p, yh.p, zh.p, xl.p, yl.p, zl.p, st);
       om32.alloc((size_t)n * d);
       y32.alloc((size_t)n * d);
       convert32(om_c.p, (int64_t)n * d, om32.p, st);
+      if (prec == H2_PREC_MIXED) {
+        omh.alloc((size_t)n * d);
+        oml.alloc((size_t)n * d);
+        split_tf32(om32.p, n, 0, n, 0, d, omh.p, oml.p, st);
+      }
     }
     H2_REQUIRE(d % 8 == 0, "d must be a multiple of 8");
     while (done < d) {
@@ -1304,7 +1319,7 @@ h2_status h2_ksum_sketch(const double *points, int64_t n, int dim, int kernel_id
         run_ksum64(kernel_id, plan, a, st);
       } else {
         KsumArgs32 a{FarLists{}, Points32{xh.p, yh.p, zh.p, xl.p, yl.p, zl.p}, om32.p, y32.p, n, idev.p,
-                     nullptr, nullptr, nullptr};
+                     nullptr, nullptr, nullptr, omh.p, oml.p};
         run_ksum32(kernel_id, plan, a, st, false, prec == H2_PREC_MIXED && tc_sketch_supported(dc));
       }
       done += dc;

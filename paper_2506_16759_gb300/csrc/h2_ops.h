@@ -74,6 +74,8 @@ struct KsumArgs32 {
   const KsumItem *items;
   float *partial;
   int *err;          // set by the tensor-core kernel if a wait timed out
+  const float *om_hi;  // TF32 parts of om (tensor-core kernel), same layout
+  const float *om_lo;
 };
 
 // Plans a launch covering, for every listed instance, all its rows and
@@ -99,6 +101,9 @@ void run_ksum64(int kid, const KsumPlan &plan, const KsumArgs64 &a, cudaStream_t
 // tensor_cores: use the tcgen05 kernel (16 or 32 columns, 128-row tiles).
 void run_ksum32(int kid, const KsumPlan &plan, const KsumArgs32 &a, cudaStream_t s,
                 bool far = false, bool tensor_cores = false);
+// TF32 split hi = rna(x), lo = rna(x - hi) of rows [row0, row0+n), columns [c0, c1).
+void split_tf32(const float *x, int64_t ld, int64_t row0, int64_t n, int c0, int c1, float *hi,
+                float *lo, cudaStream_t s);
 // tcgen05 launch of a staged plan (sketch_tc.cu).
 bool tc_sketch_supported(int ncols);
 void launch_ksum_tc(int kid, const KsumPlan &plan, const KsumArgs32 &a, bool far, cudaStream_t s);
