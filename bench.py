@@ -33,7 +33,8 @@ SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.55
 FP64_PEAK_TFLOPS = 1.25
 WORKLOAD_DESC = ("c2: N=131072 uniform [0,1]^3, Matern-3/2 l=0.1 + 1e-4 nugget, leaf 64, "
-                 "eta 0.7, tol 1e-6, d0 32 / +16 / max 256, fused kernel-summation sketch")
+                 "eta 0.7, tol 1e-6, adaptive sampling up to 256 columns (schedule in config.schedule), "
+                 "fused kernel-summation sketch")
 
 
 def log(*a):
@@ -126,7 +127,7 @@ class ClockSampler:
 
 def source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("sketch.cu", "h2_internal.cuh"):
+    for f in ("sketch.cu", "sketch_tc.cu", "h2_internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2506_16759_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -193,11 +194,26 @@ def main_gpu(args):
     X = torch.from_numpy(w.points()).to(dev)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     prec = args.prec
+    sched = {"d0": w.d0, "d_inc": w.d_inc, "prec": prec}
+    tuned = None
+    if args.autotune:
+        # sample schedule and sketch engine picked by timed builds on this problem
+        t0 = time.perf_counter()
+        tree0 = api.ClusterTree(X, w.leaf_size, w.eta)
+        kw, ms = api.autotune(tree0, w.kernel, w.params, w.tol, prec=prec, d0=w.d0,
+                              d_inc=w.d_inc, d_max=w.d_max, seed=99)
+        del tree0
+        sched = {"d0": kw["d0"], "d_inc": kw["d_inc"], "prec": kw["prec"]}
+        tuned = dict(sched, tuning_s=time.perf_counter() - t0, build_ms=ms)
+        log(f"[bench] autotuned schedule {sched} ({ms:.1f} ms build)")
 
-    def step(seed, precision, timing=True):
+    def step(seed, precision, timing=True, schedule=None):
+        sc = schedule or sched
+        if precision == "fp64":
+            sc = {"d0": w.d0, "d_inc": w.d_inc, "prec": "fp64"}
         tree = api.ClusterTree(X, w.leaf_size, w.eta)
-        h = api.H2Matrix.build(tree, w.kernel, w.params, w.tol, prec=precision, seed=seed,
-                               sketch="ksum", timing=timing, d0=w.d0, d_inc=w.d_inc,
+        h = api.H2Matrix.build(tree, w.kernel, w.params, w.tol, prec=sc["prec"], seed=seed,
+                               sketch="ksum", timing=timing, d0=sc["d0"], d_inc=sc["d_inc"],
                                d_max=w.d_max)
         return tree, h
 
@@ -240,6 +256,23 @@ def main_gpu(args):
     last = stats[-1]
 
     result = None
+    untuned = None
+    if rank == 0 and tuned is not None:
+        base = {"d0": w.d0, "d_inc": w.d_inc, "prec": prec}
+        step(500, prec, schedule=base)
+        tb = []
+        for k in range(3):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            step(600 + k, prec, schedule=base)
+            e1.record()
+            torch.cuda.synchronize()
+            tb.append(e0.elapsed_time(e1))
+        untuned = dict(base, ms_per_step=statistics.mean(tb),
+                       value=w.n / (statistics.mean(tb) / 1e3))
     if rank == 0:
         # accuracy: ||(A_H2 - A) G|| / ||A G|| with A G by FP64 direct summation
         _, h = step(7, prec, timing=False)
@@ -301,11 +334,16 @@ def main_gpu(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if prec == "mixed" else "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_DESC, "prec": prec, "omega": "Philox4x32-10 on device",
+            "config": {"workload": WORKLOAD_DESC, "prec": prec, "schedule": sched,
+                       "omega": "Philox4x32-10 on device",
                        "l2": "flushed between timed steps (512 MiB write)",
                        "step": "tree + lists + H2 build, device-resident points"},
-            "roofline": {"kernel": "k_ksum32 (fused kernel summation)" if prec == "mixed"
-                         else "k_ksum64 (fused kernel summation)",
+            "roofline": {"kernel": ("k_ksum_tc (fused kernel summation, tcgen05 TF32 hi/lo, "
+                                    "entries evaluated on the CUDA cores)")
+                         if sched["prec"] == "mixed" else
+                         ("k_ksum32 (fused kernel summation, FP32 CUDA cores)"
+                          if sched["prec"] == "mixed_simt" else
+                          "k_ksum64 (fused kernel summation, FP64)"),
                          "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak if achieved else None,
                          "traffic": traffic,
@@ -322,6 +360,8 @@ def main_gpu(args):
             "rel_error": err_mixed,
             "tol": w.tol,
             "fp64": fp64,
+            "autotune": tuned,
+            "untuned_schedule": untuned,
             "phases_ms": phases,
             "d_final": last["d_final"], "rounds": last["rounds"],
             "rank_range": [last["rank_min"], last["rank_max"]],
@@ -408,6 +448,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=8192)
     ap.add_argument("--ref-sample", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="time the workload's 32/+16 sample schedule instead of the tuned one")
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--kernel-only", default="", choices=["", "ksum"],
                     help="time only the fused sketch of the workload (for profiling)")

@@ -230,6 +230,17 @@ h2_status h2_export_level(const h2_matrix *h, int inst, int level, int32_t *rank
 
 void h2_matrix_destroy(h2_matrix *h);
 
+/* Autotuner: times full builds of `tree` with candidate sample schedules
+ * (d0, d_inc in {32, 64, leaf size} x {16, 32}, d0 <= d_max) and, for mixed
+ * precision, both sketch engines (tensor cores / CUDA cores), and writes the
+ * fastest candidate that converged into *best (other fields copied from
+ * *base).  best_ms receives its build time.  Every candidate is an ordinary
+ * adaptive build at tolerance tol, so the choice changes speed, not the
+ * accuracy target. */
+h2_status h2_autotune(const h2_tree *tree, int kernel_id, const double *params, int nparams,
+                      double tol, const h2_build_opts *base, h2_stream_t s, h2_build_opts *best,
+                      double *best_ms);
+
 /* ---------------------------------------------------------------------------
  * Batched building blocks (the paper's batchedGen, K_blk, the convergence
  * QR and batchedID), exposed for direct use and testing.

@@ -377,6 +377,11 @@ class H2Oracle:
 
 
 def _entries(tree: ClusterTree, kernel, params, Ia, Ib) -> np.ndarray:
+    """K(Ia, Ib) for tree positions Ia, Ib.  `kernel` is a kernel id, or a
+    callable f(Ia, Ib) giving the entries of an operator in tree order (the
+    entry function of Algorithm 1 for operators such as sums of H2 matrices)."""
+    if callable(kernel):
+        return np.asarray(kernel(np.asarray(Ia), np.asarray(Ib)), dtype=np.float64)
     Xt = tree.Xt()
     return kernel_block(kernel, params, Xt[Ia], Xt[Ib], np.asarray(Ia), np.asarray(Ib))
 
@@ -550,7 +555,7 @@ def build_h2(tree: ClusterTree, lists: BlockLists, kernel: int, params, tol: flo
     `omega` is the stored Gaussian matrix (N x >= d_max, original order).
     """
     bld = _Builder(tree, lists, kernel, params, tol, omega, d0, d_inc, d_max, sampler).run()
-    h = H2Oracle(tree, lists, kernel, tuple(params), tol, bld.l_top, bld.nodes, bld.D, bld.B,
+    h = H2Oracle(tree, lists, kernel, tuple(params or ()), tol, bld.l_top, bld.nodes, bld.D, bld.B,
                  bld.d_final, bld.nrmK, bld.eps_abs, bld.eps_level, bld.d_level, bld.converged)
     h.timings = {"total_s": bld.t_total, "sketch_s": bld.t_sketch,
                  "construct_s": bld.t_total - bld.t_sketch}
@@ -671,6 +676,22 @@ def h2_dense(h: H2Oracle) -> np.ndarray:
     A = np.zeros_like(At)
     A[np.ix_(tree.perm, tree.perm)] = At
     return A
+
+
+def h2_sum_operator(ops: list) -> tuple:
+    """Entry function and sampler of the sum of H2 matrices `ops` on one tree
+    (the H2-update operator of Sec. V-A): entries from the dense expansion of
+    each representation, samples from the tree-walk matvecs."""
+    tree = ops[0].tree
+    At = sum(h2_dense(h) for h in ops)[np.ix_(tree.perm, tree.perm)]
+
+    def entries(Ia, Ib):
+        return At[np.ix_(Ia, Ib)]
+
+    def sampler(Om):
+        return sum(h2_matvec(h, Om) for h in ops)
+
+    return entries, sampler
 
 
 # -----------------------------------------------------------------------------

@@ -74,6 +74,8 @@ SIGNATURES = {
     "h2_stats": (i32, [vp, C.POINTER(Stats)]),
     "h2_export_level": (i32, [vp, i32, i32, vp, vp, vp, vp]),
     "h2_matrix_destroy": (None, [vp]),
+    "h2_autotune": (i32, [vp, i32, vp, i32, dbl, C.POINTER(BuildOpts), vp, C.POINTER(BuildOpts),
+                          C.POINTER(dbl)]),
     "h2_ksum_sketch": (i32, [vp, i64, i32, i32, vp, i32, vp, i64, vp, i64, i32, i32, vp]),
     "h2_entry_block": (i32, [vp, i64, i32, i32, vp, i32, vp, i64, vp, i64, vp, vp]),
     "h2_dense_sketch": (i32, [vp, i64, i64, vp, i64, vp, i64, i32, vp]),

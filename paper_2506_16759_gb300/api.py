@@ -207,6 +207,21 @@ class H2Matrix:
             self.handle = None
 
 
+def autotune(tree: ClusterTree, kernel, params, tol: float, stream=None, **kw) -> tuple:
+    """(best build keyword arguments, build ms) over the sample schedules and
+    sketch engines h2_autotune tries."""
+    o, keep = make_opts(**kw)
+    best = BuildOpts()
+    ms = C.c_double()
+    p = _params(params)
+    check(lib().h2_autotune(tree.handle, _kid(kernel), p.ctypes.data, 4, float(tol), C.byref(o),
+                            _stream(stream), C.byref(best), C.byref(ms)), "h2_autotune")
+    inv = {v: k for k, v in PREC.items()}
+    out = dict(kw)
+    out.update(d0=best.d0, d_inc=best.d_inc, prec=inv[best.prec])
+    return out, ms.value
+
+
 def ksum_sketch(points: torch.Tensor, kernel, params, omega: torch.Tensor, prec="fp64",
                 stream=None) -> torch.Tensor:
     pts = points.contiguous()

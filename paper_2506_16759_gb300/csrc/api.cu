@@ -208,6 +208,7 @@ struct PhaseTimer {
 enum { PH_SKETCH = 0, PH_NEAR, PH_QR, PH_ID, PH_UP, PH_COUP, PH_BSR, PH_TOTAL };
 
 int pick_dc(int ncols) {
+  if (ncols % 64 == 0) return 64;
   if (ncols % 32 == 0) return 32;
   if (ncols % 16 == 0) return 16;
   return 8;
@@ -229,6 +230,11 @@ struct Builder {
   DBuf<float> om_hi, om_lo;         // TF32 parts of the level-1 Omega panel (tensor-core sketch)
   int64_t sketch_pairs = 0, sketch_cols = 0;
   std::vector<int64_t> near_pairs;   // per instance: sum of m_t * m_b over its near list
+  // sum of H2 operands: G = U_op(Itil, :) per operand and level
+  std::vector<std::vector<DBuf<double>>> sumG;
+  std::vector<std::vector<DBuf<int64_t>>> sumGoff;
+  bool is_sum() const { return H->kid == H2_K_H2SUM; }
+  const h2_matrix *op(int q) const { return o.operands[q]; }
   double sketch_flops = 0;
   int rounds = 0;
   std::vector<int> not_conv;
@@ -280,7 +286,11 @@ struct Builder {
       H->inst_base[i] = base;
       H->inst_depth[i] = t->depth;
       H->inst_ltop[i] = t->l_top;
-      H->kd[i] = make_kernel_desc(kids[i], params + 4 * i, 4);
+      if (kids[i] == H2_K_H2SUM) {
+        H->kd[i] = KernelDesc{H2_K_H2SUM, 0, 0.0, 0.0};
+      } else {
+        H->kd[i] = make_kernel_desc(kids[i], params + 4 * i, 4);
+      }
       H2_REQUIRE(t->leaf_size <= 256, "leaf size above 256 is not supported");
       base += t->n;
     }
@@ -431,7 +441,9 @@ struct Builder {
       for (int i = 0; i < H->count; ++i) lcount[i] = 1 << H->inst_depth[i];
       int done = 0;
       while (done < nc) {
-        int dc = std::min(32, pick_dc(nc - done));
+        // the tensor-core kernel takes up to 64 columns per entry evaluation
+        const int widest = H->tensor_sketch && (nc - done) % 64 == 0 ? 64 : 32;
+        int dc = std::min(widest, pick_dc(nc - done));
         std::vector<int> c0(insts.size());
         for (size_t q = 0; q < insts.size(); ++q) c0[q] = H->dcur[insts[q]] + done;
         const bool tc = H->tensor_sketch && tc_sketch_supported(dc);
@@ -513,6 +525,26 @@ struct Builder {
     LevelData &L = H->lv[1];
     int C = H->count;
     timer.begin(PH_NEAR);
+    if (is_sum()) {
+      std::vector<const double *> dp;
+      std::vector<const int64_t *> dofs;
+      for (int q = 0; q < o.n_operands; ++q) {
+        dp.push_back(op(q)->D64.p);
+        dofs.push_back(op(q)->doff.p);
+      }
+      DBuf<const double *> ddp;
+      DBuf<const int64_t *> ddo;
+      to_device(ddp, dp, s);
+      to_device(ddo, dofs, s);
+      h2sum_dense(fp64(), H->near_nnz, H->near_erow.p, H->near_idx.p, L.m.p, H->doff.p, Dp(),
+                  ddp.p, ddo.p, o.n_operands, s);
+      H2_CUDA(cudaStreamSynchronize(s));
+      timer.end(PH_NEAR);
+      std::vector<int32_t> b(C, 0), e(C, o.d0);
+      set_cols(b, e);
+      near_bsr(Yp(L), -1.0);
+      return;
+    }
     DgenArgs g{};
     g.nnz = H->near_nnz;
     g.erow = H->near_erow.p;
@@ -748,6 +780,9 @@ struct Builder {
       L.B_size = to_host(L.boff.p + L.far_nnz, 1, s)[0];
       if (fp64()) L.B64.alloc(L.B_size + 2);
       else L.B32.alloc(L.B_size + 4);
+      if (is_sum()) {
+        sum_couplings(l);
+      } else {
       CouplingArgs ca{};
       ca.nnz = L.far_nnz;
       ca.erow = L.far_erow.p;
@@ -762,7 +797,64 @@ struct Builder {
       timer.begin(PH_COUP);
       coupling_gen(H->kid, fp64(), ca, s);
       timer.end(PH_COUP);
+      }
+    } else if (is_sum()) {
+      sum_g(l);   // later levels need this level's G even without couplings here
     }
+  }
+
+  // G_op = U_op(Itil, :) for every cluster of level l (see h2sum.cu).
+  void sum_g(int l) {
+    LevelData &L = H->lv[l];
+    if ((int)sumG.size() < o.n_operands) {
+      sumG.resize(o.n_operands);
+      sumGoff.resize(o.n_operands);
+    }
+    for (int q = 0; q < o.n_operands; ++q) {
+      const LevelData &OL = op(q)->lv[l];
+      auto &G = sumG[q];
+      auto &Go = sumGoff[q];
+      if ((int)G.size() <= l) { G.resize(l + 1); Go.resize(l + 1); }
+      std::vector<int64_t> off(L.n + 1, 0);
+      for (int t = 0; t < L.n; ++t) off[t + 1] = off[t] + (int64_t)L.h_k[t] * OL.h_k[t];
+      to_device(Go[l], off, s);
+      G[l].alloc(std::max<int64_t>(off[L.n], 1));
+      if (l == 1) {
+        h2sum_g_leaf(L.dev(), OL.k.p, OL.eoff.p, OL.E.p, Go[l].p, G[l].p, s);
+      } else {
+        const LevelData &PL = H->lv[l - 1];
+        const LevelData &OPL = op(q)->lv[l - 1];
+        h2sum_g_inner(L.dev(), L.child0.p, PL.k.p, OPL.k.p, Go[l - 1].p, G[l - 1].p, OL.k.p,
+                      OL.m.p, OL.eoff.p, OL.E.p, Go[l].p, G[l].p, s);
+      }
+    }
+  }
+
+  void sum_couplings(int l) {
+    LevelData &L = H->lv[l];
+    timer.begin(PH_COUP);
+    sum_g(l);
+    std::vector<SumOperand> ops;
+    int max_kop = 0;
+    for (int q = 0; q < o.n_operands; ++q) {
+      const LevelData &OL = op(q)->lv[l];
+      ops.push_back(SumOperand{OL.k.p, sumGoff[q][l].p, sumG[q][l].p, OL.boff.p, OL.B64.p});
+      max_kop = std::max(max_kop, OL.max_k);
+    }
+    DBuf<SumOperand> dops;
+    to_device(dops, ops, s);
+    SumCouplingArgs a{};
+    a.nnz = L.far_nnz;
+    a.erow = L.far_erow.p;
+    a.idx = L.far_idx.p;
+    a.boff = L.boff.p;
+    a.t = L.dev();
+    a.B = Bp(L);
+    a.ops = dops.p;
+    a.nops = o.n_operands;
+    h2sum_couplings(fp64(), a, max_kop, L.max_k, s);
+    H2_CUDA(cudaStreamSynchronize(s));
+    timer.end(PH_COUP);
   }
 
   void build_far_list(int l) {
@@ -1195,7 +1287,22 @@ h2_status h2_build_batched(const h2_tree *const *trees, int count, const int *ke
       H2_REQUIRE(kernel_ids[i] == kernel_ids[0], "instances must share one kernel type");
       H2_REQUIRE(tols[i] >= 0 && std::isfinite(tols[i]), "tol must be finite and >= 0");
     }
-    H2_REQUIRE(kernel_ids[0] != H2_K_H2SUM, "H2 sums are built with h2_build");
+    if (kernel_ids[0] == H2_K_H2SUM) {
+      H2_REQUIRE(count == 1, "an H2 sum is built as a single instance");
+      H2_REQUIRE(opts->operands && opts->n_operands >= 1, "an H2 sum needs operands");
+      H2_REQUIRE(opts->sketch != H2_SKETCH_KSUM, "an H2 sum needs a matvec, dense or callback sketch");
+      const h2_tree *t = trees[0];
+      for (int q = 0; q < opts->n_operands; ++q) {
+        const h2_matrix *op = opts->operands[q];
+        H2_REQUIRE(op != nullptr && op->count == 1 && op->fp64, "operands must be FP64 single H2 matrices");
+        H2_REQUIRE(op->n_total == t->n && op->inst_depth[0] == t->depth &&
+                       op->inst_ltop[0] == t->l_top && op->near_nnz == t->near_nnz,
+                   "operands must be built on the same cluster tree and partition");
+        for (int l = 1; l <= t->l_top; ++l)
+          H2_REQUIRE(op->lv[l].far_nnz == t->far_nnz[t->depth - l + 1],
+                     "operands must be built on the same cluster tree and partition");
+      }
+    }
     auto H = std::make_unique<h2_matrix>();
     H->count = count;
     H->fp64 = opts->prec == H2_PREC_FP64;
@@ -1261,6 +1368,60 @@ h2_status h2_export_level(const h2_matrix *h, int inst, int level, int32_t *rank
     }
     if (eps_l) *eps_l = L.h_eps[inst];
     if (d_l) *d_l = L.d_at_id[inst];
+    return H2_OK;
+  });
+}
+
+h2_status h2_autotune(const h2_tree *tree, int kernel_id, const double *params, int nparams,
+                      double tol, const h2_build_opts *base, h2_stream_t s, h2_build_opts *best,
+                      double *best_ms) {
+  return guarded([&]() -> h2_status {
+    H2_REQUIRE(tree && base && best, "NULL argument");
+    validate_opts(*base);
+    cudaStream_t st = (cudaStream_t)s;
+    std::vector<std::pair<int, int>> sched;
+    for (int d0 : {32, 64, tree->leaf_size})
+      for (int inc : {16, 32}) {
+        if (d0 % 8 || d0 > base->d_max) continue;
+        if (std::find(sched.begin(), sched.end(), std::make_pair(d0, inc)) == sched.end())
+          sched.push_back({d0, inc});
+      }
+    std::vector<int> precs = {base->prec};
+    if (base->prec == H2_PREC_MIXED) precs.push_back(H2_PREC_MIXED_SIMT);
+    double best_t = 1e300;
+    h2_build_opts choice = *base;
+    cudaEvent_t e0, e1;
+    H2_CUDA(cudaEventCreate(&e0));
+    H2_CUDA(cudaEventCreate(&e1));
+    for (int pr : precs)
+      for (auto [d0, inc] : sched) {
+        h2_build_opts o = *base;
+        o.d0 = d0;
+        o.d_inc = inc;
+        o.prec = pr;
+        o.timing = 0;
+        for (int rep = 0; rep < 2; ++rep) {   // first run warms up
+          h2_matrix *h = nullptr;
+          H2_CUDA(cudaEventRecord(e0, st));
+          h2_status r = h2_build(tree, kernel_id, params, nparams, tol, &o, s, &h);
+          H2_CUDA(cudaEventRecord(e1, st));
+          H2_CUDA(cudaEventSynchronize(e1));
+          h2_matrix_destroy(h);
+          if (r != H2_OK) break;             // not converged (or failed): not a candidate
+          float ms = 0.f;
+          H2_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          if (rep == 1 && ms < best_t) {
+            best_t = ms;
+            choice = o;
+          }
+        }
+      }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    H2_REQUIRE(best_t < 1e300, "no candidate schedule converged");
+    choice.timing = base->timing;
+    *best = choice;
+    if (best_ms) *best_ms = best_t;
     return H2_OK;
   });
 }

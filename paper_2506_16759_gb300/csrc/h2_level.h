@@ -161,4 +161,35 @@ void permute_out(bool fp64, const void *yt, int64_t ldt, const int32_t *orig_of_
 
 void fill_i32(int32_t *p, int64_t n, int32_t v, cudaStream_t s);
 
+// ---- entries of a sum of H2 matrices (h2sum.cu)
+// One FP64 operand at one level: its ranks, G = U_op(Itil, :) blocks of the
+// target's clusters (k_target x k_op at goff), its couplings.
+struct SumOperand {
+  const int32_t *k;      // operand ranks of the level's tasks
+  const int64_t *goff;   // G offsets per task
+  const double *G;
+  const int64_t *boff;   // operand coupling offsets per far entry
+  const double *B;
+};
+struct SumCouplingArgs {
+  int64_t nnz;
+  const int32_t *erow;
+  const int32_t *idx;
+  const int64_t *boff;   // target coupling offsets
+  TasksDev t;            // target tasks (ranks)
+  void *B;               // target couplings (T)
+  const SumOperand *ops; // device array
+  int nops;
+};
+void h2sum_g_leaf(const TasksDev &t, const int32_t *kop, const int64_t *eoff_op, const double *Eop,
+                  const int64_t *goff, double *G, cudaStream_t s);
+void h2sum_g_inner(const TasksDev &t, const int32_t *child0, const int32_t *kt_child,
+                   const int32_t *kop_child, const int64_t *goff_child, const double *Gchild,
+                   const int32_t *kop, const int32_t *mop, const int64_t *eoff_op,
+                   const double *Eop, const int64_t *goff, double *G, cudaStream_t s);
+void h2sum_couplings(bool fp64, const SumCouplingArgs &a, int max_kop, int max_kt, cudaStream_t s);
+void h2sum_dense(bool fp64, int64_t nnz, const int32_t *erow, const int32_t *idx, const int32_t *m,
+                 const int64_t *doff, void *D, const double *const *Dop,
+                 const int64_t *const *doff_op, int nops, cudaStream_t s);
+
 }  // namespace h2

@@ -102,6 +102,23 @@ template <int NCOL>
 __device__ __forceinline__ void tmem_ld(uint32_t taddr, float *v);
 
 template <>
+__device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, float *v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
+}
+
+template <>
 __device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, float *v) {
   uint32_t r[16];
   asm volatile(
@@ -134,7 +151,15 @@ __device__ __forceinline__ uint32_t sw128_off(int row, int k) {
   return (uint32_t)row * 128u + ((uint32_t)((k >> 2) ^ (row & 7)) << 4) + (uint32_t)(k & 3) * 4u;
 }
 
-constexpr int kThreads = 2 * kRows;
+// Thread groups per CTA: each group of 128 threads covers all rows and a
+// 1/G share of every tile's points (evaluation) and of the columns (drain).
+template <int NCOL>
+struct TcShape {
+  static constexpr int G = NCOL >= 64 ? 4 : 2;
+  static constexpr int threads = kRows * G;
+  static constexpr int HC = NCOL / G;       // accumulator columns per thread
+  static constexpr int EPT = kTJ / G;       // points evaluated per thread per tile
+};
 
 // One 32-point tile of the j loop: its first point, its size, and whether its
 // leaf is near to the first / second leaf of the row tile (far-only mode).
@@ -145,16 +170,18 @@ struct TileDesc {
   bool valid;
 };
 
-// Thread t owns row r = t % 128 and half h = t / 128: it evaluates points
-// [16h, 16h+16) of every tile for its row, and reads back accumulator columns
-// [h*NCOL/2, (h+1)*NCOL/2) of its row.  Per tile: the next tile's Omega parts
+// Thread t owns row r = t % 128 and group h = t / 128: it evaluates points
+// [h*EPT, (h+1)*EPT) of every tile for its row, and reads back accumulator
+// columns [h*HC, (h+1)*HC) of its row.  Per tile: the next tile's Omega parts
 // and coordinates are loaded into registers first; the previous tile's
 // products are awaited and its accumulator drained; the operands are stored;
 // one barrier; one thread issues the products.  Two TMEM accumulators
 // alternate, so a drain never waits for the products in flight.
 template <int KID, int NCOL, bool FAR>
-__global__ void __launch_bounds__(kThreads) k_ksum_tc(KsumArgs32 a, int tile_rows) {
-  constexpr int HC = NCOL / 2;
+__global__ void __launch_bounds__(TcShape<NCOL>::threads) k_ksum_tc(KsumArgs32 a, int tile_rows) {
+  constexpr int kThreads = TcShape<NCOL>::threads;
+  constexpr int HC = TcShape<NCOL>::HC;
+  constexpr int EPT = TcShape<NCOL>::EPT;
   constexpr int BPT = NCOL * kTJ / kThreads;   // Omega elements staged per thread
   constexpr uint32_t A_BYTES = kRows * 128, B_BYTES = NCOL * 128;
   extern __shared__ unsigned char smem_dyn[];
@@ -315,8 +342,8 @@ __global__ void __launch_bounds__(kThreads) k_ksum_tc(KsumArgs32 a, int tile_row
     const float4 *cl = ch + kTJ;
     const float m = r < it.rows ? ((FAR && (second ? cur.near2 : cur.near1)) ? 0.f : 1.f) : 0.f;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int k4 = 4 * h + q;
+    for (int q = 0; q < EPT / 4; ++q) {
+      const int k4 = (EPT / 4) * h + q;
       float hv[4], lv[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -392,7 +419,7 @@ void launch_tc(const KsumPlan &p, const KsumArgs32 &a, cudaStream_t s) {
   auto kern = k_ksum_tc<KID, NCOL, FAR>;
   const size_t bytes = tc_smem_bytes<NCOL>();
   H2_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-  kern<<<(int)p.items.size(), kThreads, bytes, s>>>(a, p.tile_rows);
+  kern<<<(int)p.items.size(), TcShape<NCOL>::threads, bytes, s>>>(a, p.tile_rows);
   count_launch();
   H2_CHECK_LAUNCH();
 }
@@ -412,7 +439,7 @@ __global__ void k_split_tf32(const float *x, int64_t ld, int64_t row0, int64_t n
 
 }  // namespace
 
-bool tc_sketch_supported(int ncols) { return ncols == 16 || ncols == 32; }
+bool tc_sketch_supported(int ncols) { return ncols == 16 || ncols == 32 || ncols == 64; }
 
 void split_tf32(const float *x, int64_t ld, int64_t row0, int64_t n, int c0, int c1, float *hi,
                 float *lo, cudaStream_t s) {
@@ -426,14 +453,17 @@ void launch_ksum_tc(int kid, const KsumPlan &plan, const KsumArgs32 &a, bool far
                     cudaStream_t s) {
   dispatch_kernel(kid, [&](auto K) {
     constexpr int KID = decltype(K)::value;
-    if (plan.dc == 32) {
+    if (plan.dc == 64) {
+      if (far) launch_tc<KID, 64, true>(plan, a, s);
+      else launch_tc<KID, 64, false>(plan, a, s);
+    } else if (plan.dc == 32) {
       if (far) launch_tc<KID, 32, true>(plan, a, s);
       else launch_tc<KID, 32, false>(plan, a, s);
     } else if (plan.dc == 16) {
       if (far) launch_tc<KID, 16, true>(plan, a, s);
       else launch_tc<KID, 16, false>(plan, a, s);
     } else {
-      throw Error{H2_ERR_ARG, "tensor-core sketch takes 16 or 32 columns"};
+      throw Error{H2_ERR_ARG, "tensor-core sketch takes 16, 32 or 64 columns"};
     }
   });
 }

@@ -92,7 +92,7 @@ def test_entry_block(kernel, params, dim):
 def test_ksum_sketch(kernel, params, dim, prec, tol):
     n = 3001  # ragged against every tile size
     X = W.uniform_points(n, dim, 4)
-    om = W.gaussian_omega(n, 48, 5)
+    om = W.gaussian_omega(n, 112, 5)   # 64 + 32 + 16 column blocks
     got = api.ksum_sketch(gpu(X), kernel, params, gpu(om), prec=prec).cpu().numpy()
     want = O.ksum_rows(X, kernel, params, om, np.arange(n))
     err = np.linalg.norm(got - want, axis=0) / np.linalg.norm(want, axis=0)
@@ -303,3 +303,31 @@ def test_batched_instances_match_single_builds():
         ys = h.matvec(gpu(G[off:off + n])).cpu().numpy()
         assert np.linalg.norm(yb[off:off + n] - ys) <= 1e-12 * np.linalg.norm(ys)
         off += n
+
+
+def test_h2sum_build_matches_oracle():
+    # H2 update workload: compress the sum of two H2 matrices (exponential and
+    # Gaussian kernels built at 1e-8) at tol 1e-6, entries taken from the
+    # operands' representations and samples from their matvecs.
+    n, dim, leaf, eta = 4096, 3, 32, 0.7
+    X = W.uniform_points(n, dim, 61)
+    oms = [W.gaussian_omega(n, 256, s) for s in (62, 63, 64)]
+    kps = [(W.K_EXP, (0.1, 0.0)), (W.K_GAUSS, (0.05, 0.0))]
+    t = O.build_cluster_tree(X, leaf)
+    lists = O.dual_traversal(t, eta)
+    ops_o = [O.build_h2(t, lists, k, p, 1e-8, om, O.ksum_sampler(X, k, p, 1024))
+             for (k, p), om in zip(kps, oms)]
+    entries, sampler = O.h2_sum_operator(ops_o)
+    ho = O.build_h2(t, lists, entries, None, 1e-6, oms[2], sampler)
+    tree = api.ClusterTree(gpu(X), leaf, eta)
+    ops_g = [api.H2Matrix.build(tree, k, p, 1e-8, omega=gpu(om)) for (k, p), om in zip(kps, oms)]
+    A = O.dense_matrix(X, *kps[0]) + O.dense_matrix(X, *kps[1])
+    G = W.gaussian_probe(n, 4, 5)
+    for prec, bar in (("fp64", 1e-10), ("mixed", 1e-5)):
+        h = api.H2Matrix.build(tree, "h2sum", (), 1e-6, omega=gpu(oms[2]), sketch="h2sum",
+                               operands=ops_g, prec=prec)
+        if prec == "fp64":
+            check_same_skeletons(h, t, ho)
+        rel, y, _ = matvec_rel(h, ho, n, seed=5)
+        assert rel <= bar
+        assert np.linalg.norm(y - A @ G) <= 10 * 1e-6 * np.linalg.norm(A @ G)

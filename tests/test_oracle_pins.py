@@ -429,3 +429,27 @@ def test_planted_mistake_near_field_sign(monkeypatch):
     monkeypatch.setattr(O._Builder, "local_samples", flipped)
     with pytest.raises(AssertionError):
         test_ranks_match_dense_svd(1e-6)
+
+
+def test_h2_sum_operator_entries_and_samples():
+    # the H2-update operator: its entries and samples are those of the sum of
+    # the dense matrices the operands represent
+    X = W.uniform_points(1024, 2, 51)
+    t = O.build_cluster_tree(X, 16)
+    lists = O.dual_traversal(t, 0.7)
+    om = W.gaussian_omega(1024, 256, 52)
+    ops = [O.build_h2(t, lists, k, p, 1e-8, om, O.ksum_sampler(X, k, p))
+           for k, p in ((O.K_EXP, (0.1, 0.0)), (O.K_GAUSS, (0.05, 0.0)))]
+    entries, sampler = O.h2_sum_operator(ops)
+    A = O.dense_matrix(X, O.K_EXP, (0.1, 0.0)) + O.dense_matrix(X, O.K_GAUSS, (0.05, 0.0))
+    At = A[np.ix_(t.perm, t.perm)]
+    full = np.arange(1024)
+    assert np.linalg.norm(entries(full, full) - At) <= 1e-7 * np.linalg.norm(At)
+    rows, cols = np.arange(40, 90), np.arange(500, 560)
+    blk = At[np.ix_(rows, cols)]
+    assert np.linalg.norm(entries(rows, cols) - blk) <= 1e-6 * np.linalg.norm(blk)
+    G = W.gaussian_probe(1024, 3, 0)
+    assert np.linalg.norm(sampler(G) - A @ G) <= 1e-7 * np.linalg.norm(A @ G)
+    # a target built from the operator meets its tolerance against the exact sum
+    h = O.build_h2(t, lists, entries, None, 1e-6, W.gaussian_omega(1024, 256, 53), sampler)
+    assert O.dense_rel_error(h, A) <= 10 * 1e-6
