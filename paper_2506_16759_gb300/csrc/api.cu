@@ -460,7 +460,7 @@ struct Builder {
           run_ksum64(H->kid, plan, a, s, far);
         } else {
           KsumArgs32 a{far_lists(), p32(), L.Om32.p, L.Y32.p, N, H->inst_dev.p, nullptr, nullptr,
-                       nullptr, om_hi.p, om_lo.p};
+                       nullptr, om_hi.p, om_lo.p, p64()};
           run_ksum32(H->kid, plan, a, s, far, tc);
         }
         done += dc;
@@ -1480,7 +1480,7 @@ h2_status h2_ksum_sketch(const double *points, int64_t n, int dim, int kernel_id
         run_ksum64(kernel_id, plan, a, st);
       } else {
         KsumArgs32 a{FarLists{}, Points32{xh.p, yh.p, zh.p, xl.p, yl.p, zl.p}, om32.p, y32.p, n, idev.p,
-                     nullptr, nullptr, nullptr, omh.p, oml.p};
+                     nullptr, nullptr, nullptr, omh.p, oml.p, Points64{px.p, py.p, pz.p}};
         run_ksum32(kernel_id, plan, a, st, false, prec == H2_PREC_MIXED && tc_sketch_supported(dc));
       }
       done += dc;

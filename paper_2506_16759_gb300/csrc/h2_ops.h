@@ -76,6 +76,7 @@ struct KsumArgs32 {
   int *err;          // set by the tensor-core kernel if a wait timed out
   const float *om_hi;  // TF32 parts of om (tensor-core kernel), same layout
   const float *om_lo;
+  Points64 p64;        // FP64 coordinates (tensor-core kernel: tile-relative offsets)
 };
 
 // Plans a launch covering, for every listed instance, all its rows and

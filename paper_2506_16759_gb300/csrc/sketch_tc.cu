@@ -3,9 +3,10 @@
 // The sketch of Algorithm 1 is a dense contraction over the point index j
 // whose left operand K(x_i, x_j) is generated on the fly.  Here each CTA owns
 // 128 rows (TMEM lanes) and NCOL sample columns; for every 32-point tile:
-//   * the entries are evaluated in FP32 (split hi/lo coordinates), split into
-//     TF32 parts hi = rna(x), lo = rna(x - hi), and stored into two
-//     128-byte-swizzled K-major tiles (A);
+//   * the entries are evaluated in FP32 from coordinates relative to the
+//     tile's first row (offsets formed in FP64), split into TF32 parts
+//     hi = rna(x), lo = x - hi, and stored into two 128-byte-swizzled
+//     K-major tiles (A);
 //   * the Omega tile, split the same way once when its columns are drawn,
 //     is copied into two K-major tiles (B);
 //   * one thread issues the three TF32 products hi*hi, hi*lo, lo*hi for the
@@ -151,6 +152,33 @@ __device__ __forceinline__ uint32_t sw128_off(int row, int k) {
   return (uint32_t)row * 128u + ((uint32_t)((k >> 2) ^ (row & 7)) << 4) + (uint32_t)(k & 3) * 4u;
 }
 
+// Entry from coordinates relative to a reference point of the row tile:
+// offsets are formed in FP64 and rounded once to FP32, so a distance carries
+// an absolute error of a few 2^-24 of the offsets (well below the TF32 split
+// for the far pairs summed here).  The root is taken as r2 * rsqrt(max(r2, tiny)).
+template <int KID>
+__device__ __forceinline__ float kval_rel(float dx, float dy, float dz, float scale, int pw,
+                                          float dot) {
+  if constexpr (KID == H2_K_POLY) {
+    return kval<KID, float>(dot, scale, pw);
+  } else {
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    if constexpr (KID == H2_K_GAUSS) {
+      return __expf(-r2 * scale);
+    } else if constexpr (KID == H2_K_LAPLACE_IE) {
+      return r2 > 0.f ? rsqrtf(r2) * scale : 0.f;
+    } else {
+      const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
+      if constexpr (KID == H2_K_EXP) {
+        return __expf(-r * scale);
+      } else {
+        const float a2 = r * scale;
+        return (1.f + a2) * __expf(-a2);
+      }
+    }
+  }
+}
+
 // Thread groups per CTA: each group of 128 threads covers all rows and a
 // 1/G share of every tile's points (evaluation) and of the columns (drain).
 template <int NCOL>
@@ -268,7 +296,11 @@ __global__ void __launch_bounds__(TcShape<NCOL>::threads) k_ksum_tc(KsumArgs32 a
 
   // ---- prefetch of a tile's Omega parts and coordinates into registers
   float bh[BPT], bl[BPT];
-  float c6[6];
+  float c6[3];
+  // reference point: the tile's first row (the origin for the polynomial kernel)
+  const double cx = KID == H2_K_POLY ? 0.0 : a.p64.x[it.row0];
+  const double cy = KID == H2_K_POLY ? 0.0 : a.p64.y[it.row0];
+  const double cz = KID == H2_K_POLY ? 0.0 : a.p64.z[it.row0];
   auto fetch = [&](const TileDesc &d) {
 #pragma unroll
     for (int u = 0; u < BPT; ++u) {
@@ -281,20 +313,18 @@ __global__ void __launch_bounds__(TcShape<NCOL>::threads) k_ksum_tc(KsumArgs32 a
     }
     if (t < kTJ) {
       const int64_t gj = d.j0 + (d.valid && t < d.nj ? t : 0);
-      c6[0] = a.pts.xh[gj]; c6[1] = a.pts.yh[gj]; c6[2] = a.pts.zh[gj];
-      c6[3] = a.pts.xl[gj]; c6[4] = a.pts.yl[gj]; c6[5] = a.pts.zl[gj];
+      c6[0] = (float)(a.p64.x[gj] - cx);
+      c6[1] = (float)(a.p64.y[gj] - cy);
+      c6[2] = (float)(a.p64.z[gj] - cz);
     }
   };
   auto store_coords = [&](int slot) {
-    if (t < kTJ) {
-      crd[slot * 2 * kTJ + t] = make_float4(c6[0], c6[1], c6[2], 0.f);
-      crd[slot * 2 * kTJ + kTJ + t] = make_float4(c6[3], c6[4], c6[5], 0.f);
-    }
+    if (t < kTJ) crd[slot * kTJ + t] = make_float4(c6[0], c6[1], c6[2], 0.f);
   };
 
   const int64_t g = it.row0 + (r < it.rows ? r : 0);
-  const float xh = a.pts.xh[g], yh = a.pts.yh[g], zh = a.pts.zh[g];
-  const float xl = a.pts.xl[g], yl = a.pts.yl[g], zl = a.pts.zl[g];
+  const float xr = (float)(a.p64.x[g] - cx), yr = (float)(a.p64.y[g] - cy),
+              zr = (float)(a.p64.z[g] - cz);
   const bool second = FAR && r >= m1;
   float acc[HC], cmp[HC];
 #pragma unroll
@@ -338,9 +368,9 @@ __global__ void __launch_bounds__(TcShape<NCOL>::threads) k_ksum_tc(KsumArgs32 a
       *reinterpret_cast<float *>(Bhi + off) = cbh[u];
       *reinterpret_cast<float *>(Blo + off) = cbl[u];
     }
-    const float4 *ch = crd + (k & 1) * 2 * kTJ;
-    const float4 *cl = ch + kTJ;
+    const float4 *ch = crd + (k & 1) * kTJ;
     const float m = r < it.rows ? ((FAR && (second ? cur.near2 : cur.near1)) ? 0.f : 1.f) : 0.f;
+    const bool full = cur.nj == kTJ;
 #pragma unroll
     for (int q = 0; q < EPT / 4; ++q) {
       const int k4 = (EPT / 4) * h + q;
@@ -348,12 +378,12 @@ __global__ void __launch_bounds__(TcShape<NCOL>::threads) k_ksum_tc(KsumArgs32 a
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int kk = 4 * k4 + u;
-        const float4 ph = ch[kk], pl = cl[kk];
-        float kv = kval<KID, float>(
-            geom32<KID>(xh, yh, zh, xl, yl, zl, ph.x, ph.y, ph.z, pl.x, pl.y, pl.z), scale, pw);
-        kv = kk < cur.nj ? kv * m : 0.f;
+        const float4 p = ch[kk];
+        float kv = kval_rel<KID>(xr - p.x, yr - p.y, zr - p.z, scale, pw,
+                                 xr * p.x + yr * p.y + zr * p.z);
+        kv = (full || kk < cur.nj) ? kv * m : 0.f;
         hv[u] = tf32_rna(kv);
-        lv[u] = tf32_rna(kv - hv[u]);
+        lv[u] = kv - hv[u];   // the tensor core keeps its leading TF32 bits
       }
       const uint32_t off = (uint32_t)r * 128u + ((uint32_t)(k4 ^ (r & 7)) << 4);
       *reinterpret_cast<float4 *>(Ahi + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
@@ -411,7 +441,7 @@ __global__ void __launch_bounds__(TcShape<NCOL>::threads) k_ksum_tc(KsumArgs32 a
 
 template <int NCOL>
 constexpr size_t tc_smem_bytes() {
-  return 1024 + 2 * kRows * 128 + 2 * NCOL * 128 + 4 * kTJ * sizeof(float4);
+  return 1024 + 2 * kRows * 128 + 2 * NCOL * 128 + 2 * kTJ * sizeof(float4);
 }
 
 template <int KID, int NCOL, bool FAR>
