@@ -224,22 +224,29 @@ def main_gpu(args):
     L = _lib.lib()
     clocks = ClockSampler(local) if rank == 0 else None
     launches0 = L.h2_kernel_launches()
-    times, stats = [], []
+    times = []
     for k in range(args.steps):
         flush.zero_()               # L2 flush between timed steps
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        tree, h = step(k, prec)
+        tree, h = step(k, prec, timing=False)
         e1.record()
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
-        stats.append(h.stats())
         del h, tree
     barrier()
     launches = L.h2_kernel_launches() - launches0
     clk = clocks.stop() if clocks else None
+    # phase breakdown and per-launch kernel times from instrumented builds of
+    # the same problem, after the timed region (the phase timers synchronise)
+    stats = []
+    for k in range(2):
+        flush.zero_()
+        tree, h = step(k, prec, timing=True)
+        stats.append(h.stats())
+        del h, tree
     total_ms = max_over_ranks(sum(times))
     ms_per_step = total_ms / args.steps
     value = world * w.n * args.steps / (total_ms / 1e3)
@@ -317,8 +324,9 @@ def main_gpu(args):
             e0.record()
             Xd = Xh.to(dev, non_blocking=True)
             tree = api.ClusterTree(Xd, w.leaf_size, w.eta)
-            h = api.H2Matrix.build(tree, w.kernel, w.params, w.tol, prec=prec, seed=k,
-                                   sketch="ksum", d0=w.d0, d_inc=w.d_inc, d_max=w.d_max)
+            h = api.H2Matrix.build(tree, w.kernel, w.params, w.tol, prec=sched["prec"], seed=k,
+                                   sketch="ksum", d0=sched["d0"], d_inc=sched["d_inc"],
+                                   d_max=w.d_max)
             ranks, skel, _, _ = h.export_level(1)       # device -> host read of the result
             e1.record()
             torch.cuda.synchronize()
@@ -410,14 +418,35 @@ def main_reference(args):
 
 
 def main_kernel_only(args):
-    """Only the fused sketch of the benchmark workload (N=131072, 32 columns,
-    same launch plan as inside a build): a small process for ncu captures."""
+    """Small processes for ncu captures.  "ksum": only the fused sketch of the
+    benchmark workload (N=131072, 32 columns, all points, same launch plan as
+    inside a build).  "build": whole builds of the same workload family at
+    --n points with the 64/+16 mixed schedule (its first k_ksum_tc launch is
+    the 64-column far-only sketch)."""
     import torch
 
     from paper_2506_16759_gb300 import api
     from paper_2506_16759_gb300 import workloads as W
     dev = torch.device("cuda:0")
     w = W.config("c2")
+    if args.kernel_only == "build":
+        w = W.scaled(w, args.n or w.n)
+        X = torch.from_numpy(w.points()).to(dev)
+        times = []
+        for k in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            tree = api.ClusterTree(X, w.leaf_size, w.eta)
+            h = api.H2Matrix.build(tree, w.kernel, w.params, w.tol, prec="mixed", seed=k,
+                                   sketch="ksum", d0=64, d_inc=16, d_max=w.d_max)
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                times.append((time.perf_counter() - t0) * 1e3)
+            st = h.stats()
+            del h, tree
+        print(json.dumps({"kernel_only": "build", "n": w.n, "ms": statistics.mean(times),
+                          "d_final": st["d_final"], "rank_max": st["rank_max"]}), flush=True)
+        return
     X = torch.from_numpy(w.points()).to(dev)
     om = torch.from_numpy(w.omega(32)).to(dev)
     times = []
@@ -451,8 +480,9 @@ def main():
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="time the workload's 32/+16 sample schedule instead of the tuned one")
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
-    ap.add_argument("--kernel-only", default="", choices=["", "ksum"],
-                    help="time only the fused sketch of the workload (for profiling)")
+    ap.add_argument("--kernel-only", default="", choices=["", "ksum", "build"],
+                    help="time only the fused sketch, or builds at --n points (for profiling)")
+    ap.add_argument("--n", type=int, default=0, help="point count for --kernel-only build")
     args = ap.parse_args()
     if args.kernel_only:
         main_kernel_only(args)

@@ -304,6 +304,11 @@ h2_status h2_batched_qr_mindiag_static(int count, const int32_t *m, const int32_
                                        const int64_t *off, const double *panels,
                                        double *mindiag, h2_stream_t s);
 
+/* The library keeps device blocks it freed for reuse (size buckets per
+ * device), so repeated builds avoid cudaMalloc/cudaFree; this synchronises
+ * the devices and returns those cached blocks to CUDA.  Handles stay valid. */
+void h2_trim_memory(void);
+
 /* CUDA kernels the library has launched from the calling host thread so far
  * (all entry points); a profiling aid. */
 int64_t h2_kernel_launches(void);

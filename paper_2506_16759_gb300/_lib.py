@@ -63,6 +63,7 @@ SIGNATURES = {
     "h2_default_opts": (None, [C.POINTER(BuildOpts)]),
     "h2_last_error": (C.c_char_p, []),
     "h2_kernel_launches": (C.c_int64, []),
+    "h2_trim_memory": (None, []),
     "h2_build_cluster_tree": (i32, [vp, i64, i32, i32, dbl, vp, C.POINTER(vp)]),
     "h2_tree_info": (i32, [vp, C.POINTER(TreeInfo)]),
     "h2_tree_export": (i32, [vp, vp, vp, vp, vp, vp]),

@@ -304,3 +304,8 @@ def batched_row_id(panels, eps, stream=None):
         Js.append(Jh[i, :kk].copy())
         Es.append(Eh[eoff[i]:eoff[i] + ms[i] * kk].reshape(kk, ms[i]).T.copy())
     return ks, Js, Es
+
+
+def trim_memory() -> None:
+    """Return the device blocks the library caches for reuse to CUDA."""
+    lib().h2_trim_memory()

@@ -7,6 +7,8 @@
 // next level (ranks), each read with one small device-to-host copy.
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <numeric>
 
 #include "h2_level.h"
@@ -26,6 +28,113 @@ h2_status fail(h2_status code, const std::string &msg) {
   set_error(code, msg);
   return code;
 }
+
+// ---- caching device allocator
+// Blocks released while a library call runs may still be read by work that
+// call enqueued, so they go to a pool of the calling thread and are handed
+// out again only within that call (whose work is ordered on its stream).
+// When the outermost call returns, the device is synchronised and those
+// blocks join the shared pool, whose blocks have no pending work.  Releases
+// outside a call come from h2_matrix_destroy / h2_tree_destroy, which
+// synchronise the device first.
+namespace {
+using Pool = std::map<std::pair<int, size_t>, std::vector<void *>>;   // (device, bucket)
+std::mutex g_alloc_mutex;
+Pool g_free_blocks;
+thread_local Pool t_call_blocks;
+thread_local int t_call_depth = 0;
+
+size_t bucket_of(size_t bytes) {
+  if (bytes <= 256) return 256;
+  int hb = 63 - __builtin_clzll(bytes);
+  size_t step = (size_t)1 << (hb >= 2 ? hb - 2 : 0);
+  return (bytes + step - 1) / step * step;
+}
+
+void *take(Pool &pool, int dev, size_t b) {
+  auto it = pool.find({dev, b});
+  if (it == pool.end() || it->second.empty()) return nullptr;
+  void *p = it->second.back();
+  it->second.pop_back();
+  return p;
+}
+
+void free_all(Pool &pool) {
+  int cur = 0;
+  cudaGetDevice(&cur);
+  for (auto &kv : pool) {
+    cudaSetDevice(kv.first.first);
+    cudaDeviceSynchronize();
+    for (void *p : kv.second) cudaFree(p);
+    kv.second.clear();
+  }
+  cudaSetDevice(cur);
+}
+}  // namespace
+
+void *dev_alloc(size_t bytes) {
+  int dev = 0;
+  H2_CUDA(cudaGetDevice(&dev));
+  const size_t b = bucket_of(bytes);
+  if (void *p = take(t_call_blocks, dev, b)) return p;
+  {
+    std::lock_guard<std::mutex> lock(g_alloc_mutex);
+    if (void *p = take(g_free_blocks, dev, b)) return p;
+  }
+  void *p = nullptr;
+  cudaError_t e = cudaMalloc(&p, b);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    free_all(t_call_blocks);   // cudaFree waits for the pending work on them
+    dev_trim();                // then the shared pool; retry once
+    e = cudaMalloc(&p, b);
+  }
+  if (e != cudaSuccess)
+    throw Error{e == cudaErrorMemoryAllocation ? H2_ERR_OOM : H2_ERR_CUDA,
+                std::string("cudaMalloc: ") + cudaGetErrorString(e)};
+  return p;
+}
+
+void dev_free(void *p, size_t bytes) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  if (t_call_depth > 0) {
+    t_call_blocks[{dev, bucket_of(bytes)}].push_back(p);
+    return;
+  }
+  std::lock_guard<std::mutex> lock(g_alloc_mutex);
+  g_free_blocks[{dev, bucket_of(bytes)}].push_back(p);
+}
+
+void dev_trim() {
+  std::lock_guard<std::mutex> lock(g_alloc_mutex);
+  free_all(g_free_blocks);
+}
+
+// Scope of one library call (see above).
+struct CallScope {
+  CallScope() { ++t_call_depth; }
+  ~CallScope() {
+    if (--t_call_depth > 0) return;
+    bool any = false;
+    for (auto &kv : t_call_blocks) any = any || !kv.second.empty();
+    if (!any) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (auto &kv : t_call_blocks) {
+      if (kv.second.empty()) continue;
+      cudaSetDevice(kv.first.first);
+      cudaDeviceSynchronize();
+    }
+    cudaSetDevice(cur);
+    std::lock_guard<std::mutex> lock(g_alloc_mutex);
+    for (auto &kv : t_call_blocks) {
+      auto &dst = g_free_blocks[kv.first];
+      dst.insert(dst.end(), kv.second.begin(), kv.second.end());
+      kv.second.clear();
+    }
+  }
+};
 
 int device_sm_count() {
   int dev = 0, sms = 0;
@@ -1063,6 +1172,7 @@ void validate_opts(const h2_build_opts &o) {
 
 template <typename F>
 h2_status guarded(F &&f) {
+  CallScope scope;
   try {
     return f();
   } catch (const Error &e) {
@@ -1187,6 +1297,8 @@ void h2_default_opts(h2_build_opts *o) {
 const char *h2_last_error(void) { return g_last_error.c_str(); }
 
 int64_t h2_kernel_launches(void) { return g_launches; }
+
+void h2_trim_memory(void) { h2::dev_trim(); }
 
 h2_status h2_build_cluster_tree(const double *points, int64_t n, int dim, int leaf_size,
                                 double eta, h2_stream_t s, h2_tree **out) {

@@ -154,9 +154,10 @@ __global__ void __launch_bounds__(kNT) k_bsr_pipe(BsrArgs a) {
   constexpr int SLOT = kSlotBytes / sizeof(T);   // block elements per slot
   constexpr int JMAX = 64;                        // block columns per chunk at most
   constexpr int CG = DC / 4;                      // output columns per thread
+  constexpr int DCP = DC + 4;                     // padded row of the input slot
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *sBlk = reinterpret_cast<T *>(smem_raw);               // [kStages][SLOT]
-  T *sIn = sBlk + kStages * SLOT;                          // [kStages][JMAX][DC]
+  T *sIn = sBlk + kStages * SLOT;                          // [kStages][JMAX][DC + 4]
   const int tau = blockIdx.x;
   const int m = a.row_m[tau];
   const int inst = a.row_inst[tau];
@@ -191,12 +192,14 @@ __global__ void __launch_bounds__(kNT) k_bsr_pipe(BsrArgs a) {
         for (int u = threadIdx.x; u < n16; u += kNT)
           cp_async16(dst + 16 * u, reinterpret_cast<const char *>(src) + 16 * u);
         const int64_t irow = a.col_off[b] + pj;
-        T *di = sIn + slot * JMAX * DC;
+        T *di = sIn + slot * JMAX * DCP;
+        // consecutive threads take consecutive rows of one column (coalesced
+        // reads; the padded row keeps the shared-memory writes spread over banks)
         for (int q = threadIdx.x; q < JMAX * DC; q += kNT) {
-          const int j = q / DC, c = q % DC;
+          const int j = q % JMAX, c = q / JMAX;
           const bool ok = j < nj && c < ncol;
           const T *sp = ok ? in + irow + j + (int64_t)(c0 + c) * a.ld_in : in;
-          cp_async_small<sizeof(T)>(di + q, sp, ok);
+          cp_async_small<sizeof(T)>(di + j * DCP + c, sp, ok);
         }
         pj += nj;
         if (pj >= mb) { pj = 0; ++pe; }
@@ -212,7 +215,7 @@ __global__ void __launch_bounds__(kNT) k_bsr_pipe(BsrArgs a) {
       const int mb = a.col_m[a.idx[ce_]];
       const int nj = min(jc, mb - cj);
       const T *sb = sBlk + slot * SLOT;
-      const T *si = sIn + slot * JMAX * DC + g * CG;
+      const T *si = sIn + slot * JMAX * DCP + g * CG;
       T part[RPT][CG];
 #pragma unroll
       for (int r = 0; r < RPT; ++r)
@@ -221,7 +224,7 @@ __global__ void __launch_bounds__(kNT) k_bsr_pipe(BsrArgs a) {
       for (int j = 0; j < nj; ++j) {
         T ov[CG];
 #pragma unroll
-        for (int c = 0; c < CG; ++c) ov[c] = si[j * DC + c];
+        for (int c = 0; c < CG; ++c) ov[c] = si[j * DCP + c];
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
           const int i = i0 + 64 * r;
@@ -646,7 +649,7 @@ void dense_blocks_gen(int kid, bool fp64, const DgenArgs &a, cudaStream_t s) {
 template <typename T, int DC, int RPT>
 void launch_bsr(const BsrArgs &a, cudaStream_t s) {
   constexpr int SLOT = kSlotBytes / sizeof(T);
-  size_t bytes = sizeof(T) * ((size_t)kStages * SLOT + (size_t)kStages * 64 * DC);
+  size_t bytes = sizeof(T) * ((size_t)kStages * SLOT + (size_t)kStages * 64 * (DC + 4));
   auto kern = k_bsr_pipe<T, DC, RPT>;
   set_smem(kern, bytes);
   kern<<<a.n_rows, kNT, bytes, s>>>(a);
@@ -658,7 +661,9 @@ void bsr_apply(bool fp64, const BsrArgs &a, int max_m, int max_cols, cudaStream_
   if (a.n_rows == 0 || max_cols <= 0) return;
   H2_REQUIRE(max_m <= kMaxRows, "block rows above 256 are not supported");
   const bool narrow = max_cols <= 16;
-  if (max_m <= 64) {
+  if (max_m <= 64 && max_cols > 32 && !fp64) {
+    launch_bsr<float, 64, 1>(a, s);   // one pass over the blocks for 64 columns
+  } else if (max_m <= 64) {
     if (fp64) narrow ? launch_bsr<double, 16, 1>(a, s) : launch_bsr<double, 32, 1>(a, s);
     else narrow ? launch_bsr<float, 16, 1>(a, s) : launch_bsr<float, 32, 1>(a, s);
   } else {

@@ -53,8 +53,17 @@ struct KernelTimer {
 extern thread_local KernelTimer *g_ksum_timer;
 
 // ---------------------------------------------------------------------------
-// Device memory: a typed buffer freed on destruction (stream-ordered).
+// Device memory.  Blocks come from a per-device cache of size buckets (at
+// most 25% rounding) so that builds do not pay cudaMalloc/cudaFree (which
+// synchronises the device) for every temporary.  All work of one library call
+// is enqueued on one stream, so a block returned to the cache and handed out
+// again is only touched after the earlier work on that stream.
 // ---------------------------------------------------------------------------
+void *dev_alloc(size_t bytes);
+void dev_free(void *p, size_t bytes);
+void dev_trim();
+
+// A typed buffer returned to the cache on destruction.
 template <typename T>
 struct DBuf {
   T *p = nullptr;
@@ -71,14 +80,14 @@ struct DBuf {
   void alloc(size_t count) {
     release();
     n = count;
-    if (count) H2_CUDA(cudaMalloc((void **)&p, count * sizeof(T)));
+    if (count) p = static_cast<T *>(dev_alloc(count * sizeof(T)));
   }
   void alloc_zero(size_t count, cudaStream_t s) {
     alloc(count);
     if (count) H2_CUDA(cudaMemsetAsync(p, 0, count * sizeof(T), s));
   }
   void release() {
-    if (p) cudaFree(p);
+    if (p) dev_free(p, n * sizeof(T));
     p = nullptr;
     n = 0;
   }
