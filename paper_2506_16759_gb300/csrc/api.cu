@@ -336,7 +336,8 @@ struct Builder {
   std::vector<double> tols;
   DBuf<int32_t> cb, ce;             // per-instance column range of the current pass
   DBuf<double> om_stage;            // FP64 staging of new Omega columns (mixed / callbacks)
-  DBuf<float> om_hi, om_lo;         // TF32 parts of the level-1 Omega panel (tensor-core sketch)
+  TcLayout tcl;                     // padded leaf layout of the tensor-core sketch (built once)
+  bool tcl_ready = false;
   int64_t sketch_pairs = 0, sketch_cols = 0;
   std::vector<int64_t> near_pairs;   // per instance: sum of m_t * m_b over its near list
   // sum of H2 operands: G = U_op(Itil, :) per operand and level
@@ -535,42 +536,29 @@ struct Builder {
       else
         philox_gaussian64(om64 + b, N, H->orig_of_pos.p + b, n, c0, c0 + nc, o.seed, s);
       if (!fp64()) convert_cols_to32(om64, N, b, n, c0, c0 + nc, L.Om32.p, s);
-      if (H->tensor_sketch) {
-        if (!om_hi.p) {
-          om_hi.alloc((size_t)N * o.d_max);
-          om_lo.alloc((size_t)N * o.d_max);
-        }
-        split_tf32(L.Om32.p, N, b, n, c0, c0 + nc, om_hi.p, om_lo.p, s);
-      }
     }
     bool far = far_only && o.sketch == H2_SKETCH_KSUM && L.max_m <= 64;
-    if (o.sketch == H2_SKETCH_KSUM) {
+    if (o.sketch == H2_SKETCH_KSUM && H->tensor_sketch) {
+      sample_tc(insts, nc, far);
+    } else if (o.sketch == H2_SKETCH_KSUM) {
       std::vector<int64_t> nn(H->inst_n), bb(H->inst_base);
       std::vector<int> lcount(H->count);
       for (int i = 0; i < H->count; ++i) lcount[i] = 1 << H->inst_depth[i];
       int done = 0;
       while (done < nc) {
-        // the tensor-core kernel takes up to 64 columns per entry evaluation
-        const int widest = H->tensor_sketch && (nc - done) % 64 == 0 ? 64 : 32;
-        int dc = std::min(widest, pick_dc(nc - done));
+        int dc = std::min(32, pick_dc(nc - done));
         std::vector<int> c0(insts.size());
         for (size_t q = 0; q < insts.size(); ++q) c0[q] = H->dcur[insts[q]] + done;
-        const bool tc = H->tensor_sketch && tc_sketch_supported(dc);
         KsumPlan plan = far ? plan_ksum_far(L.h_row, L.h_m, L.task_base, lcount, insts, c0, dc,
-                                            sm_count, tc)
+                                            sm_count)
                             : plan_ksum(nn, bb, insts, c0, dc, fp64(), o.ksum_tile, sm_count);
-        for (int i : insts) {
-          int64_t pairs = H->inst_n[i] * H->inst_n[i] - (far ? near_pairs[i] : 0);
-          sketch_pairs += pairs;
-          sketch_flops += (double)pairs * (2.0 * dc + 10.0);
-        }
+        count_sketch(insts, far, dc);
         if (fp64()) {
           KsumArgs64 a{far_lists(), p64(), L.Om64.p, L.Y64.p, N, H->inst_dev.p, nullptr, nullptr};
           run_ksum64(H->kid, plan, a, s, far);
         } else {
-          KsumArgs32 a{far_lists(), p32(), L.Om32.p, L.Y32.p, N, H->inst_dev.p, nullptr, nullptr,
-                       nullptr, om_hi.p, om_lo.p, p64()};
-          run_ksum32(H->kid, plan, a, s, far, tc);
+          KsumArgs32 a{far_lists(), p32(), L.Om32.p, L.Y32.p, N, H->inst_dev.p, nullptr, nullptr};
+          run_ksum32(H->kid, plan, a, s, far);
         }
         done += dc;
       }
@@ -625,6 +613,73 @@ struct Builder {
   }
 
   void add_into(double *y, const double *x, int64_t n);
+
+  void count_sketch(const std::vector<int> &insts, bool far, int dc) {
+    for (int i : insts) {
+      int64_t pairs = H->inst_n[i] * H->inst_n[i] - (far ? near_pairs[i] : 0);
+      sketch_pairs += pairs;
+      sketch_flops += (double)pairs * (2.0 * dc + 10.0);
+    }
+  }
+
+  // Tensor-core sketch of the new columns [dcur_i, dcur_i + nc): the Omega
+  // image of those columns, then chunks of at most 64 columns, each one
+  // evaluation of the entries.
+  void sample_tc(const std::vector<int> &insts, int nc, bool far) {
+    LevelData &L = H->lv[1];
+    const int64_t N = H->n_total;
+    if (!tcl_ready) {
+      // FP16 parts need entries <= 1 and a bounded Omega: the drawn Gaussian
+      // columns are; a stored Omega takes the TF32 parts
+      const bool f16 = tc_f16_kernel(H->kid) && o.omega_mode == 0;
+      std::vector<KernelDesc> kds(H->kd.begin(), H->kd.end());
+      tc_layout_build(H->kid, f16, L.h_row, L.h_m, L.h_inst, kds, L.row.p, L.m.p, p64(), tcl, s);
+      tcl_ready = true;
+    }
+    const int nchunks = (nc + 63) / 64;
+    const int last = nc - 64 * (nchunks - 1);
+    const int img_nc = 64 * (nchunks - 1) + tc_chunk_ncol(last);
+    std::vector<int32_t> hc0(H->count, 0);
+    for (int i : insts) hc0[i] = H->dcur[i];
+    DBuf<int32_t> dc0;
+    to_device(dc0, hc0, s);
+    DBuf<float> img_hi, img_lo;
+    img_hi.alloc((size_t)tcl.n_tiles * 32 * img_nc);
+    img_lo.alloc((size_t)tcl.n_tiles * 32 * img_nc);
+    tc_omega_image(tcl, L.row.p, L.m.p, L.Om32.p, N, dc0.p, nc, img_nc, img_hi.p, img_lo.p, s);
+    std::vector<int64_t> nn(H->inst_n), bb(H->inst_base);
+    std::vector<int> lcount(H->count);
+    for (int i = 0; i < H->count; ++i) lcount[i] = 1 << H->inst_depth[i];
+    for (int done = 0; done < nc; done += 64) {
+      const int w = std::min(64, nc - done);
+      std::vector<int> c0(insts.size());
+      for (size_t q = 0; q < insts.size(); ++q) c0[q] = H->dcur[insts[q]] + done;
+      KsumPlan plan = far ? plan_ksum_far(L.h_row, L.h_m, L.task_base, lcount, insts, c0, w,
+                                          sm_count, true)
+                          : plan_ksum_tc_all(nn, bb, L.task_base, lcount, insts, c0, w, sm_count);
+      count_sketch(insts, far, w);
+      TcArgs a{};
+      a.inst = H->inst_dev.p;
+      a.p64 = p64();
+      a.leaf_row = L.row.p;
+      a.leaf_m = L.m.p;
+      a.leaf_tile = tcl.leaf_tile.p;
+      a.ref_hi = tcl.ref_hi.p;
+      a.ref_lo = tcl.ref_lo.p;
+      a.off = tcl.off.p;
+      a.sigma = tcl.sigma.p;
+      a.near_ptr = H->near_ptr.p;
+      a.near_idx = H->near_idx.p;
+      a.img_hi = img_hi.p;
+      a.img_lo = img_lo.p;
+      a.img_nc = img_nc;
+      a.img_c0 = done;
+      a.om = L.Om32.p;
+      a.y = L.Y32.p;
+      a.ld = N;
+      run_ksum_tc(H->kid, plan, a, far, tcl.f16, s);
+    }
+  }
 
   // ---------------- near field and sweeps ------------------------------------
   // Generates every near-field block D.  If the first samples came from the
@@ -1090,8 +1145,6 @@ struct Builder {
       L.Jtmp.release(); L.skeltmp.release(); L.conv.release();
     }
     om_stage.release();
-    om_hi.release();
-    om_lo.release();
     fill_stats(launches0);
     H->converged = not_conv.empty();
     return H->converged ? H2_OK : H2_ERR_NOT_CONVERGED;
@@ -1569,20 +1622,63 @@ h2_status h2_ksum_sketch(const double *points, int64_t n, int dim, int kernel_id
     std::vector<int64_t> nn = {n}, bb = {0};
     std::vector<int> insts = {0};
     int done = 0;
-    DBuf<float> xh, yh, zh, xl, yl, zl, om32, y32, omh, oml;
+    DBuf<float> xh, yh, zh, xl, yl, zl, om32, y32;
     if (!f64) {
       xh.alloc(n); yh.alloc(n); zh.alloc(n); xl.alloc(n); yl.alloc(n); zl.alloc(n);
       split_coords32(px.p, py.p, pz.p, n, xh.p, yh.p, zh.p, xl.p, yl.p, zl.p, st);
       om32.alloc((size_t)n * d);
       y32.alloc((size_t)n * d);
       convert32(om_c.p, (int64_t)n * d, om32.p, st);
-      if (prec == H2_PREC_MIXED) {
-        omh.alloc((size_t)n * d);
-        oml.alloc((size_t)n * d);
-        split_tf32(om32.p, n, 0, n, 0, d, omh.p, oml.p, st);
-      }
     }
     H2_REQUIRE(d % 8 == 0, "d must be a multiple of 8");
+    if (prec == H2_PREC_MIXED) {
+      // tensor cores: the points as consecutive leaves of one tile each
+      const bool f16 = tc_f16_kernel(kernel_id) && tc_max_abs(om32.p, n, n, 0, d, st) <= 1e4f;
+      const int64_t tj = f16 ? 64 : 32;
+      const int nl = (int)((n + tj - 1) / tj);
+      std::vector<int64_t> lrow(nl);
+      std::vector<int32_t> lm(nl), linst(nl, 0);
+      for (int b = 0; b < nl; ++b) {
+        lrow[b] = tj * b;
+        lm[b] = (int32_t)std::min<int64_t>(tj, n - tj * b);
+      }
+      DBuf<int64_t> dlrow;
+      DBuf<int32_t> dlm, dc0;
+      to_device(dlrow, lrow, st);
+      to_device(dlm, lm, st);
+      to_device(dc0, std::vector<int32_t>{0}, st);
+      const Points64 p64{px.p, py.p, pz.p};
+      TcLayout lay;
+      tc_layout_build(kernel_id, f16, lrow, lm, linst, {kd}, dlrow.p, dlm.p, p64, lay, st);
+      const int nchunks = (d + 63) / 64;
+      const int img_nc = 64 * (nchunks - 1) + tc_chunk_ncol(d - 64 * (nchunks - 1));
+      DBuf<float> img_hi, img_lo;
+      img_hi.alloc((size_t)lay.n_tiles * 32 * img_nc);
+      img_lo.alloc((size_t)lay.n_tiles * 32 * img_nc);
+      tc_omega_image(lay, dlrow.p, dlm.p, om32.p, n, dc0.p, d, img_nc, img_hi.p, img_lo.p, st);
+      for (; done < d; done += 64) {
+        const int w = std::min(64, d - done);
+        KsumPlan plan = plan_ksum_tc_all(nn, bb, {0}, {nl}, insts, {done}, w, device_sm_count());
+        TcArgs a{};
+        a.inst = idev.p;
+        a.p64 = p64;
+        a.leaf_row = dlrow.p;
+        a.leaf_m = dlm.p;
+        a.leaf_tile = lay.leaf_tile.p;
+        a.ref_hi = lay.ref_hi.p;
+        a.ref_lo = lay.ref_lo.p;
+        a.off = lay.off.p;
+        a.sigma = lay.sigma.p;
+        a.img_hi = img_hi.p;
+        a.img_lo = img_lo.p;
+        a.img_nc = img_nc;
+        a.img_c0 = done;
+        a.om = om32.p;
+        a.y = y32.p;
+        a.ld = n;
+        run_ksum_tc(kernel_id, plan, a, false, lay.f16, st);
+      }
+    }
     while (done < d) {
       int dc = std::min(32, pick_dc(d - done));
       std::vector<int> c0 = {done};
@@ -1592,8 +1688,8 @@ h2_status h2_ksum_sketch(const double *points, int64_t n, int dim, int kernel_id
         run_ksum64(kernel_id, plan, a, st);
       } else {
         KsumArgs32 a{FarLists{}, Points32{xh.p, yh.p, zh.p, xl.p, yl.p, zl.p}, om32.p, y32.p, n, idev.p,
-                     nullptr, nullptr, nullptr, omh.p, oml.p, Points64{px.p, py.p, pz.p}};
-        run_ksum32(kernel_id, plan, a, st, false, prec == H2_PREC_MIXED && tc_sketch_supported(dc));
+                     nullptr, nullptr};
+        run_ksum32(kernel_id, plan, a, st, false);
       }
       done += dc;
     }

@@ -73,10 +73,6 @@ struct KsumArgs32 {
   const InstDev *inst;
   const KsumItem *items;
   float *partial;
-  int *err;          // set by the tensor-core kernel if a wait timed out
-  const float *om_hi;  // TF32 parts of om (tensor-core kernel), same layout
-  const float *om_lo;
-  Points64 p64;        // FP64 coordinates (tensor-core kernel: tile-relative offsets)
 };
 
 // Plans a launch covering, for every listed instance, all its rows and
@@ -99,15 +95,71 @@ KsumPlan plan_ksum_far(const std::vector<int64_t> &leaf_row, const std::vector<i
 // values; items/reds are copied to device-side staging inside.
 void run_ksum64(int kid, const KsumPlan &plan, const KsumArgs64 &a, cudaStream_t s,
                 bool far = false);
-// tensor_cores: use the tcgen05 kernel (16 or 32 columns, 128-row tiles).
 void run_ksum32(int kid, const KsumPlan &plan, const KsumArgs32 &a, cudaStream_t s,
-                bool far = false, bool tensor_cores = false);
-// TF32 split hi = rna(x), lo = rna(x - hi) of rows [row0, row0+n), columns [c0, c1).
-void split_tf32(const float *x, int64_t ld, int64_t row0, int64_t n, int c0, int c1, float *hi,
-                float *lo, cudaStream_t s);
-// tcgen05 launch of a staged plan (sketch_tc.cu).
-bool tc_sketch_supported(int ncols);
-void launch_ksum_tc(int kid, const KsumPlan &plan, const KsumArgs32 &a, bool far, cudaStream_t s);
+                bool far = false);
+
+// ---- tensor-core sketch (sketch_tc.cu)
+// Leaves padded to whole tiles (32 points with TF32 parts, 64 with FP16
+// parts).  Per padded point: its offset from
+// its leaf's reference point; per leaf: the reference (FP32 hi/lo parts);
+// both multiplied by the instance's coordinate scale sigma.
+struct TcLayout {
+  bool f16 = false;          // FP16 parts (64-point tiles) instead of TF32 (32-point tiles)
+  int tj = 32;
+  int64_t n_tiles = 0;
+  DBuf<int64_t> leaf_tile;   // first tile of each leaf
+  DBuf<int32_t> tile_leaf;   // leaf of each tile
+  DBuf<int32_t> leaf_inst;   // instance of each leaf
+  DBuf<double> sigma;        // per instance
+  DBuf<float4> ref_hi, ref_lo, off;
+};
+// Arguments of one tensor-core launch (device pointers).
+struct TcArgs {
+  const KsumItem *items;
+  const InstDev *inst;
+  Points64 p64;              // FP64 coordinates in tree order
+  const int64_t *leaf_row;   // leaves (the layout's), first position and size
+  const int32_t *leaf_m;
+  const int64_t *leaf_tile;
+  const float4 *ref_hi, *ref_lo, *off;
+  const double *sigma;
+  const int64_t *near_ptr;   // far-only mode: near leaves of each leaf (sorted CSR)
+  const int32_t *near_idx;
+  const float *img_hi, *img_lo;   // Omega image: 128-byte rows [tile][img_nc]
+  int img_nc, img_c0;        // image columns; first one read by this launch
+  const float *om;           // Omega panel (tree order, ld) for the diagonal term
+  float *y;                  // output panel, ld
+  int64_t ld;
+  float *partial;            // plan partial slots (kRows x ncol each)
+  int *err;                  // set if an mbarrier wait timed out
+  int ncol;                  // valid columns of this launch (<= the template width)
+};
+int tc_chunk_ncol(int w);    // template width (16, 32 or 64) for w <= 64 columns
+// Kernels whose entries are at most 1 (FP16 parts allowed).
+bool tc_f16_kernel(int kid);
+// max |x| over rows [0, n) and columns [c0, c1) (synchronises the stream).
+float tc_max_abs(const float *x, int64_t ld, int64_t n, int c0, int c1, cudaStream_t s);
+void tc_layout_build(int kid, bool f16, const std::vector<int64_t> &leaf_row,
+                     const std::vector<int32_t> &leaf_m, const std::vector<int32_t> &leaf_inst,
+                     const std::vector<KernelDesc> &inst_kd, const int64_t *d_leaf_row,
+                     const int32_t *d_leaf_m, Points64 p64, TcLayout &out, cudaStream_t s);
+// Omega image of the columns [c0_inst, c0_inst + nc) (d_inst_c0 per instance)
+// with img_nc >= nc columns per tile (extra columns zero).
+void tc_omega_image(const TcLayout &L, const int64_t *d_leaf_row, const int32_t *d_leaf_m,
+                    const float *om, int64_t ld, const int32_t *d_inst_c0, int nc, int img_nc,
+                    float *img_hi, float *img_lo, cudaStream_t s);
+void launch_ksum_tc(int kid, int ncol_tmpl, bool far, bool f16, int64_t items, const TcArgs &a,
+                    cudaStream_t s);
+// Stages a plan (plan.tile_rows = 128, plan.dc = valid columns <= 64) and
+// runs it on the tensor cores; a.items/partial/err are filled in here.
+void run_ksum_tc(int kid, const KsumPlan &plan, const TcArgs &a, bool far, bool f16,
+                 cudaStream_t s);
+// Plan of the all-points summation for the tensor-core kernel: 128-row
+// tiles, the point range split over leaf ranges [lb0, lb1) of the layout.
+KsumPlan plan_ksum_tc_all(const std::vector<int64_t> &inst_n, const std::vector<int64_t> &inst_base,
+                          const std::vector<int> &leaf_base, const std::vector<int> &leaf_count,
+                          const std::vector<int> &insts, const std::vector<int> &c0, int ncols,
+                          int sm_count);
 
 // Gaussian sample columns for rows in tree order: om[pos + c*ld] for
 // c in [c0, c1), drawn from Philox4x32-10 keyed by (seed) at counter

@@ -540,35 +540,8 @@ KsumPlan plan_ksum_far(const std::vector<int64_t> &leaf_row, const std::vector<i
   return p;
 }
 
-void run_ksum32(int kid, const KsumPlan &plan, const KsumArgs32 &a, cudaStream_t s, bool far,
-                bool tensor_cores) {
+void run_ksum32(int kid, const KsumPlan &plan, const KsumArgs32 &a, cudaStream_t s, bool far) {
   if (plan.items.empty()) return;
-  if (tensor_cores) {
-    H2_REQUIRE(tc_sketch_supported(plan.dc) && plan.tile_rows == 128,
-               "tensor-core sketch needs 16/32 columns and 128-row tiles");
-    StagedPlan<float> sp;
-    stage_plan(plan, sp, s);
-    DBuf<int> err;
-    err.alloc_zero(1, s);
-    KsumArgs32 b = a;
-    b.items = sp.items.p;
-    b.partial = sp.partial.p;
-    b.err = err.p;
-    {
-      KernelEvents ev(s);
-      launch_ksum_tc(kid, plan, b, far, s);
-      ev.stop();
-    }
-    if (!plan.reds.empty()) {
-      k_ksum_reduce<float><<<(int)plan.reds.size(), 256, 0, s>>>(sp.reds.p, sp.partial.p, b.y, b.ld,
-                                                                plan.tile_rows, plan.dc);
-      count_launch();
-      H2_CHECK_LAUNCH();
-    }
-    if (to_host(err.p, 1, s)[0])
-      throw Error{H2_ERR_CUDA, "tensor-core sketch: an mbarrier wait timed out"};
-    return;
-  }
   dispatch_kernel(kid, [&](auto K) {
     constexpr int KID = decltype(K)::value;
     auto go = [&](auto F) {
@@ -583,6 +556,81 @@ void run_ksum32(int kid, const KsumPlan &plan, const KsumArgs32 &a, cudaStream_t
     if (far) go(std::true_type{});
     else go(std::false_type{});
   });
+}
+
+void run_ksum_tc(int kid, const KsumPlan &plan, const TcArgs &a0, bool far, bool f16,
+                 cudaStream_t s) {
+  if (plan.items.empty()) return;
+  H2_REQUIRE(plan.tile_rows == 128 && plan.dc >= 1 && plan.dc <= 64,
+             "tensor-core sketch needs 128-row tiles and at most 64 columns");
+  StagedPlan<float> sp;
+  stage_plan(plan, sp, s);
+  DBuf<int> err;
+  err.alloc_zero(1, s);
+  TcArgs a = a0;
+  a.items = sp.items.p;
+  a.partial = sp.partial.p;
+  a.err = err.p;
+  a.ncol = plan.dc;
+  {
+    KernelEvents ev(s);
+    launch_ksum_tc(kid, tc_chunk_ncol(plan.dc), far, f16, (int64_t)plan.items.size(), a, s);
+    ev.stop();
+  }
+  if (!plan.reds.empty()) {
+    k_ksum_reduce<float><<<(int)plan.reds.size(), 256, 0, s>>>(sp.reds.p, sp.partial.p, a.y, a.ld,
+                                                              plan.tile_rows, plan.dc);
+    count_launch();
+    H2_CHECK_LAUNCH();
+  }
+  if (to_host(err.p, 1, s)[0])
+    throw Error{H2_ERR_CUDA, "tensor-core sketch: an mbarrier wait timed out"};
+}
+
+KsumPlan plan_ksum_tc_all(const std::vector<int64_t> &inst_n, const std::vector<int64_t> &inst_base,
+                          const std::vector<int> &leaf_base, const std::vector<int> &leaf_count,
+                          const std::vector<int> &insts, const std::vector<int> &c0, int ncols,
+                          int sm_count) {
+  KsumPlan p;
+  p.tile_rows = 128;
+  p.dc = ncols;
+  int64_t tiles = 0;
+  for (int i : insts) tiles += (inst_n[i] + p.tile_rows - 1) / p.tile_rows;
+  const int64_t target = (int64_t)sm_count * 24;
+  struct Tmp {
+    int64_t work;
+    KsumItem it;
+  };
+  std::vector<Tmp> all;
+  for (size_t q = 0; q < insts.size(); ++q) {
+    const int i = insts[q];
+    const int64_t n = inst_n[i], base = inst_base[i];
+    const int nl = leaf_count[i], lb = leaf_base[i];
+    const int64_t rt = (n + p.tile_rows - 1) / p.tile_rows;
+    int64_t S = tiles > 0 ? (target + tiles - 1) / tiles : 1;
+    S = std::max<int64_t>(1, std::min<int64_t>(S, std::min<int64_t>(32, nl / 4)));
+    for (int64_t t = 0; t < rt; ++t) {
+      const int rows = (int)std::min<int64_t>(p.tile_rows, n - t * p.tile_rows);
+      const int64_t slot0 = p.n_parts;
+      for (int64_t sidx = 0; sidx < S; ++sidx) {
+        KsumItem it{};
+        it.inst = i;
+        it.rows = rows;
+        it.row0 = base + t * p.tile_rows;
+        it.c0 = c0[q];
+        it.task = -1;
+        it.lb0 = lb + (int)((nl * sidx) / S);
+        it.lb1 = lb + (int)((nl * (sidx + 1)) / S);
+        it.part = S > 1 ? (int)(p.n_parts++) : -1;
+        all.push_back({(int64_t)(it.lb1 - it.lb0) * rows, it});
+      }
+      if (S > 1) p.reds.push_back({i, rows, base + t * p.tile_rows, c0[q], slot0, (int)S});
+    }
+  }
+  std::stable_sort(all.begin(), all.end(),
+                   [](const Tmp &a, const Tmp &b) { return a.work > b.work; });
+  for (auto &t : all) p.items.push_back(t.it);
+  return p;
 }
 
 void run_ksum64(int kid, const KsumPlan &plan, const KsumArgs64 &a, cudaStream_t s, bool far) {

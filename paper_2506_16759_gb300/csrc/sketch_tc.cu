@@ -1,27 +1,70 @@
 // Fused kernel summation Y = K Omega on the 5th-generation tensor cores.
 //
 // The sketch of Algorithm 1 is a dense contraction over the point index j
-// whose left operand K(x_i, x_j) is generated on the fly.  Here each CTA owns
-// 128 rows (TMEM lanes) and NCOL sample columns; for every 32-point tile:
-//   * the entries are evaluated in FP32 from coordinates relative to the
-//     tile's first row (offsets formed in FP64), split into TF32 parts
-//     hi = rna(x), lo = x - hi, and stored into two 128-byte-swizzled
-//     K-major tiles (A);
-//   * the Omega tile, split the same way once when its columns are drawn,
-//     is copied into two K-major tiles (B);
-//   * one thread issues the three TF32 products hi*hi, hi*lo, lo*hi for the
-//     four K=8 steps of the tile (tcgen05.mma, FP32 accumulation in TMEM) and
-//     commits them to the tile's mbarrier;
-//   * each tile's 128 x NCOL accumulator is read back with tcgen05.ld and
-//     added to per-thread FP32 sums with Kahan compensation.
+// whose left operand K(x_i, x_j) is generated on the fly.
+//
+// Two-part operands.  Each FP32 value x is carried as two low-precision
+// parts, and the product is formed from three part products (the fourth is
+// below FP32 rounding):
+//   TF32 mode: x = hi + lo, hi = rna_tf32(x), lo = rna_tf32(x - hi);
+//              Y = A_hi B_hi + A_hi B_lo + A_lo B_hi   (K = 8 per MMA).
+//   FP16 mode: x = h + 2^-11 s, h = rn_f16(x), s = rn_f16(2^11 (x - h));
+//              Y = A_h B_h + 2^-11 (A_h B_s + A_s B_h)  (K = 16 per MMA).
+// FP16 halves the MMA count per point; it is used when every entry is at
+// most 1 (exponential, Matern, Gaussian kernels) and |Omega| is bounded,
+// so no part leaves the FP16 range (tiny entries fall to subnormals with an
+// absolute error near 2^-36).  Products are always of the form
+// A_1 * [B_1 | B_2] (one MMA of width 2 NCOL; the two B parts are adjacent
+// in shared memory) plus A_2 * B_1 into one half of the accumulator: a
+// tcgen05.mma costs about the same for any width up to this size, so fewer,
+// wider products win.
+//
+// Layout.  Points are grouped by leaf and every leaf is padded to whole
+// tiles of TJ points (32 in TF32 mode, 64 in FP16 mode: 128 bytes per row
+// either way).  The build stores, per padded point, its offset from its
+// leaf's reference point (FP32, already multiplied by the kernel's scale
+// factor sigma), and per leaf that reference (sigma * x_ref as FP32 hi/lo
+// parts).  Every sample call stores an "Omega image": per tile and column
+// the TJ values' two parts in the 128-byte-swizzled K-major order the MMA
+// reads, so one bulk copy per part moves a tile's operand into shared
+// memory.  Padding rows are zero.
+//
+// A distance is formed as (row - r_ref) + (r_ref - t_ref) - (point - t_ref):
+// the first and last terms are small offsets computed in FP64 and rounded
+// once, the middle one is a difference of hi/lo parts, so the FP32 result
+// carries an error of a few units of 2^-24 of the distance itself.
+//
+// CTA = 128 rows (one or two leaves, or 128 consecutive rows) x NCOL sample
+// columns, 18 warps with fixed roles:
+//   warp 0     producer: walks the tile sequence (the far leaves only, in
+//              far-only mode; metadata and near flags of 32 leaves are
+//              loaded by the whole warp at a time), writes each tile's
+//              reference shift, issues the bulk copies of its Omega parts
+//              and point offsets;
+//   warp 1     one thread issues the two MMAs of each of the four K-steps
+//              of a tile into a fresh TMEM accumulator and commits them
+//              (one commit per tile releases the B stage, the A stage and
+//              the accumulator);
+//   warps 2-17 evaluate the tile's 128 x TJ entries (thread = row x TJ/4
+//              points), store their parts into TMEM (tcgen05.st: the MMA
+//              reads operand A from tensor memory, so the entry tile never
+//              passes through shared memory), and read back the
+//              accumulator of an earlier tile (tcgen05.ld).
 // Accumulating many products in TMEM loses precision (measured: 3.8e-6
 // relative after 192 products, 3.9e-7 when every 12-product tile is read
-// back), so every tile gets a fresh accumulator; operands and accumulators
-// are double-buffered so the products overlap the next tile's evaluation.
-// Far-only mode (two leaves per CTA) skips point leaves that are near to
-// both leaves and masks, per row, those near to that row's leaf.
-// Every mbarrier wait is bounded; a timeout raises the error flag.
+// back), so every tile gets a fresh accumulator; the per-tile partials are
+// added plainly in groups of eight and the groups with compensation.
+// Rings: kSA operand-A stages (TMEM), kSB operand-B stages (shared memory),
+// NA TMEM accumulators, kR completion barriers (one per tile in flight).
+// Every mbarrier wait is bounded (0.2 s); a timeout raises the error flag,
+// the CTA ends only after its copies and products have landed, and CTAs
+// that start after the flag is raised return at once.
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
 #include <cstdint>
+#include <cstring>
 
 #include "h2_ops.h"
 #include "h2_types.h"
@@ -29,9 +72,28 @@
 namespace h2 {
 namespace {
 
-constexpr int kRows = 128;   // MMA M, TMEM lanes
-constexpr int kTJ = 32;      // points per tile (4 K-steps of 8)
-constexpr int kWaitLimit = 1 << 24;
+constexpr int kRows = 128;     // MMA M, TMEM lanes
+constexpr int kSA = 3, kSB = 6, kR = 6;
+constexpr int kEvalWarps = 16;
+constexpr int kThreads = 32 * (2 + kEvalWarps);
+constexpr int kWaitLimit = 1 << 22;
+constexpr uint64_t kWaitNs = 200000000ull;   // 0.2 s
+constexpr uint32_t kSuspendNs = 100000;        // 0.1 ms per poll at most
+// TMEM accumulators (2 x NCOL columns each) and how many tiles the read-back lags
+template <int NCOL>
+struct TcAcc {
+  static constexpr int NA = NCOL >= 64 ? 2 : 4;
+  static constexpr int LAG = NA / 2;
+};
+// Points per tile: 128-byte operand rows of TF32 or FP16 values.
+template <bool F16>
+struct TcTile {
+  static constexpr int TJ = F16 ? 64 : 32;
+};
+constexpr float kS16 = 2048.f;          // FP16 mode: scale of the second part
+constexpr float kInvS16 = 1.f / 2048.f;
+constexpr float kLn2 = 0.693147180559945309f;
+constexpr double kLog2e = 1.4426950408889634074;
 
 __device__ __forceinline__ uint32_t saddr(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -41,6 +103,16 @@ __device__ __forceinline__ float tf32_rna(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
   return __uint_as_float(r);
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups of
@@ -54,18 +126,39 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t addr) {
   return d;
 }
 
-// Instruction descriptor: D FP32, A and B TF32, both K-major, M x N.
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
+// Instruction descriptor: D FP32, A and B TF32 (or FP16), both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_mma(bool f16, int M, int N) {
+  return (1u << 4) | ((f16 ? 0u : 2u) << 7) | ((f16 ? 0u : 2u) << 10) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accumulate) {
+// D (TMEM) (+)= A (TMEM, 128 lanes x 8 columns) * B (shared memory descriptor);
+// one K-step: 8 TF32 or 16 FP16 values.
+template <bool F16>
+__device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b,
+                                       uint32_t idesc, uint32_t accumulate) {
+  if constexpr (F16) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate));
+  } else {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate));
+  }
+}
+
+// Eight 32-bit values of this thread's lane into 8 consecutive TMEM columns.
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t *v) {
   asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() {
+  asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
@@ -80,44 +173,59 @@ __device__ __forceinline__ void fence_before() {
 __device__ __forceinline__ void fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 }
-__device__ __forceinline__ void fence_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-}
 
-// Waits for the phase with the given parity to complete; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+__device__ __forceinline__ void mbar_init(uint32_t mbar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(mbar), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Waits for the phase with the given parity to complete; false once
+// kWaitNs nanoseconds have passed (or after kWaitLimit polls), or once
+// *abort (if given) is set.  Each poll may suspend the thread for up to
+// kSuspendNs until the phase completes, so waiting threads take no issue
+// slots from the working ones.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity,
+                                          const volatile int *abort = nullptr) {
+  uint64_t t0 = 0;
   for (int it = 0; it < kWaitLimit; ++it) {
     uint32_t ok;
     asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
         "selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
-        : "r"(mbar), "r"(parity)
+        : "r"(mbar), "r"(parity), "n"(kSuspendNs)
         : "memory");
     if (ok) return true;
+    if (abort && *abort) return false;
+    const uint64_t now = global_ns();
+    if (it == 0) t0 = now;
+    else if (now - t0 > kWaitNs) return false;
   }
   return false;
 }
-
-template <int NCOL>
-__device__ __forceinline__ void tmem_ld(uint32_t taddr, float *v);
-
-template <>
-__device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, float *v) {
-  uint32_t r[32];
+// Bulk copy global -> shared (16-byte aligned, multiple of 16 bytes),
+// completing `bytes` of the mbarrier's transaction count.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
+                                         uint32_t mbar) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-  for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::
+          "r"(dst),
+      "l"(src), "r"(bytes), "r"(mbar)
+      : "memory");
 }
+
+template <int N>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float *v);
 
 template <>
 __device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, float *v) {
@@ -146,355 +254,605 @@ __device__ __forceinline__ void tmem_ld<8>(uint32_t taddr, float *v) {
   for (int c = 0; c < 8; ++c) v[c] = __uint_as_float(r[c]);
 }
 
-// Byte offset of element (row, k) in a K-major 128-byte-swizzled tile whose
-// rows hold 32 FP32 values.
-__device__ __forceinline__ uint32_t sw128_off(int row, int k) {
-  return (uint32_t)row * 128u + ((uint32_t)((k >> 2) ^ (row & 7)) << 4) + (uint32_t)(k & 3) * 4u;
+template <>
+__device__ __forceinline__ void tmem_ld<4>(uint32_t taddr, float *v) {
+  uint32_t r[4];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int c = 0; c < 4; ++c) v[c] = __uint_as_float(r[c]);
 }
 
-// Entry from coordinates relative to a reference point of the row tile:
-// offsets are formed in FP64 and rounded once to FP32, so a distance carries
-// an absolute error of a few 2^-24 of the offsets (well below the TF32 split
-// for the far pairs summed here).  The root is taken as r2 * rsqrt(max(r2, tiny)).
+// Scale factor sigma applied to coordinates so that the entry needs no
+// further multiplication:  exp: K = 2^-r';  Matern 3/2: K = (1 + r' ln2) 2^-r'
+// with r' = sigma |x - y|;  Gaussian: K = 2^-(r'^2);  Laplace and polynomial
+// kernels keep unscaled coordinates.
+double tc_sigma(const KernelDesc &kd) {
+  switch (kd.kid) {
+    case H2_K_EXP:
+    case H2_K_MATERN32: return kd.scale * kLog2e;
+    case H2_K_GAUSS: return std::sqrt(kd.scale * kLog2e);
+    default: return 1.0;
+  }
+}
+
+// Entry from the scaled row coordinates (rx, ry, rz) and a scaled point
+// offset p (the polynomial kernel: absolute coordinates).  `c` is the
+// Laplace factor 1/(4 pi) or the polynomial shift.
 template <int KID>
-__device__ __forceinline__ float kval_rel(float dx, float dy, float dz, float scale, int pw,
-                                          float dot) {
+__device__ __forceinline__ float tc_entry(float rx, float ry, float rz, float4 p, float c, int pw) {
   if constexpr (KID == H2_K_POLY) {
-    return kval<KID, float>(dot, scale, pw);
+    const float base = c + (rx * p.x + ry * p.y + rz * p.z);
+    float v = 1.f;
+    for (int q = 0; q < pw; ++q) v *= base;
+    return v;
   } else {
-    const float r2 = dx * dx + dy * dy + dz * dz;
+    const float dx = rx - p.x, dy = ry - p.y, dz = rz - p.z;
+    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
     if constexpr (KID == H2_K_GAUSS) {
-      return __expf(-r2 * scale);
+      return ex2_approx(-r2);
     } else if constexpr (KID == H2_K_LAPLACE_IE) {
-      return r2 > 0.f ? rsqrtf(r2) * scale : 0.f;
+      return r2 > 0.f ? rsqrtf(r2) * c : 0.f;
     } else {
-      const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
-      if constexpr (KID == H2_K_EXP) {
-        return __expf(-r * scale);
-      } else {
-        const float a2 = r * scale;
-        return (1.f + a2) * __expf(-a2);
-      }
+      const float r = sqrt_approx(r2);
+      const float e = ex2_approx(-r);
+      if constexpr (KID == H2_K_EXP) return e;
+      else return fmaf(r * kLn2, e, e);
     }
   }
 }
 
-// Thread groups per CTA: each group of 128 threads covers all rows and a
-// 1/G share of every tile's points (evaluation) and of the columns (drain).
-template <int NCOL>
-struct TcShape {
-  static constexpr int G = NCOL >= 64 ? 4 : 2;
-  static constexpr int threads = kRows * G;
-  static constexpr int HC = NCOL / G;       // accumulator columns per thread
-  static constexpr int EPT = kTJ / G;       // points evaluated per thread per tile
+// Per-stage control word written by the producer.
+struct TcCtrl {
+  float dx, dy, dz;   // r_ref - t_ref of the tile's leaf (scaled)
+  int flags;          // 1: near to the first row leaf, 2: near to the second, 4: end
+  int64_t j0;         // tree position of the tile's first point
 };
 
-// One 32-point tile of the j loop: its first point, its size, and whether its
-// leaf is near to the first / second leaf of the row tile (far-only mode).
-struct TileDesc {
-  int64_t j0;
-  int nj;
-  bool near1, near2;
-  bool valid;
-};
+template <int NCOL, bool F16>
+constexpr size_t tc_smem_bytes() {
+  return 1024 + (size_t)kSB * (2 * NCOL * 128 + TcTile<F16>::TJ * 16);
+}
 
-// Thread t owns row r = t % 128 and group h = t / 128: it evaluates points
-// [h*EPT, (h+1)*EPT) of every tile for its row, and reads back accumulator
-// columns [h*HC, (h+1)*HC) of its row.  Per tile: the next tile's Omega parts
-// and coordinates are loaded into registers first; the previous tile's
-// products are awaited and its accumulator drained; the operands are stored;
-// one barrier; one thread issues the products.  Two TMEM accumulators
-// alternate, so a drain never waits for the products in flight.
-template <int KID, int NCOL, bool FAR>
-__global__ void __launch_bounds__(TcShape<NCOL>::threads) k_ksum_tc(KsumArgs32 a, int tile_rows) {
-  constexpr int kThreads = TcShape<NCOL>::threads;
-  constexpr int HC = TcShape<NCOL>::HC;
-  constexpr int EPT = TcShape<NCOL>::EPT;
-  constexpr int BPT = NCOL * kTJ / kThreads;   // Omega elements staged per thread
-  constexpr uint32_t A_BYTES = kRows * 128, B_BYTES = NCOL * 128;
+// The two parts of 2 x 8 (FP16 mode: 2 x 16) entries, packed as the TMEM
+// columns of one thread's lane.
+template <bool F16, int EPT>
+__device__ __forceinline__ void split_parts(const float *kv, uint32_t *p1, uint32_t *p2) {
+  if constexpr (F16) {
+#pragma unroll
+    for (int u = 0; u < EPT / 2; ++u) {
+      const __half2 h = __floats2half2_rn(kv[2 * u], kv[2 * u + 1]);
+      const float2 hf = __half22float2(h);
+      const __half2 r = __floats2half2_rn((kv[2 * u] - hf.x) * kS16, (kv[2 * u + 1] - hf.y) * kS16);
+      p1[u] = *reinterpret_cast<const uint32_t *>(&h);
+      p2[u] = *reinterpret_cast<const uint32_t *>(&r);
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < EPT; ++u) {
+      const float hv = tf32_rna(kv[u]);
+      p1[u] = __float_as_uint(hv);
+      p2[u] = __float_as_uint(kv[u] - hv);   // the tensor core keeps its leading TF32 bits
+    }
+  }
+}
+
+template <int KID, int NCOL, bool FAR, bool F16>
+__global__ void __launch_bounds__(kThreads, 1) k_ksum_tc(TcArgs a) {
+  constexpr int TJ = TcTile<F16>::TJ;
+  constexpr int EPT = TJ / 4;                         // entries per eval thread and tile
+  constexpr int CPT = NCOL / 4;                       // accumulator columns per eval thread
+  constexpr int kNA = TcAcc<NCOL>::NA, LAG = TcAcc<NCOL>::LAG;
+  constexpr uint32_t B_BYTES = NCOL * 128;            // one part of an NCOL x TJ tile
+  constexpr uint32_t OFF_BYTES = TJ * 16;
+  constexpr uint32_t TX = 2 * B_BYTES + OFF_BYTES;
+  // TMEM columns: kNA accumulators of 2 x NCOL, then kSA operand-A stages of
+  // 2 x 32 columns (the two parts of the 128 x TJ entry tile)
+  constexpr uint32_t ACC_N = 2 * NCOL;
+  constexpr uint32_t A_COL0 = kNA * ACC_N;
+  constexpr uint32_t TCOLS = A_COL0 + kSA * 64 <= 256 ? 256 : 512;
+  static_assert(A_COL0 + kSA * 64 <= 512, "TMEM columns");
+  constexpr uint32_t IDESC2 = idesc_mma(F16, kRows, 2 * NCOL);
+  constexpr uint32_t IDESC1 = idesc_mma(F16, kRows, NCOL);
+  // second product A_2 * B_1: TF32 adds it to the first half, FP16 to the
+  // scaled second half
+  constexpr uint32_t D2_OFF = F16 ? NCOL : 0;
+  constexpr float SCALE2 = F16 ? kInvS16 : 1.f;
   extern __shared__ unsigned char smem_dyn[];
   unsigned char *base = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
-  unsigned char *Ahi = base;
-  unsigned char *Alo = Ahi + A_BYTES;
-  unsigned char *Bhi = Alo + A_BYTES;
-  unsigned char *Blo = Bhi + B_BYTES;
-  float4 *crd = reinterpret_cast<float4 *>(Blo + B_BYTES);   // [2 slots][hi 32, lo 32]
-  __shared__ uint64_t mbar[2];
+  unsigned char *sB = base;                                             // [kSB][part 1, part 2]
+  float4 *sOff = reinterpret_cast<float4 *>(sB + kSB * 2 * B_BYTES);   // [kSB][TJ]
+  __shared__ TcCtrl ctrl[kSB];
+  __shared__ uint64_t bfull[kSB], afull[kSA], done[kR], accempty[4];
   __shared__ uint32_t tmem_base;
+  __shared__ volatile int s_abort;
+  __shared__ float4 m_rh[32], m_rl[32];   // producer: metadata of 32 leaves
+  __shared__ int64_t m_t0[32], m_j0[32];
+  __shared__ int m_nt[32];
 
   const KsumItem it = a.items[blockIdx.x];
-  const InstDev in = a.inst[it.inst];
-  const float scale = (float)in.kd.scale;
-  const float diag = (float)in.kd.diag;
-  const int pw = in.kd.pw;
-  const int t = threadIdx.x, warp = t >> 5;
-  const int r = t & (kRows - 1), h = t >> 7;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  auto abort_cta = [&]() {
+    s_abort = 1;
+    atomicExch(a.err, 1);
+  };
+  // completion of the products of tile j (one commit per tile)
+  auto wait_done = [&](int j) {
+    return mbar_wait(saddr(&done[j % kR]), (uint32_t)((j / kR) & 1), &s_abort);
+  };
 
   if (t == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(saddr(&mbar[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(saddr(&mbar[1])));
+    for (int i = 0; i < kSB; ++i) mbar_init(saddr(&bfull[i]), 1);
+    for (int i = 0; i < kSA; ++i) mbar_init(saddr(&afull[i]), kEvalWarps);
+    for (int i = 0; i < kR; ++i) mbar_init(saddr(&done[i]), 1);
+    for (int i = 0; i < kNA; ++i) mbar_init(saddr(&accempty[i]), kEvalWarps);
+    // a CTA that timed out earlier in this launch makes the later ones skip their work
+    s_abort = *reinterpret_cast<volatile int *>(a.err) != 0 ? 1 : 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
-  constexpr uint32_t TCOLS = 2 * NCOL < 32 ? 32 : 2 * NCOL;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
                      saddr(&tmem_base)),
                  "n"(TCOLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
-
-  // ---- tile sequence (identical in every thread)
-  int64_t aj = it.j0;                      // all-points cursor
-  int fb = it.lb0, fq = 0;                 // far-only cursor: leaf, offset in leaf
-  int64_t p1 = 0, e1 = 0, p2 = 0, e2 = 0;
-  bool two = false;
-  int m1 = 0;
-  if (FAR) {
-    const int t1 = it.task;
-    m1 = a.far.leaf_m[t1];
-    two = it.rows > m1;
-    p1 = a.far.near_ptr[t1];
-    e1 = a.far.near_ptr[t1 + 1];
-    if (two) { p2 = a.far.near_ptr[t1 + 1]; e2 = a.far.near_ptr[t1 + 2]; }
-  }
-  bool cn1 = false, cn2 = false;           // near flags of the far cursor's leaf
-  auto next = [&]() -> TileDesc {
-    TileDesc d{0, 0, false, false, false};
-    if constexpr (!FAR) {
-      if (aj < it.j1) {
-        d.j0 = aj;
-        d.nj = (int)(it.j1 - aj < kTJ ? it.j1 - aj : kTJ);
-        d.valid = true;
-        aj += kTJ;
-      }
-      return d;
-    }
-    while (FAR && fb < it.lb1) {
-      if (fq == 0) {
-        while (p1 < e1 && a.far.near_idx[p1] < fb) ++p1;
-        cn1 = p1 < e1 && a.far.near_idx[p1] == fb;
-        cn2 = true;
-        if (two) {
-          while (p2 < e2 && a.far.near_idx[p2] < fb) ++p2;
-          cn2 = p2 < e2 && a.far.near_idx[p2] == fb;
-        }
-        if (cn1 && cn2) { ++fb; continue; }
-      }
-      const int nb = a.far.leaf_m[fb];
-      d.j0 = a.far.leaf_row[fb] + fq;
-      d.nj = nb - fq < kTJ ? nb - fq : kTJ;
-      d.near1 = cn1;
-      d.near2 = cn2;
-      d.valid = true;
-      fq += kTJ;
-      if (fq >= nb) { fq = 0; ++fb; }
-      return d;
-    }
-    return d;
-  };
-
-  // ---- prefetch of a tile's Omega parts and coordinates into registers
-  float bh[BPT], bl[BPT];
-  float c6[3];
-  // reference point: the tile's first row (the origin for the polynomial kernel)
-  const double cx = KID == H2_K_POLY ? 0.0 : a.p64.x[it.row0];
-  const double cy = KID == H2_K_POLY ? 0.0 : a.p64.y[it.row0];
-  const double cz = KID == H2_K_POLY ? 0.0 : a.p64.z[it.row0];
-  auto fetch = [&](const TileDesc &d) {
-#pragma unroll
-    for (int u = 0; u < BPT; ++u) {
-      const int q = t + u * kThreads;
-      const int n = q / kTJ, kk = q % kTJ;
-      const int64_t src = d.j0 + kk + (int64_t)(it.c0 + n) * a.ld;
-      const bool ok2 = d.valid && kk < d.nj;
-      bh[u] = ok2 ? a.om_hi[src] : 0.f;
-      bl[u] = ok2 ? a.om_lo[src] : 0.f;
-    }
-    if (t < kTJ) {
-      const int64_t gj = d.j0 + (d.valid && t < d.nj ? t : 0);
-      c6[0] = (float)(a.p64.x[gj] - cx);
-      c6[1] = (float)(a.p64.y[gj] - cy);
-      c6[2] = (float)(a.p64.z[gj] - cz);
-    }
-  };
-  auto store_coords = [&](int slot) {
-    if (t < kTJ) crd[slot * kTJ + t] = make_float4(c6[0], c6[1], c6[2], 0.f);
-  };
-
-  const int64_t g = it.row0 + (r < it.rows ? r : 0);
-  const float xr = (float)(a.p64.x[g] - cx), yr = (float)(a.p64.y[g] - cy),
-              zr = (float)(a.p64.z[g] - cz);
-  const bool second = FAR && r >= m1;
-  float acc[HC], cmp[HC];
-#pragma unroll
-  for (int c = 0; c < HC; ++c) { acc[c] = 0.f; cmp[c] = 0.f; }
-  constexpr uint32_t IDESC = idesc_tf32(kRows, NCOL);
-  const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-  bool ok = true;
-
-  auto drain = [&](int k) {
-    if (!mbar_wait(saddr(&mbar[k & 1]), (uint32_t)((k >> 1) & 1))) ok = false;
-    fence_after();
-    float v[HC];
-    tmem_ld<HC>(tmem_base + lane_base + (uint32_t)((k & 1) * NCOL + h * HC), v);
-#pragma unroll
-    for (int c = 0; c < HC; ++c) {
-      float y = v[c] - cmp[c];
-      float s2 = acc[c] + y;
-      cmp[c] = (s2 - acc[c]) - y;
-      acc[c] = s2;
-    }
-  };
-
-  TileDesc cur = next();
-  fetch(cur);
-  store_coords(0);
-  float cbh[BPT], cbl[BPT];
-#pragma unroll
-  for (int u = 0; u < BPT; ++u) { cbh[u] = bh[u]; cbl[u] = bl[u]; }
   fence_before();
   __syncthreads();
   fence_after();
-  int k = 0;
-  while (cur.valid) {
-    const TileDesc nxt = next();
-    fetch(nxt);                          // loads in flight during this tile
-    if (k > 0) drain(k - 1);             // products of tile k-1 done: operands free
-#pragma unroll
-    for (int u = 0; u < BPT; ++u) {
-      const int q = t + u * kThreads;
-      const uint32_t off = sw128_off(q / kTJ, q % kTJ);
-      *reinterpret_cast<float *>(Bhi + off) = cbh[u];
-      *reinterpret_cast<float *>(Blo + off) = cbl[u];
-    }
-    const float4 *ch = crd + (k & 1) * kTJ;
-    const float m = r < it.rows ? ((FAR && (second ? cur.near2 : cur.near1)) ? 0.f : 1.f) : 0.f;
-    const bool full = cur.nj == kTJ;
-#pragma unroll
-    for (int q = 0; q < EPT / 4; ++q) {
-      const int k4 = (EPT / 4) * h + q;
-      float hv[4], lv[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int kk = 4 * k4 + u;
-        const float4 p = ch[kk];
-        float kv = kval_rel<KID>(xr - p.x, yr - p.y, zr - p.z, scale, pw,
-                                 xr * p.x + yr * p.y + zr * p.z);
-        kv = (full || kk < cur.nj) ? kv * m : 0.f;
-        hv[u] = tf32_rna(kv);
-        lv[u] = kv - hv[u];   // the tensor core keeps its leading TF32 bits
+  const uint32_t tbase = tmem_base;
+  const InstDev in = a.inst[it.inst];
+  const double sg = a.sigma[it.inst];
+  // reference of the row tile: its first row (the origin for the polynomial kernel)
+  const double cx = KID == H2_K_POLY ? 0.0 : a.p64.x[it.row0];
+  const double cy = KID == H2_K_POLY ? 0.0 : a.p64.y[it.row0];
+  const double cz = KID == H2_K_POLY ? 0.0 : a.p64.z[it.row0];
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    const double sx = cx * sg, sy = cy * sg, sz = cz * sg;
+    const float hx = (float)sx, hy = (float)sy, hz = (float)sz;
+    const float lx = (float)(sx - hx), ly = (float)(sy - hy), lz = (float)(sz - hz);
+    int k = 0;
+    bool ok = true;
+    auto emit = [&](int64_t tile, int64_t j0, const float4 &rh, const float4 &rl, int flags) {
+      const int sb = k % kSB;
+      if (k >= kSB && !wait_done(k - kSB)) {   // the stage's last products have completed
+        ok = false;
+        return;
       }
-      const uint32_t off = (uint32_t)r * 128u + ((uint32_t)(k4 ^ (r & 7)) << 4);
-      *reinterpret_cast<float4 *>(Ahi + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
-      *reinterpret_cast<float4 *>(Alo + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+      TcCtrl c;
+      c.dx = (hx - rh.x) + (lx - rl.x);
+      c.dy = (hy - rh.y) + (ly - rl.y);
+      c.dz = (hz - rh.z) + (lz - rl.z);
+      c.flags = flags;
+      c.j0 = j0;
+      ctrl[sb] = c;
+      const uint32_t bar = saddr(&bfull[sb]);
+      if (flags & 4) {
+        mbar_arrive(bar);
+      } else {
+        mbar_expect_tx(bar, TX);
+        const int64_t img = (tile * a.img_nc + a.img_c0) * 32;   // 128-byte rows
+        const uint32_t dst = saddr(sB + sb * 2 * B_BYTES);
+        bulk_g2s(dst, a.img_hi + img, B_BYTES, bar);
+        bulk_g2s(dst + B_BYTES, a.img_lo + img, B_BYTES, bar);
+        bulk_g2s(saddr(sOff + sb * TJ), a.off + tile * TJ, OFF_BYTES, bar);
+      }
+      ++k;
+    };
+    int64_t p1 = 0, e1 = 0, p2 = 0, e2 = 0;
+    bool two = false;
+    if (FAR) {
+      const int t1 = it.task;
+      two = it.rows > a.leaf_m[t1];
+      p1 = a.near_ptr[t1];
+      e1 = a.near_ptr[t1 + 1];
+      if (two) { p2 = a.near_ptr[t1 + 1]; e2 = a.near_ptr[t1 + 2]; }
     }
-    if (nxt.valid) store_coords((k + 1) & 1);
-    fence_async_smem();
-    fence_before();
-    __syncthreads();
-    if (t == 0) {
+    // bit i: leaf b0 + i is on the sorted near list [p, e); p moves past it
+    auto near_bits = [&](int64_t &p, int64_t e, int b0) -> uint32_t {
+      for (;;) {   // skip entries below b0, 32 at a time
+        const int v = p + lane < e ? a.near_idx[p + lane] : INT32_MAX;
+        const uint32_t below = __ballot_sync(0xffffffffu, v < b0);
+        p += __popc(below);
+        if (below != 0xffffffffu) break;
+      }
+      const int v = p + lane < e ? a.near_idx[p + lane] : INT32_MAX;
+      const bool in = v < b0 + 32;
+      p += __popc(__ballot_sync(0xffffffffu, in));
+      return __reduce_or_sync(0xffffffffu, in ? 1u << (v - b0) : 0u);
+    };
+    for (int b0 = it.lb0; b0 < it.lb1; b0 += 32) {
+      if (__any_sync(0xffffffffu, s_abort != 0)) ok = false;
+      if (!ok) break;
+      uint32_t n1 = 0, n2 = 0xffffffffu;
+      if (FAR) {
+        n1 = near_bits(p1, e1, b0);
+        if (two) n2 = near_bits(p2, e2, b0);
+      }
+      const int b = b0 + lane;
+      if (b < it.lb1) {
+        m_rh[lane] = a.ref_hi[b];
+        m_rl[lane] = a.ref_lo[b];
+        m_t0[lane] = a.leaf_tile[b];
+        m_j0[lane] = a.leaf_row[b];
+        m_nt[lane] = (a.leaf_m[b] + TJ - 1) / TJ;
+      }
+      __syncwarp();
+      if (lane == 0) {
+        const int nb = it.lb1 - b0 < 32 ? it.lb1 - b0 : 32;
+        for (int i = 0; i < nb && ok; ++i) {
+          const int f1 = (n1 >> i) & 1, f2 = (n2 >> i) & 1;
+          if (FAR && f1 && f2) continue;
+          const int flags = FAR ? (f1 | (f2 << 1)) : 0;
+          const float4 rh = m_rh[i], rl = m_rl[i];
+          const int64_t t0 = m_t0[i], j0 = m_j0[i];
+          for (int u = 0; u < m_nt[i] && ok; ++u) emit(t0 + u, j0 + TJ * u, rh, rl, flags);
+        }
+      }
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      __syncwarp();
+    }
+    if (lane == 0) {
+      if (ok) emit(0, 0, make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f), 4);
+      if (!ok) abort_cta();
+      // every issued copy has landed before the CTA may end
+      for (int j = k > kSB ? k - kSB : 0; j < k; ++j)
+        mbar_wait(saddr(&bfull[j % kSB]), (uint32_t)((j / kSB) & 1));
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issue
+    if (lane == 0) {
+      int k = 0;
+      for (;; ++k) {
+        if (s_abort) break;
+        const int sb = k % kSB, sa = k % kSA, ac = k % kNA;
+        if (!mbar_wait(saddr(&bfull[sb]), (uint32_t)((k / kSB) & 1), &s_abort)) {
+          abort_cta();
+          break;
+        }
+        if (ctrl[sb].flags & 4) break;
+        if (!mbar_wait(saddr(&afull[sa]), (uint32_t)((k / kSA) & 1), &s_abort)) {
+          abort_cta();
+          break;
+        }
+        if (k >= kNA &&
+            !mbar_wait(saddr(&accempty[ac]), (uint32_t)(((k / kNA) - 1) & 1), &s_abort)) {
+          abort_cta();
+          break;
+        }
+        fence_after();
+        const uint32_t a1 = tbase + A_COL0 + (uint32_t)(sa * 64), a2 = a1 + 32;
+        const uint32_t b1 = saddr(sB + sb * 2 * B_BYTES);
+        const uint32_t d = tbase + (uint32_t)(ac * ACC_N);
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+          const uint64_t db = desc_sw128(b1 + ks * 32);   // rows: B part 1 then part 2
+          mma_ts<F16>(d, a1 + ks * 8, db, IDESC2, ks > 0 ? 1u : 0u);
+          mma_ts<F16>(d + D2_OFF, a2 + ks * 8, db, IDESC1, 1u);
+        }
+        mma_commit(saddr(&done[k % kR]));
+      }
+      // the products issued last have completed before the CTA may end
+      if (k > 0) mbar_wait(saddr(&done[(k - 1) % kR]), (uint32_t)(((k - 1) / kR) & 1));
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ evaluation + read-back
+    const int quad = warp & 3;            // TMEM lane quadrant reachable by this warp
+    const int q = (warp - 2) >> 2;        // point quarter of a tile and column quarter
+    const int r = quad * 32 + lane;       // row of the tile
+    const bool rowok = r < it.rows;
+    const int64_t g = it.row0 + (rowok ? r : 0);
+    const float rx0 = (float)((a.p64.x[g] - cx) * sg);
+    const float ry0 = (float)((a.p64.y[g] - cy) * sg);
+    const float rz0 = (float)((a.p64.z[g] - cz) * sg);
+    const bool second = FAR && r >= a.leaf_m[FAR ? it.task : 0];
+    const float kc = (float)in.kd.scale;
+    const int pw = in.kd.pw;
+    const uint32_t lane_addr = (uint32_t)(quad * 32) << 16;
+    float grp[CPT], acc[CPT], cmp[CPT];
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) { grp[c] = 0.f; acc[c] = 0.f; cmp[c] = 0.f; }
+    auto fold = [&]() {
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) {
+        const float y = grp[c] - cmp[c];
+        const float s2 = acc[c] + y;
+        cmp[c] = (s2 - acc[c]) - y;
+        acc[c] = s2;
+        grp[c] = 0.f;
+      }
+    };
+    bool alive = true;
+    auto fail = [&]() {
+      alive = false;
+      if (lane == 0) abort_cta();
+    };
+    auto drain = [&](int j) {
+      const int ac = j % kNA;
+      if (!__all_sync(0xffffffffu, wait_done(j))) { fail(); return; }
       fence_after();
-      const uint32_t ah = saddr(Ahi), al = saddr(Alo), bhs = saddr(Bhi), bls = saddr(Blo);
-      const uint32_t d = tmem_base + (uint32_t)((k & 1) * NCOL);
+      float v[CPT], w[CPT];
+      const uint32_t ta = tbase + lane_addr + (uint32_t)(ac * ACC_N + q * CPT);
+      tmem_ld<CPT>(ta, v);
+      tmem_ld<CPT>(ta + NCOL, w);
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(saddr(&accempty[ac]));
 #pragma unroll
-      for (int ks = 0; ks < kTJ / 8; ++ks) {
-        const uint32_t koff = ks * 32;
-        const uint64_t dah = desc_sw128(ah + koff), dal = desc_sw128(al + koff);
-        const uint64_t dbh = desc_sw128(bhs + koff), dbl = desc_sw128(bls + koff);
-        mma_tf32(d, dah, dbh, IDESC, ks > 0 ? 1u : 0u);
-        mma_tf32(d, dah, dbl, IDESC, 1u);
-        mma_tf32(d, dal, dbh, IDESC, 1u);
+      for (int c = 0; c < CPT; ++c) grp[c] += fmaf(w[c], SCALE2, v[c]);
+      if ((j & 7) == 7) fold();
+    };
+    int k = 0;
+    for (;; ++k) {
+      const int sb = k % kSB, sa = k % kSA;
+      bool ok = !__any_sync(0xffffffffu, s_abort != 0) &&
+                mbar_wait(saddr(&bfull[sb]), (uint32_t)((k / kSB) & 1), &s_abort);
+      if (!__all_sync(0xffffffffu, ok)) { fail(); break; }
+      const TcCtrl c = ctrl[sb];
+      if (c.flags & 4) break;
+      if (k >= kSA) {   // the products that read this A stage have completed
+        if (!__all_sync(0xffffffffu, wait_done(k - kSA))) { fail(); break; }
+        fence_after();
       }
-      mma_commit(saddr(&mbar[k & 1]));
-    }
+      const bool live = rowok && !(FAR && (c.flags & (second ? 2 : 1)));
+      uint32_t p1[8], p2[8];
+      if (live) {
+        const float rx = rx0 + c.dx, ry = ry0 + c.dy, rz = rz0 + c.dz;
+        const float4 *po = sOff + sb * TJ + EPT * q;
+        float kv[EPT];
 #pragma unroll
-    for (int u = 0; u < BPT; ++u) { cbh[u] = bh[u]; cbl[u] = bl[u]; }
-    cur = nxt;
-    ++k;
+        for (int u = 0; u < EPT; ++u) {
+          kv[u] = tc_entry<KID>(rx, ry, rz, po[u], kc, pw);
+          if constexpr (KID == H2_K_LAPLACE_IE && !FAR) {
+            // the row's own point: the rounded offsets need not cancel exactly
+            if (c.j0 + EPT * q + u == g) kv[u] = 0.f;
+          }
+        }
+        split_parts<F16, EPT>(kv, p1, p2);
+      } else {   // rows outside the item or near to the tile's leaf
+#pragma unroll
+        for (int u = 0; u < 8; ++u) { p1[u] = 0u; p2[u] = 0u; }
+      }
+      // points EPT q .. EPT q + EPT - 1 are TMEM columns 8q .. 8q + 7 of the stage
+      const uint32_t at = tbase + lane_addr + A_COL0 + (uint32_t)(sa * 64 + 8 * q);
+      __syncwarp();
+      tmem_st8(at, p1);
+      tmem_st8(at + 32, p2);
+      tmem_st_wait();
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(saddr(&afull[sa]));
+      if (k >= LAG) {
+        drain(k - LAG);
+        if (!alive) break;
+      }
+    }
+    if (alive)
+      for (int j = k > LAG ? k - LAG : 0; j < k && alive; ++j) drain(j);
+    fold();
+    if (alive && rowok) {
+      const int64_t gr = it.row0 + r;
+      const int cl = q * CPT;
+      if (!FAR && KID != H2_K_POLY && in.kd.diag != 0.0) {
+        // the nugget of the row's own point, if it lies in this item's leaves
+        const int64_t p0 = a.leaf_row[it.lb0];
+        const int64_t pe = a.leaf_row[it.lb1 - 1] + a.leaf_m[it.lb1 - 1];
+        if (gr >= p0 && gr < pe) {
+          const float dg = (float)in.kd.diag;
+#pragma unroll
+          for (int c = 0; c < CPT; ++c)
+            if (cl + c < a.ncol) acc[c] += dg * a.om[gr + (int64_t)(it.c0 + cl + c) * a.ld];
+        }
+      }
+      if (it.part < 0) {
+#pragma unroll
+        for (int c = 0; c < CPT; ++c)
+          if (cl + c < a.ncol) a.y[gr + (int64_t)(it.c0 + cl + c) * a.ld] = acc[c];
+      } else {
+        float *dst = a.partial + (int64_t)it.part * kRows * a.ncol;
+#pragma unroll
+        for (int c = 0; c < CPT; ++c)
+          if (cl + c < a.ncol) dst[(int64_t)(cl + c) * kRows + r] = acc[c];
+      }
+    }
   }
-  if (k > 0) drain(k - 1);
   fence_before();
   __syncthreads();
   fence_after();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem_base),
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tbase),
                  "n"(TCOLS));
-  if (!ok && t == 0) atomicExch(a.err, 1);
-
-  if (r >= it.rows) return;
-  const int64_t gr = it.row0 + r;
-  const int c0 = it.c0 + h * HC;
-  if (!FAR && KID != H2_K_POLY && gr >= it.j0 && gr < it.j1 && diag != 0.f) {
-#pragma unroll
-    for (int c = 0; c < HC; ++c) acc[c] += diag * a.om[gr + (int64_t)(c0 + c) * a.ld];
-  }
-  if (it.part < 0) {
-#pragma unroll
-    for (int c = 0; c < HC; ++c) a.y[gr + (int64_t)(c0 + c) * a.ld] = acc[c];
-  } else {
-    float *dst = a.partial + (int64_t)it.part * tile_rows * NCOL;
-#pragma unroll
-    for (int c = 0; c < HC; ++c) dst[(h * HC + c) * tile_rows + r] = acc[c];
-  }
 }
 
-template <int NCOL>
-constexpr size_t tc_smem_bytes() {
-  return 1024 + 2 * kRows * 128 + 2 * NCOL * 128 + 2 * kTJ * sizeof(float4);
-}
-
-template <int KID, int NCOL, bool FAR>
-void launch_tc(const KsumPlan &p, const KsumArgs32 &a, cudaStream_t s) {
-  auto kern = k_ksum_tc<KID, NCOL, FAR>;
-  const size_t bytes = tc_smem_bytes<NCOL>();
+template <int KID, int NCOL, bool FAR, bool F16>
+void launch_tc(int64_t items, const TcArgs &a, cudaStream_t s) {
+  auto kern = k_ksum_tc<KID, NCOL, FAR, F16>;
+  const size_t bytes = tc_smem_bytes<NCOL, F16>();
   H2_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-  kern<<<(int)p.items.size(), TcShape<NCOL>::threads, bytes, s>>>(a, p.tile_rows);
+  kern<<<(int)items, kThreads, bytes, s>>>(a);
   count_launch();
   H2_CHECK_LAUNCH();
 }
 
-__global__ void k_split_tf32(const float *x, int64_t ld, int64_t row0, int64_t n, int c0, int c1,
-                             float *hi, float *lo) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  for (int c = c0; c < c1; ++c) {
-    const int64_t q = row0 + i + c * ld;
-    const float v = x[q];
-    const float hv = tf32_rna(v);
-    hi[q] = hv;
-    lo[q] = tf32_rna(v - hv);
+// Per leaf (one CTA): its reference sigma * x_first as FP32 hi/lo (the
+// origin for the polynomial kernel) and the scaled offsets of its points,
+// zero in the padding of its last tile.
+__global__ void k_tc_offsets(bool poly, int tj, int n_leaves, const int64_t *leaf_row,
+                             const int32_t *leaf_m, const int32_t *leaf_inst,
+                             const int64_t *leaf_tile, const double *sigma, Points64 p,
+                             float4 *ref_hi, float4 *ref_lo, float4 *off) {
+  const int b = blockIdx.x;
+  if (b >= n_leaves) return;
+  const int64_t row = leaf_row[b];
+  const int m = leaf_m[b];
+  const double sg = sigma[leaf_inst[b]];
+  const double x0 = poly ? 0.0 : p.x[row], y0 = poly ? 0.0 : p.y[row],
+               z0 = poly ? 0.0 : p.z[row];
+  if (threadIdx.x == 0) {
+    const double sx = x0 * sg, sy = y0 * sg, sz = z0 * sg;
+    const float hx = (float)sx, hy = (float)sy, hz = (float)sz;
+    ref_hi[b] = make_float4(hx, hy, hz, 0.f);
+    ref_lo[b] = make_float4((float)(sx - hx), (float)(sy - hy), (float)(sz - hz), 0.f);
+  }
+  const int np = (m + tj - 1) / tj * tj;
+  float4 *o = off + leaf_tile[b] * tj;
+  for (int u = threadIdx.x; u < np; u += blockDim.x) {
+    if (u < m) {
+      const int64_t i = row + u;
+      o[u] = make_float4((float)((p.x[i] - x0) * sg), (float)((p.y[i] - y0) * sg),
+                         (float)((p.z[i] - z0) * sg), 0.f);
+    } else {
+      o[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
   }
 }
 
+// Omega image: per tile T and image column c (< img_nc) one 128-byte row
+// per part (32 TF32 or 64 FP16 values, one per point of the tile); the
+// 16-byte chunk holding points [e k, e k + e) (e = 4 or 8 values) sits at
+// chunk position k ^ (c % 8).  Columns c >= nc and padding points are zero.
+template <bool F16>
+__global__ void k_tc_image(const float *om, int64_t ld, const int32_t *tile_leaf,
+                           const int64_t *leaf_row, const int32_t *leaf_m,
+                           const int64_t *leaf_tile, const int32_t *leaf_inst,
+                           const int32_t *inst_c0, int nc, int img_nc, float *img_1,
+                           float *img_2) {
+  constexpr int TJ = TcTile<F16>::TJ;
+  constexpr int E = F16 ? 8 : 4;      // values per 16-byte chunk
+  const int64_t T = blockIdx.x;
+  const int b = tile_leaf[T];
+  const int u0 = (int)(T - leaf_tile[b]) * TJ;
+  const int mv = leaf_m[b] - u0;
+  const int64_t row = leaf_row[b] + u0;
+  const int c0 = inst_c0[leaf_inst[b]];
+  for (int q = threadIdx.x; q < img_nc * TJ; q += blockDim.x) {
+    const int c = q / TJ, k = q % TJ;
+    const float v = (c < nc && k < mv) ? om[row + k + (int64_t)(c0 + c) * ld] : 0.f;
+    const int64_t dst = (T * img_nc + c) * TJ + (((k / E) ^ (c & 7)) * E + k % E);
+    if constexpr (F16) {
+      const __half h = __float2half_rn(v);
+      const __half r = __float2half_rn((v - __half2float(h)) * kS16);
+      reinterpret_cast<__half *>(img_1)[dst] = h;
+      reinterpret_cast<__half *>(img_2)[dst] = r;
+    } else {
+      const float hv = tf32_rna(v);
+      img_1[dst] = hv;
+      img_2[dst] = tf32_rna(v - hv);
+    }
+  }
+}
+
+__global__ void k_max_abs(const float *x, int64_t ld, int64_t n, int c0, int c1,
+                          unsigned int *out) {
+  float m = 0.f;
+  for (int c = c0; c < c1; ++c)
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+      m = fmaxf(m, fabsf(x[i + (int64_t)c * ld]));
+  // non-negative floats order like their bit patterns; NaN compares above all
+  atomicMax(out, __float_as_uint(m != m ? INFINITY : m));
+}
 }  // namespace
 
-bool tc_sketch_supported(int ncols) { return ncols == 16 || ncols == 32 || ncols == 64; }
+int tc_chunk_ncol(int w) { return w <= 16 ? 16 : (w <= 32 ? 32 : 64); }
 
-void split_tf32(const float *x, int64_t ld, int64_t row0, int64_t n, int c0, int c1, float *hi,
-                float *lo, cudaStream_t s) {
-  if (n == 0 || c1 <= c0) return;
-  k_split_tf32<<<ceil_div(n, 256), 256, 0, s>>>(x, ld, row0, n, c0, c1, hi, lo);
+bool tc_f16_kernel(int kid) {
+  return kid == H2_K_EXP || kid == H2_K_MATERN32 || kid == H2_K_GAUSS;
+}
+
+float tc_max_abs(const float *x, int64_t ld, int64_t n, int c0, int c1, cudaStream_t s) {
+  if (n == 0 || c1 <= c0) return 0.f;
+  DBuf<unsigned int> m;
+  m.alloc_zero(1, s);
+  const int blocks = std::min<int64_t>(ceil_div(n, 256), 1024);
+  k_max_abs<<<blocks, 256, 0, s>>>(x, ld, n, c0, c1, m.p);
+  count_launch();
+  H2_CHECK_LAUNCH();
+  const unsigned int bits = to_host(m.p, 1, s)[0];
+  float v;
+  std::memcpy(&v, &bits, sizeof(v));
+  return v;
+}
+
+void tc_layout_build(int kid, bool f16, const std::vector<int64_t> &leaf_row,
+                     const std::vector<int32_t> &leaf_m, const std::vector<int32_t> &leaf_inst,
+                     const std::vector<KernelDesc> &inst_kd, const int64_t *d_leaf_row,
+                     const int32_t *d_leaf_m, Points64 p64, TcLayout &out, cudaStream_t s) {
+  const int tj = f16 ? TcTile<true>::TJ : TcTile<false>::TJ;
+  const int nl = (int)leaf_row.size();
+  std::vector<int64_t> lt(nl);
+  std::vector<int32_t> tl;
+  int64_t nt = 0;
+  for (int b = 0; b < nl; ++b) {
+    lt[b] = nt;
+    const int tiles = (leaf_m[b] + tj - 1) / tj;
+    for (int u = 0; u < tiles; ++u) tl.push_back(b);
+    nt += tiles;
+  }
+  H2_REQUIRE(nt < (1ll << 31), "too many sketch tiles");
+  std::vector<double> sg(inst_kd.size());
+  for (size_t i = 0; i < inst_kd.size(); ++i) sg[i] = tc_sigma(inst_kd[i]);
+  out.f16 = f16;
+  out.tj = tj;
+  out.n_tiles = nt;
+  to_device(out.leaf_tile, lt, s);
+  to_device(out.tile_leaf, tl, s);
+  to_device(out.leaf_inst, leaf_inst, s);
+  to_device(out.sigma, sg, s);
+  out.ref_hi.alloc(nl);
+  out.ref_lo.alloc(nl);
+  out.off.alloc((size_t)nt * tj);
+  if (nl == 0) return;
+  k_tc_offsets<<<nl, 128, 0, s>>>(kid == H2_K_POLY, tj, nl, d_leaf_row, d_leaf_m,
+                                  out.leaf_inst.p, out.leaf_tile.p, out.sigma.p, p64,
+                                  out.ref_hi.p, out.ref_lo.p, out.off.p);
   count_launch();
   H2_CHECK_LAUNCH();
 }
 
-void launch_ksum_tc(int kid, const KsumPlan &plan, const KsumArgs32 &a, bool far,
+void tc_omega_image(const TcLayout &L, const int64_t *d_leaf_row, const int32_t *d_leaf_m,
+                    const float *om, int64_t ld, const int32_t *d_inst_c0, int nc, int img_nc,
+                    float *img_hi, float *img_lo, cudaStream_t s) {
+  if (L.n_tiles == 0 || img_nc == 0) return;
+  auto kern = L.f16 ? k_tc_image<true> : k_tc_image<false>;
+  kern<<<(int)L.n_tiles, 256, 0, s>>>(om, ld, L.tile_leaf.p, d_leaf_row, d_leaf_m,
+                                      L.leaf_tile.p, L.leaf_inst.p, d_inst_c0, nc, img_nc,
+                                      img_hi, img_lo);
+  count_launch();
+  H2_CHECK_LAUNCH();
+}
+
+void launch_ksum_tc(int kid, int ncol_tmpl, bool far, bool f16, int64_t items, const TcArgs &a,
                     cudaStream_t s) {
   dispatch_kernel(kid, [&](auto K) {
     constexpr int KID = decltype(K)::value;
-    if (plan.dc == 64) {
-      if (far) launch_tc<KID, 64, true>(plan, a, s);
-      else launch_tc<KID, 64, false>(plan, a, s);
-    } else if (plan.dc == 32) {
-      if (far) launch_tc<KID, 32, true>(plan, a, s);
-      else launch_tc<KID, 32, false>(plan, a, s);
-    } else if (plan.dc == 16) {
-      if (far) launch_tc<KID, 16, true>(plan, a, s);
-      else launch_tc<KID, 16, false>(plan, a, s);
-    } else {
-      throw Error{H2_ERR_ARG, "tensor-core sketch takes 16, 32 or 64 columns"};
-    }
+    auto go = [&](auto F, auto H) {
+      constexpr bool FAR = decltype(F)::value;
+      constexpr bool F16 = decltype(H)::value;
+      switch (ncol_tmpl) {
+        case 64: launch_tc<KID, 64, FAR, F16>(items, a, s); break;
+        case 32: launch_tc<KID, 32, FAR, F16>(items, a, s); break;
+        case 16: launch_tc<KID, 16, FAR, F16>(items, a, s); break;
+        default: throw Error{H2_ERR_ARG, "tensor-core sketch takes 16, 32 or 64 columns"};
+      }
+    };
+    auto pick = [&](auto F) {
+      if constexpr (KID == H2_K_EXP || KID == H2_K_MATERN32 || KID == H2_K_GAUSS) {
+        if (f16) go(F, std::true_type{});
+        else go(F, std::false_type{});
+      } else {
+        H2_REQUIRE(!f16, "FP16 sketch parts need entries bounded by 1");
+        go(F, std::false_type{});
+      }
+    };
+    if (far) pick(std::true_type{});
+    else pick(std::false_type{});
   });
 }
 
