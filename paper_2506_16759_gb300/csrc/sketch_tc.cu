@@ -73,18 +73,12 @@ namespace h2 {
 namespace {
 
 constexpr int kRows = 128;     // MMA M, TMEM lanes
-constexpr int kSA = 3, kSB = 6, kR = 6;
+constexpr int kSA = 2, kSB = 5, kR = 5, kNA = 2;
 constexpr int kEvalWarps = 16;
 constexpr int kThreads = 32 * (2 + kEvalWarps);
 constexpr int kWaitLimit = 1 << 22;
 constexpr uint64_t kWaitNs = 200000000ull;   // 0.2 s
 constexpr uint32_t kSuspendNs = 100000;        // 0.1 ms per poll at most
-// TMEM accumulators (2 x NCOL columns each) and how many tiles the read-back lags
-template <int NCOL>
-struct TcAcc {
-  static constexpr int NA = NCOL >= 64 ? 2 : 4;
-  static constexpr int LAG = NA / 2;
-};
 // Points per tile: 128-byte operand rows of TF32 or FP16 values.
 template <bool F16>
 struct TcTile {
@@ -304,20 +298,22 @@ __device__ __forceinline__ float tc_entry(float rx, float ry, float rz, float4 p
   }
 }
 
-// Per-stage control word written by the producer.
+// Per-stage control word written by the producer: one step of up to two
+// tiles.
 struct TcCtrl {
-  float dx, dy, dz;   // r_ref - t_ref of the tile's leaf (scaled)
-  int flags;          // 1: near to the first row leaf, 2: near to the second, 4: end
-  int64_t j0;         // tree position of the tile's first point
+  float dx[2], dy[2], dz[2];   // r_ref - t_ref of each tile's leaf (scaled)
+  int flags[2];                // 1: near to the first row leaf, 2: near to the second
+  int64_t j0[2];               // tree position of each tile's first point
+  int nt;                      // tiles in the step (0: end of the sequence)
 };
 
 template <int NCOL, bool F16>
 constexpr size_t tc_smem_bytes() {
-  return 1024 + (size_t)kSB * (2 * NCOL * 128 + TcTile<F16>::TJ * 16);
+  return 1024 + (size_t)kSB * 2 * (2 * NCOL * 128 + TcTile<F16>::TJ * 16);
 }
 
-// The two parts of 2 x 8 (FP16 mode: 2 x 16) entries, packed as the TMEM
-// columns of one thread's lane.
+// The two parts of 8 (FP16 mode: 16) entries, packed as the TMEM columns of
+// one thread's lane.
 template <bool F16, int EPT>
 __device__ __forceinline__ void split_parts(const float *kv, uint32_t *p1, uint32_t *p2) {
   if constexpr (F16) {
@@ -344,16 +340,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_ksum_tc(TcArgs a) {
   constexpr int TJ = TcTile<F16>::TJ;
   constexpr int EPT = TJ / 4;                         // entries per eval thread and tile
   constexpr int CPT = NCOL / 4;                       // accumulator columns per eval thread
-  constexpr int kNA = TcAcc<NCOL>::NA, LAG = TcAcc<NCOL>::LAG;
   constexpr uint32_t B_BYTES = NCOL * 128;            // one part of an NCOL x TJ tile
   constexpr uint32_t OFF_BYTES = TJ * 16;
-  constexpr uint32_t TX = 2 * B_BYTES + OFF_BYTES;
+  constexpr uint32_t B_STAGE = 2 * (2 * B_BYTES);     // two tiles, two parts each
   // TMEM columns: kNA accumulators of 2 x NCOL, then kSA operand-A stages of
-  // 2 x 32 columns (the two parts of the 128 x TJ entry tile)
+  // 128 columns: part 1 of the two tiles (32 columns each), then part 2
   constexpr uint32_t ACC_N = 2 * NCOL;
   constexpr uint32_t A_COL0 = kNA * ACC_N;
-  constexpr uint32_t TCOLS = A_COL0 + kSA * 64 <= 256 ? 256 : 512;
-  static_assert(A_COL0 + kSA * 64 <= 512, "TMEM columns");
+  constexpr uint32_t TCOLS = A_COL0 + kSA * 128 <= 256 ? 256 : 512;
+  static_assert(A_COL0 + kSA * 128 <= 512, "TMEM columns");
+  static_assert(kSA == kNA && kSA == 2, "the read-back of step k-1 releases the A stage of step k+1");
   constexpr uint32_t IDESC2 = idesc_mma(F16, kRows, 2 * NCOL);
   constexpr uint32_t IDESC1 = idesc_mma(F16, kRows, NCOL);
   // second product A_2 * B_1: TF32 adds it to the first half, FP16 to the
@@ -363,10 +359,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_ksum_tc(TcArgs a) {
   extern __shared__ unsigned char smem_dyn[];
   unsigned char *base = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
-  unsigned char *sB = base;                                             // [kSB][part 1, part 2]
-  float4 *sOff = reinterpret_cast<float4 *>(sB + kSB * 2 * B_BYTES);   // [kSB][TJ]
+  unsigned char *sB = base;                                          // [kSB][tile][part]
+  float4 *sOff = reinterpret_cast<float4 *>(sB + kSB * B_STAGE);    // [kSB][tile][TJ]
   __shared__ TcCtrl ctrl[kSB];
-  __shared__ uint64_t bfull[kSB], afull[kSA], done[kR], accempty[4];
+  __shared__ uint64_t bfull[kSB], afull[kSA], done[kR], accempty[kNA];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_abort;
   __shared__ float4 m_rh[32], m_rl[32];   // producer: metadata of 32 leaves
@@ -379,7 +375,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ksum_tc(TcArgs a) {
     s_abort = 1;
     atomicExch(a.err, 1);
   };
-  // completion of the products of tile j (one commit per tile)
+  // completion of the products of step j (one commit per step)
   auto wait_done = [&](int j) {
     return mbar_wait(saddr(&done[j % kR]), (uint32_t)((j / kR) & 1), &s_abort);
   };
@@ -412,36 +408,68 @@ __global__ void __launch_bounds__(kThreads, 1) k_ksum_tc(TcArgs a) {
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
+    // The warp loads the metadata and near flags of 32 leaves at a time into
+    // shared memory; lane 0 then pairs their tiles into steps and issues them.
     const double sx = cx * sg, sy = cy * sg, sz = cz * sg;
     const float hx = (float)sx, hy = (float)sy, hz = (float)sz;
     const float lx = (float)(sx - hx), ly = (float)(sy - hy), lz = (float)(sz - hz);
     int k = 0;
     bool ok = true;
-    auto emit = [&](int64_t tile, int64_t j0, const float4 &rh, const float4 &rl, int flags) {
+    // the first tile of the step being assembled
+    bool pend = false;
+    int64_t p_tile = 0, p_j0 = 0;
+    float4 p_rh, p_rl;
+    int p_flags = 0;
+    auto emit = [&](int nt, int64_t t1, int64_t j1, const float4 &rh1, const float4 &rl1,
+                    int f1) {
       const int sb = k % kSB;
       if (k >= kSB && !wait_done(k - kSB)) {   // the stage's last products have completed
         ok = false;
         return;
       }
       TcCtrl c;
-      c.dx = (hx - rh.x) + (lx - rl.x);
-      c.dy = (hy - rh.y) + (ly - rl.y);
-      c.dz = (hz - rh.z) + (lz - rl.z);
-      c.flags = flags;
-      c.j0 = j0;
+      c.nt = nt;
+      const int64_t tiles[2] = {p_tile, t1};
+      const float4 rhs[2] = {p_rh, rh1}, rls[2] = {p_rl, rl1};
+      c.flags[0] = p_flags;
+      c.flags[1] = f1;
+      c.j0[0] = p_j0;
+      c.j0[1] = j1;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        c.dx[h] = (hx - rhs[h].x) + (lx - rls[h].x);
+        c.dy[h] = (hy - rhs[h].y) + (ly - rls[h].y);
+        c.dz[h] = (hz - rhs[h].z) + (lz - rls[h].z);
+      }
       ctrl[sb] = c;
       const uint32_t bar = saddr(&bfull[sb]);
-      if (flags & 4) {
+      if (nt == 0) {
         mbar_arrive(bar);
       } else {
-        mbar_expect_tx(bar, TX);
-        const int64_t img = (tile * a.img_nc + a.img_c0) * 32;   // 128-byte rows
-        const uint32_t dst = saddr(sB + sb * 2 * B_BYTES);
-        bulk_g2s(dst, a.img_hi + img, B_BYTES, bar);
-        bulk_g2s(dst + B_BYTES, a.img_lo + img, B_BYTES, bar);
-        bulk_g2s(saddr(sOff + sb * TJ), a.off + tile * TJ, OFF_BYTES, bar);
+        mbar_expect_tx(bar, (uint32_t)nt * (2 * B_BYTES + OFF_BYTES));
+        for (int h = 0; h < nt; ++h) {
+          const int64_t img = (tiles[h] * a.img_nc + a.img_c0) * 32;   // 128-byte rows
+          const uint32_t dst = saddr(sB + sb * B_STAGE + h * 2 * B_BYTES);
+          bulk_g2s(dst, a.img_hi + img, B_BYTES, bar);
+          bulk_g2s(dst + B_BYTES, a.img_lo + img, B_BYTES, bar);
+          bulk_g2s(saddr(sOff + (sb * 2 + h) * TJ), a.off + tiles[h] * TJ, OFF_BYTES, bar);
+        }
       }
       ++k;
+    };
+    auto add_tile = [&](int64_t tile, int64_t j0, const float4 &rh, const float4 &rl,
+                        int flags) {
+      if (!pend) {
+        pend = true;
+        p_tile = tile;
+        p_j0 = j0;
+        p_rh = rh;
+        p_rl = rl;
+        p_flags = flags;
+      } else {
+        emit(2, tile, j0, rh, rl, flags);
+        pend = false;
+      }
     };
     int64_t p1 = 0, e1 = 0, p2 = 0, e2 = 0;
     bool two = false;
@@ -490,14 +518,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_ksum_tc(TcArgs a) {
           const int flags = FAR ? (f1 | (f2 << 1)) : 0;
           const float4 rh = m_rh[i], rl = m_rl[i];
           const int64_t t0 = m_t0[i], j0 = m_j0[i];
-          for (int u = 0; u < m_nt[i] && ok; ++u) emit(t0 + u, j0 + TJ * u, rh, rl, flags);
+          for (int u = 0; u < m_nt[i] && ok; ++u) add_tile(t0 + u, j0 + TJ * u, rh, rl, flags);
         }
       }
       ok = __shfl_sync(0xffffffffu, ok, 0);
       __syncwarp();
     }
     if (lane == 0) {
-      if (ok) emit(0, 0, make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f), 4);
+      const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (ok && pend) emit(1, 0, 0, z, z, 0);
+      if (ok) emit(0, 0, 0, z, z, 0);
       if (!ok) abort_cta();
       // every issued copy has landed before the CTA may end
       for (int j = k > kSB ? k - kSB : 0; j < k; ++j)
@@ -509,13 +539,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_ksum_tc(TcArgs a) {
     if (lane == 0) {
       int k = 0;
       for (;; ++k) {
-        if (s_abort) break;
         const int sb = k % kSB, sa = k % kSA, ac = k % kNA;
         if (!mbar_wait(saddr(&bfull[sb]), (uint32_t)((k / kSB) & 1), &s_abort)) {
           abort_cta();
           break;
         }
-        if (ctrl[sb].flags & 4) break;
+        const int nt = ctrl[sb].nt;
+        if (nt == 0) break;
         if (!mbar_wait(saddr(&afull[sa]), (uint32_t)((k / kSA) & 1), &s_abort)) {
           abort_cta();
           break;
@@ -526,14 +556,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_ksum_tc(TcArgs a) {
           break;
         }
         fence_after();
-        const uint32_t a1 = tbase + A_COL0 + (uint32_t)(sa * 64), a2 = a1 + 32;
-        const uint32_t b1 = saddr(sB + sb * 2 * B_BYTES);
+        const uint32_t a1 = tbase + A_COL0 + (uint32_t)(sa * 128), a2 = a1 + 64;
+        const uint32_t b1 = saddr(sB + sb * B_STAGE);
         const uint32_t d = tbase + (uint32_t)(ac * ACC_N);
+        for (int h = 0; h < nt; ++h) {
 #pragma unroll
-        for (int ks = 0; ks < 4; ++ks) {
-          const uint64_t db = desc_sw128(b1 + ks * 32);   // rows: B part 1 then part 2
-          mma_ts<F16>(d, a1 + ks * 8, db, IDESC2, ks > 0 ? 1u : 0u);
-          mma_ts<F16>(d + D2_OFF, a2 + ks * 8, db, IDESC1, 1u);
+          for (int ks = 0; ks < 4; ++ks) {
+            // rows: B part 1 then part 2 of tile h
+            const uint64_t db = desc_sw128(b1 + h * 2 * B_BYTES + ks * 32);
+            const uint32_t ac_ = (h | ks) ? 1u : 0u;
+            mma_ts<F16>(d, a1 + h * 32 + ks * 8, db, IDESC2, ac_);
+            mma_ts<F16>(d + D2_OFF, a2 + h * 32 + ks * 8, db, IDESC1, 1u);
+          }
         }
         mma_commit(saddr(&done[k % kR]));
       }
@@ -551,7 +585,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ksum_tc(TcArgs a) {
     const float rx0 = (float)((a.p64.x[g] - cx) * sg);
     const float ry0 = (float)((a.p64.y[g] - cy) * sg);
     const float rz0 = (float)((a.p64.z[g] - cz) * sg);
-    const bool second = FAR && r >= a.leaf_m[FAR ? it.task : 0];
+    const int nearbit = (FAR && r >= a.leaf_m[FAR ? it.task : 0]) ? 2 : 1;
     const float kc = (float)in.kd.scale;
     const int pw = in.kd.pw;
     const uint32_t lane_addr = (uint32_t)(quad * 32) << 16;
@@ -573,6 +607,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ksum_tc(TcArgs a) {
       alive = false;
       if (lane == 0) abort_cta();
     };
+    // read-back of step j; it also proves the A stage of step j + kSA free
     auto drain = [&](int j) {
       const int ac = j % kNA;
       if (!__all_sync(0xffffffffu, wait_done(j))) { fail(); return; }
@@ -586,55 +621,55 @@ __global__ void __launch_bounds__(kThreads, 1) k_ksum_tc(TcArgs a) {
       if (lane == 0) mbar_arrive(saddr(&accempty[ac]));
 #pragma unroll
       for (int c = 0; c < CPT; ++c) grp[c] += fmaf(w[c], SCALE2, v[c]);
-      if ((j & 7) == 7) fold();
+      if ((j & 3) == 3) fold();
     };
     int k = 0;
     for (;; ++k) {
       const int sb = k % kSB, sa = k % kSA;
-      bool ok = !__any_sync(0xffffffffu, s_abort != 0) &&
-                mbar_wait(saddr(&bfull[sb]), (uint32_t)((k / kSB) & 1), &s_abort);
-      if (!__all_sync(0xffffffffu, ok)) { fail(); break; }
-      const TcCtrl c = ctrl[sb];
-      if (c.flags & 4) break;
-      if (k >= kSA) {   // the products that read this A stage have completed
-        if (!__all_sync(0xffffffffu, wait_done(k - kSA))) { fail(); break; }
-        fence_after();
+      if (!__all_sync(0xffffffffu, mbar_wait(saddr(&bfull[sb]), (uint32_t)((k / kSB) & 1),
+                                             &s_abort))) {
+        fail();
+        break;
       }
-      const bool live = rowok && !(FAR && (c.flags & (second ? 2 : 1)));
-      uint32_t p1[8], p2[8];
-      if (live) {
-        const float rx = rx0 + c.dx, ry = ry0 + c.dy, rz = rz0 + c.dz;
-        const float4 *po = sOff + sb * TJ + EPT * q;
-        float kv[EPT];
+      const int nt = ctrl[sb].nt;
+      if (nt == 0) break;
+      const uint32_t at = tbase + lane_addr + A_COL0 + (uint32_t)(sa * 128 + 8 * q);
+      for (int h = 0; h < nt; ++h) {
+        const bool live = rowok && !(FAR && (ctrl[sb].flags[h] & nearbit));
+        uint32_t p1[8], p2[8];
+        if (live) {
+          const float rx = rx0 + ctrl[sb].dx[h], ry = ry0 + ctrl[sb].dy[h],
+                      rz = rz0 + ctrl[sb].dz[h];
+          const float4 *po = sOff + (sb * 2 + h) * TJ + EPT * q;
+          float kv[EPT];
 #pragma unroll
-        for (int u = 0; u < EPT; ++u) {
-          kv[u] = tc_entry<KID>(rx, ry, rz, po[u], kc, pw);
-          if constexpr (KID == H2_K_LAPLACE_IE && !FAR) {
-            // the row's own point: the rounded offsets need not cancel exactly
-            if (c.j0 + EPT * q + u == g) kv[u] = 0.f;
+          for (int u = 0; u < EPT; ++u) {
+            kv[u] = tc_entry<KID>(rx, ry, rz, po[u], kc, pw);
+            if constexpr (KID == H2_K_LAPLACE_IE && !FAR) {
+              // the row's own point: the rounded offsets need not cancel exactly
+              if (ctrl[sb].j0[h] + EPT * q + u == g) kv[u] = 0.f;
+            }
           }
-        }
-        split_parts<F16, EPT>(kv, p1, p2);
-      } else {   // rows outside the item or near to the tile's leaf
+          split_parts<F16, EPT>(kv, p1, p2);
+        } else {   // rows outside the item or near to the tile's leaf
 #pragma unroll
-        for (int u = 0; u < 8; ++u) { p1[u] = 0u; p2[u] = 0u; }
+          for (int u = 0; u < 8; ++u) { p1[u] = 0u; p2[u] = 0u; }
+        }
+        // points EPT q .. EPT q + EPT - 1 of tile h: columns 32 h + 8 q .. + 7 of each part
+        __syncwarp();
+        tmem_st8(at + h * 32, p1);
+        tmem_st8(at + 64 + h * 32, p2);
       }
-      // points EPT q .. EPT q + EPT - 1 are TMEM columns 8q .. 8q + 7 of the stage
-      const uint32_t at = tbase + lane_addr + A_COL0 + (uint32_t)(sa * 64 + 8 * q);
-      __syncwarp();
-      tmem_st8(at, p1);
-      tmem_st8(at + 32, p2);
       tmem_st_wait();
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(saddr(&afull[sa]));
-      if (k >= LAG) {
-        drain(k - LAG);
+      if (k >= 1) {
+        drain(k - 1);
         if (!alive) break;
       }
     }
-    if (alive)
-      for (int j = k > LAG ? k - LAG : 0; j < k && alive; ++j) drain(j);
+    if (alive && k >= 1) drain(k - 1);
     fold();
     if (alive && rowok) {
       const int64_t gr = it.row0 + r;
