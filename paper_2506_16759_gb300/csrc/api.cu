@@ -340,6 +340,8 @@ struct Builder {
   bool tcl_ready = false;
   int64_t sketch_pairs = 0, sketch_cols = 0;
   std::vector<int64_t> near_pairs;   // per instance: sum of m_t * m_b over its near list
+  std::vector<int64_t> h_near_ptr;   // near CSR over leaf tasks (host copy)
+  std::vector<int32_t> h_near_idx;
   // sum of H2 operands: G = U_op(Itil, :) per operand and level
   std::vector<std::vector<DBuf<double>>> sumG;
   std::vector<std::vector<DBuf<int64_t>>> sumGoff;
@@ -483,10 +485,12 @@ struct Builder {
       nb += t->near_nnz;
     }
     {
-      std::vector<int32_t> er = to_host(H->near_erow.p, nnz, s), ci = to_host(H->near_idx.p, nnz, s);
+      std::vector<int32_t> er = to_host(H->near_erow.p, nnz, s);
+      h_near_idx = to_host(H->near_idx.p, nnz, s);
+      h_near_ptr = to_host(H->near_ptr.p, L.n + 1, s);
       near_pairs.assign(C, 0);
       for (int64_t e = 0; e < nnz; ++e)
-        near_pairs[L.h_inst[er[e]]] += (int64_t)L.h_m[er[e]] * L.h_m[ci[e]];
+        near_pairs[L.h_inst[er[e]]] += (int64_t)L.h_m[er[e]] * L.h_m[h_near_idx[e]];
     }
     DBuf<int64_t> sz;
     sz.alloc(std::max<int64_t>(nnz, 1));
@@ -626,6 +630,15 @@ struct Builder {
   // image of those columns, then chunks of at most 64 columns, each one
   // evaluation of the entries.
   void sample_tc(const std::vector<int> &insts, int nc, bool far) {
+    std::vector<int> c0(H->count, 0);
+    for (int i : insts) c0[i] = H->dcur[i];
+    run_tc(insts, c0, nc, far ? 1 : 0, Yp(H->lv[1]));
+  }
+
+  // out(:, c0_i + c) for c < nc of the listed instances: mode 0 all points,
+  // 1 far-only, 2 near-only (out: a float panel of N rows, ld N).
+  void run_tc(const std::vector<int> &insts, const std::vector<int> &c0, int nc, int mode,
+              void *out) {
     LevelData &L = H->lv[1];
     const int64_t N = H->n_total;
     if (!tcl_ready) {
@@ -639,8 +652,7 @@ struct Builder {
     const int nchunks = (nc + 63) / 64;
     const int last = nc - 64 * (nchunks - 1);
     const int img_nc = 64 * (nchunks - 1) + tc_chunk_ncol(last);
-    std::vector<int32_t> hc0(H->count, 0);
-    for (int i : insts) hc0[i] = H->dcur[i];
+    std::vector<int32_t> hc0(c0.begin(), c0.end());
     DBuf<int32_t> dc0;
     to_device(dc0, hc0, s);
     DBuf<float> img_hi, img_lo;
@@ -650,14 +662,25 @@ struct Builder {
     std::vector<int64_t> nn(H->inst_n), bb(H->inst_base);
     std::vector<int> lcount(H->count);
     for (int i = 0; i < H->count; ++i) lcount[i] = 1 << H->inst_depth[i];
+    std::vector<int32_t> ul_leaf, ul_flags;
+    DBuf<int32_t> d_ul_leaf, d_ul_flags;
     for (int done = 0; done < nc; done += 64) {
       const int w = std::min(64, nc - done);
-      std::vector<int> c0(insts.size());
-      for (size_t q = 0; q < insts.size(); ++q) c0[q] = H->dcur[insts[q]] + done;
-      KsumPlan plan = far ? plan_ksum_far(L.h_row, L.h_m, L.task_base, lcount, insts, c0, w,
-                                          sm_count, true)
-                          : plan_ksum_tc_all(nn, bb, L.task_base, lcount, insts, c0, w, sm_count);
-      count_sketch(insts, far, w);
+      std::vector<int> cq(insts.size());
+      for (size_t q = 0; q < insts.size(); ++q) cq[q] = c0[insts[q]] + done;
+      KsumPlan plan;
+      if (mode == 1) {
+        plan = plan_ksum_far(L.h_row, L.h_m, L.task_base, lcount, insts, cq, w, sm_count, true);
+        count_sketch(insts, true, w);
+      } else if (mode == 0) {
+        plan = plan_ksum_tc_all(nn, bb, L.task_base, lcount, insts, cq, w, sm_count);
+        count_sketch(insts, false, w);
+      } else {
+        plan = plan_ksum_tc_near(L.h_m, L.h_row, L.task_base, lcount, h_near_ptr, h_near_idx,
+                                 insts, cq, w, ul_leaf, ul_flags);
+        to_device(d_ul_leaf, ul_leaf, s);
+        to_device(d_ul_flags, ul_flags, s);
+      }
       TcArgs a{};
       a.inst = H->inst_dev.p;
       a.p64 = p64();
@@ -670,14 +693,16 @@ struct Builder {
       a.sigma = tcl.sigma.p;
       a.near_ptr = H->near_ptr.p;
       a.near_idx = H->near_idx.p;
+      a.ul_leaf = d_ul_leaf.p;
+      a.ul_flags = d_ul_flags.p;
       a.img_hi = img_hi.p;
       a.img_lo = img_lo.p;
       a.img_nc = img_nc;
       a.img_c0 = done;
       a.om = L.Om32.p;
-      a.y = L.Y32.p;
+      a.y = static_cast<float *>(out);
       a.ld = N;
-      run_ksum_tc(H->kid, plan, a, far, tcl.f16, s);
+      run_ksum_tc(H->kid, plan, a, mode, tcl.f16, s);
     }
   }
 
@@ -727,7 +752,17 @@ struct Builder {
     set_cols(b, e);
     if (far) {
       P.alloc_zero((size_t)H->n_total * o.d0 * (fp64() ? 8 : 4), s);
-      near_bsr(P.p, 1.0);
+      if (H->tensor_sketch) {
+        // D Omega of the first columns from the generated entries of the near
+        // leaves (it only enters the norm estimate)
+        timer.begin(PH_SKETCH);
+        std::vector<int> all(C);
+        std::iota(all.begin(), all.end(), 0);
+        run_tc(all, std::vector<int>(C, 0), o.d0, 2, P.p);
+        timer.end(PH_SKETCH);
+      } else {
+        near_bsr(P.p, 1.0);
+      }
     } else {
       near_bsr(Yp(L), -1.0);
     }

@@ -125,6 +125,8 @@ struct TcArgs {
   const double *sigma;
   const int64_t *near_ptr;   // far-only mode: near leaves of each leaf (sorted CSR)
   const int32_t *near_idx;
+  const int32_t *ul_leaf;    // near-only mode: per item entries [lb0, lb1) of the union
+  const int32_t *ul_flags;   //   of its leaves' near lists; bit 1/2: not near to leaf 1/2
   const float *img_hi, *img_lo;   // Omega image: 128-byte rows [tile][img_nc]
   int img_nc, img_c0;        // image columns; first one read by this launch
   const float *om;           // Omega panel (tree order, ld) for the diagonal term
@@ -148,12 +150,22 @@ void tc_layout_build(int kid, bool f16, const std::vector<int64_t> &leaf_row,
 void tc_omega_image(const TcLayout &L, const int64_t *d_leaf_row, const int32_t *d_leaf_m,
                     const float *om, int64_t ld, const int32_t *d_inst_c0, int nc, int img_nc,
                     float *img_hi, float *img_lo, cudaStream_t s);
-void launch_ksum_tc(int kid, int ncol_tmpl, bool far, bool f16, int64_t items, const TcArgs &a,
+// mode: 0 all points, 1 far-only, 2 near-only.
+void launch_ksum_tc(int kid, int ncol_tmpl, int mode, bool f16, int64_t items, const TcArgs &a,
                     cudaStream_t s);
 // Stages a plan (plan.tile_rows = 128, plan.dc = valid columns <= 64) and
 // runs it on the tensor cores; a.items/partial/err are filled in here.
-void run_ksum_tc(int kid, const KsumPlan &plan, const TcArgs &a, bool far, bool f16,
+void run_ksum_tc(int kid, const KsumPlan &plan, const TcArgs &a, int mode, bool f16,
                  cudaStream_t s);
+// Near-only plan: one item per pair of consecutive leaves of each listed
+// instance, over the union of the pair's near lists (host CSR near_ptr /
+// near_idx over leaf tasks); fills ul_leaf / ul_flags (host).
+KsumPlan plan_ksum_tc_near(const std::vector<int32_t> &leaf_m, const std::vector<int64_t> &leaf_row,
+                           const std::vector<int> &leaf_base, const std::vector<int> &leaf_count,
+                           const std::vector<int64_t> &near_ptr,
+                           const std::vector<int32_t> &near_idx, const std::vector<int> &insts,
+                           const std::vector<int> &c0, int ncols, std::vector<int32_t> &ul_leaf,
+                           std::vector<int32_t> &ul_flags);
 // Plan of the all-points summation for the tensor-core kernel: 128-row
 // tiles, the point range split over leaf ranges [lb0, lb1) of the layout.
 KsumPlan plan_ksum_tc_all(const std::vector<int64_t> &inst_n, const std::vector<int64_t> &inst_base,

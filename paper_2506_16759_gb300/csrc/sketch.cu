@@ -4,6 +4,7 @@
 // Gaussian test matrix (batchedRand), the dense-matrix sketch and single
 // entry blocks (batchedGen for one block).
 #include <algorithm>
+#include <climits>
 
 #include "h2_ops.h"
 #include "h2_types.h"
@@ -558,7 +559,7 @@ void run_ksum32(int kid, const KsumPlan &plan, const KsumArgs32 &a, cudaStream_t
   });
 }
 
-void run_ksum_tc(int kid, const KsumPlan &plan, const TcArgs &a0, bool far, bool f16,
+void run_ksum_tc(int kid, const KsumPlan &plan, const TcArgs &a0, int mode, bool f16,
                  cudaStream_t s) {
   if (plan.items.empty()) return;
   H2_REQUIRE(plan.tile_rows == 128 && plan.dc >= 1 && plan.dc <= 64,
@@ -574,7 +575,7 @@ void run_ksum_tc(int kid, const KsumPlan &plan, const TcArgs &a0, bool far, bool
   a.ncol = plan.dc;
   {
     KernelEvents ev(s);
-    launch_ksum_tc(kid, tc_chunk_ncol(plan.dc), far, f16, (int64_t)plan.items.size(), a, s);
+    launch_ksum_tc(kid, tc_chunk_ncol(plan.dc), mode, f16, (int64_t)plan.items.size(), a, s);
     ev.stop();
   }
   if (!plan.reds.empty()) {
@@ -585,6 +586,50 @@ void run_ksum_tc(int kid, const KsumPlan &plan, const TcArgs &a0, bool far, bool
   }
   if (to_host(err.p, 1, s)[0])
     throw Error{H2_ERR_CUDA, "tensor-core sketch: an mbarrier wait timed out"};
+}
+
+KsumPlan plan_ksum_tc_near(const std::vector<int32_t> &leaf_m, const std::vector<int64_t> &leaf_row,
+                           const std::vector<int> &leaf_base, const std::vector<int> &leaf_count,
+                           const std::vector<int64_t> &near_ptr,
+                           const std::vector<int32_t> &near_idx, const std::vector<int> &insts,
+                           const std::vector<int> &c0, int ncols, std::vector<int32_t> &ul_leaf,
+                           std::vector<int32_t> &ul_flags) {
+  KsumPlan p;
+  p.tile_rows = 128;
+  p.dc = ncols;
+  ul_leaf.clear();
+  ul_flags.clear();
+  for (size_t q = 0; q < insts.size(); ++q) {
+    const int i = insts[q];
+    const int lb = leaf_base[i], nl = leaf_count[i];
+    for (int t = lb; t < lb + nl; t += 2) {
+      const bool two = t + 1 < lb + nl;
+      H2_REQUIRE(leaf_m[t] + (two ? leaf_m[t + 1] : 0) <= 128, "leaf pair above 128 rows");
+      KsumItem it{};
+      it.inst = i;
+      it.rows = leaf_m[t] + (two ? leaf_m[t + 1] : 0);
+      it.row0 = leaf_row[t];
+      it.c0 = c0[q];
+      it.task = t;
+      it.part = -1;
+      it.lb0 = (int)ul_leaf.size();
+      // merge the sorted near lists of t and t+1
+      int64_t a = near_ptr[t], ae = near_ptr[t + 1];
+      int64_t b = two ? near_ptr[t + 1] : 0, be = two ? near_ptr[t + 2] : 0;
+      while (a < ae || b < be) {
+        const int va = a < ae ? near_idx[a] : INT32_MAX, vb = b < be ? near_idx[b] : INT32_MAX;
+        const int v = std::min(va, vb);
+        ul_leaf.push_back(v);
+        ul_flags.push_back((va == v ? 0 : 1) | (vb == v ? 0 : 2));
+        if (va == v) ++a;
+        if (vb == v) ++b;
+      }
+      it.lb1 = (int)ul_leaf.size();
+      p.items.push_back(it);
+    }
+  }
+  H2_REQUIRE(ul_leaf.size() < (1u << 31), "near lists too long");
+  return p;
 }
 
 KsumPlan plan_ksum_tc_all(const std::vector<int64_t> &inst_n, const std::vector<int64_t> &inst_base,

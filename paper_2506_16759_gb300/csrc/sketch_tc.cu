@@ -36,8 +36,10 @@
 //
 // CTA = 128 rows (one or two leaves, or 128 consecutive rows) x NCOL sample
 // columns, 18 warps with fixed roles:
-//   warp 0     producer: walks the tile sequence (the far leaves only, in
-//              far-only mode; metadata and near flags of 32 leaves are
+//   warp 0     producer: walks the tile sequence (all leaves; the far
+//              leaves only; or the union of the row leaves' near lists, for
+//              the near-field product of the norm estimate; metadata and
+//              near flags of 32 leaves are
 //              loaded by the whole warp at a time), writes each tile's
 //              reference shift, issues the bulk copies of its Omega parts
 //              and point offsets;
@@ -335,8 +337,12 @@ __device__ __forceinline__ void split_parts(const float *kv, uint32_t *p1, uint3
   }
 }
 
-template <int KID, int NCOL, bool FAR, bool F16>
+// MODE: 0 all points, 1 far-only (leaves not on a row leaf's near list),
+// 2 near-only (the union of the row leaves' near lists, from a.ul_leaf).
+template <int KID, int NCOL, int MODE, bool F16>
 __global__ void __launch_bounds__(kThreads, 1) k_ksum_tc(TcArgs a) {
+  constexpr bool FAR = MODE == 1;
+  constexpr bool MASKED = MODE != 0;
   constexpr int TJ = TcTile<F16>::TJ;
   constexpr int EPT = TJ / 4;                         // entries per eval thread and tile
   constexpr int CPT = NCOL / 4;                       // accumulator columns per eval thread
@@ -367,7 +373,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ksum_tc(TcArgs a) {
   __shared__ volatile int s_abort;
   __shared__ float4 m_rh[32], m_rl[32];   // producer: metadata of 32 leaves
   __shared__ int64_t m_t0[32], m_j0[32];
-  __shared__ int m_nt[32];
+  __shared__ int m_nt[32], m_fl[32];
 
   const KsumItem it = a.items[blockIdx.x];
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -501,8 +507,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_ksum_tc(TcArgs a) {
         n1 = near_bits(p1, e1, b0);
         if (two) n2 = near_bits(p2, e2, b0);
       }
-      const int b = b0 + lane;
-      if (b < it.lb1) {
+      const int e = b0 + lane;
+      int b = e;
+      if (MODE == 2 && e < it.lb1) {   // entry e of the item's near-union list
+        b = a.ul_leaf[e];
+        m_fl[lane] = a.ul_flags[e];
+      }
+      if (e < it.lb1) {
         m_rh[lane] = a.ref_hi[b];
         m_rl[lane] = a.ref_lo[b];
         m_t0[lane] = a.leaf_tile[b];
@@ -515,7 +526,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ksum_tc(TcArgs a) {
         for (int i = 0; i < nb && ok; ++i) {
           const int f1 = (n1 >> i) & 1, f2 = (n2 >> i) & 1;
           if (FAR && f1 && f2) continue;
-          const int flags = FAR ? (f1 | (f2 << 1)) : 0;
+          const int flags = FAR ? (f1 | (f2 << 1)) : (MODE == 2 ? m_fl[i] : 0);
           const float4 rh = m_rh[i], rl = m_rl[i];
           const int64_t t0 = m_t0[i], j0 = m_j0[i];
           for (int u = 0; u < m_nt[i] && ok; ++u) add_tile(t0 + u, j0 + TJ * u, rh, rl, flags);
@@ -585,7 +596,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ksum_tc(TcArgs a) {
     const float rx0 = (float)((a.p64.x[g] - cx) * sg);
     const float ry0 = (float)((a.p64.y[g] - cy) * sg);
     const float rz0 = (float)((a.p64.z[g] - cz) * sg);
-    const int nearbit = (FAR && r >= a.leaf_m[FAR ? it.task : 0]) ? 2 : 1;
+    const int nearbit = (MASKED && r >= a.leaf_m[MASKED ? it.task : 0]) ? 2 : 1;
     const float kc = (float)in.kd.scale;
     const int pw = in.kd.pw;
     const uint32_t lane_addr = (uint32_t)(quad * 32) << 16;
@@ -635,7 +646,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ksum_tc(TcArgs a) {
       if (nt == 0) break;
       const uint32_t at = tbase + lane_addr + A_COL0 + (uint32_t)(sa * 128 + 8 * q);
       for (int h = 0; h < nt; ++h) {
-        const bool live = rowok && !(FAR && (ctrl[sb].flags[h] & nearbit));
+        const bool live = rowok && !(MASKED && (ctrl[sb].flags[h] & nearbit));
         uint32_t p1[8], p2[8];
         if (live) {
           const float rx = rx0 + ctrl[sb].dx[h], ry = ry0 + ctrl[sb].dy[h],
@@ -676,8 +687,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_ksum_tc(TcArgs a) {
       const int cl = q * CPT;
       if (!FAR && KID != H2_K_POLY && in.kd.diag != 0.0) {
         // the nugget of the row's own point, if it lies in this item's leaves
-        const int64_t p0 = a.leaf_row[it.lb0];
-        const int64_t pe = a.leaf_row[it.lb1 - 1] + a.leaf_m[it.lb1 - 1];
+        // (near-only items cover the row's own leaf)
+        const int64_t p0 = MODE == 2 ? gr : a.leaf_row[it.lb0];
+        const int64_t pe = MODE == 2 ? gr + 1 : a.leaf_row[it.lb1 - 1] + a.leaf_m[it.lb1 - 1];
         if (gr >= p0 && gr < pe) {
           const float dg = (float)in.kd.diag;
 #pragma unroll
@@ -705,9 +717,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_ksum_tc(TcArgs a) {
                  "n"(TCOLS));
 }
 
-template <int KID, int NCOL, bool FAR, bool F16>
+template <int KID, int NCOL, int MODE, bool F16>
 void launch_tc(int64_t items, const TcArgs &a, cudaStream_t s) {
-  auto kern = k_ksum_tc<KID, NCOL, FAR, F16>;
+  auto kern = k_ksum_tc<KID, NCOL, MODE, F16>;
   const size_t bytes = tc_smem_bytes<NCOL, F16>();
   H2_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   kern<<<(int)items, kThreads, bytes, s>>>(a);
@@ -863,31 +875,35 @@ void tc_omega_image(const TcLayout &L, const int64_t *d_leaf_row, const int32_t 
   H2_CHECK_LAUNCH();
 }
 
-void launch_ksum_tc(int kid, int ncol_tmpl, bool far, bool f16, int64_t items, const TcArgs &a,
+void launch_ksum_tc(int kid, int ncol_tmpl, int mode, bool f16, int64_t items, const TcArgs &a,
                     cudaStream_t s) {
   dispatch_kernel(kid, [&](auto K) {
     constexpr int KID = decltype(K)::value;
-    auto go = [&](auto F, auto H) {
-      constexpr bool FAR = decltype(F)::value;
+    auto go = [&](auto M, auto H) {
+      constexpr int MODE = decltype(M)::value;
       constexpr bool F16 = decltype(H)::value;
       switch (ncol_tmpl) {
-        case 64: launch_tc<KID, 64, FAR, F16>(items, a, s); break;
-        case 32: launch_tc<KID, 32, FAR, F16>(items, a, s); break;
-        case 16: launch_tc<KID, 16, FAR, F16>(items, a, s); break;
+        case 64: launch_tc<KID, 64, MODE, F16>(items, a, s); break;
+        case 32: launch_tc<KID, 32, MODE, F16>(items, a, s); break;
+        case 16: launch_tc<KID, 16, MODE, F16>(items, a, s); break;
         default: throw Error{H2_ERR_ARG, "tensor-core sketch takes 16, 32 or 64 columns"};
       }
     };
-    auto pick = [&](auto F) {
+    auto pick = [&](auto M) {
       if constexpr (KID == H2_K_EXP || KID == H2_K_MATERN32 || KID == H2_K_GAUSS) {
-        if (f16) go(F, std::true_type{});
-        else go(F, std::false_type{});
+        if (f16) go(M, std::true_type{});
+        else go(M, std::false_type{});
       } else {
         H2_REQUIRE(!f16, "FP16 sketch parts need entries bounded by 1");
-        go(F, std::false_type{});
+        go(M, std::false_type{});
       }
     };
-    if (far) pick(std::true_type{});
-    else pick(std::false_type{});
+    switch (mode) {
+      case 0: pick(std::integral_constant<int, 0>{}); break;
+      case 1: pick(std::integral_constant<int, 1>{}); break;
+      case 2: pick(std::integral_constant<int, 2>{}); break;
+      default: throw Error{H2_ERR_ARG, "unknown tensor-core sketch mode"};
+    }
   });
 }
 
