@@ -32,6 +32,11 @@ METRIC = "H2 build time & points/s at tol, mixed vs FP64 on 1 GB300; % HBM/compu
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.55
 FP64_PEAK_TFLOPS = 1.25
+# The tensor-core sketch is bound by entry generation on the special-function
+# units: a Matern-3/2 entry takes two of their operations (square root and
+# exp2); 16 SFU lanes per SM (4 per sub-partition).
+SFU_LANES, SFU_OPS_PER_PAIR = 16, 2
+SFU_PEAK_GPAIRS = SMS * SFU_LANES * SM_MAX_MHZ * 1e6 / SFU_OPS_PER_PAIR / 1e9   # 2516.5
 WORKLOAD_DESC = ("c2: N=131072 uniform [0,1]^3, Matern-3/2 l=0.1 + 1e-4 nugget, leaf 64, "
                  "eta 0.7, tol 1e-6, adaptive sampling up to 256 columns (schedule in config.schedule), "
                  "fused kernel-summation sketch")
@@ -127,7 +132,7 @@ class ClockSampler:
 
 def source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("sketch.cu", "sketch_tc.cu", "h2_internal.cuh"):
+    for f in ("sketch.cu", "sketch_tc.cu", "h2_internal.cuh", "h2_ops.h"):
         h.update(open(os.path.join(ROOT, "paper_2506_16759_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -135,13 +140,42 @@ def source_hash() -> str:
 def profiled_traffic(prec: str):
     """DRAM bytes per sketch launch from the committed ncu summary, if the
     kernel source is unchanged since it was taken."""
-    path = os.path.join(ROOT, "profiles", f"ksum_sketch_c2_{prec}.json")
+    path = os.path.join(ROOT, "profiles", f"ksum_tc_c2_{prec}.json")
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
     if d.get("source_hash") != source_hash():
         return None
     return d.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------- ranks
+# One process per GPU; each rank builds its own replica of the workload (no
+# data-path collective).  These helpers are the only cross-rank steps: a
+# barrier around the timed region and the maximum of the ranks' times.
+RANK_TIMEOUT_S = 300   # a rank that dies makes the others' next collective fail
+
+
+def rank_env():
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(v: float, world: int, device=None) -> float:
+    """Largest value over the ranks (every rank gets it)."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, n_per_rank: int, steps: int, max_total_ms: float) -> float:
+    """Points per second of the whole job: every rank built steps x n points
+    and the job took the slowest rank's time."""
+    return world * n_per_rank * steps / (max_total_ms / 1e3)
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -154,25 +188,18 @@ def main_gpu(args):
     from paper_2506_16759_gb300 import _lib
     from paper_2506_16759_gb300 import workloads as W
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    import datetime
+    world, rank, local = rank_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
-        dist.init_process_group("nccl", device_id=dev)
+        dist.init_process_group("nccl", device_id=dev,
+                                timeout=datetime.timedelta(seconds=RANK_TIMEOUT_S))
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
-
-    def max_over_ranks(v: float) -> float:
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
 
     # CPU oracle sample first (a child process; no fork of a CUDA process)
     cpu = None
@@ -247,17 +274,24 @@ def main_gpu(args):
         tree, h = step(k, prec, timing=True)
         stats.append(h.stats())
         del h, tree
-    total_ms = max_over_ranks(sum(times))
+    total_ms = max_over_ranks(sum(times), world, dev)
     ms_per_step = total_ms / args.steps
-    value = world * w.n * args.steps / (total_ms / 1e3)
+    value = job_throughput(world, w.n, args.steps, total_ms)
     log(f"[bench] {prec}: {ms_per_step:.1f} ms/step, {value:.3e} points/s")
 
     # roofline of the dominant kernel (fused kernel summation)
     ksum_ms = sum(s["ms_sketch_kernel"] for s in stats)
     ksum_n = sum(s["sketch_launches"] for s in stats)
     ksum_flops = sum(s["sketch_flops"] for s in stats)
-    achieved = ksum_flops / (ksum_ms * 1e-3) / 1e12 if ksum_ms > 0 else None
-    peak = FP32_PEAK_TFLOPS if prec == "mixed" else FP64_PEAK_TFLOPS
+    ksum_pairs = sum(s["sketch_pairs"] for s in stats)
+    if prec == "mixed":
+        # entries generated per second against the special-function-unit bound
+        achieved = ksum_pairs / (ksum_ms * 1e-3) / 1e9 if ksum_ms > 0 else None
+        peak, r_unit = SFU_PEAK_GPAIRS, "Gpair/s"
+    else:
+        achieved = ksum_flops / (ksum_ms * 1e-3) / 1e12 if ksum_ms > 0 else None
+        peak, r_unit = FP64_PEAK_TFLOPS, "TFLOP/s"
+    ksum_tflops = ksum_flops / (ksum_ms * 1e-3) / 1e12 if ksum_ms > 0 else None
     phases = {p: statistics.mean(s[f"ms_{p}"] for s in stats)
               for p in ("sketch", "nearfield", "qr", "id", "upsweep", "coupling", "bsr", "total")}
     last = stats[-1]
@@ -346,18 +380,20 @@ def main_gpu(args):
                        "omega": "Philox4x32-10 on device",
                        "l2": "flushed between timed steps (512 MiB write)",
                        "step": "tree + lists + H2 build, device-resident points"},
-            "roofline": {"kernel": ("k_ksum_tc (fused kernel summation, tcgen05 TF32 hi/lo, "
-                                    "entries evaluated on the CUDA cores)")
+            "roofline": {"kernel": ("k_ksum_tc (fused kernel summation: entries generated on "
+                                    "the CUDA cores and special-function units, contracted on "
+                                    "tcgen05 with two-part FP16 operands)")
                          if sched["prec"] == "mixed" else
                          ("k_ksum32 (fused kernel summation, FP32 CUDA cores)"
                           if sched["prec"] == "mixed_simt" else
                           "k_ksum64 (fused kernel summation, FP64)"),
-                         "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "bound": "alu", "achieved": achieved, "peak": peak, "unit": r_unit,
                          "frac": achieved / peak if achieved else None,
                          "traffic": traffic,
-                         "peak_source": ("152 SMs x 128 FP32 lanes x 2 x 2070 MHz (unit counts "
-                                         "and max clock)" if prec == "mixed" else
-                                         "nominal GB300 FP64 1.25 TFLOP/s"),
+                         "peak_source": ("152 SMs x 16 SFU lanes x 2070 MHz / 2 SFU operations per "
+                                         "Matern entry (unit counts and max clock)"
+                                         if prec == "mixed" else "nominal GB300 FP64 1.25 TFLOP/s"),
+                         "algorithmic_tflops": ksum_tflops,
                          "flops_per_pair": "2*columns + 10", "launches": ksum_n,
                          "avg_launch_ms": ksum_ms / ksum_n if ksum_n else None},
             "cpu_baseline": cpu,

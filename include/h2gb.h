@@ -42,6 +42,9 @@ typedef enum {
   H2_ERR_OOM = -3,            /* device allocation failed */
   H2_ERR_NOT_CONVERGED = -4,  /* d_max reached before every cluster converged;
                                  the H2 matrix is still complete and usable */
+  H2_ERR_TIMEOUT = -5,        /* a bounded wait inside a kernel ran out; the
+                                 kernel ended without faulting and the device
+                                 context stays usable */
   H2_ERR_SAMPLER = -6,        /* the user sampler returned non-zero */
   H2_ERR_INPUT = -7           /* non-finite coordinates or sketch values */
 } h2_status;
@@ -67,8 +70,10 @@ typedef enum {
 typedef enum {
   H2_PREC_FP64 = 0,       /* every step in FP64 */
   H2_PREC_MIXED = 1,      /* entries and block products in FP32, the fused
-                             sketch on the tensor cores (TF32 hi/lo split,
-                             FP32 accumulation); QR convergence test and
+                             sketch on the tensor cores (two-part operands:
+                             FP16 for the exponential, Matern and Gaussian
+                             kernels with drawn Omega, TF32 otherwise; FP32
+                             accumulation); QR convergence test and
                              pivoted-QR ID in FP64 */
   H2_PREC_MIXED_SIMT = 2  /* as H2_PREC_MIXED with the sketch in FP32 on the
                              CUDA cores */
@@ -303,6 +308,14 @@ h2_status h2_batched_row_id(int count, const int32_t *m, const int32_t *d, const
 h2_status h2_batched_qr_mindiag_static(int count, const int32_t *m, const int32_t *d,
                                        const int64_t *off, const double *panels,
                                        double *mindiag, h2_stream_t s);
+
+/* Failure-detection self-test of the tensor-core sketch: one small launch in
+ * which the producer warp withholds the first tile, so the waits of the
+ * other warps run out (0.2 s bound each), followed by a normal launch of the
+ * same problem.  Returns H2_OK when the stalled launch reported
+ * H2_ERR_TIMEOUT and the normal one then completed; otherwise the status
+ * that went wrong.  Not part of the construction. */
+h2_status h2_selftest_wait_timeout(h2_stream_t stream);
 
 /* The library keeps device blocks it freed for reuse (size buckets per
  * device), so repeated builds avoid cudaMalloc/cudaFree; this synchronises

@@ -16,7 +16,8 @@ LIB_PATH = os.environ.get("H2GB_LIB") or os.path.join(os.path.dirname(os.path.ab
 H2_OK = 0
 H2_ERR_NOT_CONVERGED = -4
 STATUS_NAMES = {0: "H2_OK", -1: "H2_ERR_ARG", -2: "H2_ERR_CUDA", -3: "H2_ERR_OOM",
-                -4: "H2_ERR_NOT_CONVERGED", -6: "H2_ERR_SAMPLER", -7: "H2_ERR_INPUT"}
+                -4: "H2_ERR_NOT_CONVERGED", -5: "H2_ERR_TIMEOUT", -6: "H2_ERR_SAMPLER",
+                -7: "H2_ERR_INPUT"}
 
 SAMPLER_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
                          C.c_int64, C.c_int, C.c_int64, C.c_void_p)
@@ -64,6 +65,7 @@ SIGNATURES = {
     "h2_last_error": (C.c_char_p, []),
     "h2_kernel_launches": (C.c_int64, []),
     "h2_trim_memory": (None, []),
+    "h2_selftest_wait_timeout": (C.c_int, [C.c_void_p]),
     "h2_build_cluster_tree": (i32, [vp, i64, i32, i32, dbl, vp, C.POINTER(vp)]),
     "h2_tree_info": (i32, [vp, C.POINTER(TreeInfo)]),
     "h2_tree_export": (i32, [vp, vp, vp, vp, vp, vp]),

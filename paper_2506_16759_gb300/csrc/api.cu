@@ -678,6 +678,10 @@ struct Builder {
       } else {
         plan = plan_ksum_tc_near(L.h_m, L.h_row, L.task_base, lcount, h_near_ptr, h_near_idx,
                                  insts, cq, w, ul_leaf, ul_flags);
+        for (int i : insts) {   // the near pairs only
+          sketch_pairs += near_pairs[i];
+          sketch_flops += (double)near_pairs[i] * (2.0 * w + 10.0);
+        }
         to_device(d_ul_leaf, ul_leaf, s);
         to_device(d_ul_flags, ul_flags, s);
       }
@@ -1368,6 +1372,60 @@ void matvec_impl(const h2_matrix *H, const double *x, double *y, int nrhs, cudaS
 
 using namespace h2;
 
+namespace h2 {
+// Y = K Omega on the tensor cores for a flat point set (original order), the
+// points taken as consecutive leaves of one tile each.  stall: self-test.
+void tc_sum_points(int kernel_id, const KernelDesc &kd, const InstDev *idev, Points64 p64,
+                   int64_t n, const float *om32, float *y32, int d, bool stall, cudaStream_t st) {
+  const bool f16 = tc_f16_kernel(kernel_id) && tc_max_abs(om32, n, n, 0, d, st) <= 1e4f;
+  const int64_t tj = f16 ? 64 : 32;
+  const int nl = (int)((n + tj - 1) / tj);
+  std::vector<int64_t> lrow(nl);
+  std::vector<int32_t> lm(nl), linst(nl, 0);
+  for (int b = 0; b < nl; ++b) {
+    lrow[b] = tj * b;
+    lm[b] = (int32_t)std::min<int64_t>(tj, n - tj * b);
+  }
+  DBuf<int64_t> dlrow;
+  DBuf<int32_t> dlm, dc0;
+  to_device(dlrow, lrow, st);
+  to_device(dlm, lm, st);
+  to_device(dc0, std::vector<int32_t>{0}, st);
+  TcLayout lay;
+  tc_layout_build(kernel_id, f16, lrow, lm, linst, {kd}, dlrow.p, dlm.p, p64, lay, st);
+  const int nchunks = (d + 63) / 64;
+  const int img_nc = 64 * (nchunks - 1) + tc_chunk_ncol(d - 64 * (nchunks - 1));
+  DBuf<float> img_hi, img_lo;
+  img_hi.alloc((size_t)lay.n_tiles * 32 * img_nc);
+  img_lo.alloc((size_t)lay.n_tiles * 32 * img_nc);
+  tc_omega_image(lay, dlrow.p, dlm.p, om32, n, dc0.p, d, img_nc, img_hi.p, img_lo.p, st);
+  const std::vector<int64_t> nn = {n}, bb = {0};
+  for (int done = 0; done < d; done += 64) {
+    const int w = std::min(64, d - done);
+    KsumPlan plan = plan_ksum_tc_all(nn, bb, {0}, {nl}, {0}, {done}, w, device_sm_count());
+    TcArgs a{};
+    a.inst = idev;
+    a.p64 = p64;
+    a.leaf_row = dlrow.p;
+    a.leaf_m = dlm.p;
+    a.leaf_tile = lay.leaf_tile.p;
+    a.ref_hi = lay.ref_hi.p;
+    a.ref_lo = lay.ref_lo.p;
+    a.off = lay.off.p;
+    a.sigma = lay.sigma.p;
+    a.img_hi = img_hi.p;
+    a.img_lo = img_lo.p;
+    a.img_nc = img_nc;
+    a.img_c0 = done;
+    a.om = om32;
+    a.y = y32;
+    a.ld = n;
+    a.stall = stall ? 1 : 0;
+    run_ksum_tc(kernel_id, plan, a, 0, lay.f16, st);
+  }
+}
+}  // namespace h2
+
 extern "C" {
 
 void h2_default_opts(h2_build_opts *o) {
@@ -1387,6 +1445,51 @@ const char *h2_last_error(void) { return g_last_error.c_str(); }
 int64_t h2_kernel_launches(void) { return g_launches; }
 
 void h2_trim_memory(void) { h2::dev_trim(); }
+
+h2_status h2_selftest_wait_timeout(h2_stream_t stream) {
+  return guarded([&]() -> h2_status {
+    cudaStream_t st = (cudaStream_t)stream;
+    // a small deterministic problem: 1024 points, 16 columns
+    const int64_t n = 1024;
+    const int d = 16;
+    std::vector<double> hx(n), hy(n), hz(n);
+    std::vector<float> hom((size_t)n * d);
+    uint64_t z = 0x9E3779B97F4A7C15ull;
+    auto next = [&]() {   // splitmix64 -> [0, 1)
+      z += 0x9E3779B97F4A7C15ull;
+      uint64_t v = z;
+      v = (v ^ (v >> 30)) * 0xBF58476D1CE4E5B9ull;
+      v = (v ^ (v >> 27)) * 0x94D049BB133111EBull;
+      return (double)((v ^ (v >> 31)) >> 11) * (1.0 / 9007199254740992.0);
+    };
+    for (int64_t i = 0; i < n; ++i) { hx[i] = next(); hy[i] = next(); hz[i] = next(); }
+    for (auto &v : hom) v = (float)(next() - 0.5);
+    h2::DBuf<double> px, py, pz;
+    h2::DBuf<float> om, y;
+    h2::to_device(px, hx, st);
+    h2::to_device(py, hy, st);
+    h2::to_device(pz, hz, st);
+    h2::to_device(om, hom, st);
+    y.alloc((size_t)n * d);
+    const double params[2] = {0.2, 0.0};
+    h2::KernelDesc kd = h2::make_kernel_desc(H2_K_EXP, params, 2);
+    h2::DBuf<h2::InstDev> idev;
+    h2::to_device(idev, std::vector<h2::InstDev>{h2::InstDev{0, n, kd}}, st);
+    const h2::Points64 p64{px.p, py.p, pz.p};
+    h2_status stalled = H2_OK;
+    try {
+      h2::tc_sum_points(H2_K_EXP, kd, idev.p, p64, n, om.p, y.p, d, true, st);
+    } catch (const h2::Error &e) {
+      stalled = e.code;
+    }
+    if (stalled != H2_ERR_TIMEOUT)
+      return h2::fail(stalled == H2_OK ? H2_ERR_CUDA : stalled,
+                      "the stalled launch did not report a timeout");
+    h2::tc_sum_points(H2_K_EXP, kd, idev.p, p64, n, om.p, y.p, d, false, st);
+    H2_CUDA(cudaStreamSynchronize(st));
+    return H2_OK;
+  });
+}
 
 h2_status h2_build_cluster_tree(const double *points, int64_t n, int dim, int leaf_size,
                                 double eta, h2_stream_t s, h2_tree **out) {
@@ -1667,52 +1770,9 @@ h2_status h2_ksum_sketch(const double *points, int64_t n, int dim, int kernel_id
     }
     H2_REQUIRE(d % 8 == 0, "d must be a multiple of 8");
     if (prec == H2_PREC_MIXED) {
-      // tensor cores: the points as consecutive leaves of one tile each
-      const bool f16 = tc_f16_kernel(kernel_id) && tc_max_abs(om32.p, n, n, 0, d, st) <= 1e4f;
-      const int64_t tj = f16 ? 64 : 32;
-      const int nl = (int)((n + tj - 1) / tj);
-      std::vector<int64_t> lrow(nl);
-      std::vector<int32_t> lm(nl), linst(nl, 0);
-      for (int b = 0; b < nl; ++b) {
-        lrow[b] = tj * b;
-        lm[b] = (int32_t)std::min<int64_t>(tj, n - tj * b);
-      }
-      DBuf<int64_t> dlrow;
-      DBuf<int32_t> dlm, dc0;
-      to_device(dlrow, lrow, st);
-      to_device(dlm, lm, st);
-      to_device(dc0, std::vector<int32_t>{0}, st);
-      const Points64 p64{px.p, py.p, pz.p};
-      TcLayout lay;
-      tc_layout_build(kernel_id, f16, lrow, lm, linst, {kd}, dlrow.p, dlm.p, p64, lay, st);
-      const int nchunks = (d + 63) / 64;
-      const int img_nc = 64 * (nchunks - 1) + tc_chunk_ncol(d - 64 * (nchunks - 1));
-      DBuf<float> img_hi, img_lo;
-      img_hi.alloc((size_t)lay.n_tiles * 32 * img_nc);
-      img_lo.alloc((size_t)lay.n_tiles * 32 * img_nc);
-      tc_omega_image(lay, dlrow.p, dlm.p, om32.p, n, dc0.p, d, img_nc, img_hi.p, img_lo.p, st);
-      for (; done < d; done += 64) {
-        const int w = std::min(64, d - done);
-        KsumPlan plan = plan_ksum_tc_all(nn, bb, {0}, {nl}, insts, {done}, w, device_sm_count());
-        TcArgs a{};
-        a.inst = idev.p;
-        a.p64 = p64;
-        a.leaf_row = dlrow.p;
-        a.leaf_m = dlm.p;
-        a.leaf_tile = lay.leaf_tile.p;
-        a.ref_hi = lay.ref_hi.p;
-        a.ref_lo = lay.ref_lo.p;
-        a.off = lay.off.p;
-        a.sigma = lay.sigma.p;
-        a.img_hi = img_hi.p;
-        a.img_lo = img_lo.p;
-        a.img_nc = img_nc;
-        a.img_c0 = done;
-        a.om = om32.p;
-        a.y = y32.p;
-        a.ld = n;
-        run_ksum_tc(kernel_id, plan, a, false, lay.f16, st);
-      }
+      h2::tc_sum_points(kernel_id, kd, idev.p, Points64{px.p, py.p, pz.p}, n, om32.p, y32.p, d,
+                        false, st);
+      done = d;
     }
     while (done < d) {
       int dc = std::min(32, pick_dc(d - done));

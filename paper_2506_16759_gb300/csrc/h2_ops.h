@@ -135,6 +135,7 @@ struct TcArgs {
   float *partial;            // plan partial slots (kRows x ncol each)
   int *err;                  // set if an mbarrier wait timed out
   int ncol;                  // valid columns of this launch (<= the template width)
+  int stall;                 // self-test: the producer issues nothing, the waits run out
 };
 int tc_chunk_ncol(int w);    // template width (16, 32 or 64) for w <= 64 columns
 // Kernels whose entries are at most 1 (FP16 parts allowed).
@@ -166,6 +167,10 @@ KsumPlan plan_ksum_tc_near(const std::vector<int32_t> &leaf_m, const std::vector
                            const std::vector<int32_t> &near_idx, const std::vector<int> &insts,
                            const std::vector<int> &c0, int ncols, std::vector<int32_t> &ul_leaf,
                            std::vector<int32_t> &ul_flags);
+// Y = K Omega on the tensor cores for a flat point set (the points taken as
+// consecutive leaves of one tile each); stall: self-test (waits run out).
+void tc_sum_points(int kernel_id, const KernelDesc &kd, const InstDev *idev, Points64 p64,
+                   int64_t n, const float *om32, float *y32, int d, bool stall, cudaStream_t st);
 // Plan of the all-points summation for the tensor-core kernel: 128-row
 // tiles, the point range split over leaf ranges [lb0, lb1) of the layout.
 KsumPlan plan_ksum_tc_all(const std::vector<int64_t> &inst_n, const std::vector<int64_t> &inst_base,

@@ -585,7 +585,7 @@ void run_ksum_tc(int kid, const KsumPlan &plan, const TcArgs &a0, int mode, bool
     H2_CHECK_LAUNCH();
   }
   if (to_host(err.p, 1, s)[0])
-    throw Error{H2_ERR_CUDA, "tensor-core sketch: an mbarrier wait timed out"};
+    throw Error{H2_ERR_TIMEOUT, "tensor-core sketch: an mbarrier wait ran out"};
 }
 
 KsumPlan plan_ksum_tc_near(const std::vector<int32_t> &leaf_m, const std::vector<int64_t> &leaf_row,

@@ -499,7 +499,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ksum_tc(TcArgs a) {
       p += __popc(__ballot_sync(0xffffffffu, in));
       return __reduce_or_sync(0xffffffffu, in ? 1u << (v - b0) : 0u);
     };
-    for (int b0 = it.lb0; b0 < it.lb1; b0 += 32) {
+    for (int b0 = a.stall ? it.lb1 : it.lb0; b0 < it.lb1; b0 += 32) {
       if (__any_sync(0xffffffffu, s_abort != 0)) ok = false;
       if (!ok) break;
       uint32_t n1 = 0, n2 = 0xffffffffu;
@@ -535,7 +535,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ksum_tc(TcArgs a) {
       ok = __shfl_sync(0xffffffffu, ok, 0);
       __syncwarp();
     }
-    if (lane == 0) {
+    if (lane == 0 && !a.stall) {
       const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
       if (ok && pend) emit(1, 0, 0, z, z, 0);
       if (ok) emit(0, 0, 0, z, z, 0);
