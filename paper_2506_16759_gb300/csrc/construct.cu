@@ -17,6 +17,7 @@ namespace h2 {
 namespace {
 
 constexpr int kNT = 256;   // threads per cluster CTA
+constexpr int kMaxCols = 256;   // sample columns at most (d_max)
 constexpr int kMaxRows = 256;     // rows of a block-product row task
 constexpr int kMaxIdRows = 512;   // rows of a cluster in the QR test / row ID
 
@@ -291,8 +292,12 @@ __global__ void k_dgen(DgenArgs a) {
 // ----------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kNT) k_qr_test(QrArgs a) {
+  // One thread per column of Y_loc (m x d), stored row-major in shared
+  // memory (a thread's column is read with unit stride across the warp).
+  // Each column's trailing norm for the next step is summed while the column
+  // is updated, so a step needs no block reduction.
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[33];
+  __shared__ double nrm2[kMaxCols];
   int tau = blockIdx.x;
   int inst = a.t.inst[tau];
   if (!a.active[inst] || a.conv[tau]) return;
@@ -311,34 +316,45 @@ __global__ void __launch_bounds__(kNT) k_qr_test(QrArgs a) {
   int64_t row = a.t.row[tau];
   for (int64_t q = threadIdx.x; q < (int64_t)m * d; q += kNT) {
     int i = (int)(q % m), c = (int)(q / m);
-    A[q] = (double)Y[row + i + (int64_t)c * a.ld];
+    A[(int64_t)i * d + c] = (double)Y[row + i + (int64_t)c * a.ld];
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < d; c += kNT) {
+    double s2 = 0.0;
+    for (int i = 0; i < m; ++i) s2 += A[(int64_t)i * d + c] * A[(int64_t)i * d + c];
+    nrm2[c] = s2;
   }
   __syncthreads();
   const double eps = a.eps[inst];
   double minr = INFINITY;
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kNT >> 5;
   for (int j = 0; j < d; ++j) {
-    double *colj = A + (int64_t)j * m;
-    double part = 0.0;
-    for (int i = j + threadIdx.x; i < m; i += kNT) part += colj[i] * colj[i];
-    double nrm2 = block_sum(part, red);
-    double nrm = sqrt(nrm2);
+    const double nrm = sqrt(nrm2[j]);
     minr = fmin(minr, nrm);
     if (minr <= eps && !a.mindiag) break;  // converged: the minimum only decreases
     if (nrm == 0.0) continue;
-    double x0 = colj[j];
-    double alpha = x0 != 0.0 ? -copysign(nrm, x0) : -nrm;
-    double v0 = x0 - alpha;
-    double beta = 1.0 / (nrm * (nrm + fabs(x0)));   // 2 / (v^T v)
+    const double x0 = A[(int64_t)j * d + j];
+    const double alpha = x0 != 0.0 ? -copysign(nrm, x0) : -nrm;
+    const double beta = 1.0 / (nrm * (nrm + fabs(x0)));   // 2 / (v^T v)
     __syncthreads();
-    if (threadIdx.x == 0) colj[j] = v0;
+    if (threadIdx.x == 0) A[(int64_t)j * d + j] = x0 - alpha;   // v_j
     __syncthreads();
-    for (int c = j + 1 + warp; c < d; c += nw) {
-      double *colc = A + (int64_t)c * m;
-      double w = 0.0;
-      for (int i = j + lane; i < m; i += 32) w += colj[i] * colc[i];
-      w = warp_sum(w) * beta;
-      for (int i = j + lane; i < m; i += 32) colc[i] -= w * colj[i];
+    for (int c = j + 1 + threadIdx.x; c < d; c += kNT) {
+      double w0 = 0.0, w1 = 0.0;
+      int i = j;
+      for (; i + 1 < m; i += 2) {
+        w0 += A[(int64_t)i * d + j] * A[(int64_t)i * d + c];
+        w1 += A[(int64_t)(i + 1) * d + j] * A[(int64_t)(i + 1) * d + c];
+      }
+      if (i < m) w0 += A[(int64_t)i * d + j] * A[(int64_t)i * d + c];
+      const double w = (w0 + w1) * beta;
+      A[(int64_t)j * d + c] -= w * A[(int64_t)j * d + j];
+      double s2 = 0.0;
+      for (int r = j + 1; r < m; ++r) {
+        const double x = A[(int64_t)r * d + c] - w * A[(int64_t)r * d + j];
+        A[(int64_t)r * d + c] = x;
+        s2 += x * x;
+      }
+      nrm2[c] = s2;
     }
     __syncthreads();
   }
@@ -354,6 +370,9 @@ __global__ void __launch_bounds__(kNT) k_qr_test(QrArgs a) {
 // ----------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kNT) k_row_id(IdArgs a) {
+  // One thread per column (a point of the cluster) of A = Y_loc^T / sqrt(d),
+  // d x m, stored row-major in shared memory; each column's trailing norm for
+  // the next step is recomputed while the column is updated.
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[33];
   __shared__ double redv[33];
@@ -378,24 +397,20 @@ __global__ void __launch_bounds__(kNT) k_row_id(IdArgs a) {
   const double sd = sqrt((double)d);
   for (int64_t q = threadIdx.x; q < (int64_t)m * d; q += kNT) {
     int i = (int)(q % m), c = (int)(q / m);
-    A[c + (int64_t)i * d] = (double)Y[row + i + (int64_t)c * a.ld] / sd;
+    A[(int64_t)c * m + i] = (double)Y[row + i + (int64_t)c * a.ld] / sd;   // A(c, i)
   }
   for (int i = threadIdx.x; i < m; i += kNT) piv[i] = i;
   __syncthreads();
+  for (int c = threadIdx.x; c < m; c += kNT) {
+    double s2 = 0.0;
+    for (int r = 0; r < d; ++r) s2 += A[(int64_t)r * m + c] * A[(int64_t)r * m + c];
+    nrm2[c] = s2;
+  }
+  __syncthreads();
   const double eps = a.eps[inst];
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kNT >> 5;
   int kmax = min(d, m);
   int k = 0;
   while (k < kmax) {
-    // norms of the trailing columns, recomputed from scratch
-    for (int c = k + warp; c < m; c += nw) {
-      const double *col = A + (int64_t)c * d;
-      double s = 0.0;
-      for (int r = k + lane; r < d; r += 32) s += col[r] * col[r];
-      s = warp_sum(s);
-      if (lane == 0) nrm2[c] = s;
-    }
-    __syncthreads();
     double tot = 0.0, best = -1.0;
     int bi = 0x7fffffff;
     for (int c = k + threadIdx.x; c < m; c += kNT) {
@@ -407,43 +422,55 @@ __global__ void __launch_bounds__(kNT) k_row_id(IdArgs a) {
     if (sqrt(tot) <= eps) break;
     int p = block_argmax(best, bi, redv, redi);
     if (p < k || p >= m) break;  // no finite pivot left
+    const double nk = sqrt(nrm2[p]);
+    __syncthreads();
     if (p != k) {
-      double *ck = A + (int64_t)k * d, *cp = A + (int64_t)p * d;
       for (int r = threadIdx.x; r < d; r += kNT) {
-        double t0 = ck[r]; ck[r] = cp[r]; cp[r] = t0;
+        double t0 = A[(int64_t)r * m + k];
+        A[(int64_t)r * m + k] = A[(int64_t)r * m + p];
+        A[(int64_t)r * m + p] = t0;
       }
-      if (threadIdx.x == 0) { int t1 = piv[k]; piv[k] = piv[p]; piv[p] = t1; }
-    }
-    __syncthreads();
-    double *colk = A + (int64_t)k * d;
-    double nk = sqrt(nrm2[p]);
-    double x0 = colk[k];
-    double alpha = x0 != 0.0 ? -copysign(nk, x0) : -nk;
-    double beta = nk > 0.0 ? 1.0 / (nk * (nk + fabs(x0))) : 0.0;
-    __syncthreads();
-    if (threadIdx.x == 0) colk[k] = x0 - alpha;
-    __syncthreads();
-    if (beta != 0.0) {
-      for (int c = k + 1 + warp; c < m; c += nw) {
-        double *colc = A + (int64_t)c * d;
-        double w = 0.0;
-        for (int r = k + lane; r < d; r += 32) w += colk[r] * colc[r];
-        w = warp_sum(w) * beta;
-        for (int r = k + lane; r < d; r += 32) colc[r] -= w * colk[r];
+      if (threadIdx.x == 0) {
+        int t1 = piv[k]; piv[k] = piv[p]; piv[p] = t1;
+        double t2 = nrm2[k]; nrm2[k] = nrm2[p]; nrm2[p] = t2;
       }
     }
     __syncthreads();
-    if (threadIdx.x == 0) colk[k] = alpha;
+    const double x0 = A[(int64_t)k * m + k];
+    const double alpha = x0 != 0.0 ? -copysign(nk, x0) : -nk;
+    const double beta = nk > 0.0 ? 1.0 / (nk * (nk + fabs(x0))) : 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0) A[(int64_t)k * m + k] = x0 - alpha;   // v_k
+    __syncthreads();
+    for (int c = k + 1 + threadIdx.x; c < m; c += kNT) {
+      double w0 = 0.0, w1 = 0.0;
+      int r = k;
+      for (; r + 1 < d; r += 2) {
+        w0 += A[(int64_t)r * m + k] * A[(int64_t)r * m + c];
+        w1 += A[(int64_t)(r + 1) * m + k] * A[(int64_t)(r + 1) * m + c];
+      }
+      if (r < d) w0 += A[(int64_t)r * m + k] * A[(int64_t)r * m + c];
+      const double w = (w0 + w1) * beta;
+      A[(int64_t)k * m + c] -= w * A[(int64_t)k * m + k];
+      double s2 = 0.0;
+      for (int q = k + 1; q < d; ++q) {
+        const double x = A[(int64_t)q * m + c] - w * A[(int64_t)q * m + k];
+        A[(int64_t)q * m + c] = x;
+        s2 += x * x;
+      }
+      nrm2[c] = s2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) A[(int64_t)k * m + k] = alpha;
     __syncthreads();
     ++k;
   }
-  // T = R11^{-1} R12 by back substitution, written over R12 (column-wise)
+  // T = R11^{-1} R12 by back substitution, written over R12 (one thread per column)
   for (int c = k + threadIdx.x; c < m; c += kNT) {
-    double *col = A + (int64_t)c * d;
     for (int i = k - 1; i >= 0; --i) {
-      double t = col[i];
-      for (int j = i + 1; j < k; ++j) t -= A[i + (int64_t)j * d] * col[j];
-      col[i] = t / A[i + (int64_t)i * d];
+      double t = A[(int64_t)i * m + c];
+      for (int j = i + 1; j < k; ++j) t -= A[(int64_t)i * m + j] * A[(int64_t)j * m + c];
+      A[(int64_t)i * m + c] = t / A[(int64_t)i * m + i];
     }
   }
   // sorted skeleton order
@@ -465,7 +492,7 @@ __global__ void __launch_bounds__(kNT) k_row_id(IdArgs a) {
   }
   for (int64_t q = threadIdx.x; q < (int64_t)(m - k) * k; q += kNT) {
     int rr = (int)(q % (m - k)), ap = (int)(q / (m - k));
-    E[piv[k + rr] + (int64_t)ap * m] = A[sig[ap] + (int64_t)(k + rr) * d];
+    E[piv[k + rr] + (int64_t)ap * m] = A[(int64_t)sig[ap] * m + (k + rr)];
   }
   if (threadIdx.x == 0) a.k_out[tau] = k;
 }
