@@ -649,9 +649,9 @@ struct Builder {
       tc_layout_build(H->kid, f16, L.h_row, L.h_m, L.h_inst, kds, L.row.p, L.m.p, p64(), tcl, s);
       tcl_ready = true;
     }
-    const int nchunks = (nc + 63) / 64;
-    const int last = nc - 64 * (nchunks - 1);
-    const int img_nc = 64 * (nchunks - 1) + tc_chunk_ncol(last);
+    const int nchunks = (nc + kTcChunk - 1) / kTcChunk;
+    const int last = nc - kTcChunk * (nchunks - 1);
+    const int img_nc = kTcChunk * (nchunks - 1) + tc_chunk_ncol(last);
     std::vector<int32_t> hc0(c0.begin(), c0.end());
     DBuf<int32_t> dc0;
     to_device(dc0, hc0, s);
@@ -664,8 +664,8 @@ struct Builder {
     for (int i = 0; i < H->count; ++i) lcount[i] = 1 << H->inst_depth[i];
     std::vector<int32_t> ul_leaf, ul_flags;
     DBuf<int32_t> d_ul_leaf, d_ul_flags;
-    for (int done = 0; done < nc; done += 64) {
-      const int w = std::min(64, nc - done);
+    for (int done = 0; done < nc; done += kTcChunk) {
+      const int w = std::min(kTcChunk, nc - done);
       std::vector<int> cq(insts.size());
       for (size_t q = 0; q < insts.size(); ++q) cq[q] = c0[insts[q]] + done;
       KsumPlan plan;
@@ -1393,15 +1393,15 @@ void tc_sum_points(int kernel_id, const KernelDesc &kd, const InstDev *idev, Poi
   to_device(dc0, std::vector<int32_t>{0}, st);
   TcLayout lay;
   tc_layout_build(kernel_id, f16, lrow, lm, linst, {kd}, dlrow.p, dlm.p, p64, lay, st);
-  const int nchunks = (d + 63) / 64;
-  const int img_nc = 64 * (nchunks - 1) + tc_chunk_ncol(d - 64 * (nchunks - 1));
+  const int nchunks = (d + kTcChunk - 1) / kTcChunk;
+  const int img_nc = kTcChunk * (nchunks - 1) + tc_chunk_ncol(d - kTcChunk * (nchunks - 1));
   DBuf<float> img_hi, img_lo;
   img_hi.alloc((size_t)lay.n_tiles * 32 * img_nc);
   img_lo.alloc((size_t)lay.n_tiles * 32 * img_nc);
   tc_omega_image(lay, dlrow.p, dlm.p, om32, n, dc0.p, d, img_nc, img_hi.p, img_lo.p, st);
   const std::vector<int64_t> nn = {n}, bb = {0};
-  for (int done = 0; done < d; done += 64) {
-    const int w = std::min(64, d - done);
+  for (int done = 0; done < d; done += kTcChunk) {
+    const int w = std::min(kTcChunk, d - done);
     KsumPlan plan = plan_ksum_tc_all(nn, bb, {0}, {nl}, {0}, {done}, w, device_sm_count());
     TcArgs a{};
     a.inst = idev;
@@ -1683,7 +1683,7 @@ h2_status h2_autotune(const h2_tree *tree, int kernel_id, const double *params, 
     validate_opts(*base);
     cudaStream_t st = (cudaStream_t)s;
     std::vector<std::pair<int, int>> sched;
-    for (int d0 : {32, 64, tree->leaf_size})
+    for (int d0 : {32, 64, 80, tree->leaf_size})
       for (int inc : {16, 32}) {
         if (d0 % 8 || d0 > base->d_max) continue;
         if (std::find(sched.begin(), sched.end(), std::make_pair(d0, inc)) == sched.end())

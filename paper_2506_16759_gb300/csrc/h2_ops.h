@@ -137,7 +137,8 @@ struct TcArgs {
   int ncol;                  // valid columns of this launch (<= the template width)
   int stall;                 // self-test: the producer issues nothing, the waits run out
 };
-int tc_chunk_ncol(int w);    // template width (16, 32 or 64) for w <= 64 columns
+constexpr int kTcChunk = 80;  // sample columns per tensor-core launch at most
+int tc_chunk_ncol(int w);    // template width (16, 32, 64 or 80) for w <= 80 columns
 // Kernels whose entries are at most 1 (FP16 parts allowed).
 bool tc_f16_kernel(int kid);
 // max |x| over rows [0, n) and columns [c0, c1) (synchronises the stream).

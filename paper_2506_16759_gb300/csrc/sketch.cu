@@ -562,8 +562,8 @@ void run_ksum32(int kid, const KsumPlan &plan, const KsumArgs32 &a, cudaStream_t
 void run_ksum_tc(int kid, const KsumPlan &plan, const TcArgs &a0, int mode, bool f16,
                  cudaStream_t s) {
   if (plan.items.empty()) return;
-  H2_REQUIRE(plan.tile_rows == 128 && plan.dc >= 1 && plan.dc <= 64,
-             "tensor-core sketch needs 128-row tiles and at most 64 columns");
+  H2_REQUIRE(plan.tile_rows == 128 && plan.dc >= 1 && plan.dc <= kTcChunk,
+             "tensor-core sketch needs 128-row tiles and at most 80 columns");
   StagedPlan<float> sp;
   stage_plan(plan, sp, s);
   DBuf<int> err;

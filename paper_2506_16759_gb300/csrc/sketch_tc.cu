@@ -75,7 +75,19 @@ namespace h2 {
 namespace {
 
 constexpr int kRows = 128;     // MMA M, TMEM lanes
-constexpr int kSA = 2, kSB = 5, kR = 5, kNA = 2;
+constexpr int kSA = 2, kSB = 5, kR = 5;
+// TMEM accumulators of 2 x NCOL columns: two up to 64 columns, one for 80
+// (2 x 160 + 256 operand columns would not fit in 512); the read-back of
+// step k-1 always follows the operands of step k.
+template <int NCOL>
+struct TcAcc {
+  static constexpr int NA = NCOL > 64 ? 1 : 2;
+  // 18 warps put five on two sub-partitions, whose 16K registers cap a
+  // thread at 96: beyond 64 columns the compensated sums live in shared
+  // memory (and the B ring is shorter to make room)
+  static constexpr bool SMEM_SUMS = NCOL > 64;
+  static constexpr int SB = NCOL > 64 ? 3 : kSB;
+};
 constexpr int kEvalWarps = 16;
 constexpr int kThreads = 32 * (2 + kEvalWarps);
 constexpr int kWaitLimit = 1 << 22;
@@ -239,6 +251,14 @@ __device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, float *v) {
 }
 
 template <>
+__device__ __forceinline__ void tmem_ld<4>(uint32_t taddr, float *v);
+template <>
+__device__ __forceinline__ void tmem_ld<20>(uint32_t taddr, float *v) {
+  tmem_ld<16>(taddr, v);
+  tmem_ld<4>(taddr + 16, v + 16);
+}
+
+template <>
 __device__ __forceinline__ void tmem_ld<8>(uint32_t taddr, float *v) {
   uint32_t r[8];
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
@@ -311,7 +331,8 @@ struct TcCtrl {
 
 template <int NCOL, bool F16>
 constexpr size_t tc_smem_bytes() {
-  return 1024 + (size_t)kSB * 2 * (2 * NCOL * 128 + TcTile<F16>::TJ * 16);
+  return 1024 + (size_t)TcAcc<NCOL>::SB * 2 * (2 * NCOL * 128 + TcTile<F16>::TJ * 16) +
+         (TcAcc<NCOL>::SMEM_SUMS ? (size_t)2 * kRows * NCOL * sizeof(float) : 0);
 }
 
 // The two parts of 8 (FP16 mode: 16) entries, packed as the TMEM columns of
@@ -351,11 +372,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_ksum_tc(TcArgs a) {
   constexpr uint32_t B_STAGE = 2 * (2 * B_BYTES);     // two tiles, two parts each
   // TMEM columns: kNA accumulators of 2 x NCOL, then kSA operand-A stages of
   // 128 columns: part 1 of the two tiles (32 columns each), then part 2
+  constexpr int kNA = TcAcc<NCOL>::NA;
+  constexpr int kSB = TcAcc<NCOL>::SB;              // B stages of this width
+  constexpr bool SMEM_SUMS = TcAcc<NCOL>::SMEM_SUMS;
   constexpr uint32_t ACC_N = 2 * NCOL;
   constexpr uint32_t A_COL0 = kNA * ACC_N;
   constexpr uint32_t TCOLS = A_COL0 + kSA * 128 <= 256 ? 256 : 512;
   static_assert(A_COL0 + kSA * 128 <= 512, "TMEM columns");
-  static_assert(kSA == kNA && kSA == 2, "the read-back of step k-1 releases the A stage of step k+1");
+  static_assert(kSA == 2, "the read-back of step k-1 releases the A stage of step k+1");
   constexpr uint32_t IDESC2 = idesc_mma(F16, kRows, 2 * NCOL);
   constexpr uint32_t IDESC1 = idesc_mma(F16, kRows, NCOL);
   // second product A_2 * B_1: TF32 adds it to the first half, FP16 to the
@@ -367,8 +391,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_ksum_tc(TcArgs a) {
       (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
   unsigned char *sB = base;                                          // [kSB][tile][part]
   float4 *sOff = reinterpret_cast<float4 *>(sB + kSB * B_STAGE);    // [kSB][tile][TJ]
+  // compensated sums [column][row] (SMEM_SUMS only)
+  float *sAcc = reinterpret_cast<float *>(sOff + kSB * 2 * TJ);
+  float *sCmp = sAcc + kRows * NCOL;
   __shared__ TcCtrl ctrl[kSB];
-  __shared__ uint64_t bfull[kSB], afull[kSA], done[kR], accempty[kNA];
+  __shared__ uint64_t bfull[kSB], afull[kSA], done[kR], accempty[2];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_abort;
   __shared__ float4 m_rh[32], m_rl[32];   // producer: metadata of 32 leaves
@@ -600,19 +627,30 @@ __global__ void __launch_bounds__(kThreads, 1) k_ksum_tc(TcArgs a) {
     const float kc = (float)in.kd.scale;
     const int pw = in.kd.pw;
     const uint32_t lane_addr = (uint32_t)(quad * 32) << 16;
-    float grp[CPT], acc[CPT], cmp[CPT];
+    constexpr int CR = SMEM_SUMS ? 1 : CPT;   // register-resident compensated sums
+    float grp[CPT], acc[CR], cmp[CR];
+    float *sa = sAcc + (q * CPT) * kRows + r, *sc = sCmp + (q * CPT) * kRows + r;
 #pragma unroll
-    for (int c = 0; c < CPT; ++c) { grp[c] = 0.f; acc[c] = 0.f; cmp[c] = 0.f; }
+    for (int c = 0; c < CPT; ++c) grp[c] = 0.f;
+#pragma unroll
+    for (int c = 0; c < CR; ++c) { acc[c] = 0.f; cmp[c] = 0.f; }
+    if constexpr (SMEM_SUMS) {
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) { sa[c * kRows] = 0.f; sc[c * kRows] = 0.f; }
+    }
     auto fold = [&]() {
 #pragma unroll
       for (int c = 0; c < CPT; ++c) {
-        const float y = grp[c] - cmp[c];
-        const float s2 = acc[c] + y;
-        cmp[c] = (s2 - acc[c]) - y;
-        acc[c] = s2;
+        float &ac = SMEM_SUMS ? sa[c * kRows] : acc[c % CR];
+        float &cm = SMEM_SUMS ? sc[c * kRows] : cmp[c % CR];
+        const float y = grp[c] - cm;
+        const float s2 = ac + y;
+        cm = (s2 - ac) - y;
+        ac = s2;
         grp[c] = 0.f;
       }
     };
+    auto total = [&](int c) -> float { return SMEM_SUMS ? sa[c * kRows] : acc[c % CR]; };
     bool alive = true;
     auto fail = [&]() {
       alive = false;
@@ -685,27 +723,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_ksum_tc(TcArgs a) {
     if (alive && rowok) {
       const int64_t gr = it.row0 + r;
       const int cl = q * CPT;
+      // the nugget of the row's own point, if it lies in this item's leaves
+      // (near-only items cover the row's own leaf)
+      bool diag = false;
       if (!FAR && KID != H2_K_POLY && in.kd.diag != 0.0) {
-        // the nugget of the row's own point, if it lies in this item's leaves
-        // (near-only items cover the row's own leaf)
         const int64_t p0 = MODE == 2 ? gr : a.leaf_row[it.lb0];
         const int64_t pe = MODE == 2 ? gr + 1 : a.leaf_row[it.lb1 - 1] + a.leaf_m[it.lb1 - 1];
-        if (gr >= p0 && gr < pe) {
-          const float dg = (float)in.kd.diag;
-#pragma unroll
-          for (int c = 0; c < CPT; ++c)
-            if (cl + c < a.ncol) acc[c] += dg * a.om[gr + (int64_t)(it.c0 + cl + c) * a.ld];
-        }
+        diag = gr >= p0 && gr < pe;
       }
-      if (it.part < 0) {
+      const float dg = (float)in.kd.diag;
+      float *dst = it.part < 0 ? a.y + gr + (int64_t)(it.c0 + cl) * a.ld
+                               : a.partial + (int64_t)it.part * kRows * a.ncol + (int64_t)cl * kRows + r;
+      const int64_t stride = it.part < 0 ? a.ld : kRows;
 #pragma unroll
-        for (int c = 0; c < CPT; ++c)
-          if (cl + c < a.ncol) a.y[gr + (int64_t)(it.c0 + cl + c) * a.ld] = acc[c];
-      } else {
-        float *dst = a.partial + (int64_t)it.part * kRows * a.ncol;
-#pragma unroll
-        for (int c = 0; c < CPT; ++c)
-          if (cl + c < a.ncol) dst[(int64_t)(cl + c) * kRows + r] = acc[c];
+      for (int c = 0; c < CPT; ++c) {
+        if (cl + c >= a.ncol) continue;
+        float v = total(c);
+        if (diag) v += dg * a.om[gr + (int64_t)(it.c0 + cl + c) * a.ld];
+        dst[(int64_t)c * stride] = v;
       }
     }
   }
@@ -807,7 +842,7 @@ __global__ void k_max_abs(const float *x, int64_t ld, int64_t n, int c0, int c1,
 }
 }  // namespace
 
-int tc_chunk_ncol(int w) { return w <= 16 ? 16 : (w <= 32 ? 32 : 64); }
+int tc_chunk_ncol(int w) { return w <= 16 ? 16 : (w <= 32 ? 32 : (w <= 64 ? 64 : 80)); }
 
 bool tc_f16_kernel(int kid) {
   return kid == H2_K_EXP || kid == H2_K_MATERN32 || kid == H2_K_GAUSS;
@@ -883,10 +918,11 @@ void launch_ksum_tc(int kid, int ncol_tmpl, int mode, bool f16, int64_t items, c
       constexpr int MODE = decltype(M)::value;
       constexpr bool F16 = decltype(H)::value;
       switch (ncol_tmpl) {
+        case 80: launch_tc<KID, 80, MODE, F16>(items, a, s); break;
         case 64: launch_tc<KID, 64, MODE, F16>(items, a, s); break;
         case 32: launch_tc<KID, 32, MODE, F16>(items, a, s); break;
         case 16: launch_tc<KID, 16, MODE, F16>(items, a, s); break;
-        default: throw Error{H2_ERR_ARG, "tensor-core sketch takes 16, 32 or 64 columns"};
+        default: throw Error{H2_ERR_ARG, "tensor-core sketch takes 16, 32, 64 or 80 columns"};
       }
     };
     auto pick = [&](auto M) {
