@@ -364,11 +364,16 @@ struct Builder {
   void *Dp() { return fp64() ? (void *)H->D64.p : (void *)H->D32.p; }
 
   int max_cols = 0;
+  int col_hi = 0;   // the highest column end over the instances
   void set_cols(const std::vector<int32_t> &b, const std::vector<int32_t> &e) {
     to_device(cb, b, s);
     to_device(ce, e, s);
     max_cols = 0;
-    for (size_t i = 0; i < b.size(); ++i) max_cols = std::max(max_cols, e[i] - b[i]);
+    col_hi = 0;
+    for (size_t i = 0; i < b.size(); ++i) {
+      max_cols = std::max(max_cols, e[i] - b[i]);
+      if (e[i] > b[i]) col_hi = std::max(col_hi, e[i]);
+    }
   }
   InstCols cols() const { return InstCols{cb.p, ce.p}; }
 
@@ -794,6 +799,8 @@ struct Builder {
     a.ld_out = L.M;
     a.sign = sign;
     a.cols = cols();
+    a.in_rows = L.M;
+    a.col_hi = col_hi;
     bsr_apply(fp64(), a, L.max_m, max_cols, s);
     timer.end(PH_BSR);
   }
@@ -825,6 +832,8 @@ struct Builder {
     a.ld_out = U.M;
     a.sign = -1.0;
     a.cols = cols();
+    a.in_rows = U.M;
+    a.col_hi = col_hi;
     bsr_apply(fp64(), a, L.max_k, max_cols, s);
     timer.end(PH_BSR);
   }
@@ -1307,6 +1316,8 @@ void matvec_impl(const h2_matrix *H, const double *x, double *y, int nrhs, cudaS
     a.blocks = f64 ? (const void *)H->D64.p : (const void *)H->D32.p;
     a.in = xt.p;
     a.ld_in = N;
+    a.in_rows = N;
+    a.col_hi = nrhs;
     a.out = yt.p;
     a.ld_out = N;
     a.sign = 1.0;
@@ -1347,6 +1358,8 @@ void matvec_impl(const h2_matrix *H, const double *x, double *y, int nrhs, cudaS
       a.blocks = f64 ? (const void *)L.B64.p : (const void *)L.B32.p;
       a.in = xh[l].p;
       a.ld_in = L.K;
+      a.in_rows = L.K;
+      a.col_hi = nrhs;
       a.out = yh[l].p;
       a.ld_out = L.K;
       a.sign = 1.0;

@@ -263,6 +263,134 @@ __global__ void __launch_bounds__(kNT) k_bsr_pipe(BsrArgs a) {
   }
 }
 
+// ----------------------------------------------------------------------------
+// FP32 block-sparse row products with register tiles (blocks of at most 64 x
+// 64).  One CTA per row block; thread (rg, cg) owns rows 4rg..4rg+3 and
+// columns 4cg..4cg+3 of a DC-column chunk.  The partner blocks stream through
+// a two-slot ring (cp.async, 16-byte copies): the block itself (contiguous,
+// column-major) and its DC-column slice of the input rows, read from a
+// row-major copy of the input panel so that every row slice is contiguous.
+// Each block's product is summed plainly, the blocks with compensation.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16z(void *smem, const void *gmem, bool valid) {
+  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  int src = valid ? 16 : 0;   // src-size 0 fills the destination with zeros
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(src));
+}
+
+template <int DC>
+__global__ void __launch_bounds__(4 * DC) k_bsr_tile(BsrArgs a, const float *tin, int64_t ldt) {
+  constexpr int NT = 4 * DC;          // 16 row groups x DC/4 column groups
+  constexpr int SLOT_B = 64 * 64;     // floats
+  constexpr int SLOT_O = 64 * DC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float *sB = reinterpret_cast<float *>(smem_raw);   // [2][SLOT_B]
+  float *sO = sB + 2 * SLOT_B;                         // [2][64][DC]
+  const int tau = blockIdx.x;
+  const int m = a.row_m[tau];
+  const int inst = a.row_inst[tau];
+  const int cb = a.cols.cb[inst], ce = a.cols.ce[inst];
+  const int64_t e0 = a.ptr[tau], e1 = a.ptr[tau + 1];
+  if (m == 0 || ce <= cb || e0 == e1) return;
+  const int rg = threadIdx.x & 15, cg = threadIdx.x >> 4;
+  const int r0 = 4 * rg;
+  const float *blocks = reinterpret_cast<const float *>(a.blocks);
+  float *out = reinterpret_cast<float *>(a.out);
+  const float sgn = (float)a.sign;
+  for (int c0 = cb; c0 < ce; c0 += DC) {
+    const int ncol = min(DC, ce - c0);
+    float acc[16], cmp[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) { acc[q] = 0.f; cmp[q] = 0.f; }
+    auto issue = [&](int64_t e, int slot) {
+      if (e < e1) {
+        const int b = a.idx[e];
+        const int mb = a.col_m[b];
+        const char *src = reinterpret_cast<const char *>(blocks + a.boff[e]);
+        char *dst = reinterpret_cast<char *>(sB + slot * SLOT_B);
+        const int n16 = (m * mb * 4 + 15) / 16;
+        for (int u = threadIdx.x; u < n16; u += NT) cp_async16(dst + 16 * u, src + 16 * u);
+        const float *irow = tin + a.col_off[b] * ldt + c0;
+        float *di = sO + slot * SLOT_O;
+        for (int u = threadIdx.x; u < mb * (DC / 4); u += NT) {
+          const int j = u / (DC / 4), v = u % (DC / 4);
+          const bool ok = 4 * v < ncol;
+          cp_async16z(di + j * DC + 4 * v, ok ? irow + j * ldt + 4 * v : irow, ok);
+        }
+      }
+      cp_async_commit();
+    };
+    issue(e0, 0);
+    for (int64_t e = e0; e < e1; ++e) {
+      const int slot = (int)((e - e0) & 1);
+      issue(e + 1, slot ^ 1);
+      cp_async_wait<1>();
+      __syncthreads();
+      const int mb = a.col_m[a.idx[e]];
+      const float *Bs = sB + slot * SLOT_B;
+      const float *Os = sO + slot * SLOT_O + 4 * cg;
+      float part[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) part[q] = 0.f;
+      for (int j = 0; j < mb; ++j) {
+        const float4 o = *reinterpret_cast<const float4 *>(Os + j * DC);
+        float bv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) bv[i] = r0 + i < m ? Bs[j * m + r0 + i] : 0.f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          part[4 * i + 0] += bv[i] * o.x;
+          part[4 * i + 1] += bv[i] * o.y;
+          part[4 * i + 2] += bv[i] * o.z;
+          part[4 * i + 3] += bv[i] * o.w;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const float y = sgn * part[q] - cmp[q];
+        const float t = acc[q] + y;
+        cmp[q] = (t - acc[q]) - y;
+        acc[q] = t;
+      }
+      __syncthreads();
+    }
+    cp_async_wait<0>();
+    __syncthreads();
+    const int64_t orow = a.row_off[tau];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (r0 + i >= m) continue;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int col = 4 * cg + c;
+        if (col >= ncol) continue;
+        float *op = out + orow + r0 + i + (int64_t)(c0 + col) * a.ld_out;
+        const float y = *op - cmp[4 * i + c];
+        *op = acc[4 * i + c] + y;
+      }
+    }
+  }
+}
+
+// Row-major copy t[r * ldt + c] = in[r + c * ld] of rows [0, n), columns [0, nc).
+__global__ void k_transpose_panel(const float *in, int64_t ld, int64_t n, int nc, float *t,
+                                  int64_t ldt) {
+  __shared__ float tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+  for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+    const int64_t r = r0 + threadIdx.x;
+    const int c = c0 + q;
+    tile[q][threadIdx.x] = (r < n && c < nc) ? in[r + (int64_t)c * ld] : 0.f;
+  }
+  __syncthreads();
+  for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+    const int64_t r = r0 + q;
+    const int c = c0 + threadIdx.x;
+    if (r < n && c < (int)ldt) t[r * ldt + c] = c < nc ? tile[threadIdx.x][q] : 0.f;
+  }
+}
+
 // Dense near-field blocks D_{t,b} = K(I_t, I_b) for every near pair: one CTA
 // per block, coalesced column-major stores.
 template <int KID, typename T>
@@ -684,9 +812,35 @@ void launch_bsr(const BsrArgs &a, cudaStream_t s) {
   H2_CHECK_LAUNCH();
 }
 
+template <int DC>
+void launch_bsr_tile(const BsrArgs &a, const float *tin, int64_t ldt, cudaStream_t s) {
+  const size_t bytes = sizeof(float) * 2 * (64 * 64 + 64 * DC);
+  auto kern = k_bsr_tile<DC>;
+  set_smem(kern, bytes);
+  kern<<<a.n_rows, 4 * DC, bytes, s>>>(a, tin, ldt);
+  count_launch();
+  H2_CHECK_LAUNCH();
+}
+
 void bsr_apply(bool fp64, const BsrArgs &a, int max_m, int max_cols, cudaStream_t s) {
   if (a.n_rows == 0 || max_cols <= 0) return;
   H2_REQUIRE(max_m <= kMaxRows, "block rows above 256 are not supported");
+  if (!fp64 && max_m <= 64 && a.col_hi > 0 && a.in_rows > 0) {
+    // register-tiled path on a row-major copy of the input columns [0, col_hi)
+    const int64_t ldt = (a.col_hi + 3) / 4 * 4;
+    DBuf<float> tin;
+    tin.alloc((size_t)a.in_rows * ldt + 4);
+    dim3 grid((unsigned)ceil_div(a.in_rows, 32), (unsigned)ceil_div(ldt, 32));
+    k_transpose_panel<<<grid, dim3(32, 8), 0, s>>>(reinterpret_cast<const float *>(a.in), a.ld_in,
+                                                    a.in_rows, a.col_hi, tin.p, ldt);
+    count_launch();
+    H2_CHECK_LAUNCH();
+    if (max_cols <= 16) launch_bsr_tile<16>(a, tin.p, ldt, s);
+    else if (max_cols <= 32) launch_bsr_tile<32>(a, tin.p, ldt, s);
+    else if (max_cols <= 64) launch_bsr_tile<64>(a, tin.p, ldt, s);
+    else launch_bsr_tile<80>(a, tin.p, ldt, s);
+    return;
+  }
   const bool narrow = max_cols <= 16;
   if (max_m <= 64 && max_cols > 32 && !fp64) {
     launch_bsr<float, 64, 1>(a, s);   // one pass over the blocks for 64 columns
