@@ -233,6 +233,10 @@ __device__ __forceinline__ bool admissible_pair(int s, int t, const double *__re
 // the children of its parent's inadmissible partners (in increasing id) and
 // counts admissible (-> F) and inadmissible (-> next frontier or N) pairs.
 // Pass 2 (fill = true) writes them in the same order, so rows come out sorted.
+// One warp per node s of depth k: the lanes take the parent's inadmissible
+// partners 32 at a time; each partner contributes its two children in order,
+// so both output lists stay sorted.  Positions come from ballots (a lane adds
+// 0, 1 or 2 entries to each list).
 template <bool FILL>
 __global__ void k_traverse(int k, int n_nodes, const double *__restrict__ lo,
                            const double *__restrict__ hi, const double *__restrict__ diam,
@@ -241,28 +245,42 @@ __global__ void k_traverse(int k, int n_nodes, const double *__restrict__ lo,
                            int64_t *cnt_in, const int64_t *__restrict__ far_ptr,
                            int32_t *far_idx, const int64_t *__restrict__ in_ptr,
                            int32_t *in_idx) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  int n_at = 1 << k;
-  if (r >= n_at) return;
-  int s = (1 << k) - 1 + r;
-  int p = (s - 1) / 2;
-  int pr = p - ((1 << (k - 1)) - 1);
+  const int lane = threadIdx.x & 31;
+  const int r = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int n_at = 1 << k;
+  if (r >= n_at) return;   // whole warps leave together
+  const int s = (1 << k) - 1 + r;
+  const int p = (s - 1) / 2;
+  const int pr = p - ((1 << (k - 1)) - 1);
   int64_t nf = 0, ni = 0;
-  int64_t of = FILL ? far_ptr[r] : 0, oi = FILL ? in_ptr[r] : 0;
-  for (int64_t e = par_ptr[pr]; e < par_ptr[pr + 1]; ++e) {
-    int tp = par_idx[e];
-    for (int c = 1; c <= 2; ++c) {
-      int t = 2 * tp + c;
-      if (admissible_pair(s, t, lo, hi, diam, n_nodes, eta)) {
-        if (FILL) far_idx[of + nf] = t;
-        ++nf;
-      } else {
-        if (FILL) in_idx[oi + ni] = t;
-        ++ni;
-      }
+  const int64_t of = FILL ? far_ptr[r] : 0, oi = FILL ? in_ptr[r] : 0;
+  const uint32_t lt = (1u << lane) - 1u;
+  for (int64_t e0 = par_ptr[pr]; e0 < par_ptr[pr + 1]; e0 += 32) {
+    const int64_t e = e0 + lane;
+    const bool has = e < par_ptr[pr + 1];
+    int t1 = 0, t2 = 0;
+    bool a1 = false, a2 = false;
+    if (has) {
+      const int tp = par_idx[e];
+      t1 = 2 * tp + 1;
+      t2 = 2 * tp + 2;
+      a1 = admissible_pair(s, t1, lo, hi, diam, n_nodes, eta);
+      a2 = admissible_pair(s, t2, lo, hi, diam, n_nodes, eta);
     }
+    const int fc = (int)a1 + (int)a2;
+    const int ic = has ? 2 - fc : 0;
+    const uint32_t f1 = __ballot_sync(0xffffffffu, fc >= 1), f2 = __ballot_sync(0xffffffffu, fc == 2);
+    const uint32_t i1 = __ballot_sync(0xffffffffu, ic >= 1), i2 = __ballot_sync(0xffffffffu, ic == 2);
+    if (FILL && has) {
+      int64_t pf = of + nf + __popc(f1 & lt) + __popc(f2 & lt);
+      int64_t pi = oi + ni + __popc(i1 & lt) + __popc(i2 & lt);
+      if (a1) far_idx[pf++] = t1; else in_idx[pi++] = t1;
+      if (a2) far_idx[pf] = t2; else in_idx[pi] = t2;
+    }
+    nf += __popc(f1) + __popc(f2);
+    ni += __popc(i1) + __popc(i2);
   }
-  if (!FILL) {
+  if (!FILL && lane == 0) {
     cnt_far[r] = nf;
     cnt_in[r] = ni;
   }
@@ -473,8 +491,8 @@ void build_tree(const double *pts, int64_t n, int dim, int leaf, double eta, cud
     ci.alloc(n_at);
     pf.alloc(n_at + 1);
     pi.alloc(n_at + 1);
-    int nb = ceil_div(n_at, 128);
-    k_traverse<false><<<nb, 128, 0, s>>>(k, n_nodes, t->lo.p, t->hi.p, t->diam.p, eta, in_ptr.p,
+    int nb = ceil_div((int64_t)n_at * 32, 256);   // one warp per node
+    k_traverse<false><<<nb, 256, 0, s>>>(k, n_nodes, t->lo.p, t->hi.p, t->diam.p, eta, in_ptr.p,
                                          in_idx.p, cf.p, ci.p, nullptr, nullptr, nullptr,
                                          nullptr);
     count_launch();
@@ -488,7 +506,7 @@ void build_tree(const double *pts, int64_t n, int dim, int leaf, double eta, cud
     DBuf<int32_t> fidx, iidx;
     fidx.alloc(std::max<int64_t>(tot[0], 1));
     iidx.alloc(std::max<int64_t>(tot[1], 1));
-    k_traverse<true><<<nb, 128, 0, s>>>(k, n_nodes, t->lo.p, t->hi.p, t->diam.p, eta, in_ptr.p,
+    k_traverse<true><<<nb, 256, 0, s>>>(k, n_nodes, t->lo.p, t->hi.p, t->diam.p, eta, in_ptr.p,
                                         in_idx.p, nullptr, nullptr, pf.p, fidx.p, pi.p, iidx.p);
     count_launch();
     H2_CHECK_LAUNCH();
