@@ -457,8 +457,8 @@ def main_kernel_only(args):
     """Small processes for ncu captures.  "ksum": only the fused sketch of the
     benchmark workload (N=131072, 32 columns, all points, same launch plan as
     inside a build).  "build": whole builds of the same workload family at
-    --n points with the 64/+16 mixed schedule (its first k_ksum_tc launch is
-    the 64-column far-only sketch)."""
+    --n points with the 80/+16 mixed schedule (its first k_ksum_tc launch is
+    the 80-column far-only sketch)."""
     import torch
 
     from paper_2506_16759_gb300 import api
@@ -474,7 +474,7 @@ def main_kernel_only(args):
             t0 = time.perf_counter()
             tree = api.ClusterTree(X, w.leaf_size, w.eta)
             h = api.H2Matrix.build(tree, w.kernel, w.params, w.tol, prec="mixed", seed=k,
-                                   sketch="ksum", d0=64, d_inc=16, d_max=w.d_max)
+                                   sketch="ksum", d0=80, d_inc=16, d_max=w.d_max)
             torch.cuda.synchronize()
             if k >= args.warmup:
                 times.append((time.perf_counter() - t0) * 1e3)

@@ -897,7 +897,7 @@ struct Builder {
     a.ws_off = ws_off.p;
     a.mindiag = nullptr;
     timer.begin(PH_QR);
-    qr_test(fp64(), a, smem, s);
+    qr_test(fp64(), a, smem, *std::max_element(hd.begin(), hd.end()), s);
     timer.end(PH_QR);
     H2_CUDA(cudaStreamSynchronize(s));
   }
@@ -971,7 +971,7 @@ struct Builder {
     a.ws = ws.p;
     a.ws_off = ws_off.p;
     timer.begin(PH_ID);
-    row_id(fp64(), a, smem, s);
+    row_id(fp64(), a, smem, L.max_m, s);
     timer.end(PH_ID);
     L.krow.alloc(L.n + 1);
     scan_exclusive_i32(L.k.p, L.krow.p, L.n, s);
@@ -1894,7 +1894,7 @@ h2_status h2_batched_qr_mindiag(int count, const int32_t *m, const int32_t *d, c
       a.ws = ws.p + hw[t];
       a.ws_off = wo.p;
       a.mindiag = mindiag + t;
-      qr_test(true, a, 0, st);
+      qr_test(true, a, 0, 0, st);
       H2_CUDA(cudaStreamSynchronize(st));
     }
     return H2_OK;
@@ -1948,7 +1948,7 @@ h2_status h2_batched_row_id(int count, const int32_t *m, const int32_t *d, const
       a.E = basis + he[t];
       a.ws = ws.p;
       a.ws_off = wo.p;
-      row_id(true, a, 0, st);
+      row_id(true, a, 0, 0, st);
       H2_CUDA(cudaMemcpyAsync(J + (int64_t)t * ldj, jt.p, hm[t] * 4, cudaMemcpyDeviceToDevice, st));
       H2_CUDA(cudaStreamSynchronize(st));
     }

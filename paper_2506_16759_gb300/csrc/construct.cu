@@ -418,8 +418,8 @@ __global__ void k_dgen(DgenArgs a) {
 // ----------------------------------------------------------------------------
 // QR convergence test (FP64 Householder, one CTA per cluster).
 // ----------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(kNT) k_qr_test(QrArgs a) {
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_qr_test(QrArgs a) {
   // One thread per column of Y_loc (m x d), stored row-major in shared
   // memory (a thread's column is read with unit stride across the warp).
   // Each column's trailing norm for the next step is summed while the column
@@ -442,12 +442,12 @@ __global__ void __launch_bounds__(kNT) k_qr_test(QrArgs a) {
                                              : reinterpret_cast<double *>(smem_raw);
   const T *Y = reinterpret_cast<const T *>(a.Y);
   int64_t row = a.t.row[tau];
-  for (int64_t q = threadIdx.x; q < (int64_t)m * d; q += kNT) {
+  for (int64_t q = threadIdx.x; q < (int64_t)m * d; q += NT) {
     int i = (int)(q % m), c = (int)(q / m);
     A[(int64_t)i * d + c] = (double)Y[row + i + (int64_t)c * a.ld];
   }
   __syncthreads();
-  for (int c = threadIdx.x; c < d; c += kNT) {
+  for (int c = threadIdx.x; c < d; c += NT) {
     double s2 = 0.0;
     for (int i = 0; i < m; ++i) s2 += A[(int64_t)i * d + c] * A[(int64_t)i * d + c];
     nrm2[c] = s2;
@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(kNT) k_qr_test(QrArgs a) {
     __syncthreads();
     if (threadIdx.x == 0) A[(int64_t)j * d + j] = x0 - alpha;   // v_j
     __syncthreads();
-    for (int c = j + 1 + threadIdx.x; c < d; c += kNT) {
+    for (int c = j + 1 + threadIdx.x; c < d; c += NT) {
       double w0 = 0.0, w1 = 0.0;
       int i = j;
       for (; i + 1 < m; i += 2) {
@@ -496,8 +496,8 @@ __global__ void __launch_bounds__(kNT) k_qr_test(QrArgs a) {
 // ----------------------------------------------------------------------------
 // Row ID by column-pivoted Householder QR of A = Y_loc^T / sqrt(d), d x m.
 // ----------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(kNT) k_row_id(IdArgs a) {
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_row_id(IdArgs a) {
   // One thread per column (a point of the cluster) of A = Y_loc^T / sqrt(d),
   // d x m, stored row-major in shared memory; each column's trailing norm for
   // the next step is recomputed while the column is updated.
@@ -523,13 +523,13 @@ __global__ void __launch_bounds__(kNT) k_row_id(IdArgs a) {
                                              : reinterpret_cast<double *>(sig + kMaxIdRows);
   const T *Y = reinterpret_cast<const T *>(a.Y);
   const double sd = sqrt((double)d);
-  for (int64_t q = threadIdx.x; q < (int64_t)m * d; q += kNT) {
+  for (int64_t q = threadIdx.x; q < (int64_t)m * d; q += NT) {
     int i = (int)(q % m), c = (int)(q / m);
     A[(int64_t)c * m + i] = (double)Y[row + i + (int64_t)c * a.ld] / sd;   // A(c, i)
   }
-  for (int i = threadIdx.x; i < m; i += kNT) piv[i] = i;
+  for (int i = threadIdx.x; i < m; i += NT) piv[i] = i;
   __syncthreads();
-  for (int c = threadIdx.x; c < m; c += kNT) {
+  for (int c = threadIdx.x; c < m; c += NT) {
     double s2 = 0.0;
     for (int r = 0; r < d; ++r) s2 += A[(int64_t)r * m + c] * A[(int64_t)r * m + c];
     nrm2[c] = s2;
@@ -541,7 +541,7 @@ __global__ void __launch_bounds__(kNT) k_row_id(IdArgs a) {
   while (k < kmax) {
     double tot = 0.0, best = -1.0;
     int bi = 0x7fffffff;
-    for (int c = k + threadIdx.x; c < m; c += kNT) {
+    for (int c = k + threadIdx.x; c < m; c += NT) {
       double nv = sqrt(nrm2[c]);
       tot += nv * nv;
       if (nv > best) { best = nv; bi = c; }
@@ -553,7 +553,7 @@ __global__ void __launch_bounds__(kNT) k_row_id(IdArgs a) {
     const double nk = sqrt(nrm2[p]);
     __syncthreads();
     if (p != k) {
-      for (int r = threadIdx.x; r < d; r += kNT) {
+      for (int r = threadIdx.x; r < d; r += NT) {
         double t0 = A[(int64_t)r * m + k];
         A[(int64_t)r * m + k] = A[(int64_t)r * m + p];
         A[(int64_t)r * m + p] = t0;
@@ -570,7 +570,7 @@ __global__ void __launch_bounds__(kNT) k_row_id(IdArgs a) {
     __syncthreads();
     if (threadIdx.x == 0) A[(int64_t)k * m + k] = x0 - alpha;   // v_k
     __syncthreads();
-    for (int c = k + 1 + threadIdx.x; c < m; c += kNT) {
+    for (int c = k + 1 + threadIdx.x; c < m; c += NT) {
       double w0 = 0.0, w1 = 0.0;
       int r = k;
       for (; r + 1 < d; r += 2) {
@@ -594,7 +594,7 @@ __global__ void __launch_bounds__(kNT) k_row_id(IdArgs a) {
     ++k;
   }
   // T = R11^{-1} R12 by back substitution, written over R12 (one thread per column)
-  for (int c = k + threadIdx.x; c < m; c += kNT) {
+  for (int c = k + threadIdx.x; c < m; c += NT) {
     for (int i = k - 1; i >= 0; --i) {
       double t = A[(int64_t)i * m + c];
       for (int j = i + 1; j < k; ++j) t -= A[(int64_t)i * m + j] * A[(int64_t)j * m + c];
@@ -602,7 +602,7 @@ __global__ void __launch_bounds__(kNT) k_row_id(IdArgs a) {
     }
   }
   // sorted skeleton order
-  for (int q = threadIdx.x; q < k; q += kNT) {
+  for (int q = threadIdx.x; q < k; q += NT) {
     int r = 0;
     for (int b = 0; b < k; ++b) r += piv[b] < piv[q];
     rnk[q] = r;
@@ -610,15 +610,15 @@ __global__ void __launch_bounds__(kNT) k_row_id(IdArgs a) {
   }
   __syncthreads();
   double *E = a.E + a.eoff[tau];
-  for (int64_t q = threadIdx.x; q < (int64_t)m * k; q += kNT) E[q] = 0.0;
+  for (int64_t q = threadIdx.x; q < (int64_t)m * k; q += NT) E[q] = 0.0;
   __syncthreads();
-  for (int q = threadIdx.x; q < k; q += kNT) {
+  for (int q = threadIdx.x; q < k; q += NT) {
     int jr = piv[sig[q]];
     E[jr + (int64_t)q * m] = 1.0;
     a.J_tmp[row + q] = jr;
     a.skel_tmp[row + q] = a.ibar ? a.ibar[row + jr] : (int32_t)(row + jr);
   }
-  for (int64_t q = threadIdx.x; q < (int64_t)(m - k) * k; q += kNT) {
+  for (int64_t q = threadIdx.x; q < (int64_t)(m - k) * k; q += NT) {
     int rr = (int)(q % (m - k)), ap = (int)(q / (m - k));
     E[piv[k + rr] + (int64_t)ap * m] = A[(int64_t)sig[ap] * m + (k + rr)];
   }
@@ -853,37 +853,49 @@ void bsr_apply(bool fp64, const BsrArgs &a, int max_m, int max_cols, cudaStream_
   }
 }
 
-void qr_test(bool fp64, const QrArgs &a, size_t smem_bytes, cudaStream_t s) {
-  if (a.t.n == 0) return;
+// CTA width for clusters of up to `width` columns (64, 128 or 256 threads).
+template <template <typename, int> class K, typename A>
+void launch_width(bool fp64, int width, const A &a, int n, size_t bytes, cudaStream_t s);
+
+template <typename T, int NT>
+struct QrKern {
+  static constexpr auto f = k_qr_test<T, NT>;
+};
+template <typename T, int NT>
+struct IdKern {
+  static constexpr auto f = k_row_id<T, NT>;
+};
+
+template <template <typename, int> class K, typename A>
+void launch_width(bool fp64, int width, const A &a, int n, size_t bytes, cudaStream_t s) {
+  auto go = [&](auto kern, int nt) {
+    set_smem(kern, bytes);
+    kern<<<n, nt, bytes, s>>>(a);
+  };
+  const int w = width <= 0 ? 256 : width;
   if (fp64) {
-    auto kern = k_qr_test<double>;
-    set_smem(kern, smem_bytes);
-    kern<<<a.t.n, kNT, smem_bytes, s>>>(a);
+    if (w <= 64) go(K<double, 64>::f, 64);
+    else if (w <= 128) go(K<double, 128>::f, 128);
+    else go(K<double, 256>::f, 256);
   } else {
-    auto kern = k_qr_test<float>;
-    set_smem(kern, smem_bytes);
-    kern<<<a.t.n, kNT, smem_bytes, s>>>(a);
+    if (w <= 64) go(K<float, 64>::f, 64);
+    else if (w <= 128) go(K<float, 128>::f, 128);
+    else go(K<float, 256>::f, 256);
   }
   count_launch();
   H2_CHECK_LAUNCH();
 }
 
+void qr_test(bool fp64, const QrArgs &a, size_t smem_bytes, int width, cudaStream_t s) {
+  if (a.t.n == 0) return;
+  launch_width<QrKern>(fp64, width, a, a.t.n, smem_bytes, s);
+}
+
 size_t row_id_fixed_smem() { return kMaxIdRows * (sizeof(double) + 3 * sizeof(int)); }
 
-void row_id(bool fp64, const IdArgs &a, size_t smem_bytes, cudaStream_t s) {
+void row_id(bool fp64, const IdArgs &a, size_t smem_bytes, int width, cudaStream_t s) {
   if (a.t.n == 0) return;
-  size_t bytes = smem_bytes + row_id_fixed_smem();
-  if (fp64) {
-    auto kern = k_row_id<double>;
-    set_smem(kern, bytes);
-    kern<<<a.t.n, kNT, bytes, s>>>(a);
-  } else {
-    auto kern = k_row_id<float>;
-    set_smem(kern, bytes);
-    kern<<<a.t.n, kNT, bytes, s>>>(a);
-  }
-  count_launch();
-  H2_CHECK_LAUNCH();
+  launch_width<IdKern>(fp64, width, a, a.t.n, smem_bytes + row_id_fixed_smem(), s);
 }
 
 void compact_skeletons(const TasksDev &t, const int32_t *J_tmp, const int32_t *skel_tmp,

@@ -82,7 +82,8 @@ struct QrArgs {
   const int64_t *ws_off;    // per task offset into ws, -1 = shared memory
   double *mindiag;          // optional per task output (may be NULL)
 };
-void qr_test(bool fp64, const QrArgs &a, size_t smem_bytes, cudaStream_t s);
+// width: the widest cluster of the call (threads = columns), 0 = 256 threads.
+void qr_test(bool fp64, const QrArgs &a, size_t smem_bytes, int width, cudaStream_t s);
 
 // Row ID (batchedID) of each active task: CPQR of Y^T/sqrt(d).
 struct IdArgs {
@@ -101,7 +102,7 @@ struct IdArgs {
   double *ws;
   const int64_t *ws_off;
 };
-void row_id(bool fp64, const IdArgs &a, size_t smem_bytes, cudaStream_t s);
+void row_id(bool fp64, const IdArgs &a, size_t smem_bytes, int width, cudaStream_t s);
 // Shared memory the ID kernel needs besides the d x m panel.
 size_t row_id_fixed_smem();
 
