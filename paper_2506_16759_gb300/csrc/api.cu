@@ -953,9 +953,11 @@ struct Builder {
     L.skeltmp.alloc(std::max<int64_t>(L.M, 1));
     DBuf<int64_t> ws_off;
     DBuf<double> ws;
-    size_t fixed = row_id_fixed_smem();
+    const int mcap = (std::max(L.max_m, 1) + 7) / 8 * 8;
+    size_t fixed = row_id_fixed_smem(mcap);
     size_t smem = plan_workspace(L, 200 * 1024, fixed, ws_off, ws, false);
     IdArgs a{};
+    a.mcap = mcap;
     a.t = L.dev();
     a.Y = Yp(L);
     a.ld = L.M;
@@ -1934,6 +1936,7 @@ h2_status h2_batched_row_id(int count, const int32_t *m, const int32_t *d, const
       sk.alloc(std::max(hm[t], 1));
       TasksDev td{1, inst.p, mm.p, row.p, nullptr, nullptr, nullptr, eo.p};
       IdArgs a{};
+      a.mcap = 512;
       a.t = td;
       a.Y = panels + ho[t];
       a.ld = hm[t];

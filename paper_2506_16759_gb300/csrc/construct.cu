@@ -516,11 +516,11 @@ __global__ void __launch_bounds__(NT) k_row_id(IdArgs a) {
   int d = a.dcur[inst];
   // shared layout: norms[m] (double), piv[m], rank[m], sig[m] (int), then A
   double *nrm2 = reinterpret_cast<double *>(smem_raw);
-  int *piv = reinterpret_cast<int *>(nrm2 + kMaxIdRows);
-  int *rnk = piv + kMaxIdRows;
-  int *sig = rnk + kMaxIdRows;
+  int *piv = reinterpret_cast<int *>(nrm2 + a.mcap);
+  int *rnk = piv + a.mcap;
+  int *sig = rnk + a.mcap;
   double *A = a.ws_off && a.ws_off[tau] >= 0 ? a.ws + a.ws_off[tau]
-                                             : reinterpret_cast<double *>(sig + kMaxIdRows);
+                                             : reinterpret_cast<double *>(sig + a.mcap);
   const T *Y = reinterpret_cast<const T *>(a.Y);
   const double sd = sqrt((double)d);
   for (int64_t q = threadIdx.x; q < (int64_t)m * d; q += NT) {
@@ -571,22 +571,33 @@ __global__ void __launch_bounds__(NT) k_row_id(IdArgs a) {
     if (threadIdx.x == 0) A[(int64_t)k * m + k] = x0 - alpha;   // v_k
     __syncthreads();
     for (int c = k + 1 + threadIdx.x; c < m; c += NT) {
-      double w0 = 0.0, w1 = 0.0;
+      double w0 = 0.0, w1 = 0.0, w2 = 0.0, w3 = 0.0;
       int r = k;
-      for (; r + 1 < d; r += 2) {
+      for (; r + 3 < d; r += 4) {
         w0 += A[(int64_t)r * m + k] * A[(int64_t)r * m + c];
         w1 += A[(int64_t)(r + 1) * m + k] * A[(int64_t)(r + 1) * m + c];
+        w2 += A[(int64_t)(r + 2) * m + k] * A[(int64_t)(r + 2) * m + c];
+        w3 += A[(int64_t)(r + 3) * m + k] * A[(int64_t)(r + 3) * m + c];
       }
-      if (r < d) w0 += A[(int64_t)r * m + k] * A[(int64_t)r * m + c];
-      const double w = (w0 + w1) * beta;
+      for (; r < d; ++r) w0 += A[(int64_t)r * m + k] * A[(int64_t)r * m + c];
+      const double w = ((w0 + w1) + (w2 + w3)) * beta;
       A[(int64_t)k * m + c] -= w * A[(int64_t)k * m + k];
-      double s2 = 0.0;
-      for (int q = k + 1; q < d; ++q) {
-        const double x = A[(int64_t)q * m + c] - w * A[(int64_t)q * m + k];
-        A[(int64_t)q * m + c] = x;
-        s2 += x * x;
+      double s0 = 0.0, s1 = 0.0;
+      int q = k + 1;
+      for (; q + 1 < d; q += 2) {
+        const double x0 = A[(int64_t)q * m + c] - w * A[(int64_t)q * m + k];
+        const double x1 = A[(int64_t)(q + 1) * m + c] - w * A[(int64_t)(q + 1) * m + k];
+        A[(int64_t)q * m + c] = x0;
+        A[(int64_t)(q + 1) * m + c] = x1;
+        s0 += x0 * x0;
+        s1 += x1 * x1;
       }
-      nrm2[c] = s2;
+      if (q < d) {
+        const double x0 = A[(int64_t)q * m + c] - w * A[(int64_t)q * m + k];
+        A[(int64_t)q * m + c] = x0;
+        s0 += x0 * x0;
+      }
+      nrm2[c] = s0 + s1;
     }
     __syncthreads();
     if (threadIdx.x == 0) A[(int64_t)k * m + k] = alpha;
@@ -891,11 +902,12 @@ void qr_test(bool fp64, const QrArgs &a, size_t smem_bytes, int width, cudaStrea
   launch_width<QrKern>(fp64, width, a, a.t.n, smem_bytes, s);
 }
 
-size_t row_id_fixed_smem() { return kMaxIdRows * (sizeof(double) + 3 * sizeof(int)); }
+size_t row_id_fixed_smem(int mcap) { return (size_t)mcap * (sizeof(double) + 3 * sizeof(int)); }
 
 void row_id(bool fp64, const IdArgs &a, size_t smem_bytes, int width, cudaStream_t s) {
   if (a.t.n == 0) return;
-  launch_width<IdKern>(fp64, width, a, a.t.n, smem_bytes + row_id_fixed_smem(), s);
+  H2_REQUIRE(a.mcap >= 8 && a.mcap % 8 == 0 && a.mcap <= kMaxIdRows, "row ID capacity");
+  launch_width<IdKern>(fp64, width, a, a.t.n, smem_bytes + row_id_fixed_smem(a.mcap), s);
 }
 
 void compact_skeletons(const TasksDev &t, const int32_t *J_tmp, const int32_t *skel_tmp,

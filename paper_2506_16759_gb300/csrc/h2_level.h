@@ -101,10 +101,12 @@ struct IdArgs {
   double *E;                // bases (m x k at eoff)
   double *ws;
   const int64_t *ws_off;
+  int mcap;                 // rows the per-cluster index arrays hold (>= every m, <= 512)
 };
 void row_id(bool fp64, const IdArgs &a, size_t smem_bytes, int width, cudaStream_t s);
-// Shared memory the ID kernel needs besides the d x m panel.
-size_t row_id_fixed_smem();
+// Shared memory the ID kernel needs besides the d x m panel (clusters of at
+// most mcap rows).
+size_t row_id_fixed_smem(int mcap);
 
 // Moves the per-task skeleton arrays from row offsets to krow offsets.
 void compact_skeletons(const TasksDev &t, const int32_t *J_tmp, const int32_t *skel_tmp,
