@@ -97,7 +97,9 @@ typedef int (*h2_sampler_fn)(void *ctx, const double *omega, double *y, int64_t 
 
 typedef struct {
   int d0;              /* initial samples (32) */
-  int d_inc;           /* samples added per adaptive round (16); 0 = fixed sampling */
+  int d_inc;           /* samples added per adaptive round (16); 0 = fixed sampling:
+                          no convergence test, every cluster compressed from
+                          its d0 samples (the non-adaptive construction) */
   int d_max;           /* sample budget (256) */
   int prec;            /* h2_prec */
   int omega_mode;      /* 0: Gaussian Omega from Philox4x32-10 (seed);

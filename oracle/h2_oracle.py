@@ -508,7 +508,8 @@ class _Builder:
                 nd.Yloc, nd.Om = Y, O
                 self.nodes[tau] = nd
             # adaptive sampling: add d_inc columns until every node converges
-            while True:
+            # (d_inc = 0: fixed sample count, no convergence test)
+            while self.d_inc > 0:
                 pending = [t for t in nodes if not node_converged(self.nodes[t].Yloc, eps_l)]
                 if not pending:
                     break

@@ -909,15 +909,16 @@ struct Builder {
     L.conv.alloc_zero(L.n, s);
     DBuf<int32_t> unconv;
     unconv.alloc(C);
-    // adaptive sampling (Sec. III-B)
-    for (;;) {
+    // adaptive sampling (Sec. III-B); d_inc = 0 is the fixed-sample
+    // construction (no convergence test, every cluster compressed from d0)
+    for (; o.d_inc > 0;) {
       H2_CUDA(cudaMemsetAsync(unconv.p, 0, C * sizeof(int32_t), s));
       qr_round(l, unconv);
       std::vector<int32_t> hu = to_host(unconv.p, C, s);
       std::vector<int> need;
       for (int i = 0; i < C; ++i) {
         if (!L.h_active[i] || hu[i] == 0) continue;
-        if (o.d_inc <= 0 || H->dcur[i] + o.d_inc > o.d_max) {
+        if (H->dcur[i] + o.d_inc > o.d_max) {
           if (std::find(not_conv.begin(), not_conv.end(), i) == not_conv.end())
             not_conv.push_back(i);
           continue;

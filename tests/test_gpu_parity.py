@@ -331,3 +331,19 @@ def test_h2sum_build_matches_oracle():
         rel, y, _ = matvec_rel(h, ho, n, seed=5)
         assert rel <= bar
         assert np.linalg.norm(y - A @ G) <= 10 * 1e-6 * np.linalg.norm(A @ G)
+
+
+@pytest.mark.parametrize("leaf,d0", [(32, 96), (128, 128)])
+def test_fixed_sampling_matches_oracle(leaf, d0):
+    # d_inc = 0: the fixed-sample construction (Sec. V-B), leaves up to 128
+    # points (the all-points sketch and the general block-sparse kernel)
+    n, dim, kernel, params, tol = 4096, 3, W.K_MATERN32, (0.1, 1e-4), 1e-6
+    X, om, t, lists, ho = oracle_build(n, dim, kernel, params, tol, leaf, 0.7, 21, d0=d0, d_inc=0)
+    tree, h = gpu_build(X, om, kernel, params, tol, leaf, 0.7, d0=d0, d_inc=0)
+    assert h.stats()["rounds"] == 0
+    check_same_skeletons(h, t, ho)
+    rel, y, G = matvec_rel(h, ho, n)
+    assert rel <= 1e-10
+    _, hm = gpu_build(X, om, kernel, params, tol, leaf, 0.7, prec="mixed", d0=d0, d_inc=0)
+    y2 = hm.matvec(gpu(G)).cpu().numpy()
+    assert np.linalg.norm(y2 - y) <= 1e-5 * np.linalg.norm(y)

@@ -326,6 +326,22 @@ def test_adaptive_rounds_and_budget():
     assert not h2.converged
 
 
+def test_fixed_sampling_mode():
+    # d_inc = 0: the non-adaptive construction with a fixed sample count
+    # (the fixed-d runs of Sec. V-B / Table I).  With enough samples it meets
+    # the tolerance and matches the adaptive run that needed no extra round;
+    # with fewer samples than the ranks the truncation caps every rank at d.
+    X, om, t, lists, A, ha = _build(2048, 2, O.K_EXP, (0.2, 1e-4), 1e-6, leaf=32, d0=96)
+    assert ha.converged and max(ha.d_level.values()) == 96   # no adaptive round
+    _, _, _, _, _, hf = _build(2048, 2, O.K_EXP, (0.2, 1e-4), 1e-6, leaf=32, d0=96, d_inc=0)
+    assert O.dense_rel_error(hf, A) <= 10 * 1e-6
+    for tau, nd in hf.nodes.items():
+        assert np.array_equal(nd.J, ha.nodes[tau].J)
+    _, _, _, _, _, hs = _build(2048, 2, O.K_EXP, (0.2, 1e-4), 1e-6, leaf=32, d0=8, d_inc=0)
+    assert max(nd.k for nd in hs.nodes.values()) <= 8
+    assert O.dense_rel_error(hs, A) > 10 * 1e-6
+
+
 def test_power_method_matches_dense_two_norm():
     X, om, t, lists, A, h = _build(1024, 2, O.K_EXP, (0.2, 1e-4), 1e-5, leaf=16)
     Ad = O.h2_dense(h)
