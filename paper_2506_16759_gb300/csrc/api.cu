@@ -725,17 +725,21 @@ struct Builder {
     timer.begin(PH_NEAR);
     if (is_sum()) {
       std::vector<const double *> dp;
+      std::vector<const float *> dp32;
       std::vector<const int64_t *> dofs;
       for (int q = 0; q < o.n_operands; ++q) {
-        dp.push_back(op(q)->D64.p);
+        dp.push_back(op(q)->fp64 ? op(q)->D64.p : nullptr);
+        dp32.push_back(op(q)->fp64 ? nullptr : op(q)->D32.p);
         dofs.push_back(op(q)->doff.p);
       }
       DBuf<const double *> ddp;
+      DBuf<const float *> ddp32;
       DBuf<const int64_t *> ddo;
       to_device(ddp, dp, s);
+      to_device(ddp32, dp32, s);
       to_device(ddo, dofs, s);
       h2sum_dense(fp64(), H->near_nnz, H->near_erow.p, H->near_idx.p, L.m.p, H->doff.p, Dp(),
-                  ddp.p, ddo.p, o.n_operands, s);
+                  ddp.p, ddp32.p, ddo.p, o.n_operands, s);
       H2_CUDA(cudaStreamSynchronize(s));
       timer.end(PH_NEAR);
       std::vector<int32_t> b(C, 0), e(C, o.d0);
@@ -1053,7 +1057,9 @@ struct Builder {
     int max_kop = 0;
     for (int q = 0; q < o.n_operands; ++q) {
       const LevelData &OL = op(q)->lv[l];
-      ops.push_back(SumOperand{OL.k.p, sumGoff[q][l].p, sumG[q][l].p, OL.boff.p, OL.B64.p});
+      ops.push_back(SumOperand{OL.k.p, sumGoff[q][l].p, sumG[q][l].p, OL.boff.p,
+                               op(q)->fp64 ? OL.B64.p : nullptr,
+                               op(q)->fp64 ? nullptr : OL.B32.p});
       max_kop = std::max(max_kop, OL.max_k);
     }
     DBuf<SumOperand> dops;
@@ -1613,7 +1619,7 @@ h2_status h2_build_batched(const h2_tree *const *trees, int count, const int *ke
       const h2_tree *t = trees[0];
       for (int q = 0; q < opts->n_operands; ++q) {
         const h2_matrix *op = opts->operands[q];
-        H2_REQUIRE(op != nullptr && op->count == 1 && op->fp64, "operands must be FP64 single H2 matrices");
+        H2_REQUIRE(op != nullptr && op->count == 1, "operands must be single-instance H2 matrices");
         H2_REQUIRE(op->n_total == t->n && op->inst_depth[0] == t->depth &&
                        op->inst_ltop[0] == t->l_top && op->near_nnz == t->near_nnz,
                    "operands must be built on the same cluster tree and partition");

@@ -174,7 +174,8 @@ struct SumOperand {
   const int64_t *goff;   // G offsets per task
   const double *G;
   const int64_t *boff;   // operand coupling offsets per far entry
-  const double *B;
+  const double *B;       // FP64 operand couplings, or
+  const float *B32;      // FP32 ones (an operand built in mixed precision)
 };
 struct SumCouplingArgs {
   int64_t nnz;
@@ -194,7 +195,7 @@ void h2sum_g_inner(const TasksDev &t, const int32_t *child0, const int32_t *kt_c
                    const double *Eop, const int64_t *goff, double *G, cudaStream_t s);
 void h2sum_couplings(bool fp64, const SumCouplingArgs &a, int max_kop, int max_kt, cudaStream_t s);
 void h2sum_dense(bool fp64, int64_t nnz, const int32_t *erow, const int32_t *idx, const int32_t *m,
-                 const int64_t *doff, void *D, const double *const *Dop,
+                 const int64_t *doff, void *D, const double *const *Dop, const float *const *Dop32,
                  const int64_t *const *doff_op, int nops, cudaStream_t s);
 
 }  // namespace h2

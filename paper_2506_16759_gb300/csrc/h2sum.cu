@@ -10,7 +10,8 @@
 //    nested bases: at a leaf G_s = U_op,s(J_s, :); above,
 //    G_s = (blkdiag(G_op,nu1, G_op,nu2) E_op,s)(J_s, :), because the candidate
 //    rows of s are the children's skeleton rows.
-// Operands are FP64; the result is written in the target's precision.
+// Operands are FP64 or FP32 (built in mixed precision; their bases E are
+// FP64 either way); the result is written in the target's precision.
 #include <algorithm>
 
 #include "h2_level.h"
@@ -73,13 +74,18 @@ __global__ void k_b_h2sum(SumCouplingArgs a, int max_kop) {
     const int kos = op.k[s], kot = op.k[tt];
     const double *Gs = op.G + op.goff[s];
     const double *Gt = op.G + op.goff[tt];
-    const double *Bo = op.B + op.boff[e];
+    const double *Bo = op.B ? op.B + op.boff[e] : nullptr;
+    const float *Bo32 = op.B32 ? op.B32 + op.boff[e] : nullptr;
     __syncthreads();
     // tmp = B_op G_t^T  (kos x kt)
     for (int q = threadIdx.x; q < kos * kt; q += blockDim.x) {
       const int p = q % kos, b = q / kos;
       double v = 0.0;
-      for (int c = 0; c < kot; ++c) v += Bo[p + (int64_t)c * kos] * Gt[b + (int64_t)c * kt];
+      if (Bo)
+        for (int c = 0; c < kot; ++c) v += Bo[p + (int64_t)c * kos] * Gt[b + (int64_t)c * kt];
+      else
+        for (int c = 0; c < kot; ++c)
+          v += (double)Bo32[p + (int64_t)c * kos] * Gt[b + (int64_t)c * kt];
       tmp[q] = v;
     }
     __syncthreads();
@@ -97,13 +103,14 @@ __global__ void k_b_h2sum(SumCouplingArgs a, int max_kop) {
 template <typename T>
 __global__ void k_d_h2sum(int64_t nnz, const int32_t *erow, const int32_t *idx, const int32_t *m,
                           const int64_t *doff, T *D, const double *const *Dop,
-                          const int64_t *const *doff_op, int nops) {
+                          const float *const *Dop32, const int64_t *const *doff_op, int nops) {
   const int64_t e = blockIdx.x;
   const int n = m[erow[e]] * m[idx[e]];
   T *out = D + doff[e];
   for (int q = threadIdx.x; q < n; q += blockDim.x) {
     double v = 0.0;
-    for (int o = 0; o < nops; ++o) v += Dop[o][doff_op[o][e] + q];
+    for (int o = 0; o < nops; ++o)
+      v += Dop[o] ? Dop[o][doff_op[o][e] + q] : (double)Dop32[o][doff_op[o][e] + q];
     out[q] = (T)v;
   }
 }
@@ -150,16 +157,16 @@ void h2sum_couplings(bool fp64, const SumCouplingArgs &a, int max_kop, int max_k
 }
 
 void h2sum_dense(bool fp64, int64_t nnz, const int32_t *erow, const int32_t *idx, const int32_t *m,
-                 const int64_t *doff, void *D, const double *const *Dop,
+                 const int64_t *doff, void *D, const double *const *Dop, const float *const *Dop32,
                  const int64_t *const *doff_op, int nops, cudaStream_t s) {
   if (nnz == 0) return;
   H2_REQUIRE(nnz < (1ll << 31), "too many near-field blocks");
   if (fp64)
-    k_d_h2sum<double><<<(int)nnz, 256, 0, s>>>(nnz, erow, idx, m, doff, (double *)D, Dop, doff_op,
-                                               nops);
+    k_d_h2sum<double><<<(int)nnz, 256, 0, s>>>(nnz, erow, idx, m, doff, (double *)D, Dop, Dop32,
+                                               doff_op, nops);
   else
-    k_d_h2sum<float><<<(int)nnz, 256, 0, s>>>(nnz, erow, idx, m, doff, (float *)D, Dop, doff_op,
-                                              nops);
+    k_d_h2sum<float><<<(int)nnz, 256, 0, s>>>(nnz, erow, idx, m, doff, (float *)D, Dop, Dop32,
+                                              doff_op, nops);
   count_launch();
   H2_CHECK_LAUNCH();
 }

@@ -347,3 +347,22 @@ def test_fixed_sampling_matches_oracle(leaf, d0):
     _, hm = gpu_build(X, om, kernel, params, tol, leaf, 0.7, prec="mixed", d0=d0, d_inc=0)
     y2 = hm.matvec(gpu(G)).cpu().numpy()
     assert np.linalg.norm(y2 - y) <= 1e-5 * np.linalg.norm(y)
+
+
+def test_h2sum_with_mixed_precision_operands():
+    # operands stored in FP32 (built in mixed precision): the sum is still
+    # compressed to the tolerance of the exact operator
+    n, dim, leaf, eta = 4096, 3, 32, 0.7
+    X = W.uniform_points(n, dim, 61)
+    kps = [(W.K_EXP, (0.1, 0.0)), (W.K_GAUSS, (0.05, 0.0))]
+    tree = api.ClusterTree(gpu(X), leaf, eta)
+    ops = [api.H2Matrix.build(tree, k, p, 1e-8, prec="mixed", seed=3 + i)
+           for i, (k, p) in enumerate(kps)]
+    A = O.dense_matrix(X, *kps[0]) + O.dense_matrix(X, *kps[1])
+    G = W.gaussian_probe(n, 4, 5)
+    AG = A @ G
+    for prec in ("fp64", "mixed"):
+        h = api.H2Matrix.build(tree, "h2sum", (), 1e-6, sketch="h2sum", operands=ops, prec=prec,
+                               seed=9)
+        y = h.matvec(gpu(G)).cpu().numpy()
+        assert np.linalg.norm(y - AG) <= 10 * 1e-6 * np.linalg.norm(AG)
