@@ -759,6 +759,8 @@ struct Builder {
     g.p64 = p64();
     g.p32 = p32();
     g.D = Dp();
+    g.n_rows = L.n;
+    g.ptr = H->near_ptr.p;
     dense_blocks_gen(H->kid, fp64(), g, s);
     timer.end(PH_NEAR);
     std::vector<int32_t> b(C, 0), e(C, o.d0);
@@ -1013,6 +1015,7 @@ struct Builder {
       ca.p64 = p64();
       ca.p32 = p32();
       ca.B = Bp(L);
+      ca.ptr = L.far_ptr.p;
       timer.begin(PH_COUP);
       coupling_gen(H->kid, fp64(), ca, s);
       timer.end(PH_COUP);

@@ -391,30 +391,6 @@ __global__ void k_transpose_panel(const float *in, int64_t ld, int64_t n, int nc
   }
 }
 
-// Dense near-field blocks D_{t,b} = K(I_t, I_b) for every near pair: one CTA
-// per block, coalesced column-major stores.
-template <int KID, typename T>
-__global__ void k_dgen(DgenArgs a) {
-  constexpr int NC = PtsOf<T>::NC;
-  __shared__ T sa[kMaxRows * NC], sb[kMaxRows * NC];
-  const int64_t e = blockIdx.x;
-  const int tr = a.erow[e], tc = a.idx[e];
-  const int m = a.m[tr], mb = a.m[tc];
-  const int64_t rt = a.row[tr], rb = a.row[tc];
-  const InstDev in = a.inst[a.tinst[tr]];
-  const T scale = (T)in.kd.scale, diag = (T)in.kd.diag;
-  const int pw = in.kd.pw;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) PtsOf<T>::load(a.p64, a.p32, rt + i, sa + i * NC);
-  for (int j = threadIdx.x; j < mb; j += blockDim.x) PtsOf<T>::load(a.p64, a.p32, rb + j, sb + j * NC);
-  __syncthreads();
-  T *D = reinterpret_cast<T *>(a.D) + a.doff[e];
-  for (int q = threadIdx.x; q < m * mb; q += blockDim.x) {
-    const int i = q % m, j = q / m;
-    const T gm = PtsOf<T>::template geom<KID>(sa + i * NC, sb + j * NC);
-    D[q] = (rt + i == rb + j) ? kdiag<KID, T>(gm, scale, pw, diag) : kval<KID, T>(gm, scale, pw);
-  }
-}
-
 // ----------------------------------------------------------------------------
 // QR convergence test (FP64 Householder, one CTA per cluster).
 // ----------------------------------------------------------------------------
@@ -704,26 +680,74 @@ __global__ void k_basis_n(TasksDev t, const TE *E, const T *in, int64_t ld_in, T
   }
 }
 
-template <int KID, typename T>
-__global__ void k_coupling(CouplingArgs a) {
-  int64_t e = blockIdx.x;
-  int tr = a.erow[e], tc = a.idx[e];
-  int kr = a.t.k[tr], kc = a.t.k[tc];
-  if (kr == 0 || kc == 0) return;
-  const InstDev in = a.inst[a.t.inst[tr]];
+// One CTA per row task: its points (the leaf's, or its skeleton points) are
+// staged once, then every partner block of its CSR row is evaluated from a
+// staged copy of the partner's points; the next partner's points are loaded
+// into registers while the current block is evaluated.  Column-major block
+// stores, coalesced.
+template <int KID, typename T, bool SKEL>
+__global__ void __launch_bounds__(256) k_gen_rows(int n_rows, const int64_t *ptr,
+                                                  const int32_t *idx, const int64_t *off,
+                                                  const int32_t *rows_of, const int64_t *row0,
+                                                  const int64_t *krow, const int32_t *skel,
+                                                  const int32_t *tinst, const InstDev *inst,
+                                                  Points64 p64, Points32 p32, void *out_) {
+  constexpr int NC = PtsOf<T>::NC;
+  constexpr int NS = (NC * (int)sizeof(T) + 15) / 16 * 16 / (int)sizeof(T);   // 16-byte rows
+  __shared__ __align__(16) T sa[kMaxRows * NS], sb[2][kMaxRows * NS];
+  __shared__ int64_t ga[kMaxRows], gb[2][kMaxRows];
+  const int tr = blockIdx.x;
+  if (tr >= n_rows) return;
+  const int64_t e0 = ptr[tr], e1 = ptr[tr + 1];
+  if (e0 == e1) return;
+  const int m = rows_of[tr];
+  if (m == 0) return;
+  const InstDev in = inst[tinst[tr]];
   const T scale = (T)in.kd.scale, diag = (T)in.kd.diag;
   const int pw = in.kd.pw;
-  const int32_t *sr = a.skel + a.t.krow[tr];
-  const int32_t *sc = a.skel + a.t.krow[tc];
-  T *B = reinterpret_cast<T *>(a.B) + a.boff[e];
-  constexpr int NC = PtsOf<T>::NC;
-  for (int64_t q = threadIdx.x; q < (int64_t)kr * kc; q += blockDim.x) {
-    int i = (int)(q % kr), j = (int)(q / kr);
-    T pa[NC], pb[NC];
-    PtsOf<T>::load(a.p64, a.p32, sr[i], pa);
-    PtsOf<T>::load(a.p64, a.p32, sc[j], pb);
-    T g = PtsOf<T>::template geom<KID>(pa, pb);
-    B[q] = sr[i] == sc[j] ? kdiag<KID, T>(g, scale, pw, diag) : kval<KID, T>(g, scale, pw);
+  auto gpos = [&](int task, int i) -> int64_t {
+    return SKEL ? (int64_t)skel[krow[task] + i] : row0[task] + i;
+  };
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const int64_t g = gpos(tr, i);
+    ga[i] = g;
+    PtsOf<T>::load(p64, p32, g, sa + i * NS);
+  }
+  // partner points of entry e into buffer slot
+  auto load_partner = [&](int64_t e, int slot) {
+    const int tc = idx[e];
+    const int mb = rows_of[tc];
+    for (int j = threadIdx.x; j < mb; j += blockDim.x) {
+      const int64_t g = gpos(tc, j);
+      gb[slot][j] = g;
+      PtsOf<T>::load(p64, p32, g, sb[slot] + j * NS);
+    }
+  };
+  load_partner(e0, 0);
+  __syncthreads();
+  T *out = reinterpret_cast<T *>(out_);
+  // thread = row i (of 64 at a time) x every 4th column j: a warp shares j,
+  // so the partner point is a broadcast read and the stores are coalesced
+  const int ig = threadIdx.x & 63, jg = threadIdx.x >> 6;
+  for (int64_t e = e0; e < e1; ++e) {
+    const int slot = (int)((e - e0) & 1);
+    if (e + 1 < e1) load_partner(e + 1, slot ^ 1);   // overlaps the evaluation below
+    const int mb = rows_of[idx[e]];
+    T *blk = out + off[e];
+    const T *pb = sb[slot];
+    const int64_t *gbs = gb[slot];
+    for (int i = ig; i < m; i += 64) {
+      T pa[NS];
+#pragma unroll
+      for (int c = 0; c < NS; ++c) pa[c] = sa[i * NS + c];
+      const int64_t gi = ga[i];
+      for (int j = jg; j < mb; j += 4) {
+        const T gm = PtsOf<T>::template geom<KID>(pa, pb + j * NS);
+        blk[i + (int64_t)j * m] =
+            gi == gbs[j] ? kdiag<KID, T>(gm, scale, pw, diag) : kval<KID, T>(gm, scale, pw);
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -805,8 +829,14 @@ void dense_blocks_gen(int kid, bool fp64, const DgenArgs &a, cudaStream_t s) {
   H2_REQUIRE(a.nnz < (1ll << 31), "too many near-field blocks");
   dispatch_kernel(kid, [&](auto K) {
     constexpr int KID = decltype(K)::value;
-    if (fp64) k_dgen<KID, double><<<(int)a.nnz, 256, 0, s>>>(a);
-    else k_dgen<KID, float><<<(int)a.nnz, 256, 0, s>>>(a);
+    if (fp64)
+      k_gen_rows<KID, double, false><<<a.n_rows, 256, 0, s>>>(
+          a.n_rows, a.ptr, a.idx, a.doff, a.m, a.row, nullptr, nullptr, a.tinst, a.inst, a.p64,
+          a.p32, a.D);
+    else
+      k_gen_rows<KID, float, false><<<a.n_rows, 256, 0, s>>>(
+          a.n_rows, a.ptr, a.idx, a.doff, a.m, a.row, nullptr, nullptr, a.tinst, a.inst, a.p64,
+          a.p32, a.D);
     count_launch();
     H2_CHECK_LAUNCH();
   });
@@ -963,8 +993,14 @@ void coupling_gen(int kid, bool fp64, const CouplingArgs &a, cudaStream_t s) {
   H2_REQUIRE(a.nnz < (1ll << 31), "too many coupling blocks");
   dispatch_kernel(kid, [&](auto K) {
     constexpr int KID = decltype(K)::value;
-    if (fp64) k_coupling<KID, double><<<(int)a.nnz, 128, 0, s>>>(a);
-    else k_coupling<KID, float><<<(int)a.nnz, 128, 0, s>>>(a);
+    if (fp64)
+      k_gen_rows<KID, double, true><<<a.t.n, 256, 0, s>>>(
+          a.t.n, a.ptr, a.idx, a.boff, a.t.k, nullptr, a.t.krow, a.skel, a.t.inst, a.inst, a.p64,
+          a.p32, a.B);
+    else
+      k_gen_rows<KID, float, true><<<a.t.n, 256, 0, s>>>(
+          a.t.n, a.ptr, a.idx, a.boff, a.t.k, nullptr, a.t.krow, a.skel, a.t.inst, a.inst, a.p64,
+          a.p32, a.B);
     count_launch();
     H2_CHECK_LAUNCH();
   });

@@ -65,6 +65,8 @@ struct DgenArgs {
   Points64 p64;
   Points32 p32;
   void *D;                  // T
+  int n_rows;               // leaf tasks (rows of the near CSR)
+  const int64_t *ptr;       // near CSR over the leaf tasks
 };
 void dense_blocks_gen(int kid, bool fp64, const DgenArgs &a, cudaStream_t s);
 
@@ -136,6 +138,7 @@ struct CouplingArgs {
   Points64 p64;
   Points32 p32;
   void *B;
+  const int64_t *ptr;       // far CSR over the level's tasks (t.n rows)
 };
 void coupling_gen(int kid, bool fp64, const CouplingArgs &a, cudaStream_t s);
 
