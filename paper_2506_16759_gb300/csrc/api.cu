@@ -817,7 +817,8 @@ struct Builder {
     LevelData &L = H->lv[l], &U = H->lv[l + 1];
     timer.begin(PH_UP);
     gather_skeleton_rows(fp64(), L.dev(), Yp(L), L.M, Yp(U), U.M, cols(), L.active_next.p, s);
-    basis_t_apply(fp64(), L.dev(), Ep(L), Omp(L), L.M, Omp(U), U.M, cols(), L.active_next.p, s);
+    basis_t_apply(fp64(), L.dev(), Ep(L), Omp(L), L.M, Omp(U), U.M, cols(), L.active_next.p,
+                  L.max_m, L.max_k, s);
     timer.end(PH_UP);
     if (L.far_nnz == 0) return;
     timer.begin(PH_BSR);
@@ -1348,10 +1349,11 @@ void matvec_impl(const h2_matrix *H, const double *x, double *y, int nrhs, cudaS
     for (int l = 1; l <= levels; ++l) {
       const LevelData &L = H->lv[l];
       const void *E = (const void *)L.E.p;
-      if (l == 1) basis_t_apply(f64, L.dev(), E, xt.p, N, xh[1].p, L.K, cols, L.active.p, s);
+      if (l == 1)
+        basis_t_apply(f64, L.dev(), E, xt.p, N, xh[1].p, L.K, cols, L.active.p, L.max_m, L.max_k, s);
       else
         basis_t_apply(f64, L.dev(), E, xh[l - 1].p, H->lv[l - 1].K, xh[l].p, L.K, cols,
-                      L.active.p, s);
+                      L.active.p, L.max_m, L.max_k, s);
     }
     // couplings
     for (int l = 1; l <= levels; ++l) {

@@ -660,6 +660,49 @@ __global__ void k_basis_t(TasksDev t, const TE *E, const T *in, int64_t ld_in, T
   }
 }
 
+// FP32 panels (mixed precision): the cluster's basis (converted to FP32) and
+// its input rows are staged in shared memory, each output is an FP32 dot
+// product over the cluster's rows.  The identity rows of the basis (its
+// skeleton rows) contribute exact products, so the rounding is that of the
+// m - k interpolated rows.  Column chunks of 64.
+__global__ void __launch_bounds__(256) k_basis_t32(TasksDev t, const double *E, const float *in,
+                                                   int64_t ld_in, float *out, int64_t ld_out,
+                                                   InstCols cols, const int32_t *active) {
+  extern __shared__ __align__(16) float sm[];
+  const int tau = blockIdx.x;
+  const int inst = t.inst[tau];
+  if (active && !active[inst]) return;
+  const int k = t.k[tau], m = t.m[tau];
+  const int cb = cols.cb[inst], ce = cols.ce[inst];
+  if (k == 0 || ce <= cb) return;
+  const int64_t row = t.row[tau], kr = t.krow[tau];
+  const double *Et = E + t.eoff[tau];
+  float *sE = sm;                          // [k][m] (basis column a contiguous)
+  float *sX = sm + (size_t)k * m;          // [64][m] (input column c contiguous)
+  for (int q = threadIdx.x; q < m * k; q += blockDim.x) sE[q] = (float)Et[q];
+  for (int c0 = cb; c0 < ce; c0 += 64) {
+    const int nc = min(64, ce - c0);
+    __syncthreads();
+    for (int q = threadIdx.x; q < m * nc; q += blockDim.x) {
+      const int i = q % m, c = q / m;
+      sX[c * m + i] = in[row + i + (int64_t)(c0 + c) * ld_in];
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < k * nc; q += blockDim.x) {
+      const int a = q % k, c = q / k;
+      const float *ea = sE + a * m, *xc = sX + c * m;
+      float s0 = 0.f, s1 = 0.f;
+      int i = 0;
+      for (; i + 1 < m; i += 2) {
+        s0 = fmaf(ea[i], xc[i], s0);
+        s1 = fmaf(ea[i + 1], xc[i + 1], s1);
+      }
+      if (i < m) s0 = fmaf(ea[i], xc[i], s0);
+      out[kr + a + (int64_t)(c0 + c) * ld_out] = s0 + s1;
+    }
+  }
+}
+
 // out(row+i, c) += sum_a E(i,a) in(krow+a, c)
 template <typename T, typename TE>
 __global__ void k_basis_n(TasksDev t, const TE *E, const T *in, int64_t ld_in, T *out,
@@ -962,15 +1005,25 @@ void gather_skeleton_rows(bool fp64, const TasksDev &t, const void *Y, int64_t l
 }
 
 void basis_t_apply(bool fp64, const TasksDev &t, const void *E, const void *in, int64_t ld_in,
-                   void *out, int64_t ld_out, InstCols cols, const int32_t *active,
-                   cudaStream_t s) {
+                   void *out, int64_t ld_out, InstCols cols, const int32_t *active, int max_m,
+                   int max_k, cudaStream_t s) {
   if (t.n == 0) return;
   if (fp64)
     k_basis_t<double, double><<<t.n, 256, 0, s>>>(t, (const double *)E, (const double *)in,
                                                   ld_in, (double *)out, ld_out, cols, active);
-  else
-    k_basis_t<float, double><<<t.n, 256, 0, s>>>(t, (const double *)E, (const float *)in, ld_in,
-                                                (float *)out, ld_out, cols, active);
+  else {
+    // staged basis (k x m) and 64 input columns (64 x m), FP32; clusters too
+    // large for shared memory take the FP64-accumulating kernel
+    const size_t bytes = sizeof(float) * (size_t)(max_k * max_m + 64 * max_m);
+    if (bytes <= 200 * 1024) {
+      set_smem(k_basis_t32, bytes);
+      k_basis_t32<<<t.n, 256, bytes, s>>>(t, (const double *)E, (const float *)in, ld_in,
+                                          (float *)out, ld_out, cols, active);
+    } else {
+      k_basis_t<float, double><<<t.n, 256, 0, s>>>(t, (const double *)E, (const float *)in,
+                                                  ld_in, (float *)out, ld_out, cols, active);
+    }
+  }
   count_launch();
   H2_CHECK_LAUNCH();
 }

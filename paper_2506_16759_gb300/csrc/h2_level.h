@@ -120,8 +120,8 @@ void gather_skeleton_rows(bool fp64, const TasksDev &t, const void *Y, int64_t l
 // out(krow+a, c) = sum_i E(i,a) in(row+i, c)       (E^T products: upsweep)
 // E is FP64 in both modes; the sums accumulate in FP64.
 void basis_t_apply(bool fp64, const TasksDev &t, const void *E, const void *in, int64_t ld_in,
-                   void *out, int64_t ld_out, InstCols cols, const int32_t *active,
-                   cudaStream_t s);
+                   void *out, int64_t ld_out, InstCols cols, const int32_t *active, int max_m,
+                   int max_k, cudaStream_t s);
 // out(row+i, c) += sum_a E(i,a) in(krow+a, c)      (E products: downsweep)
 void basis_n_apply(bool fp64, const TasksDev &t, const void *E, const void *in, int64_t ld_in,
                    void *out, int64_t ld_out, InstCols cols, cudaStream_t s);
