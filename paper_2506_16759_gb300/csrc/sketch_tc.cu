@@ -83,10 +83,10 @@ template <int NCOL>
 struct TcAcc {
   static constexpr int NA = NCOL > 64 ? 1 : 2;
   // 18 warps put five on two sub-partitions, whose 16K registers cap a
-  // thread at 96: beyond 64 columns the compensated sums live in shared
+  // thread at 96: from 64 columns on the compensated sums live in shared
   // memory (and the B ring is shorter to make room)
-  static constexpr bool SMEM_SUMS = NCOL > 64;
-  static constexpr int SB = NCOL > 64 ? 3 : kSB;
+  static constexpr bool SMEM_SUMS = NCOL >= 64;
+  static constexpr int SB = NCOL > 64 ? 3 : (NCOL == 64 ? 4 : kSB);
 };
 constexpr int kEvalWarps = 16;
 constexpr int kThreads = 32 * (2 + kEvalWarps);
@@ -641,16 +641,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_ksum_tc(TcArgs a) {
     auto fold = [&]() {
 #pragma unroll
       for (int c = 0; c < CPT; ++c) {
-        float &ac = SMEM_SUMS ? sa[c * kRows] : acc[c % CR];
-        float &cm = SMEM_SUMS ? sc[c * kRows] : cmp[c % CR];
-        const float y = grp[c] - cm;
-        const float s2 = ac + y;
-        cm = (s2 - ac) - y;
-        ac = s2;
+        if constexpr (SMEM_SUMS) {
+          const float ac = sa[c * kRows], cm = sc[c * kRows];
+          const float y = grp[c] - cm;
+          const float s2 = ac + y;
+          sc[c * kRows] = (s2 - ac) - y;
+          sa[c * kRows] = s2;
+        } else {
+          const float y = grp[c] - cmp[c % CR];
+          const float s2 = acc[c % CR] + y;
+          cmp[c % CR] = (s2 - acc[c % CR]) - y;
+          acc[c % CR] = s2;
+        }
         grp[c] = 0.f;
       }
     };
-    auto total = [&](int c) -> float { return SMEM_SUMS ? sa[c * kRows] : acc[c % CR]; };
+    auto total = [&](int c) -> float {
+      if constexpr (SMEM_SUMS) return sa[c * kRows];
+      else return acc[c % CR];
+    };
     bool alive = true;
     auto fail = [&]() {
       alive = false;
