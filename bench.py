@@ -465,6 +465,9 @@ def main_kernel_only(args):
     from paper_2506_16759_gb300 import workloads as W
     dev = torch.device("cuda:0")
     w = W.config("c2")
+    if args.kernel_only == "paper":
+        main_paper_problem(args, dev)
+        return
     if args.kernel_only == "build":
         w = W.scaled(w, args.n or w.n)
         X = torch.from_numpy(w.points()).to(dev)
@@ -502,6 +505,63 @@ def main_kernel_only(args):
                       "ms": ms, "tflops": flops / (ms * 1e-3) / 1e12}), flush=True)
 
 
+def main_paper_problem(args, dev):
+    """A Sec. V-A kernel problem (exp3d or helmholtz) sketched through the
+    matvec of an H2 matrix prebuilt for the same kernel (untimed); timed:
+    tree + construction with direct entry evaluation, as in the paper."""
+    import numpy as np
+    import torch
+
+    from paper_2506_16759_gb300 import api
+    from paper_2506_16759_gb300 import workloads as W
+    w = W.paper_problem(args.problem, args.n or 262144)
+    X = torch.from_numpy(w.points()).to(dev)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    tree = api.ClusterTree(X, w.leaf_size, w.eta)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pre = api.H2Matrix.build(tree, w.kernel, w.params, w.extra["operand_tol"], prec=args.prec,
+                             seed=1, sketch="ksum")
+    torch.cuda.synchronize()
+    pre_ms = (time.perf_counter() - t0) * 1e3
+
+    def step(seed, timing=False):
+        tr = api.ClusterTree(X, w.leaf_size, w.eta)
+        return tr, api.H2Matrix.build(tr, w.kernel, w.params, w.tol, prec=args.prec, seed=seed,
+                                      sketch="h2sum", operands=[pre], timing=timing,
+                                      d0=w.d0, d_inc=w.d_inc, d_max=w.d_max)
+
+    times = []
+    for k in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        tr, h = step(100 + k)
+        e1.record()
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            times.append(e0.elapsed_time(e1))
+        del h, tr
+    tr, h = step(7, timing=True)
+    st = h.stats()
+    G = torch.from_numpy(W.gaussian_probe(w.n, 4, 0)).to(dev)
+    exact = api.ksum_sketch(X, w.kernel, w.params, G, prec="fp64")
+    err = float(torch.linalg.norm(h.matvec(G) - exact) / torch.linalg.norm(exact))
+    err_pre = float(torch.linalg.norm(pre.matvec(G) - exact) / torch.linalg.norm(exact))
+    ms = statistics.mean(times)
+    print(json.dumps({
+        "kernel_only": "paper", "problem": w.name, "n": w.n, "prec": args.prec,
+        "ms": ms, "points_per_s": w.n / (ms * 1e-3), "steps": args.steps, "warmup": args.warmup,
+        "rel_error": err, "operand_rel_error": err_pre, "operand_tol": w.extra["operand_tol"],
+        "operand_build_ms": pre_ms, "tol": w.tol, "d_final": st["d_final"],
+        "rank_max": st["rank_max"], "rounds": st["rounds"],
+        "memory_gb": (st["bytes_dense"] + st["bytes_coupling"] + st["bytes_basis"]) / 1e9,
+        "phases_ms": {p: st[f"ms_{p}"] for p in ("sketch", "nearfield", "qr", "id", "upsweep",
+                                                 "coupling", "bsr", "total")}}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -516,8 +576,11 @@ def main():
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="time the workload's 32/+16 sample schedule instead of the tuned one")
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
-    ap.add_argument("--kernel-only", default="", choices=["", "ksum", "build"],
-                    help="time only the fused sketch, or builds at --n points (for profiling)")
+    ap.add_argument("--kernel-only", default="", choices=["", "ksum", "build", "paper"],
+                    help="time only the fused sketch, builds at --n points (for profiling), "
+                         "or a paper kernel problem with the H2-matvec sampler")
+    ap.add_argument("--problem", default="helmholtz", choices=["exp3d", "helmholtz"],
+                    help="kernel problem for --kernel-only paper")
     ap.add_argument("--n", type=int, default=0, help="point count for --kernel-only build")
     args = ap.parse_args()
     if args.kernel_only:

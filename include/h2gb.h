@@ -57,14 +57,18 @@ typedef enum {
  *   H2_K_LAPLACE_IE 1/(4 pi r) off the diagonal, diag on it {diag}
  *   H2_K_POLY       (c + x.y)^p, p a small integer          {c, p}
  *   H2_K_H2SUM      sum of existing H2 matrices (the update workload of
- *                   Sec. V-A); operands given in h2_build_opts            */
+ *                   Sec. V-A); operands given in h2_build_opts
+ *   H2_K_HELMHOLTZ_IE cos(k r)/r off the diagonal, diag on it {k, diag}
+ *                   -- the Helmholtz volume-IE operator of Sec. V-A (the
+ *                   paper fixes k = 3 and defines only x != y)           */
 typedef enum {
   H2_K_EXP = 0,
   H2_K_MATERN32 = 1,
   H2_K_GAUSS = 2,
   H2_K_LAPLACE_IE = 3,
   H2_K_POLY = 4,
-  H2_K_H2SUM = 5
+  H2_K_H2SUM = 5,
+  H2_K_HELMHOLTZ_IE = 6
 } h2_kernel;
 
 typedef enum {

@@ -47,11 +47,11 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-K_EXP, K_MATERN32, K_GAUSS, K_LAPLACE_IE, K_POLY = 0, 1, 2, 3, 4
+K_EXP, K_MATERN32, K_GAUSS, K_LAPLACE_IE, K_POLY, K_HELMHOLTZ_IE = 0, 1, 2, 3, 4, 6
 
 # -----------------------------------------------------------------------------
 # Matrix entries  (Sec. V-A test problems: exponential covariance and the
-# volume-IE kernel, plus the kernels of the synthetic workloads)
+# Helmholtz volume-IE kernel, plus the kernels of the synthetic workloads)
 # -----------------------------------------------------------------------------
 
 
@@ -91,6 +91,13 @@ def kernel_block(kernel: int, params, Xa: np.ndarray, Xb: np.ndarray,
         (diag,) = params
         with np.errstate(divide="ignore"):
             off = 1.0 / (4.0 * math.pi * r)
+        return np.where(same, diag, off)
+    if kernel == K_HELMHOLTZ_IE:
+        # Sec. V-A: cos(k|x-y|)/|x-y| for x != y; the diagonal is a parameter
+        wave = float(params[0])
+        diag = float(params[1]) if len(params) > 1 else 0.0
+        with np.errstate(divide="ignore", invalid="ignore"):
+            off = np.cos(wave * r) / r
         return np.where(same, diag, off)
     raise ValueError(f"unknown kernel {kernel}")
 
@@ -677,6 +684,15 @@ def h2_dense(h: H2Oracle) -> np.ndarray:
     A = np.zeros_like(At)
     A[np.ix_(tree.perm, tree.perm)] = At
     return A
+
+
+def h2_sampler(h: H2Oracle):
+    """The black box K_blk of the covariance and IE test problems (Sec. V-A):
+    samples Y = H Omega from the matvec of an H2 matrix H prebuilt for the
+    same kernel; the entries of the new matrix are still evaluated directly."""
+    def sampler(Om):
+        return h2_matvec(h, Om)
+    return sampler
 
 
 def h2_sum_operator(ops: list) -> tuple:

@@ -16,7 +16,8 @@ import torch
 from . import _lib
 from ._lib import BuildOpts, Stats, TreeInfo, check, lib
 
-KERNELS = {"exp": 0, "matern32": 1, "gauss": 2, "laplace_ie": 3, "poly": 4, "h2sum": 5}
+KERNELS = {"exp": 0, "matern32": 1, "gauss": 2, "laplace_ie": 3, "poly": 4, "h2sum": 5,
+           "helmholtz_ie": 6}
 PREC = {"fp64": 0, "mixed": 1, "mixed_simt": 2}
 SKETCH = {"ksum": 0, "dense": 1, "callback": 2, "h2sum": 3}
 

@@ -173,6 +173,12 @@ KernelDesc make_kernel_desc(int kid, const double *params, int nparams) {
       k.scale = 1.0 / (4.0 * M_PI);
       k.diag = params[0];
       break;
+    case H2_K_HELMHOLTZ_IE:
+      need(1);
+      H2_REQUIRE(params[0] >= 0, "wave number must be >= 0");
+      k.scale = params[0];
+      k.diag = nparams > 1 ? params[1] : 0.0;
+      break;
     case H2_K_POLY:
       need(2);
       k.scale = params[0];

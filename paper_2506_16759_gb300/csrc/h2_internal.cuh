@@ -118,8 +118,9 @@ inline std::vector<T> to_host(const T *p, size_t n, cudaStream_t s) {
 struct KernelDesc {
   int kid;      // h2_kernel
   int pw;       // polynomial power
-  double scale; // exp: 1/l; matern: sqrt3/l; gauss: 1/(2 s^2); laplace: 1/(4 pi); poly: c
-  double diag;  // nugget (exp/matern/gauss) or the diagonal value (laplace)
+  double scale; // exp: 1/l; matern: sqrt3/l; gauss: 1/(2 s^2); laplace: 1/(4 pi); poly: c;
+                // helmholtz: the wave number k
+  double diag;  // nugget (exp/matern/gauss) or the diagonal value (laplace, helmholtz)
 };
 
 KernelDesc make_kernel_desc(int kid, const double *params, int nparams);
@@ -147,6 +148,38 @@ __device__ __forceinline__ double dev_rsqrt<double>(double x) { return 1.0 / sqr
 template <>
 __device__ __forceinline__ float dev_rsqrt<float>(float x) { return rsqrtf(x); }
 
+// cos(t) in FP32 to a few units of the last place for moderate |t|:
+// Cody-Waite reduction u = t - q pi/2 (pi/2 split in two, the high part
+// with 8 significant bits so that q * high is exact for |q| < 2^15), then
+// the Taylor series of cos and sin on |u| <= pi/4 (truncation below 2e-9)
+// and the quadrant q mod 4 picks +-cos(u) or +-sin(u).  All of it runs on
+// the FMA pipe.
+__device__ __forceinline__ float cos_reduced(float t) {
+  const float q = rintf(t * 0.636619772367581343f);
+  float u = fmaf(-q, 1.5703125f, t);
+  u = fmaf(-q, 4.83826794896619231e-4f, u);
+  const float u2 = u * u;
+  float c = fmaf(u2, -2.75573192239858907e-7f, 2.48015873015873016e-5f);
+  c = fmaf(u2, c, -1.38888888888888889e-3f);
+  c = fmaf(u2, c, 4.16666666666666667e-2f);
+  c = fmaf(u2, c, -0.5f);
+  c = fmaf(u2, c, 1.f);
+  float sn = fmaf(u2, 2.75573192239858907e-6f, -1.98412698412698413e-4f);
+  sn = fmaf(u2, sn, 8.33333333333333333e-3f);
+  sn = fmaf(u2, sn, -1.66666666666666667e-1f);
+  sn = fmaf(u2 * u, sn, u);
+  const int qi = (int)q & 3;
+  const float v = (qi & 1) ? sn : c;
+  return (qi == 1 || qi == 2) ? -v : v;
+}
+
+template <typename T>
+__device__ __forceinline__ T dev_cos(T x);
+template <>
+__device__ __forceinline__ double dev_cos<double>(double x) { return cos(x); }
+template <>
+__device__ __forceinline__ float dev_cos<float>(float x) { return cos_reduced(x); }
+
 // Off-diagonal kernel value from r^2 (or the dot product for POLY).
 template <int KID, typename T>
 __device__ __forceinline__ T kval(T r2_or_dot, T scale, int pw) {
@@ -159,6 +192,10 @@ __device__ __forceinline__ T kval(T r2_or_dot, T scale, int pw) {
     return dev_exp<T>(-r2_or_dot * scale);
   } else if constexpr (KID == H2_K_LAPLACE_IE) {
     return r2_or_dot > T(0) ? dev_rsqrt<T>(r2_or_dot) * scale : T(0);
+  } else if constexpr (KID == H2_K_HELMHOLTZ_IE) {
+    if (!(r2_or_dot > T(0))) return T(0);
+    const T ir = dev_rsqrt<T>(r2_or_dot);
+    return dev_cos<T>(scale * (r2_or_dot * ir)) * ir;
   } else {  // POLY
     T base = scale + r2_or_dot;
     T v = T(1);
@@ -170,7 +207,7 @@ __device__ __forceinline__ T kval(T r2_or_dot, T scale, int pw) {
 // Value on the diagonal (same point index).
 template <int KID, typename T>
 __device__ __forceinline__ T kdiag(T r2_or_dot, T scale, int pw, T diag) {
-  if constexpr (KID == H2_K_LAPLACE_IE) {
+  if constexpr (KID == H2_K_LAPLACE_IE || KID == H2_K_HELMHOLTZ_IE) {
     return diag;
   } else if constexpr (KID == H2_K_POLY) {
     return kval<KID, T>(r2_or_dot, scale, pw);
@@ -228,6 +265,7 @@ inline void dispatch_kernel(int kid, F &&f) {
     case H2_K_GAUSS: f(std::integral_constant<int, H2_K_GAUSS>{}); break;
     case H2_K_LAPLACE_IE: f(std::integral_constant<int, H2_K_LAPLACE_IE>{}); break;
     case H2_K_POLY: f(std::integral_constant<int, H2_K_POLY>{}); break;
+    case H2_K_HELMHOLTZ_IE: f(std::integral_constant<int, H2_K_HELMHOLTZ_IE>{}); break;
     default: throw Error{H2_ERR_ARG, "unknown kernel id"};
   }
 }

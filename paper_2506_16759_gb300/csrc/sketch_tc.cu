@@ -283,8 +283,8 @@ __device__ __forceinline__ void tmem_ld<4>(uint32_t taddr, float *v) {
 
 // Scale factor sigma applied to coordinates so that the entry needs no
 // further multiplication:  exp: K = 2^-r';  Matern 3/2: K = (1 + r' ln2) 2^-r'
-// with r' = sigma |x - y|;  Gaussian: K = 2^-(r'^2);  Laplace and polynomial
-// kernels keep unscaled coordinates.
+// with r' = sigma |x - y|;  Gaussian: K = 2^-(r'^2);  Laplace, Helmholtz and
+// polynomial kernels keep unscaled coordinates.
 double tc_sigma(const KernelDesc &kd) {
   switch (kd.kid) {
     case H2_K_EXP:
@@ -296,7 +296,7 @@ double tc_sigma(const KernelDesc &kd) {
 
 // Entry from the scaled row coordinates (rx, ry, rz) and a scaled point
 // offset p (the polynomial kernel: absolute coordinates).  `c` is the
-// Laplace factor 1/(4 pi) or the polynomial shift.
+// Laplace factor 1/(4 pi), the Helmholtz wave number or the polynomial shift.
 template <int KID>
 __device__ __forceinline__ float tc_entry(float rx, float ry, float rz, float4 p, float c, int pw) {
   if constexpr (KID == H2_K_POLY) {
@@ -311,6 +311,10 @@ __device__ __forceinline__ float tc_entry(float rx, float ry, float rz, float4 p
       return ex2_approx(-r2);
     } else if constexpr (KID == H2_K_LAPLACE_IE) {
       return r2 > 0.f ? rsqrtf(r2) * c : 0.f;
+    } else if constexpr (KID == H2_K_HELMHOLTZ_IE) {
+      if (!(r2 > 0.f)) return 0.f;
+      const float ir = rsqrtf(r2);
+      return cos_reduced(c * (r2 * ir)) * ir;
     } else {
       const float r = sqrt_approx(r2);
       const float e = ex2_approx(-r);
@@ -703,7 +707,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ksum_tc(TcArgs a) {
 #pragma unroll
           for (int u = 0; u < EPT; ++u) {
             kv[u] = tc_entry<KID>(rx, ry, rz, po[u], kc, pw);
-            if constexpr (KID == H2_K_LAPLACE_IE && !FAR) {
+            if constexpr ((KID == H2_K_LAPLACE_IE || KID == H2_K_HELMHOLTZ_IE) && !FAR) {
               // the row's own point: the rounded offsets need not cancel exactly
               if (ctrl[sb].j0[h] + EPT * q + u == g) kv[u] = 0.f;
             }

@@ -18,6 +18,14 @@ Workloads (the paper's test problems are synthetic point clouds, Sec. V-A):
 * ``c5``  64 independent 2D/3D exponential covariance instances with N drawn
           log-uniform in [2048, 32768] and l uniform in [0.05, 0.3].
 
+The two kernel problems exactly as the paper states them (Sec. V-A), both on
+points uniform in the unit cube, sketched through the matvec of an H2 matrix
+prebuilt for the same kernel (``paper_problem``):
+
+* ``exp3d``      exp(-r/0.2), no nugget;
+* ``helmholtz``  cos(3r)/r off the diagonal, 0 on it (the paper defines the
+                 operator for x != y only).
+
 Every workload uses 32 initial Gaussian samples, increments of 16 and at most
 256 samples.
 """
@@ -35,9 +43,11 @@ K_GAUSS = 2
 K_LAPLACE_IE = 3
 K_POLY = 4
 K_H2SUM = 5
+K_HELMHOLTZ_IE = 6
 
 KERNEL_NAMES = {K_EXP: "exp", K_MATERN32: "matern32", K_GAUSS: "gauss",
-                K_LAPLACE_IE: "laplace_ie", K_POLY: "poly", K_H2SUM: "h2sum"}
+                K_LAPLACE_IE: "laplace_ie", K_POLY: "poly", K_H2SUM: "h2sum",
+                K_HELMHOLTZ_IE: "helmholtz_ie"}
 
 
 @dataclass
@@ -142,3 +152,17 @@ def c5_instances(count: int = 64, seed: int = 5) -> list[Workload]:
         out.append(Workload(f"c5[{i}]", n, dim, K_EXP, (ell, 1e-4), tol=1e-6, sketch="ksum",
                             point_seed=1000 + i, omega_seed=2000 + i))
     return out
+
+
+def paper_problem(name: str, n: int = 262144) -> Workload:
+    """A Sec. V-A kernel problem at n points: tol 1e-6, leaf 64, eta 0.7; the
+    black-box sampler is an H2 matrix of the same kernel prebuilt at
+    ``extra["operand_tol"]`` (ten times tighter than the target)."""
+    if name == "exp3d":
+        return Workload("exp3d", n, 3, K_EXP, (0.2, 0.0), tol=1e-6, sketch="h2matvec",
+                        point_seed=6, omega_seed=43, extra={"operand_tol": 1e-7})
+    if name == "helmholtz":
+        return Workload("helmholtz", n, 3, K_HELMHOLTZ_IE, (3.0, 0.0), tol=1e-6,
+                        sketch="h2matvec", point_seed=7, omega_seed=53,
+                        extra={"operand_tol": 1e-7})
+    raise KeyError(name)

@@ -73,7 +73,8 @@ def test_tree_bit_exact_full_size(name):
 
 
 KCASES = [(W.K_EXP, (0.2, 1e-4), 2), (W.K_MATERN32, (0.1, 1e-4), 3), (W.K_GAUSS, (0.05, 1e-3), 3),
-          (W.K_LAPLACE_IE, (0.3799 / 48 / 48,), 3), (W.K_POLY, (1.0, 3), 2)]
+          (W.K_LAPLACE_IE, (0.3799 / 48 / 48,), 3), (W.K_POLY, (1.0, 3), 2),
+          (W.K_HELMHOLTZ_IE, (3.0, 1e-3), 3)]
 
 
 @pytest.mark.parametrize("kernel,params,dim", KCASES)
@@ -196,6 +197,7 @@ BUILD_CASES = [
     (4096, 2, W.K_EXP, (0.2, 1e-4), 1e-9, 64, 0.7, 11),       # adaptive rounds
     (3000, 3, W.K_MATERN32, (0.1, 1e-4), 1e-6, 32, 0.7, 12),  # ragged 3D
     (2048, 3, W.K_LAPLACE_IE, (0.3799 / 48 / 48,), 1e-5, 32, 0.7, 13),
+    (3000, 3, W.K_HELMHOLTZ_IE, (3.0, 0.0), 1e-6, 32, 0.7, 16),  # Sec. V-A IE operator
     (2048, 2, W.K_POLY, (1.0, 3), 1e-10, 32, 0.7, 14),       # exact rank 10
     (1500, 2, W.K_GAUSS, (0.05, 1e-4), 1e-6, 16, 1.0, 15),
 ]
@@ -230,7 +232,7 @@ def test_build_c1_dense_sketch():
     assert rel <= 1e-10
 
 
-@pytest.mark.parametrize("case", BUILD_CASES[:4], ids=lambda c: f"n{c[0]}d{c[1]}k{c[2]}")
+@pytest.mark.parametrize("case", BUILD_CASES[:5], ids=lambda c: f"n{c[0]}d{c[1]}k{c[2]}")
 def test_build_mixed_within_tolerance(case):
     n, dim, kernel, params, tol, leaf, eta, seed = case
     X, om, t, lists, ho = oracle_build(n, dim, kernel, params, tol, leaf, eta, seed)
@@ -366,3 +368,30 @@ def test_h2sum_with_mixed_precision_operands():
                                seed=9)
         y = h.matvec(gpu(G)).cpu().numpy()
         assert np.linalg.norm(y - AG) <= 10 * 1e-6 * np.linalg.norm(AG)
+
+
+@pytest.mark.parametrize("kernel,params", [(W.K_HELMHOLTZ_IE, (3.0, 0.0)), (W.K_EXP, (0.2, 0.0))])
+def test_h2_matvec_sampler_matches_oracle(kernel, params):
+    # Sec. V-A: the kernel problems sketched through the matvec of an H2
+    # matrix prebuilt for the same kernel (tol 1e-7), entries evaluated
+    # directly; target tol 1e-6
+    n, dim, leaf, eta, tol = 4096, 3, 32, 0.7, 1e-6
+    X = W.uniform_points(n, dim, 72)
+    om_pre, om = W.gaussian_omega(n, 256, 73), W.gaussian_omega(n, 256, 74)
+    t = O.build_cluster_tree(X, leaf)
+    lists = O.dual_traversal(t, eta)
+    pre_o = O.build_h2(t, lists, kernel, params, tol / 10, om_pre,
+                       O.ksum_sampler(X, kernel, params, 1024))
+    ho = O.build_h2(t, lists, kernel, params, tol, om, O.h2_sampler(pre_o))
+    tree = api.ClusterTree(gpu(X), leaf, eta)
+    pre_g = api.H2Matrix.build(tree, kernel, params, tol / 10, omega=gpu(om_pre))
+    G = W.gaussian_probe(n, 4, 5)
+    AG = O.ksum_rows(X, kernel, params, G, np.arange(n))
+    for prec, bar in (("fp64", 1e-10), ("mixed", 1e-5)):
+        h = api.H2Matrix.build(tree, kernel, params, tol, omega=gpu(om), sketch="h2sum",
+                               operands=[pre_g], prec=prec)
+        if prec == "fp64":
+            check_same_skeletons(h, t, ho)
+        rel, y, _ = matvec_rel(h, ho, n, seed=5)
+        assert rel <= bar
+        assert np.linalg.norm(y - AG) <= 10 * tol * np.linalg.norm(AG)
