@@ -546,7 +546,7 @@ def main_paper_problem(args, dev):
         del h, tr
     tr, h = step(7, timing=True)
     st = h.stats()
-    G = torch.from_numpy(W.gaussian_probe(w.n, 4, 0)).to(dev)
+    G = torch.from_numpy(W.gaussian_probe(w.n, 8, 0)).to(dev)
     exact = api.ksum_sketch(X, w.kernel, w.params, G, prec="fp64")
     err = float(torch.linalg.norm(h.matvec(G) - exact) / torch.linalg.norm(exact))
     err_pre = float(torch.linalg.norm(pre.matvec(G) - exact) / torch.linalg.norm(exact))
