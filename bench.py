@@ -506,9 +506,12 @@ def main_kernel_only(args):
 
 
 def main_paper_problem(args, dev):
-    """A Sec. V-A kernel problem (exp3d or helmholtz) sketched through the
-    matvec of an H2 matrix prebuilt for the same kernel (untimed); timed:
-    tree + construction with direct entry evaluation, as in the paper."""
+    """A Sec. V-A problem sketched through the matvec of an H2 matrix prebuilt
+    for its kernel (untimed).  exp3d / helmholtz: timed tree + construction
+    with direct entry evaluation, as in the paper.  update: that H2 matrix
+    plus a symmetric rank-32 product recompressed into one H2 matrix (entries
+    from the operand's representation plus the product's; the operands share
+    the tree, so only the construction is timed)."""
     import numpy as np
     import torch
 
@@ -518,18 +521,27 @@ def main_paper_problem(args, dev):
     X = torch.from_numpy(w.points()).to(dev)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     tree = api.ClusterTree(X, w.leaf_size, w.eta)
+    # the operand: an H2 matrix of the kernel (for "update", of the covariance
+    # kernel, to which the low-rank product is added)
+    kop, pop = (w.extra["operands"][0] if w.kernel == W.K_H2SUM else (w.kernel, w.params))
+    lowrank, kw = None, {}
+    if "rank" in w.extra:
+        U, V = W.low_rank_factors(w.n, w.extra["rank"], w.extra["lowrank_seed"],
+                                  w.extra["lowrank_scale"])
+        lowrank = (torch.from_numpy(U).to(dev), torch.from_numpy(V).to(dev))
+        kw["lowrank"] = lowrank
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    pre = api.H2Matrix.build(tree, w.kernel, w.params, w.extra["operand_tol"], prec=args.prec,
-                             seed=1, sketch="ksum")
+    pre = api.H2Matrix.build(tree, kop, pop, w.extra["operand_tol"], prec=args.prec, seed=1,
+                             sketch="ksum")
     torch.cuda.synchronize()
     pre_ms = (time.perf_counter() - t0) * 1e3
 
     def step(seed, timing=False):
-        tr = api.ClusterTree(X, w.leaf_size, w.eta)
+        tr = api.ClusterTree(X, w.leaf_size, w.eta) if w.kernel != W.K_H2SUM else tree
         return tr, api.H2Matrix.build(tr, w.kernel, w.params, w.tol, prec=args.prec, seed=seed,
                                       sketch="h2sum", operands=[pre], timing=timing,
-                                      d0=w.d0, d_inc=w.d_inc, d_max=w.d_max)
+                                      d0=w.d0, d_inc=w.d_inc, d_max=w.d_max, **kw)
 
     times = []
     for k in range(args.warmup + args.steps):
@@ -547,9 +559,11 @@ def main_paper_problem(args, dev):
     tr, h = step(7, timing=True)
     st = h.stats()
     G = torch.from_numpy(W.gaussian_probe(w.n, 8, 0)).to(dev)
-    exact = api.ksum_sketch(X, w.kernel, w.params, G, prec="fp64")
+    kernel_part = api.ksum_sketch(X, kop, pop, G, prec="fp64")
+    exact = kernel_part if lowrank is None else kernel_part + lowrank[0] @ (lowrank[1].T @ G)
     err = float(torch.linalg.norm(h.matvec(G) - exact) / torch.linalg.norm(exact))
-    err_pre = float(torch.linalg.norm(pre.matvec(G) - exact) / torch.linalg.norm(exact))
+    err_pre = float(torch.linalg.norm(pre.matvec(G) - kernel_part) /
+                    torch.linalg.norm(kernel_part))
     ms = statistics.mean(times)
     print(json.dumps({
         "kernel_only": "paper", "problem": w.name, "n": w.n, "prec": args.prec,
@@ -579,7 +593,7 @@ def main():
     ap.add_argument("--kernel-only", default="", choices=["", "ksum", "build", "paper"],
                     help="time only the fused sketch, builds at --n points (for profiling), "
                          "or a paper kernel problem with the H2-matvec sampler")
-    ap.add_argument("--problem", default="helmholtz", choices=["exp3d", "helmholtz"],
+    ap.add_argument("--problem", default="helmholtz", choices=["exp3d", "helmholtz", "update"],
                     help="kernel problem for --kernel-only paper")
     ap.add_argument("--n", type=int, default=0, help="point count for --kernel-only build")
     args = ap.parse_args()

@@ -120,6 +120,17 @@ typedef struct {
   int n_operands;
   int timing;                 /* 1: record per-phase CUDA-event timers */
   int ksum_tile;              /* 0 = autotuned; else rows per sketch CTA tile */
+  /* Optional low-rank term: the operator becomes (kernel or H2 sum) + U V^T,
+   * the update problem of Sec. V-A (an H2 matrix plus a rank-r product).
+   * U, V: device, N x lowrank_rank column-major with ld = N, original point
+   * order, FP64, read during the call only.  U V^T must be symmetric (the
+   * construction shares row and column bases), e.g. V = U S with S
+   * symmetric.  Needs a single instance and a sketch in original order
+   * (dense, callback or H2 sum): the library adds U (V^T Omega) to the
+   * sampler's output and U(I,:) V(J,:)^T to every generated block. */
+  const double *lowrank_u;
+  const double *lowrank_v;
+  int lowrank_rank;           /* 0 = none, at most 64 */
 } h2_build_opts;
 
 /* Fills opts with the workload defaults (32/16/256, FP64, Philox seed 0,

@@ -695,6 +695,28 @@ def h2_sampler(h: H2Oracle):
     return sampler
 
 
+def low_rank_update(tree: ClusterTree, entries, sampler, U: np.ndarray, V: np.ndarray) -> tuple:
+    """Entry function and sampler of an operator plus the product U V^T (the
+    update problem of Sec. V-A: an existing H2 matrix plus a rank-32 product;
+    U V^T is taken symmetric, like the operator).  `entries` is a kernel id
+    with its parameters as a pair (kernel, params), or a callable on tree
+    positions; `sampler` gives the operator's products in original order; U
+    and V are (N, r) in original order."""
+    Ut, Vt = U[tree.perm], V[tree.perm]
+
+    def entries2(Ia, Ib):
+        if callable(entries):
+            base = np.asarray(entries(Ia, Ib), dtype=np.float64)
+        else:
+            base = _entries(tree, entries[0], entries[1], Ia, Ib)
+        return base + Ut[Ia] @ Vt[Ib].T
+
+    def sampler2(Om):
+        return sampler(Om) + U @ (V.T @ Om)
+
+    return entries2, sampler2
+
+
 def h2_sum_operator(ops: list) -> tuple:
     """Entry function and sampler of the sum of H2 matrices `ops` on one tree
     (the H2-update operator of Sec. V-A): entries from the dense expansion of

@@ -29,7 +29,8 @@ class BuildOpts(C.Structure):
                 ("omega_stored", C.c_void_p), ("sketch", C.c_int), ("dense_a", C.c_void_p),
                 ("sampler", SAMPLER_FN), ("sampler_ctx", C.c_void_p),
                 ("operands", C.c_void_p), ("n_operands", C.c_int), ("timing", C.c_int),
-                ("ksum_tile", C.c_int)]
+                ("ksum_tile", C.c_int), ("lowrank_u", C.c_void_p), ("lowrank_v", C.c_void_p),
+                ("lowrank_rank", C.c_int)]
 
 
 class TreeInfo(C.Structure):

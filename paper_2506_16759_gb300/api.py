@@ -107,7 +107,8 @@ class ClusterTree:
 
 
 def make_opts(d0=32, d_inc=16, d_max=256, prec="fp64", omega=None, seed=0, sketch="ksum",
-              dense_a=None, timing=False, sampler=None, operands=None, ksum_tile=0):
+              dense_a=None, timing=False, sampler=None, operands=None, ksum_tile=0,
+              lowrank=None):
     o = BuildOpts()
     lib().h2_default_opts(C.byref(o))
     o.d0, o.d_inc, o.d_max = d0, d_inc, d_max
@@ -135,6 +136,11 @@ def make_opts(d0=32, d_inc=16, d_max=256, prec="fp64", omega=None, seed=0, sketc
         o.n_operands = len(operands)
     o.timing = 1 if timing else 0
     o.ksum_tile = ksum_tile
+    if lowrank is not None:
+        # (U, V): the operator gets the symmetric term U V^T
+        u, v = (colmajor(x.to(torch.float64)) for x in lowrank)
+        keep += [u, v]
+        o.lowrank_u, o.lowrank_v, o.lowrank_rank = u.data_ptr(), v.data_ptr(), u.shape[1]
     return o, keep
 
 

@@ -342,6 +342,7 @@ struct Builder {
   std::vector<double> tols;
   DBuf<int32_t> cb, ce;             // per-instance column range of the current pass
   DBuf<double> om_stage;            // FP64 staging of new Omega columns (mixed / callbacks)
+  DBuf<char> lr_ut, lr_vt;          // low-rank factors, tree-order rows (T)
   TcLayout tcl;                     // padded leaf layout of the tensor-core sketch (built once)
   bool tcl_ready = false;
   int64_t sketch_pairs = 0, sketch_cols = 0;
@@ -606,6 +607,8 @@ struct Builder {
           add_into(yo.p, tmp.p, (int64_t)N * nc);
         }
       }
+      if (o.lowrank_rank > 0)
+        lowrank_sample(o.lowrank_u, o.lowrank_v, N, N, o.lowrank_rank, omo.p, N, nc, yo.p, N, s);
       DBuf<int> bad;
       bad.alloc_zero(1, s);
       k_check_finite_cols<<<ceil_div(N, 256), 256, 0, s>>>(yo.p, N, N, 0, nc, bad.p);
@@ -746,6 +749,7 @@ struct Builder {
       to_device(ddo, dofs, s);
       h2sum_dense(fp64(), H->near_nnz, H->near_erow.p, H->near_idx.p, L.m.p, H->doff.p, Dp(),
                   ddp.p, ddp32.p, ddo.p, o.n_operands, s);
+      lowrank_near();
       H2_CUDA(cudaStreamSynchronize(s));
       timer.end(PH_NEAR);
       std::vector<int32_t> b(C, 0), e(C, o.d0);
@@ -768,6 +772,7 @@ struct Builder {
     g.n_rows = L.n;
     g.ptr = H->near_ptr.p;
     dense_blocks_gen(H->kid, fp64(), g, s);
+    lowrank_near();
     timer.end(PH_NEAR);
     std::vector<int32_t> b(C, 0), e(C, o.d0);
     set_cols(b, e);
@@ -787,6 +792,20 @@ struct Builder {
     } else {
       near_bsr(Yp(L), -1.0);
     }
+  }
+
+  // The low-rank term's share of the near blocks D and of level l's couplings.
+  void lowrank_near() {
+    if (o.lowrank_rank == 0) return;
+    LevelData &L = H->lv[1];
+    lowrank_blocks(fp64(), false, L.n, H->near_ptr.p, H->near_idx.p, H->doff.p, L.m.p, L.row.p,
+                   nullptr, nullptr, lr_ut.p, lr_vt.p, o.lowrank_rank, Dp(), s);
+  }
+  void lowrank_couplings(int l) {
+    if (o.lowrank_rank == 0) return;
+    LevelData &L = H->lv[l];
+    lowrank_blocks(fp64(), true, L.n, L.far_ptr.p, L.far_idx.p, L.boff.p, L.k.p, nullptr,
+                   L.krow.p, L.skel.p, lr_ut.p, lr_vt.p, o.lowrank_rank, Bp(L), s);
   }
 
   // out(cols) += sign * D Om1(cols) over the leaf tasks, columns from cb/ce
@@ -1010,6 +1029,7 @@ struct Builder {
       else L.B32.alloc(L.B_size + 4);
       if (is_sum()) {
         sum_couplings(l);
+        lowrank_couplings(l);
       } else {
       CouplingArgs ca{};
       ca.nnz = L.far_nnz;
@@ -1025,6 +1045,7 @@ struct Builder {
       ca.ptr = L.far_ptr.p;
       timer.begin(PH_COUP);
       coupling_gen(H->kid, fp64(), ca, s);
+      lowrank_couplings(l);
       timer.end(PH_COUP);
       }
     } else if (is_sum()) {
@@ -1174,6 +1195,14 @@ struct Builder {
     H->lv.resize(std::max(H->levels, 1) + 2);
     setup_leaves();
     set_level_flags(1);
+    if (o.lowrank_rank > 0) {
+      const int64_t N = H->n_total;
+      const size_t bytes = (size_t)N * o.lowrank_rank * (fp64() ? 8 : 4);
+      lr_ut.alloc(bytes);
+      lr_vt.alloc(bytes);
+      lowrank_tree_rows(fp64(), o.lowrank_u, N, H->orig_of_pos.p, N, o.lowrank_rank, lr_ut.p, s);
+      lowrank_tree_rows(fp64(), o.lowrank_v, N, H->orig_of_pos.p, N, o.lowrank_rank, lr_vt.p, s);
+    }
     // initial samples and the norm estimate
     std::vector<int> all(C);
     std::iota(all.begin(), all.end(), 0);
@@ -1288,6 +1317,11 @@ void validate_opts(const h2_build_opts &o) {
              "unknown precision");
   H2_REQUIRE(o.omega_mode == 0 || (o.omega_mode == 1 && o.omega_stored != nullptr),
              "stored Omega mode needs omega_stored");
+  H2_REQUIRE(o.lowrank_rank >= 0 && o.lowrank_rank <= 64, "low-rank term of rank 0..64");
+  H2_REQUIRE(o.lowrank_rank == 0 || (o.lowrank_u != nullptr && o.lowrank_v != nullptr),
+             "a low-rank term needs U and V");
+  H2_REQUIRE(o.lowrank_rank == 0 || o.sketch != H2_SKETCH_KSUM,
+             "a low-rank term needs a dense, callback or H2-matvec sketch");
 }
 
 template <typename F>
@@ -1623,6 +1657,7 @@ h2_status h2_build_batched(const h2_tree *const *trees, int count, const int *ke
       H2_REQUIRE(kernel_ids[i] == kernel_ids[0], "instances must share one kernel type");
       H2_REQUIRE(tols[i] >= 0 && std::isfinite(tols[i]), "tol must be finite and >= 0");
     }
+    H2_REQUIRE(opts->lowrank_rank == 0 || count == 1, "a low-rank term needs a single instance");
     if (kernel_ids[0] == H2_K_H2SUM) {
       H2_REQUIRE(count == 1, "an H2 sum is built as a single instance");
       H2_REQUIRE(opts->operands && opts->n_operands >= 1, "an H2 sum needs operands");

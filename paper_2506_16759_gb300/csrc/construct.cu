@@ -265,12 +265,15 @@ __global__ void __launch_bounds__(kNT) k_bsr_pipe(BsrArgs a) {
 
 // ----------------------------------------------------------------------------
 // FP32 block-sparse row products with register tiles (blocks of at most 64 x
-// 64).  One CTA per row block; thread (rg, cg) owns rows 4rg..4rg+3 and
-// columns 4cg..4cg+3 of a DC-column chunk.  The partner blocks stream through
-// a two-slot ring (cp.async, 16-byte copies): the block itself (contiguous,
-// column-major) and its DC-column slice of the input rows, read from a
-// row-major copy of the input panel so that every row slice is contiguous.
-// Each block's product is summed plainly, the blocks with compensation.
+// 64).  One CTA per row block; thread (rg, cg) owns rows rg, rg+16, rg+32,
+// rg+48 (a warp's 16 row groups read 16 consecutive words of a block column:
+// no bank conflicts) and columns 4cg..4cg+3 of a DC-column chunk.  The partner
+// blocks stream through a two-slot ring (cp.async, 16-byte copies): the block
+// itself (contiguous, column-major) and its DC-column slice of the input rows,
+// read from a row-major copy of the input panel so that every row slice is
+// contiguous.  Rows at or past the block's height read other words of the
+// slot and are never stored, so the inner loop has no bounds tests.  Each
+// block's product is summed plainly, the blocks with compensation.
 // ----------------------------------------------------------------------------
 __device__ __forceinline__ void cp_async16z(void *smem, const void *gmem, bool valid) {
   unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -293,7 +296,9 @@ __global__ void __launch_bounds__(4 * DC) k_bsr_tile(BsrArgs a, const float *tin
   const int64_t e0 = a.ptr[tau], e1 = a.ptr[tau + 1];
   if (m == 0 || ce <= cb || e0 == e1) return;
   const int rg = threadIdx.x & 15, cg = threadIdx.x >> 4;
-  const int r0 = 4 * rg;
+  // input-slice copy: NT = 16 * (DC / 4), so thread t always copies chunk
+  // t % (DC / 4) of rows t / (DC / 4) + 16 q
+  const int cv = threadIdx.x % (DC / 4), cj0 = threadIdx.x / (DC / 4);
   const float *blocks = reinterpret_cast<const float *>(a.blocks);
   float *out = reinterpret_cast<float *>(a.out);
   const float sgn = (float)a.sign;
@@ -310,13 +315,11 @@ __global__ void __launch_bounds__(4 * DC) k_bsr_tile(BsrArgs a, const float *tin
         char *dst = reinterpret_cast<char *>(sB + slot * SLOT_B);
         const int n16 = (m * mb * 4 + 15) / 16;
         for (int u = threadIdx.x; u < n16; u += NT) cp_async16(dst + 16 * u, src + 16 * u);
-        const float *irow = tin + a.col_off[b] * ldt + c0;
-        float *di = sO + slot * SLOT_O;
-        for (int u = threadIdx.x; u < mb * (DC / 4); u += NT) {
-          const int j = u / (DC / 4), v = u % (DC / 4);
-          const bool ok = 4 * v < ncol;
-          cp_async16z(di + j * DC + 4 * v, ok ? irow + j * ldt + 4 * v : irow, ok);
-        }
+        const float *irow = tin + a.col_off[b] * ldt + c0 + 4 * cv;
+        float *di = sO + slot * SLOT_O + 4 * cv;
+        const bool ok = 4 * cv < ncol;
+        for (int j = cj0; j < mb; j += 16)
+          cp_async16z(di + j * DC, ok ? irow + j * ldt : irow, ok);
       }
       cp_async_commit();
     };
@@ -332,11 +335,12 @@ __global__ void __launch_bounds__(4 * DC) k_bsr_tile(BsrArgs a, const float *tin
       float part[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) part[q] = 0.f;
+      const float *Br = Bs + rg;
       for (int j = 0; j < mb; ++j) {
         const float4 o = *reinterpret_cast<const float4 *>(Os + j * DC);
         float bv[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) bv[i] = r0 + i < m ? Bs[j * m + r0 + i] : 0.f;
+        for (int i = 0; i < 4; ++i) bv[i] = Br[j * m + 16 * i];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           part[4 * i + 0] += bv[i] * o.x;
@@ -359,12 +363,12 @@ __global__ void __launch_bounds__(4 * DC) k_bsr_tile(BsrArgs a, const float *tin
     const int64_t orow = a.row_off[tau];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      if (r0 + i >= m) continue;
+      if (rg + 16 * i >= m) continue;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const int col = 4 * cg + c;
         if (col >= ncol) continue;
-        float *op = out + orow + r0 + i + (int64_t)(c0 + col) * a.ld_out;
+        float *op = out + orow + rg + 16 * i + (int64_t)(c0 + col) * a.ld_out;
         const float y = *op - cmp[4 * i + c];
         *op = acc[4 * i + c] + y;
       }

@@ -201,4 +201,20 @@ void h2sum_dense(bool fp64, int64_t nnz, const int32_t *erow, const int32_t *idx
                  const int64_t *doff, void *D, const double *const *Dop, const float *const *Dop32,
                  const int64_t *const *doff_op, int nops, cudaStream_t s);
 
+// ---- low-rank term U V^T of the operator (lowrank.cu)
+// Tree-order row-major copy out[p * r + k] = src[orig[p] + k * ld] (T by fp64).
+void lowrank_tree_rows(bool fp64, const double *src, int64_t ld, const int32_t *orig, int64_t n,
+                       int r, void *out, cudaStream_t s);
+// y(:, 0:nc) += U (V^T om(:, 0:nc)), all FP64 column-major in original order
+// (U, V with leading dimension ld).
+void lowrank_sample(const double *U, const double *V, int64_t ld, int64_t n, int r,
+                    const double *om, int64_t ldo, int nc, double *y, int64_t ldy,
+                    cudaStream_t s);
+// Every block e of the CSR (rows n_rows tasks) += U(rows) V(cols)^T, the rows
+// of a task being its points (row0) or its skeleton points (skel at krow).
+void lowrank_blocks(bool fp64, bool skel_rows, int n_rows, const int64_t *ptr, const int32_t *idx,
+                    const int64_t *off, const int32_t *rows_of, const int64_t *row0,
+                    const int64_t *krow, const int32_t *skel, const void *Ut, const void *Vt,
+                    int r, void *out, cudaStream_t s);
+
 }  // namespace h2

@@ -24,7 +24,10 @@ prebuilt for the same kernel (``paper_problem``):
 
 * ``exp3d``      exp(-r/0.2), no nugget;
 * ``helmholtz``  cos(3r)/r off the diagonal, 0 on it (the paper defines the
-                 operator for x != y only).
+                 operator for x != y only);
+* ``update``     the exp3d H2 matrix plus a symmetric rank-32 product U S U^T,
+                 recompressed into one H2 matrix (entries from the operand's
+                 representation plus the product's entries).
 
 Every workload uses 32 initial Gaussian samples, increments of 16 and at most
 256 samples.
@@ -154,6 +157,16 @@ def c5_instances(count: int = 64, seed: int = 5) -> list[Workload]:
     return out
 
 
+def low_rank_factors(n: int, r: int, seed: int, scale: float) -> tuple:
+    """Factors (U, V) of a symmetric rank-r product U V^T = U S U^T: U has
+    i.i.d. N(0, 1/n) entries, S = diag(s) with s_k ~ scale * N(0, 1); both
+    (n, r) FP64, column-major, original point order."""
+    rng = np.random.default_rng(seed)
+    U = rng.standard_normal((n, r)) / math.sqrt(n)
+    s = scale * rng.standard_normal(r)
+    return np.asfortranarray(U), np.asfortranarray(U * s[None, :])
+
+
 def paper_problem(name: str, n: int = 262144) -> Workload:
     """A Sec. V-A kernel problem at n points: tol 1e-6, leaf 64, eta 0.7; the
     black-box sampler is an H2 matrix of the same kernel prebuilt at
@@ -165,4 +178,11 @@ def paper_problem(name: str, n: int = 262144) -> Workload:
         return Workload("helmholtz", n, 3, K_HELMHOLTZ_IE, (3.0, 0.0), tol=1e-6,
                         sketch="h2matvec", point_seed=7, omega_seed=53,
                         extra={"operand_tol": 1e-7})
+    if name == "update":
+        # the covariance H2 of exp3d plus a symmetric rank-32 product whose
+        # weights are of the order of the matrix's largest entries times n
+        return Workload("update", n, 3, K_H2SUM, (), tol=1e-6, sketch="h2sum",
+                        point_seed=6, omega_seed=63,
+                        extra={"operands": [(K_EXP, (0.2, 0.0))], "operand_tol": 1e-7,
+                               "rank": 32, "lowrank_seed": 64, "lowrank_scale": 0.01 * n})
     raise KeyError(name)

@@ -395,3 +395,58 @@ def test_h2_matvec_sampler_matches_oracle(kernel, params):
         rel, y, _ = matvec_rel(h, ho, n, seed=5)
         assert rel <= bar
         assert np.linalg.norm(y - AG) <= 10 * tol * np.linalg.norm(AG)
+
+
+def test_low_rank_update_matches_oracle():
+    # Sec. V-A update problem: an H2 matrix (exp kernel, built at 1e-8) plus a
+    # symmetric rank-32 product, recompressed at 1e-6; samples from the
+    # operand's matvec plus U (V^T Omega), entries from the operand's
+    # representation plus U(I,:) V(J,:)^T
+    n, dim, leaf, eta, tol = 4096, 3, 32, 0.7, 1e-6
+    X = W.uniform_points(n, dim, 91)
+    kp = (W.K_EXP, (0.2, 0.0))
+    om_op, om = W.gaussian_omega(n, 256, 92), W.gaussian_omega(n, 256, 93)
+    U, V = W.low_rank_factors(n, 32, 94, 0.01 * n)
+    t = O.build_cluster_tree(X, leaf)
+    lists = O.dual_traversal(t, eta)
+    op_o = O.build_h2(t, lists, *kp, 1e-8, om_op, O.ksum_sampler(X, *kp, 1024))
+    entries, sampler = O.low_rank_update(t, *O.h2_sum_operator([op_o]), U, V)
+    ho = O.build_h2(t, lists, entries, None, tol, om, sampler)
+    tree = api.ClusterTree(gpu(X), leaf, eta)
+    op_g = api.H2Matrix.build(tree, *kp, 1e-8, omega=gpu(om_op))
+    G = W.gaussian_probe(n, 4, 5)
+    FG = O.ksum_rows(X, *kp, G, np.arange(n)) + U @ (V.T @ G)
+    for prec, bar in (("fp64", 1e-10), ("mixed", 1e-5)):
+        h = api.H2Matrix.build(tree, "h2sum", (), tol, omega=gpu(om), sketch="h2sum",
+                               operands=[op_g], prec=prec, lowrank=(gpu(U), gpu(V)))
+        if prec == "fp64":
+            check_same_skeletons(h, t, ho)
+        rel, y, _ = matvec_rel(h, ho, n, seed=5)
+        assert rel <= bar
+        assert np.linalg.norm(y - FG) <= 10 * tol * np.linalg.norm(FG)
+
+
+def test_low_rank_update_of_a_kernel_with_dense_sketch():
+    # the product added to a kernel matrix: entries evaluated directly plus
+    # the product's, samples from the dense kernel matrix plus U (V^T Omega)
+    n, dim, leaf, eta, tol = 2048, 2, 32, 0.7, 1e-6
+    X = W.uniform_points(n, dim, 95)
+    kp = (W.K_EXP, (0.2, 1e-4))
+    om = W.gaussian_omega(n, 256, 96)
+    U, V = W.low_rank_factors(n, 16, 97, 0.01 * n)
+    A = O.dense_matrix(X, *kp)
+    t = O.build_cluster_tree(X, leaf)
+    lists = O.dual_traversal(t, eta)
+    entries, sampler = O.low_rank_update(t, kp, O.dense_sampler(A), U, V)
+    ho = O.build_h2(t, lists, entries, None, tol, om, sampler)
+    tree = api.ClusterTree(gpu(X), leaf, eta)
+    F = A + U @ V.T
+    G = W.gaussian_probe(n, 4, 5)
+    for prec, bar in (("fp64", 1e-10), ("mixed", 1e-5)):
+        h = api.H2Matrix.build(tree, *kp, tol, omega=gpu(om), sketch="dense", dense_a=gpu(A),
+                               prec=prec, lowrank=(gpu(U), gpu(V)))
+        if prec == "fp64":
+            check_same_skeletons(h, t, ho)
+        rel, y, _ = matvec_rel(h, ho, n, seed=5)
+        assert rel <= bar
+        assert np.linalg.norm(y - F @ G) <= 10 * tol * np.linalg.norm(F @ G)

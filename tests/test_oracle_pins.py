@@ -504,3 +504,35 @@ def test_helmholtz_build_with_h2_matvec_sampler():
                    O.h2_sampler(pre))
     assert h.converged and h.l_top >= 2
     assert O.dense_rel_error(h, A) <= 10 * tol
+
+
+def test_low_rank_update_operator():
+    # Sec. V-A update problem: an H2 matrix plus a symmetric rank-r product.
+    # Entries and samples are those of the exact dense sum, and a target
+    # built from them meets the tolerance against it (and not against the
+    # operand alone: the product is not negligible).
+    n = 1024
+    X = W.uniform_points(n, 2, 81)
+    t = O.build_cluster_tree(X, 16)
+    lists = O.dual_traversal(t, 0.7)
+    kp = (O.K_EXP, (0.2, 0.0))
+    A = O.dense_matrix(X, *kp)
+    op = O.build_h2(t, lists, *kp, 1e-8, W.gaussian_omega(n, 256, 82), O.dense_sampler(A))
+    U, V = W.low_rank_factors(n, 8, 83, 0.01 * n)
+    assert np.allclose(U @ V.T, V @ U.T, rtol=0, atol=1e-14 * n)
+    full = A + U @ V.T
+    base_entries, base_sampler = O.h2_sum_operator([op])
+    entries, sampler = O.low_rank_update(t, base_entries, base_sampler, U, V)
+    Ft = full[np.ix_(t.perm, t.perm)]
+    idx = np.arange(n)
+    assert np.linalg.norm(entries(idx, idx) - Ft) <= 1e-7 * np.linalg.norm(Ft)
+    G = W.gaussian_probe(n, 3, 0)
+    assert np.linalg.norm(sampler(G) - full @ G) <= 1e-7 * np.linalg.norm(full @ G)
+    h = O.build_h2(t, lists, entries, None, 1e-6, W.gaussian_omega(n, 256, 84), sampler)
+    assert O.dense_rel_error(h, full) <= 10 * 1e-6
+    assert O.dense_rel_error(h, A) > 1e3 * 1e-6
+    # the same update of the kernel itself (entries evaluated, dense samples)
+    entries_k, sampler_k = O.low_rank_update(t, kp, O.dense_sampler(A), U, V)
+    assert np.linalg.norm(entries_k(idx, idx) - Ft) <= 1e-13 * np.linalg.norm(Ft)
+    hk = O.build_h2(t, lists, entries_k, None, 1e-6, W.gaussian_omega(n, 256, 84), sampler_k)
+    assert O.dense_rel_error(hk, full) <= 10 * 1e-6
