@@ -100,6 +100,150 @@ __global__ void k_b_h2sum(SumCouplingArgs a, int max_kop) {
   (void)max_kop;
 }
 
+// Mixed-precision couplings of an H2 sum (target stored in FP32): FP32
+// products on the CUDA cores, every 32-term chunk summed plainly and the
+// chunks with compensation.  One CTA of 256 threads per far block (s, t);
+// per pass over 64 target columns b0 .. b0+63:
+//   T = B_op(s,t) G_op,t(b0.., :)^T  (kos x 64), in row passes of 128, into
+//       shared memory (rows padded to 68 floats: aligned float4 reads);
+//   out(r0.., b0..) += G_op,s(r0.., :) T, in row passes of 64.
+// Operand ranks up to 256; target ranks of any size.
+constexpr int kB32MaxKop = 256, kB32Ld = 68;
+constexpr size_t kB32Smem =
+    sizeof(float) * ((size_t)kB32MaxKop * kB32Ld + 32 * 128 + 32 * 64 + 32 * 64);
+
+struct Kahan32 {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+};
+
+__global__ void __launch_bounds__(256, 2) k_b_h2sum32(SumCouplingArgs a) {
+  extern __shared__ __align__(16) float b32_smem[];
+  float *sT = b32_smem;                       // [kB32MaxKop][kB32Ld]
+  float *sB = sT + kB32MaxKop * kB32Ld;       // [32][128]  B_op(p0 + pp, c0 + c)
+  float *sG = sB + 32 * 128;                  // [32][64]   G_t(b0 + b, c0 + c)
+  float *sS = sG + 32 * 64;                   // [32][64]   G_s(r0 + r, c0 + c)
+  const int64_t e = blockIdx.x;
+  const int s = a.erow[e], tt = a.idx[e];
+  const int ks = a.t.k[s], kt = a.t.k[tt];
+  if (ks == 0 || kt == 0) return;
+  float *out = reinterpret_cast<float *>(a.B) + a.boff[e];
+  const int t = threadIdx.x;
+  for (int q = t; q < ks * kt; q += blockDim.x) out[q] = 0.f;
+  const int tp = t & 31, tb = t >> 5;     // step 1: rows p0 + tp + 32 i, columns 8 tb + j
+  const int tb2 = t & 15, tr = t >> 4;    // step 2: rows r0 + tr + 16 i, columns 4 tb2 + j
+  for (int o = 0; o < a.nops; ++o) {
+    const SumOperand &op = a.ops[o];
+    const int kos = op.k[s], kot = op.k[tt];
+    if (kos == 0 || kot == 0) continue;
+    const double *Gs = op.G + op.goff[s];
+    const double *Gt = op.G + op.goff[tt];
+    const double *Bo = op.B ? op.B + op.boff[e] : nullptr;
+    const float *Bo32 = op.B32 ? op.B32 + op.boff[e] : nullptr;
+    for (int b0 = 0; b0 < kt; b0 += 64) {
+      // ---- T = B_op G_t(b0.., :)^T
+      for (int p0 = 0; p0 < kos; p0 += 128) {
+        Kahan32 acc[4][8];
+        for (int c0 = 0; c0 < kot; c0 += 32) {
+          __syncthreads();
+          for (int u = t; u < 32 * 128; u += 256) {
+            const int c = u >> 7, pp = u & 127;
+            const int p = p0 + pp, cc = c0 + c;
+            float v = 0.f;
+            if (p < kos && cc < kot) {
+              const int64_t i = p + (int64_t)cc * kos;
+              v = Bo ? (float)Bo[i] : Bo32[i];
+            }
+            sB[u] = v;
+          }
+          for (int u = t; u < 32 * 64; u += 256) {
+            const int c = u >> 6, b = b0 + (u & 63);
+            sG[u] = (b < kt && c0 + c < kot) ? (float)Gt[b + (int64_t)(c0 + c) * kt] : 0.f;
+          }
+          __syncthreads();
+          float part[4][8];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) part[i][j] = 0.f;
+#pragma unroll 4
+          for (int c = 0; c < 32; ++c) {
+            const float4 g0 = *reinterpret_cast<const float4 *>(sG + c * 64 + 8 * tb);
+            const float4 g1 = *reinterpret_cast<const float4 *>(sG + c * 64 + 8 * tb + 4);
+            const float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const float bv = sB[c * 128 + tp + 32 * i];
+#pragma unroll
+              for (int j = 0; j < 8; ++j) part[i][j] = fmaf(bv, gv[j], part[i][j]);
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j].add(part[i][j]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int p = p0 + tp + 32 * i;
+          if (p < kos) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) sT[p * kB32Ld + 8 * tb + j] = acc[i][j].s;
+          }
+        }
+      }
+      // ---- out(r0.., b0..) += G_s(r0.., :) T
+      for (int r0 = 0; r0 < ks; r0 += 64) {
+        Kahan32 acc2[4][4];
+        for (int c0 = 0; c0 < kos; c0 += 32) {
+          __syncthreads();
+          for (int u = t; u < 32 * 64; u += 256) {
+            const int c = u >> 6, r = r0 + (u & 63);
+            sS[u] = (r < ks && c0 + c < kos) ? (float)Gs[r + (int64_t)(c0 + c) * ks] : 0.f;
+          }
+          __syncthreads();
+          float part[4][4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) part[i][j] = 0.f;
+          const int cn = min(32, kos - c0);
+          for (int c = 0; c < cn; ++c) {
+            const float4 tv = *reinterpret_cast<const float4 *>(sT + (c0 + c) * kB32Ld + 4 * tb2);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const float gv = sS[c * 64 + tr + 16 * i];
+              part[i][0] = fmaf(gv, tv.x, part[i][0]);
+              part[i][1] = fmaf(gv, tv.y, part[i][1]);
+              part[i][2] = fmaf(gv, tv.z, part[i][2]);
+              part[i][3] = fmaf(gv, tv.w, part[i][3]);
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc2[i][j].add(part[i][j]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int r = r0 + tr + 16 * i;
+          if (r >= ks) continue;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int b = b0 + 4 * tb2 + j;
+            if (b < kt) out[r + (int64_t)b * ks] += acc2[i][j].s;
+          }
+        }
+      }
+    }
+  }
+}
+
 template <typename T>
 __global__ void k_d_h2sum(int64_t nnz, const int32_t *erow, const int32_t *idx, const int32_t *m,
                           const int64_t *doff, T *D, const double *const *Dop,
@@ -141,7 +285,11 @@ void h2sum_couplings(bool fp64, const SumCouplingArgs &a, int max_kop, int max_k
   H2_REQUIRE(a.nnz < (1ll << 31), "too many coupling blocks");
   const size_t bytes = sizeof(double) * (size_t)std::max(max_kop, 1) * std::max(max_kt, 1);
   H2_REQUIRE(bytes <= 200 * 1024, "operand ranks too large for the H2-sum coupling kernel");
-  if (fp64) {
+  if (!fp64 && max_kop <= kB32MaxKop) {
+    H2_CUDA(cudaFuncSetAttribute(k_b_h2sum32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kB32Smem));
+    k_b_h2sum32<<<(int)a.nnz, 256, kB32Smem, s>>>(a);
+  } else if (fp64) {
     auto kern = k_b_h2sum<double>;
     if (bytes > 48 * 1024)
       H2_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
