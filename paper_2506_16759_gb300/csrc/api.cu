@@ -1425,9 +1425,10 @@ void matvec_impl(const h2_matrix *H, const double *x, double *y, int nrhs, cudaS
       const LevelData &L = H->lv[l];
       const void *E = (const void *)L.E.p;
       if (l > 1)
-        basis_n_apply(f64, L.dev(), E, yh[l].p, L.K, yh[l - 1].p, H->lv[l - 1].K, cols, s);
+        basis_n_apply(f64, L.dev(), E, yh[l].p, L.K, yh[l - 1].p, H->lv[l - 1].K, cols, L.max_m,
+                      L.max_k, s);
       else
-        basis_n_apply(f64, L.dev(), E, yh[1].p, L.K, yt.p, N, cols, s);
+        basis_n_apply(f64, L.dev(), E, yh[1].p, L.K, yt.p, N, cols, L.max_m, L.max_k, s);
     }
   }
   permute_out(f64, yt.p, N, H->orig_of_pos.p, N, nrhs, y, N, s);

@@ -228,6 +228,7 @@ __global__ void __launch_bounds__(kNT) k_bsr_pipe(BsrArgs a) {
         for (int c = 0; c < CG; ++c) ov[c] = si[j * DCP + c];
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
+          if (64 * r >= m) break;   // row groups past the block (uniform over the CTA)
           const int i = i0 + 64 * r;
           const T bv = i < m ? sb[j * m + i] : T(0);
 #pragma unroll
@@ -727,6 +728,46 @@ __global__ void k_basis_n(TasksDev t, const TE *E, const T *in, int64_t ld_in, T
   }
 }
 
+// FP32 downsweep (mixed precision): out(row+i, c) += sum_a E(i,a) in(krow+a, c)
+// with the cluster's basis (converted to FP32, column a contiguous) and 64
+// columns of its skeleton-row inputs staged in shared memory.
+__global__ void __launch_bounds__(256) k_basis_n32(TasksDev t, const double *E, const float *in,
+                                                   int64_t ld_in, float *out, int64_t ld_out,
+                                                   InstCols cols) {
+  extern __shared__ __align__(16) float sm[];
+  const int tau = blockIdx.x;
+  const int inst = t.inst[tau];
+  const int k = t.k[tau], m = t.m[tau];
+  const int cb = cols.cb[inst], ce = cols.ce[inst];
+  if (k == 0 || ce <= cb) return;
+  const int64_t row = t.row[tau], kr = t.krow[tau];
+  const double *Et = E + t.eoff[tau];
+  float *sE = sm;                          // [k][m]: E(i, a) at a * m + i
+  float *sY = sm + (size_t)k * m;          // [64][k]: in(krow + a, c) at c * k + a
+  for (int q = threadIdx.x; q < m * k; q += blockDim.x) sE[q] = (float)Et[q];
+  for (int c0 = cb; c0 < ce; c0 += 64) {
+    const int nc = min(64, ce - c0);
+    __syncthreads();
+    for (int q = threadIdx.x; q < k * nc; q += blockDim.x) {
+      const int a = q % k, c = q / k;
+      sY[c * k + a] = in[kr + a + (int64_t)(c0 + c) * ld_in];
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < m * nc; q += blockDim.x) {
+      const int i = q % m, c = q / m;
+      const float *yc = sY + c * k;
+      float s0 = 0.f, s1 = 0.f;
+      int a = 0;
+      for (; a + 1 < k; a += 2) {
+        s0 = fmaf(sE[a * m + i], yc[a], s0);
+        s1 = fmaf(sE[(a + 1) * m + i], yc[a + 1], s1);
+      }
+      if (a < k) s0 = fmaf(sE[a * m + i], yc[a], s0);
+      out[row + i + (int64_t)(c0 + c) * ld_out] += s0 + s1;
+    }
+  }
+}
+
 // One CTA per row task: its points (the leaf's, or its skeleton points) are
 // staged once, then every partner block of its CSR row is evaluated from a
 // staged copy of the partner's points; the next partner's points are loaded
@@ -1033,12 +1074,18 @@ void basis_t_apply(bool fp64, const TasksDev &t, const void *E, const void *in, 
 }
 
 void basis_n_apply(bool fp64, const TasksDev &t, const void *E, const void *in, int64_t ld_in,
-                   void *out, int64_t ld_out, InstCols cols, cudaStream_t s) {
+                   void *out, int64_t ld_out, InstCols cols, int max_m, int max_k,
+                   cudaStream_t s) {
   if (t.n == 0) return;
+  const size_t bytes = sizeof(float) * (size_t)(max_k * max_m + 64 * max_k);
   if (fp64)
     k_basis_n<double, double><<<t.n, 256, 0, s>>>(t, (const double *)E, (const double *)in,
                                                   ld_in, (double *)out, ld_out, cols);
-  else
+  else if (bytes <= 200 * 1024) {
+    set_smem(k_basis_n32, bytes);
+    k_basis_n32<<<t.n, 256, bytes, s>>>(t, (const double *)E, (const float *)in, ld_in,
+                                        (float *)out, ld_out, cols);
+  } else
     k_basis_n<float, double><<<t.n, 256, 0, s>>>(t, (const double *)E, (const float *)in, ld_in,
                                                 (float *)out, ld_out, cols);
   count_launch();

@@ -124,7 +124,8 @@ void basis_t_apply(bool fp64, const TasksDev &t, const void *E, const void *in, 
                    int max_k, cudaStream_t s);
 // out(row+i, c) += sum_a E(i,a) in(krow+a, c)      (E products: downsweep)
 void basis_n_apply(bool fp64, const TasksDev &t, const void *E, const void *in, int64_t ld_in,
-                   void *out, int64_t ld_out, InstCols cols, cudaStream_t s);
+                   void *out, int64_t ld_out, InstCols cols, int max_m, int max_k,
+                   cudaStream_t s);
 
 // Couplings B(e) = K(Itil_row, Itil_col) for each far entry e.
 struct CouplingArgs {
