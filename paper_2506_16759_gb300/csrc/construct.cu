@@ -224,8 +224,17 @@ __global__ void __launch_bounds__(kNT) k_bsr_pipe(BsrArgs a) {
         for (int c = 0; c < CG; ++c) part[r][c] = T(0);
       for (int j = 0; j < nj; ++j) {
         T ov[CG];
+        if constexpr (sizeof(T) == 4 && CG % 4 == 0) {
+          // 16-byte rows: DCP and the group offset are multiples of 4 floats
 #pragma unroll
-        for (int c = 0; c < CG; ++c) ov[c] = si[j * DCP + c];
+          for (int c = 0; c < CG; c += 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(si + j * DCP + c);
+            ov[c] = v.x; ov[c + 1] = v.y; ov[c + 2] = v.z; ov[c + 3] = v.w;
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < CG; ++c) ov[c] = si[j * DCP + c];
+        }
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
           if (64 * r >= m) break;   // row groups past the block (uniform over the CTA)
@@ -481,7 +490,9 @@ template <typename T, int NT>
 __global__ void __launch_bounds__(NT) k_row_id(IdArgs a) {
   // One thread per column (a point of the cluster) of A = Y_loc^T / sqrt(d),
   // d x m, stored row-major in shared memory; each column's trailing norm for
-  // the next step is recomputed while the column is updated.
+  // the next step is recomputed while the column is updated (FP64 panels) or
+  // downdated (FP32 panels).
+  constexpr bool DOWNDATE = sizeof(T) == 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[33];
   __shared__ double redv[33];
@@ -562,7 +573,15 @@ __global__ void __launch_bounds__(NT) k_row_id(IdArgs a) {
       }
       for (; r < d; ++r) w0 += A[(int64_t)r * m + k] * A[(int64_t)r * m + c];
       const double w = ((w0 + w1) + (w2 + w3)) * beta;
-      A[(int64_t)k * m + c] -= w * A[(int64_t)k * m + k];
+      const double rkc = A[(int64_t)k * m + c] - w * A[(int64_t)k * m + k];
+      A[(int64_t)k * m + c] = rkc;
+      // FP32 panels (mixed precision): the trailing norm is downdated,
+      // |A(k+1:, c)|^2 = |A(k:, c)|^2 - R(k, c)^2 (the reflection keeps the
+      // norm), and recomputed only after a cancellation of four digits; FP64
+      // panels recompute it every step, as the FP64 parity of the skeletons
+      // with the reference construction requires
+      const double down = nrm2[c] - rkc * rkc;
+      const bool recompute = !DOWNDATE || !(down > 1e-4 * nrm2[c]);
       double s0 = 0.0, s1 = 0.0;
       int q = k + 1;
       for (; q + 1 < d; q += 2) {
@@ -570,15 +589,17 @@ __global__ void __launch_bounds__(NT) k_row_id(IdArgs a) {
         const double x1 = A[(int64_t)(q + 1) * m + c] - w * A[(int64_t)(q + 1) * m + k];
         A[(int64_t)q * m + c] = x0;
         A[(int64_t)(q + 1) * m + c] = x1;
-        s0 += x0 * x0;
-        s1 += x1 * x1;
+        if (recompute) {
+          s0 += x0 * x0;
+          s1 += x1 * x1;
+        }
       }
       if (q < d) {
         const double x0 = A[(int64_t)q * m + c] - w * A[(int64_t)q * m + k];
         A[(int64_t)q * m + c] = x0;
-        s0 += x0 * x0;
+        if (recompute) s0 += x0 * x0;
       }
-      nrm2[c] = s0 + s1;
+      nrm2[c] = recompute ? s0 + s1 : down;
     }
     __syncthreads();
     if (threadIdx.x == 0) A[(int64_t)k * m + k] = alpha;
@@ -976,6 +997,8 @@ void bsr_apply(bool fp64, const BsrArgs &a, int max_m, int max_cols, cudaStream_
   } else if (max_m <= 64) {
     if (fp64) narrow ? launch_bsr<double, 16, 1>(a, s) : launch_bsr<double, 32, 1>(a, s);
     else narrow ? launch_bsr<float, 16, 1>(a, s) : launch_bsr<float, 32, 1>(a, s);
+  } else if (max_m <= 128 && !fp64) {
+    narrow ? launch_bsr<float, 16, 2>(a, s) : launch_bsr<float, 32, 2>(a, s);
   } else {
     if (fp64) narrow ? launch_bsr<double, 16, 4>(a, s) : launch_bsr<double, 32, 4>(a, s);
     else narrow ? launch_bsr<float, 16, 4>(a, s) : launch_bsr<float, 32, 4>(a, s);

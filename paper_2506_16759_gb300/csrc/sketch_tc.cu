@@ -683,7 +683,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ksum_tc(TcArgs a) {
       if (lane == 0) mbar_arrive(saddr(&accempty[ac]));
 #pragma unroll
       for (int c = 0; c < CPT; ++c) grp[c] += fmaf(w[c], SCALE2, v[c]);
-      if ((j & 3) == 3) fold();
+      if ((j & 7) == 7) fold();   // plain sums over 8 steps, compensated across
     };
     int k = 0;
     for (;; ++k) {
