@@ -14,6 +14,7 @@ LIB_PATH = os.environ.get("H2GB_LIB") or os.path.join(os.path.dirname(os.path.ab
                                                       "libh2gb.so")
 
 H2_OK = 0
+H2_ERR_ARG = -1
 H2_ERR_NOT_CONVERGED = -4
 STATUS_NAMES = {0: "H2_OK", -1: "H2_ERR_ARG", -2: "H2_ERR_CUDA", -3: "H2_ERR_OOM",
                 -4: "H2_ERR_NOT_CONVERGED", -5: "H2_ERR_TIMEOUT", -6: "H2_ERR_SAMPLER",

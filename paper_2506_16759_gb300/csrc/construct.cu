@@ -346,6 +346,7 @@ __global__ void __launch_bounds__(4 * DC) k_bsr_tile(BsrArgs a, const float *tin
 #pragma unroll
       for (int q = 0; q < 16; ++q) part[q] = 0.f;
       const float *Br = Bs + rg;
+#pragma unroll 2
       for (int j = 0; j < mb; ++j) {
         const float4 o = *reinterpret_cast<const float4 *>(Os + j * DC);
         float bv[4];

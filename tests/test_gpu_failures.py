@@ -74,3 +74,26 @@ def test_non_finite_points_rejected():
     with pytest.raises(_lib.H2Error) as e:
         api.ClusterTree(gpu(X), 32, 0.7)
     assert e.value.status == -7
+
+
+def test_low_rank_term_argument_errors():
+    # a low-rank term needs a sketch in original order, a rank of at most
+    # 64 and both factors; each violation is an H2_ERR_ARG, not a fault
+    n = 1024
+    X = W.uniform_points(n, 2, 13)
+    tree = api.ClusterTree(gpu(X), 32, 0.7)
+    U, V = (gpu(a) for a in W.low_rank_factors(n, 4, 14, 1.0))
+    with pytest.raises(_lib.H2Error) as e:
+        api.H2Matrix.build(tree, "exp", (0.2, 1e-4), 1e-6, sketch="ksum", lowrank=(U, V))
+    assert e.value.status == _lib.H2_ERR_ARG
+    from oracle import h2_oracle as O
+    A = gpu(O.dense_matrix(X, O.K_EXP, (0.2, 1e-4)))
+    Ub, Vb = (gpu(a) for a in W.low_rank_factors(n, 65, 14, 1.0))
+    with pytest.raises(_lib.H2Error) as e:
+        api.H2Matrix.build(tree, "exp", (0.2, 1e-4), 1e-6, sketch="dense", dense_a=A,
+                           lowrank=(Ub, Vb))
+    assert e.value.status == _lib.H2_ERR_ARG
+    # the context still works afterwards
+    h = api.H2Matrix.build(tree, "exp", (0.2, 1e-4), 1e-6, sketch="dense", dense_a=A,
+                           lowrank=(U, V))
+    assert h.converged
