@@ -159,11 +159,13 @@ __global__ void __launch_bounds__(kNT) k_bsr_pipe(BsrArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *sBlk = reinterpret_cast<T *>(smem_raw);               // [kStages][SLOT]
   T *sIn = sBlk + kStages * SLOT;                          // [kStages][JMAX][DC + 4]
-  const int tau = blockIdx.x;
+  // a.seg CTAs share a row task, each a contiguous part of its CSR row
+  const int tau = blockIdx.x / a.seg, part_id = blockIdx.x % a.seg;
   const int m = a.row_m[tau];
   const int inst = a.row_inst[tau];
   const int cb = a.cols.cb[inst], ce = a.cols.ce[inst];
-  const int64_t e0 = a.ptr[tau], e1 = a.ptr[tau + 1];
+  const int64_t r0 = a.ptr[tau], rn = a.ptr[tau + 1] - r0;
+  const int64_t e0 = r0 + rn * part_id / a.seg, e1 = r0 + rn * (part_id + 1) / a.seg;
   if (m == 0 || ce <= cb || e0 == e1) return;
   // block columns per chunk: fits a slot, multiple of 4 (16-byte aligned starts)
   int jc = SLOT / m;
@@ -264,9 +266,13 @@ __global__ void __launch_bounds__(kNT) k_bsr_pipe(BsrArgs a) {
         const int col = g * CG + c;
         if (col < ncol) {
           T *op = out + orow + i + (int64_t)(c0 + col) * a.ld_out;
-          Acc<T> t = acc[r][c];
-          t.add(*op);
-          *op = t.value();
+          if (a.seg > 1) {
+            atomicAdd(op, acc[r][c].value());
+          } else {
+            Acc<T> t = acc[r][c];
+            t.add(*op);
+            *op = t.value();
+          }
         }
       }
     }
@@ -299,11 +305,13 @@ __global__ void __launch_bounds__(4 * DC) k_bsr_tile(BsrArgs a, const float *tin
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float *sB = reinterpret_cast<float *>(smem_raw);   // [2][SLOT_B]
   float *sO = sB + 2 * SLOT_B;                         // [2][64][DC]
-  const int tau = blockIdx.x;
+  // a.seg CTAs share a row task, each a contiguous part of its CSR row
+  const int tau = blockIdx.x / a.seg, part_id = blockIdx.x % a.seg;
   const int m = a.row_m[tau];
   const int inst = a.row_inst[tau];
   const int cb = a.cols.cb[inst], ce = a.cols.ce[inst];
-  const int64_t e0 = a.ptr[tau], e1 = a.ptr[tau + 1];
+  const int64_t r0 = a.ptr[tau], rn = a.ptr[tau + 1] - r0;
+  const int64_t e0 = r0 + rn * part_id / a.seg, e1 = r0 + rn * (part_id + 1) / a.seg;
   if (m == 0 || ce <= cb || e0 == e1) return;
   const int rg = threadIdx.x & 15, cg = threadIdx.x >> 4;
   // input-slice copy: NT = 16 * (DC / 4), so thread t always copies chunk
@@ -380,8 +388,12 @@ __global__ void __launch_bounds__(4 * DC) k_bsr_tile(BsrArgs a, const float *tin
         const int col = 4 * cg + c;
         if (col >= ncol) continue;
         float *op = out + orow + rg + 16 * i + (int64_t)(c0 + col) * a.ld_out;
-        const float y = *op - cmp[4 * i + c];
-        *op = acc[4 * i + c] + y;
+        if (a.seg > 1) {
+          atomicAdd(op, acc[4 * i + c] - cmp[4 * i + c]);
+        } else {
+          const float y = *op - cmp[4 * i + c];
+          *op = acc[4 * i + c] + y;
+        }
       }
     }
   }
@@ -582,25 +594,32 @@ __global__ void __launch_bounds__(NT) k_row_id(IdArgs a) {
       // panels recompute it every step, as the FP64 parity of the skeletons
       // with the reference construction requires
       const double down = nrm2[c] - rkc * rkc;
-      const bool recompute = !DOWNDATE || !(down > 1e-4 * nrm2[c]);
-      double s0 = 0.0, s1 = 0.0;
-      int q = k + 1;
-      for (; q + 1 < d; q += 2) {
-        const double x0 = A[(int64_t)q * m + c] - w * A[(int64_t)q * m + k];
-        const double x1 = A[(int64_t)(q + 1) * m + c] - w * A[(int64_t)(q + 1) * m + k];
-        A[(int64_t)q * m + c] = x0;
-        A[(int64_t)(q + 1) * m + c] = x1;
-        if (recompute) {
+      if (DOWNDATE && down > 1e-4 * nrm2[c]) {
+        int q = k + 1;
+        for (; q + 1 < d; q += 2) {
+          A[(int64_t)q * m + c] -= w * A[(int64_t)q * m + k];
+          A[(int64_t)(q + 1) * m + c] -= w * A[(int64_t)(q + 1) * m + k];
+        }
+        if (q < d) A[(int64_t)q * m + c] -= w * A[(int64_t)q * m + k];
+        nrm2[c] = down;
+      } else {
+        double s0 = 0.0, s1 = 0.0;
+        int q = k + 1;
+        for (; q + 1 < d; q += 2) {
+          const double x0 = A[(int64_t)q * m + c] - w * A[(int64_t)q * m + k];
+          const double x1 = A[(int64_t)(q + 1) * m + c] - w * A[(int64_t)(q + 1) * m + k];
+          A[(int64_t)q * m + c] = x0;
+          A[(int64_t)(q + 1) * m + c] = x1;
           s0 += x0 * x0;
           s1 += x1 * x1;
         }
+        if (q < d) {
+          const double x0 = A[(int64_t)q * m + c] - w * A[(int64_t)q * m + k];
+          A[(int64_t)q * m + c] = x0;
+          s0 += x0 * x0;
+        }
+        nrm2[c] = s0 + s1;
       }
-      if (q < d) {
-        const double x0 = A[(int64_t)q * m + c] - w * A[(int64_t)q * m + k];
-        A[(int64_t)q * m + c] = x0;
-        if (recompute) s0 += x0 * x0;
-      }
-      nrm2[c] = recompute ? s0 + s1 : down;
     }
     __syncthreads();
     if (threadIdx.x == 0) A[(int64_t)k * m + k] = alpha;
@@ -958,7 +977,7 @@ void launch_bsr(const BsrArgs &a, cudaStream_t s) {
   size_t bytes = sizeof(T) * ((size_t)kStages * SLOT + (size_t)kStages * 64 * (DC + 4));
   auto kern = k_bsr_pipe<T, DC, RPT>;
   set_smem(kern, bytes);
-  kern<<<a.n_rows, kNT, bytes, s>>>(a);
+  kern<<<a.n_rows * a.seg, kNT, bytes, s>>>(a);
   count_launch();
   H2_CHECK_LAUNCH();
 }
@@ -968,14 +987,19 @@ void launch_bsr_tile(const BsrArgs &a, const float *tin, int64_t ldt, cudaStream
   const size_t bytes = sizeof(float) * 2 * (64 * 64 + 64 * DC);
   auto kern = k_bsr_tile<DC>;
   set_smem(kern, bytes);
-  kern<<<a.n_rows, 4 * DC, bytes, s>>>(a, tin, ldt);
+  kern<<<a.n_rows * a.seg, 4 * DC, bytes, s>>>(a, tin, ldt);
   count_launch();
   H2_CHECK_LAUNCH();
 }
 
-void bsr_apply(bool fp64, const BsrArgs &a, int max_m, int max_cols, cudaStream_t s) {
-  if (a.n_rows == 0 || max_cols <= 0) return;
+void bsr_apply(bool fp64, const BsrArgs &a_in, int max_m, int max_cols, cudaStream_t s) {
+  if (a_in.n_rows == 0 || max_cols <= 0) return;
   H2_REQUIRE(max_m <= kMaxRows, "block rows above 256 are not supported");
+  // Levels with few row tasks split each CSR row over several CTAs (FP32:
+  // their partial sums meet in atomic adds; FP64 keeps one CTA per row so
+  // that its sums stay in a fixed order)
+  BsrArgs a = a_in;
+  a.seg = fp64 ? 1 : std::max(1, std::min(16, 4 * device_sm_count() / a.n_rows));
   if (!fp64 && max_m <= 64 && a.col_hi > 0 && a.in_rows > 0) {
     // register-tiled path on a row-major copy of the input columns [0, col_hi)
     const int64_t ldt = (a.col_hi + 3) / 4 * 4;

@@ -47,6 +47,7 @@ struct BsrArgs {
   InstCols cols;
   int64_t in_rows;          // rows of the input panel (FP32 tiled path)
   int col_hi;               // max over instances of ce (0: use the row-block kernel)
+  int seg = 1;              // CTAs per row task (set by bsr_apply; > 1: atomic adds)
 };
 // max_cols: the widest per-instance column range of this call.
 void bsr_apply(bool fp64, const BsrArgs &a, int max_m, int max_cols, cudaStream_t s);

@@ -450,3 +450,37 @@ def test_low_rank_update_of_a_kernel_with_dense_sketch():
         rel, y, _ = matvec_rel(h, ho, n, seed=5)
         assert rel <= bar
         assert np.linalg.norm(y - F @ G) <= 10 * tol * np.linalg.norm(F @ G)
+
+
+@pytest.mark.parametrize("name,prec,d0,d_inc", [("c2", "mixed", 80, 32), ("c2", "fp64", 32, 16),
+                                                ("c3", "mixed", 64, 32)])
+def test_full_size_build_sampled_rows(name, prec, d0, d_inc):
+    # the full-size workloads in the bench's launch configuration: rows of
+    # the H2 matvec, sampled, against the oracle's direct kernel sums
+    w = W.config(name)
+    X = w.points()
+    tree = api.ClusterTree(gpu(X), w.leaf_size, w.eta)
+    h = api.H2Matrix.build(tree, w.kernel, w.params, w.tol, prec=prec, seed=5, d0=d0, d_inc=d_inc)
+    assert h.converged
+    G = W.gaussian_probe(w.n, 8, 3)
+    rows = np.random.default_rng(2).integers(0, w.n, 64)
+    y = h.matvec(gpu(G)).cpu().numpy()[rows]
+    want = O.ksum_rows(X, w.kernel, w.params, G, rows)
+    assert np.linalg.norm(y - want) <= 10 * w.tol * np.linalg.norm(want)
+
+
+def test_full_size_helmholtz_with_h2_matvec_sampler():
+    # the paper's IE problem at N = 2^18 sketched through a prebuilt H2 matvec
+    w = W.paper_problem("helmholtz")
+    X = w.points()
+    tree = api.ClusterTree(gpu(X), w.leaf_size, w.eta)
+    pre = api.H2Matrix.build(tree, w.kernel, w.params, w.extra["operand_tol"], prec="mixed",
+                             seed=1)
+    h = api.H2Matrix.build(tree, w.kernel, w.params, w.tol, prec="mixed", seed=2,
+                           sketch="h2sum", operands=[pre])
+    assert h.converged
+    G = W.gaussian_probe(w.n, 8, 3)
+    rows = np.random.default_rng(4).integers(0, w.n, 64)
+    y = h.matvec(gpu(G)).cpu().numpy()[rows]
+    want = O.ksum_rows(X, w.kernel, w.params, G, rows)
+    assert np.linalg.norm(y - want) <= 10 * w.tol * np.linalg.norm(want)
