@@ -569,7 +569,8 @@ def main_paper_problem(args, dev):
         "kernel_only": "paper", "problem": w.name, "n": w.n, "prec": args.prec,
         "ms": ms, "points_per_s": w.n / (ms * 1e-3), "steps": args.steps, "warmup": args.warmup,
         "rel_error": err, "operand_rel_error": err_pre, "operand_tol": w.extra["operand_tol"],
-        "operand_build_ms": pre_ms, "tol": w.tol, "d_final": st["d_final"],
+        "operand_build_ms": pre_ms, "operand_rank_max": pre.stats()["rank_max"],
+        "tol": w.tol, "d_final": st["d_final"],
         "rank_max": st["rank_max"], "rounds": st["rounds"],
         "memory_gb": (st["bytes_dense"] + st["bytes_coupling"] + st["bytes_basis"]) / 1e9,
         "phases_ms": {p: st[f"ms_{p}"] for p in ("sketch", "nearfield", "qr", "id", "upsweep",

@@ -284,17 +284,18 @@ void h2sum_couplings(bool fp64, const SumCouplingArgs &a, int max_kop, int max_k
   if (a.nnz == 0) return;
   H2_REQUIRE(a.nnz < (1ll << 31), "too many coupling blocks");
   const size_t bytes = sizeof(double) * (size_t)std::max(max_kop, 1) * std::max(max_kt, 1);
-  H2_REQUIRE(bytes <= 200 * 1024, "operand ranks too large for the H2-sum coupling kernel");
   if (!fp64 && max_kop <= kB32MaxKop) {
     H2_CUDA(cudaFuncSetAttribute(k_b_h2sum32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kB32Smem));
     k_b_h2sum32<<<(int)a.nnz, 256, kB32Smem, s>>>(a);
   } else if (fp64) {
+    H2_REQUIRE(bytes <= 200 * 1024, "operand ranks too large for the H2-sum coupling kernel");
     auto kern = k_b_h2sum<double>;
     if (bytes > 48 * 1024)
       H2_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
     kern<<<(int)a.nnz, 128, bytes, s>>>(a, max_kop);
   } else {
+    H2_REQUIRE(bytes <= 200 * 1024, "operand ranks too large for the H2-sum coupling kernel");
     auto kern = k_b_h2sum<float>;
     if (bytes > 48 * 1024)
       H2_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
