@@ -151,7 +151,7 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 template <typename T, int DC, int RPT>
-__global__ void __launch_bounds__(kNT) k_bsr_pipe(BsrArgs a) {
+__global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? 2 : 1) k_bsr_pipe(BsrArgs a) {
   constexpr int SLOT = kSlotBytes / sizeof(T);   // block elements per slot
   constexpr int JMAX = 64;                        // block columns per chunk at most
   constexpr int CG = DC / 4;                      // output columns per thread
@@ -210,6 +210,12 @@ __global__ void __launch_bounds__(kNT) k_bsr_pipe(BsrArgs a) {
       cp_async_commit();
     };
     for (int st = 0; st < kStages - 1; ++st) issue(st);
+    // plain sums over one block's chunks, compensated sums across blocks
+    T part[RPT][CG];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r)
+#pragma unroll
+      for (int c = 0; c < CG; ++c) part[r][c] = T(0);
     for (int it = 0; ce_ < e1; ++it) {
       issue((it + kStages - 1) % kStages);
       cp_async_wait<kStages - 1>();
@@ -219,11 +225,6 @@ __global__ void __launch_bounds__(kNT) k_bsr_pipe(BsrArgs a) {
       const int nj = min(jc, mb - cj);
       const T *sb = sBlk + slot * SLOT;
       const T *si = sIn + slot * JMAX * DCP + g * CG;
-      T part[RPT][CG];
-#pragma unroll
-      for (int r = 0; r < RPT; ++r)
-#pragma unroll
-        for (int c = 0; c < CG; ++c) part[r][c] = T(0);
       for (int j = 0; j < nj; ++j) {
         T ov[CG];
         if constexpr (sizeof(T) == 4 && CG % 4 == 0) {
@@ -240,19 +241,26 @@ __global__ void __launch_bounds__(kNT) k_bsr_pipe(BsrArgs a) {
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
           if (64 * r >= m) break;   // row groups past the block (uniform over the CTA)
-          const int i = i0 + 64 * r;
-          const T bv = i < m ? sb[j * m + i] : T(0);
+          // rows at or past m read other words of the shared buffers (at most
+          // 63 past the slot) and are never stored
+          const T bv = sb[j * m + i0 + 64 * r];
 #pragma unroll
           for (int c = 0; c < CG; ++c) part[r][c] += bv * ov[c];
         }
       }
-      const T sgn = (T)a.sign;
-#pragma unroll
-      for (int r = 0; r < RPT; ++r)
-#pragma unroll
-        for (int c = 0; c < CG; ++c) acc[r][c].add(sgn * part[r][c]);
       cj += nj;
-      if (cj >= mb) { cj = 0; ++ce_; }
+      if (cj >= mb) {
+        cj = 0;
+        ++ce_;
+        const T sgn = (T)a.sign;
+#pragma unroll
+        for (int r = 0; r < RPT; ++r)
+#pragma unroll
+          for (int c = 0; c < CG; ++c) {
+            acc[r][c].add(sgn * part[r][c]);
+            part[r][c] = T(0);
+          }
+      }
       __syncthreads();
     }
     cp_async_wait<0>();
