@@ -953,9 +953,12 @@ __global__ void k_fill_i32(int32_t *p, int64_t n, int32_t v) {
   if (i < n) p[i] = v;
 }
 
+// Opt-in to `bytes` of dynamic shared memory.  Set above 32 KB, not 48 KB:
+// the 48 KB default covers static and dynamic shared memory together, and the
+// QR / ID kernels have static arrays of their own.
 template <typename K>
 void set_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024)
+  if (bytes > 32 * 1024)
     H2_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
 }
 
