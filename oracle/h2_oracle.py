@@ -782,3 +782,224 @@ def storage_entries(h: H2Oracle) -> dict:
     bn = sum(v.size for v in h.B.values())
     un = sum(nd.U.size for nd in h.nodes.values())
     return {"D": dn, "B": bn, "U": un, "total": dn + bn + un}
+
+
+# -----------------------------------------------------------------------------
+# Non-symmetric operators.  Sec. II-A writes an admissible block as
+# U_s B_st V_t^T; for a symmetric operator V = U and Algorithm 1 needs one
+# sketch.  For a non-symmetric one the same bottom-up steps run twice per
+# level: the row side on Y = A Omega gives U (row IDs), the column side on
+# Z = A^T Psi gives V (column IDs).  The inner subtraction of each side uses
+# the other side's bases: A(I_nu, I_b) Omega_b = U_nu B_nu,b (V_b^T Omega_b)
+# and A(I_b, I_nu)^T Psi_b = V_nu B_b,nu^T (U_b^T Psi_b).  Couplings are
+# B_st = A(Itil_row(s), Itil_col(t)).
+# -----------------------------------------------------------------------------
+
+
+@dataclass
+class H2OracleNonSym:
+    tree: ClusterTree
+    lists: BlockLists
+    tol: float
+    l_top: int
+    rows: dict                  # heap id -> NodeData of the row side (U, row skeletons)
+    cols: dict                  # heap id -> NodeData of the column side (V in .U)
+    D: dict
+    B: dict
+    d_final: int
+    nrmK: float
+    eps_abs: float
+    eps_level: dict
+    d_level: dict
+    converged: bool
+
+
+class _NonSymBuilder:
+    """Algorithm 1 with separate row and column bases (see above)."""
+
+    def __init__(self, tree, lists, entries, tol, omega, psi, sampler, sampler_t, d0, d_inc,
+                 d_max):
+        self.tree, self.lists, self.entries, self.tol = tree, lists, entries, tol
+        self.omega = np.asarray(omega, dtype=np.float64)
+        self.psi = np.asarray(psi, dtype=np.float64)
+        self.sampler, self.sampler_t = sampler, sampler_t
+        self.d0, self.d_inc, self.d_max = d0, d_inc, d_max
+        self.rows, self.cols, self.D, self.B = {}, {}, {}, {}
+        self.l_top = top_level(tree, lists)
+        self.eps_level, self.d_level = {}, {}
+        self.converged = True
+
+    def sample(self, c0, c1):
+        """(Y, Omega, Z, Psi) of columns c0:c1 in tree order."""
+        perm = self.tree.perm
+        om = np.ascontiguousarray(self.omega[:, c0:c1])
+        ps = np.ascontiguousarray(self.psi[:, c0:c1])
+        Y = np.asarray(self.sampler(om))
+        Z = np.asarray(self.sampler_t(ps))
+        return Y[perm], om[perm], Z[perm], ps[perm]
+
+    def level_nodes(self, level):
+        return self.tree.nodes_at_depth(self.tree.level_depth(level))
+
+    def far(self, level, node):
+        return self.lists.far[self.tree.level_depth(level)].get(node, [])
+
+    def local_samples(self, level, S, below):
+        """Per node: (Y_loc, Omega^l, Z_loc, Psi^l).  S = (Y, Om, Z, Psi) of the
+        block in tree order at level 1; `below` holds per node of level - 1
+        (Yhat, Omhat, Zhat, Psihat)."""
+        tree = self.tree
+        out = {}
+        for tau in self.level_nodes(level):
+            if level == 1:
+                Yt, Ot, Zt, Pt = S
+                r = np.arange(tree.begin[tau], tree.end[tau])
+                Y, Z = Yt[r].copy(), Zt[r].copy()
+                for b in self.lists.near.get(tau, []):
+                    c = np.arange(tree.begin[b], tree.end[b])
+                    Y -= self.D[(tau, b)] @ Ot[c]
+                    Z -= self.D[(b, tau)].T @ Pt[c]
+                out[tau] = (Y, Ot[r].copy(), Z, Pt[r].copy())
+            else:
+                py, po, pz, pp = [], [], [], []
+                for nu in (2 * tau + 1, 2 * tau + 2):
+                    Yh, Oh, Zh, Ph = below[nu]
+                    Ys, Zs = Yh.copy(), Zh.copy()
+                    for b in self.far(level - 1, nu):
+                        Ys -= self.B[(nu, b)] @ below[b][1]
+                        Zs -= self.B[(b, nu)].T @ below[b][3]
+                    py.append(Ys)
+                    po.append(Oh)
+                    pz.append(Zs)
+                    pp.append(Ph)
+                out[tau] = (np.vstack(py), np.vstack(po), np.vstack(pz), np.vstack(pp))
+        return out
+
+    def upsweep(self, local):
+        """Yhat = Y_loc(J_row), Omhat = V^T Omega^l, Zhat = Z_loc(J_col),
+        Psihat = U^T Psi^l."""
+        res = {}
+        for tau, (Y, O, Z, P) in local.items():
+            rn, cn = self.rows[tau], self.cols[tau]
+            res[tau] = (Y[rn.J, :], cn.U.T @ O, Z[cn.J, :], rn.U.T @ P)
+        return res
+
+    def sweep_new_columns(self, level, c0, c1):
+        S = self.sample(c0, c1)
+        below = None
+        for lv in range(1, level + 1):
+            local = self.local_samples(lv, S, below)
+            if lv == level:
+                return local
+            below = self.upsweep(local)
+        return None
+
+    def run(self):
+        tree = self.tree
+        d = self.d0
+        S = self.sample(0, d)
+        # ||A||_F estimated from both sketches (the same number for A and A^T)
+        self.nrmK = float(math.sqrt((np.linalg.norm(S[0]) ** 2 + np.linalg.norm(S[2]) ** 2)
+                                    / (2 * d)))
+        self.eps_abs = self.tol * self.nrmK
+        for tau in tree.nodes_at_depth(tree.depth):
+            r = np.arange(tree.begin[tau], tree.end[tau])
+            for b in self.lists.near.get(tau, []):
+                c = np.arange(tree.begin[b], tree.end[b])
+                self.D[(tau, b)] = _entries(tree, self.entries, None, r, c)
+        below = None
+        for level in range(1, self.l_top + 1):
+            nodes = list(self.level_nodes(level))
+            eps_l = self.eps_abs / math.sqrt(self.l_top * len(nodes))
+            self.eps_level[level] = eps_l
+            local = self.local_samples(level, S if level == 1 else None, below)
+            for tau in nodes:
+                Y, O, Z, P = local[tau]
+                rn, cn = NodeData(), NodeData()
+                for nd, side in ((rn, self.rows), (cn, self.cols)):
+                    nd.m = Y.shape[0]
+                    if level == 1:
+                        nd.Ibar = np.arange(tree.begin[tau], tree.end[tau])
+                    else:
+                        nd.Ibar = np.concatenate([side[2 * tau + 1].Itil, side[2 * tau + 2].Itil])
+                rn.Yloc, rn.Om, cn.Yloc, cn.Om = Y, O, Z, P
+                self.rows[tau], self.cols[tau] = rn, cn
+            while self.d_inc > 0:
+                pending = [t for t in nodes
+                           if not (node_converged(self.rows[t].Yloc, eps_l)
+                                   and node_converged(self.cols[t].Yloc, eps_l))]
+                if not pending:
+                    break
+                if d + self.d_inc > self.d_max:
+                    self.converged = False
+                    break
+                new = self.sweep_new_columns(level, d, d + self.d_inc)
+                d += self.d_inc
+                for tau in nodes:
+                    Yn, On, Zn, Pn = new[tau]
+                    rn, cn = self.rows[tau], self.cols[tau]
+                    rn.Yloc, rn.Om = np.hstack([rn.Yloc, Yn]), np.hstack([rn.Om, On])
+                    cn.Yloc, cn.Om = np.hstack([cn.Yloc, Zn]), np.hstack([cn.Om, Pn])
+            self.d_level[level] = d
+            for tau in nodes:
+                for nd in (self.rows[tau], self.cols[tau]):
+                    rid = row_id(nd.Yloc, eps_l)
+                    nd.k, nd.J, nd.U = rid.k, rid.J, rid.U
+                    nd.Itil = nd.Ibar[nd.J]
+            up = self.upsweep({tau: (self.rows[tau].Yloc, self.rows[tau].Om,
+                                     self.cols[tau].Yloc, self.cols[tau].Om) for tau in nodes})
+            for tau in nodes:
+                for b in self.far(level, tau):
+                    self.B[(tau, b)] = _entries(tree, self.entries, None, self.rows[tau].Itil,
+                                                self.cols[b].Itil)
+            below = up
+        self.d_final = d
+        return self
+
+
+def build_h2_nonsym(tree: ClusterTree, lists: BlockLists, entries, tol: float, omega: np.ndarray,
+                    psi: np.ndarray, sampler, sampler_t, d0: int = 32, d_inc: int = 16,
+                    d_max: int = 256) -> H2OracleNonSym:
+    """H2 construction of a non-symmetric operator: `entries(Ia, Ib)` on tree
+    positions, `sampler(Om)` = A Om and `sampler_t(Psi)` = A^T Psi in original
+    order, `omega` and `psi` the stored Gaussian matrices of the two sides."""
+    b = _NonSymBuilder(tree, lists, entries, tol, omega, psi, sampler, sampler_t, d0, d_inc,
+                       d_max).run()
+    return H2OracleNonSym(tree, lists, tol, b.l_top, b.rows, b.cols, b.D, b.B, b.d_final,
+                          b.nrmK, b.eps_abs, b.eps_level, b.d_level, b.converged)
+
+
+def h2_matvec_nonsym(h: H2OracleNonSym, x: np.ndarray) -> np.ndarray:
+    """y = A_H2 x: near field, upsweep with the column bases V, couplings,
+    downsweep with the row bases U."""
+    tree = h.tree
+    x = np.asarray(x, dtype=np.float64)
+    squeeze = x.ndim == 1
+    if squeeze:
+        x = x[:, None]
+    xt = x[tree.perm]
+    yt = np.zeros_like(xt)
+    for (s, t), Dst in h.D.items():
+        yt[tree.begin[s]:tree.end[s]] += Dst @ xt[tree.begin[t]:tree.end[t]]
+    if h.l_top > 0:
+        xhat = {}
+        for level in range(1, h.l_top + 1):
+            for tau in tree.nodes_at_depth(tree.level_depth(level)):
+                xin = (xt[tree.begin[tau]:tree.end[tau]] if level == 1
+                       else np.vstack([xhat[2 * tau + 1], xhat[2 * tau + 2]]))
+                xhat[tau] = h.cols[tau].U.T @ xin
+        yhat = {tau: np.zeros((h.rows[tau].k, x.shape[1])) for tau in xhat}
+        for (s, t), Bst in h.B.items():
+            yhat[s] += Bst @ xhat[t]
+        for level in range(h.l_top, 0, -1):
+            for tau in tree.nodes_at_depth(tree.level_depth(level)):
+                z = h.rows[tau].U @ yhat[tau]
+                if level == 1:
+                    yt[tree.begin[tau]:tree.end[tau]] += z
+                else:
+                    k1 = h.rows[2 * tau + 1].k
+                    yhat[2 * tau + 1] += z[:k1]
+                    yhat[2 * tau + 2] += z[k1:]
+    y = np.zeros_like(yt)
+    y[tree.perm] = yt
+    return y[:, 0] if squeeze else y

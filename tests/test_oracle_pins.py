@@ -536,3 +536,69 @@ def test_low_rank_update_operator():
     assert np.linalg.norm(entries_k(idx, idx) - Ft) <= 1e-13 * np.linalg.norm(Ft)
     hk = O.build_h2(t, lists, entries_k, None, 1e-6, W.gaussian_omega(n, 256, 84), sampler_k)
     assert O.dense_rel_error(hk, full) <= 10 * 1e-6
+
+
+# --- non-symmetric operators (separate row and column bases) -------------------
+
+
+def _nonsym_problem(n=1024, seed=101, scale=0.02):
+    X = W.uniform_points(n, 2, seed)
+    t = O.build_cluster_tree(X, 16)
+    lists = O.dual_traversal(t, 0.7)
+    K = O.dense_matrix(X, O.K_EXP, (0.2, 1e-4))
+    rng = np.random.default_rng(seed + 1)
+    U = rng.standard_normal((n, 6)) / math.sqrt(n)
+    V = rng.standard_normal((n, 6)) / math.sqrt(n)
+    A = K + scale * n * U @ V.T          # not symmetric
+    At = A[np.ix_(t.perm, t.perm)]
+    return X, t, lists, A, At
+
+
+def test_nonsym_build_on_a_symmetric_operator_matches_the_symmetric_build():
+    # with A = A^T and Psi = Omega both sides see the same samples: the row and
+    # the column bases are the symmetric construction's U
+    n = 1024
+    X, t, lists, A, _ = _nonsym_problem(n, scale=0.0)
+    om = W.gaussian_omega(n, 256, 102)
+    hs = O.build_h2(t, lists, O.K_EXP, (0.2, 1e-4), 1e-6, om, O.dense_sampler(A))
+    hn = O.build_h2_nonsym(t, lists, lambda Ia, Ib: O._entries(t, O.K_EXP, (0.2, 1e-4), Ia, Ib),
+                           1e-6, om, om, O.dense_sampler(A), O.dense_sampler(A.T))
+    for tau, nd in hs.nodes.items():
+        for side in (hn.rows[tau], hn.cols[tau]):
+            assert side.k == nd.k and np.array_equal(side.J, nd.J)
+            assert np.allclose(side.U, nd.U, rtol=0, atol=1e-12)
+    G = W.gaussian_probe(n, 3, 0)
+    y1, y2 = O.h2_matvec(hs, G), O.h2_matvec_nonsym(hn, G)
+    assert np.linalg.norm(y1 - y2) <= 1e-12 * np.linalg.norm(y1)
+
+
+def test_nonsym_build_meets_tolerance_where_the_symmetric_one_cannot():
+    n, tol = 1024, 1e-6
+    X, t, lists, A, At = _nonsym_problem(n)
+    assert np.linalg.norm(A - A.T) > 0.1 * np.linalg.norm(A)
+    entries = lambda Ia, Ib: At[np.ix_(Ia, Ib)]
+    om, ps = W.gaussian_omega(n, 256, 103), W.gaussian_omega(n, 256, 104)
+    hn = O.build_h2_nonsym(t, lists, entries, tol, om, ps, O.dense_sampler(A),
+                           O.dense_sampler(A.T))
+    assert hn.converged and hn.l_top >= 2
+    dense = O.h2_matvec_nonsym(hn, np.eye(n))
+    assert np.linalg.norm(dense - A) <= 10 * tol * np.linalg.norm(A)
+    # one shared basis (the symmetric construction) misses the column space
+    hs = O.build_h2(t, lists, entries, None, tol, om, O.dense_sampler(A))
+    assert np.linalg.norm(O.h2_matvec(hs, np.eye(n)) - A) > 1e3 * tol * np.linalg.norm(A)
+
+
+def test_nonsym_build_of_the_transpose_is_the_transpose():
+    # swapping the operator for its transpose swaps the two sides exactly
+    n, tol = 1024, 1e-6
+    X, t, lists, A, At = _nonsym_problem(n)
+    om, ps = W.gaussian_omega(n, 256, 105), W.gaussian_omega(n, 256, 106)
+    h = O.build_h2_nonsym(t, lists, lambda Ia, Ib: At[np.ix_(Ia, Ib)], tol, om, ps,
+                          O.dense_sampler(A), O.dense_sampler(A.T))
+    hT = O.build_h2_nonsym(t, lists, lambda Ia, Ib: At.T[np.ix_(Ia, Ib)], tol, ps, om,
+                           O.dense_sampler(A.T), O.dense_sampler(A))
+    for tau in h.rows:
+        assert np.array_equal(h.rows[tau].J, hT.cols[tau].J)
+        assert np.array_equal(h.cols[tau].J, hT.rows[tau].J)
+    M, MT = O.h2_matvec_nonsym(h, np.eye(n)), O.h2_matvec_nonsym(hT, np.eye(n))
+    assert np.linalg.norm(MT - M.T) <= 1e-12 * np.linalg.norm(M)
