@@ -55,6 +55,9 @@ def test_structs_match_c_layout(built_lib):
     _lib.lib().h2_default_opts(ctypes.byref(o))
     assert (o.d0, o.d_inc, o.d_max, o.prec, o.omega_mode, o.sketch) == (32, 16, 256, 0, 0, 0)
     assert o.seed == 0 and not o.omega_stored and o.timing == 0
+    # the low-rank term is off by default (the struct's last fields)
+    assert o.lowrank_rank == 0 and not o.lowrank_u and not o.lowrank_v
+    assert ctypes.sizeof(_lib.BuildOpts) % 8 == 0
 
 
 def test_library_targets_sm103a(built_lib):
@@ -70,3 +73,18 @@ def test_argument_errors_without_a_device(built_lib):
     st = _lib.lib().h2_build_cluster_tree(None, 10, 2, 8, 0.7, None, ctypes.byref(h))
     assert st == -1
     assert b"points" in _lib.lib().h2_last_error()
+
+
+@pytest.mark.parametrize("n,dim,leaf,eta,word", [(0, 2, 8, 0.7, b"n must"), (10, 0, 8, 0.7, b"dim"),
+                                                 (10, 4, 8, 0.7, b"dim"), (10, 2, 1, 0.7, b"leaf"),
+                                                 (10, 2, 8, -1.0, b"eta"),
+                                                 (10, 2, 8, float("inf"), b"eta")])
+def test_degenerate_tree_arguments(built_lib, n, dim, leaf, eta, word):
+    # empty and degenerate inputs are rejected before the points are touched
+    # (the pointer below is never dereferenced)
+    h = ctypes.c_void_p()
+    dummy = ctypes.c_void_p(16)
+    st = _lib.lib().h2_build_cluster_tree(dummy, n, dim, leaf, eta, None, ctypes.byref(h))
+    assert st == -1
+    assert word in _lib.lib().h2_last_error()
+    assert not h.value
