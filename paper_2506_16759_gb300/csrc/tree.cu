@@ -321,6 +321,42 @@ __global__ void k_scan_single(const int64_t *in, const int32_t *in32, int64_t *o
   if (threadIdx.x == 0) out[n] = carry;
 }
 
+// Three-phase scan for long arrays: each CTA scans its 1024-element tile in
+// place (exclusive) and writes the tile's total; the totals are scanned by one
+// CTA; each tile then adds its offset.
+__global__ void k_scan_tiles(const int64_t *in, const int32_t *in32, int64_t *out, int64_t n,
+                             int64_t *tile_sums) {
+  __shared__ int64_t warp_sums[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t v = i < n ? (in ? in[i] : (int64_t)in32[i]) : 0;
+  int64_t x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sums[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x / 32;
+    int64_t w = lane < nw ? warp_sums[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < nw) warp_sums[lane] = w;
+  }
+  __syncthreads();
+  const int64_t incl = x + (warp > 0 ? warp_sums[warp - 1] : 0);
+  if (i < n) out[i] = incl - v;
+  if (threadIdx.x == blockDim.x - 1) tile_sums[blockIdx.x] = incl;
+}
+
+__global__ void k_scan_add(int64_t *out, int64_t n, const int64_t *tile_offsets) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] += tile_offsets[blockIdx.x];
+}
+
 int64_t next_pow2(int64_t v) {
   int64_t p = 1;
   while (p < v) p <<= 1;
@@ -349,16 +385,40 @@ void sort_segments(SortItem *items, int64_t total, int64_t P, cudaStream_t s) {
 
 }  // namespace
 
-void scan_exclusive(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s) {
-  k_scan_single<<<1, 1024, 0, s>>>(in, nullptr, out, n);
+namespace {
+// out[0..n] = exclusive scan of in (int64 or int32) with out[n] = the total.
+void scan_any(const int64_t *in, const int32_t *in32, int64_t *out, int64_t n, cudaStream_t s) {
+  constexpr int kTile = 1024;
+  if (n <= 8 * kTile) {
+    k_scan_single<<<1, kTile, 0, s>>>(in, in32, out, n);
+    count_launch();
+    H2_CHECK_LAUNCH();
+    return;
+  }
+  const int64_t nb = (n + kTile - 1) / kTile;
+  DBuf<int64_t> sums, offs;
+  sums.alloc(nb);
+  offs.alloc(nb + 1);
+  k_scan_tiles<<<(unsigned)nb, kTile, 0, s>>>(in, in32, out, n, sums.p);
   count_launch();
   H2_CHECK_LAUNCH();
+  k_scan_single<<<1, kTile, 0, s>>>(sums.p, nullptr, offs.p, nb);
+  count_launch();
+  H2_CHECK_LAUNCH();
+  k_scan_add<<<(unsigned)nb, kTile, 0, s>>>(out, n, offs.p);
+  count_launch();
+  H2_CHECK_LAUNCH();
+  // the total is the scan of the tile sums at nb
+  H2_CUDA(cudaMemcpyAsync(out + n, offs.p + nb, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+}
+}  // namespace
+
+void scan_exclusive(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s) {
+  scan_any(in, nullptr, out, n, s);
 }
 
 void scan_exclusive_i32(const int32_t *in, int64_t *out, int64_t n, cudaStream_t s) {
-  k_scan_single<<<1, 1024, 0, s>>>(nullptr, in, out, n);
-  count_launch();
-  H2_CHECK_LAUNCH();
+  scan_any(nullptr, in, out, n, s);
 }
 
 int leaf_depth(int64_t n, int leaf) {
