@@ -407,6 +407,126 @@ __global__ void __launch_bounds__(4 * DC) k_bsr_tile(BsrArgs a, const float *tin
   }
 }
 
+// Block-sparse row products for row blocks of 65 to 128 rows (ranks above 64,
+// e.g. the couplings of operands built at tight tolerances).  As k_bsr_tile,
+// with 32 row groups (thread rows rg + 32 i, i < 4: a warp reads 32
+// consecutive words of a block column) and the partner blocks streamed in
+// chunks of 64 columns: a chunk of a column-major block is one contiguous,
+// 16-byte aligned range.  Plain sums over a whole block, compensated across.
+template <int DC>
+__global__ void __launch_bounds__(8 * DC) k_bsr_tile128(BsrArgs a, const float *tin,
+                                                        int64_t ldt) {
+  constexpr int NT = 8 * DC;          // 32 row groups x DC/4 column groups
+  constexpr int JC = 64;              // block columns per chunk
+  constexpr int SLOT_B = 128 * JC;    // floats
+  constexpr int SLOT_O = JC * DC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float *sB = reinterpret_cast<float *>(smem_raw);   // [2][SLOT_B]
+  float *sO = sB + 2 * SLOT_B;                         // [2][JC][DC]
+  const int tau = blockIdx.x / a.seg, part_id = blockIdx.x % a.seg;
+  const int m = a.row_m[tau];
+  const int inst = a.row_inst[tau];
+  const int cb = a.cols.cb[inst], ce = a.cols.ce[inst];
+  const int64_t r0 = a.ptr[tau], rn = a.ptr[tau + 1] - r0;
+  const int64_t e0 = r0 + rn * part_id / a.seg, e1 = r0 + rn * (part_id + 1) / a.seg;
+  if (m == 0 || ce <= cb || e0 == e1) return;
+  const int rg = threadIdx.x & 31, cg = threadIdx.x >> 5;
+  // input-slice copy: NT = 32 * (DC / 4), so thread t copies chunk t % (DC / 4)
+  // of rows t / (DC / 4) + 32 q
+  const int cv = threadIdx.x % (DC / 4), cj0 = threadIdx.x / (DC / 4);
+  const float *blocks = reinterpret_cast<const float *>(a.blocks);
+  float *out = reinterpret_cast<float *>(a.out);
+  const float sgn = (float)a.sign;
+  for (int c0 = cb; c0 < ce; c0 += DC) {
+    const int ncol = min(DC, ce - c0);
+    float acc[16], cmp[16], part[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) { acc[q] = 0.f; cmp[q] = 0.f; part[q] = 0.f; }
+    int64_t pe = e0;   // next chunk to issue: block pe, columns from pj
+    int pj = 0;
+    auto issue = [&](int slot) {
+      if (pe < e1) {
+        const int b = a.idx[pe];
+        const int mb = a.col_m[b];
+        const int nj = min(JC, mb - pj);
+        const char *src = reinterpret_cast<const char *>(blocks + a.boff[pe] + (int64_t)pj * m);
+        char *dst = reinterpret_cast<char *>(sB + slot * SLOT_B);
+        const int n16 = (m * nj * 4 + 15) / 16;
+        for (int u = threadIdx.x; u < n16; u += NT) cp_async16(dst + 16 * u, src + 16 * u);
+        const float *irow = tin + (a.col_off[b] + pj) * ldt + c0 + 4 * cv;
+        float *di = sO + slot * SLOT_O + 4 * cv;
+        const bool ok = 4 * cv < ncol;
+        for (int j = cj0; j < nj; j += 32)
+          cp_async16z(di + j * DC, ok ? irow + (int64_t)j * ldt : irow, ok);
+        pj += nj;
+        if (pj >= mb) { pj = 0; ++pe; }
+      }
+      cp_async_commit();
+    };
+    int64_t ce_ = e0;  // chunk being computed: block ce_, columns from cj
+    int cj = 0;
+    issue(0);
+    for (int it = 0; ce_ < e1; ++it) {
+      const int slot = it & 1;
+      issue(slot ^ 1);
+      cp_async_wait<1>();
+      __syncthreads();
+      const int mb = a.col_m[a.idx[ce_]];
+      const int nj = min(JC, mb - cj);
+      // rows at or past m read other words of the slot and are never stored
+      const float *Br = sB + slot * SLOT_B + rg;
+      const float *Os = sO + slot * SLOT_O + 4 * cg;
+#pragma unroll 2
+      for (int j = 0; j < nj; ++j) {
+        const float4 o = *reinterpret_cast<const float4 *>(Os + j * DC);
+        float bv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) bv[i] = Br[j * m + 32 * i];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          part[4 * i + 0] += bv[i] * o.x;
+          part[4 * i + 1] += bv[i] * o.y;
+          part[4 * i + 2] += bv[i] * o.z;
+          part[4 * i + 3] += bv[i] * o.w;
+        }
+      }
+      cj += nj;
+      if (cj >= mb) {
+        cj = 0;
+        ++ce_;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const float y = sgn * part[q] - cmp[q];
+          const float t = acc[q] + y;
+          cmp[q] = (t - acc[q]) - y;
+          acc[q] = t;
+          part[q] = 0.f;
+        }
+      }
+      __syncthreads();
+    }
+    cp_async_wait<0>();
+    __syncthreads();
+    const int64_t orow = a.row_off[tau];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (rg + 32 * i >= m) continue;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int col = 4 * cg + c;
+        if (col >= ncol) continue;
+        float *op = out + orow + rg + 32 * i + (int64_t)(c0 + col) * a.ld_out;
+        if (a.seg > 1) {
+          atomicAdd(op, acc[4 * i + c] - cmp[4 * i + c]);
+        } else {
+          const float y = *op - cmp[4 * i + c];
+          *op = acc[4 * i + c] + y;
+        }
+      }
+    }
+  }
+}
+
 // Row-major copy t[r * ldt + c] = in[r + c * ld] of rows [0, n), columns [0, nc).
 __global__ void k_transpose_panel(const float *in, int64_t ld, int64_t n, int nc, float *t,
                                   int64_t ldt) {
@@ -994,6 +1114,16 @@ void launch_bsr(const BsrArgs &a, cudaStream_t s) {
 }
 
 template <int DC>
+void launch_bsr_tile128(const BsrArgs &a, const float *tin, int64_t ldt, cudaStream_t s) {
+  const size_t bytes = sizeof(float) * 2 * (128 * 64 + 64 * DC);
+  auto kern = k_bsr_tile128<DC>;
+  set_smem(kern, bytes);
+  kern<<<a.n_rows * a.seg, 8 * DC, bytes, s>>>(a, tin, ldt);
+  count_launch();
+  H2_CHECK_LAUNCH();
+}
+
+template <int DC>
 void launch_bsr_tile(const BsrArgs &a, const float *tin, int64_t ldt, cudaStream_t s) {
   const size_t bytes = sizeof(float) * 2 * (64 * 64 + 64 * DC);
   auto kern = k_bsr_tile<DC>;
@@ -1011,7 +1141,7 @@ void bsr_apply(bool fp64, const BsrArgs &a_in, int max_m, int max_cols, cudaStre
   // that its sums stay in a fixed order)
   BsrArgs a = a_in;
   a.seg = fp64 ? 1 : std::max(1, std::min(16, 4 * device_sm_count() / a.n_rows));
-  if (!fp64 && max_m <= 64 && a.col_hi > 0 && a.in_rows > 0) {
+  if (!fp64 && max_m <= 128 && a.col_hi > 0 && a.in_rows > 0) {
     // register-tiled path on a row-major copy of the input columns [0, col_hi)
     const int64_t ldt = (a.col_hi + 3) / 4 * 4;
     DBuf<float> tin;
@@ -1021,7 +1151,12 @@ void bsr_apply(bool fp64, const BsrArgs &a_in, int max_m, int max_cols, cudaStre
                                                     a.in_rows, a.col_hi, tin.p, ldt);
     count_launch();
     H2_CHECK_LAUNCH();
-    if (max_cols <= 16) launch_bsr_tile<16>(a, tin.p, ldt, s);
+    if (max_m > 64) {
+      if (max_cols <= 16) launch_bsr_tile128<16>(a, tin.p, ldt, s);
+      else if (max_cols <= 32) launch_bsr_tile128<32>(a, tin.p, ldt, s);
+      else if (max_cols <= 64) launch_bsr_tile128<64>(a, tin.p, ldt, s);
+      else launch_bsr_tile128<80>(a, tin.p, ldt, s);
+    } else if (max_cols <= 16) launch_bsr_tile<16>(a, tin.p, ldt, s);
     else if (max_cols <= 32) launch_bsr_tile<32>(a, tin.p, ldt, s);
     else if (max_cols <= 64) launch_bsr_tile<64>(a, tin.p, ldt, s);
     else launch_bsr_tile<80>(a, tin.p, ldt, s);
