@@ -407,18 +407,18 @@ __global__ void __launch_bounds__(4 * DC) k_bsr_tile(BsrArgs a, const float *tin
   }
 }
 
-// Block-sparse row products for row blocks of 65 to 128 rows (ranks above 64,
-// e.g. the couplings of operands built at tight tolerances).  As k_bsr_tile,
-// with 32 row groups (thread rows rg + 32 i, i < 4: a warp reads 32
-// consecutive words of a block column) and the partner blocks streamed in
-// chunks of 64 columns: a chunk of a column-major block is one contiguous,
+// Block-sparse row products for row blocks of 65 to 32 RI rows (ranks above
+// 64, e.g. the couplings of operands built at tight tolerances).  As
+// k_bsr_tile, with 32 row groups (thread rows rg + 32 i, i < RI: a warp reads
+// 32 consecutive words of a block column) and the partner blocks streamed in
+// chunks of JC columns: a chunk of a column-major block is one contiguous,
 // 16-byte aligned range.  Plain sums over a whole block, compensated across.
-template <int DC>
-__global__ void __launch_bounds__(8 * DC) k_bsr_tile128(BsrArgs a, const float *tin,
-                                                        int64_t ldt) {
+template <int DC, int RI, int JC>
+__global__ void __launch_bounds__(8 * DC) k_bsr_tile_big(BsrArgs a, const float *tin,
+                                                         int64_t ldt) {
   constexpr int NT = 8 * DC;          // 32 row groups x DC/4 column groups
-  constexpr int JC = 64;              // block columns per chunk
-  constexpr int SLOT_B = 128 * JC;    // floats
+  constexpr int NR = 4 * RI;          // accumulators per thread
+  constexpr int SLOT_B = 32 * RI * JC;   // floats
   constexpr int SLOT_O = JC * DC;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float *sB = reinterpret_cast<float *>(smem_raw);   // [2][SLOT_B]
@@ -439,9 +439,9 @@ __global__ void __launch_bounds__(8 * DC) k_bsr_tile128(BsrArgs a, const float *
   const float sgn = (float)a.sign;
   for (int c0 = cb; c0 < ce; c0 += DC) {
     const int ncol = min(DC, ce - c0);
-    float acc[16], cmp[16], part[16];
+    float acc[NR], cmp[NR], part[NR];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) { acc[q] = 0.f; cmp[q] = 0.f; part[q] = 0.f; }
+    for (int q = 0; q < NR; ++q) { acc[q] = 0.f; cmp[q] = 0.f; part[q] = 0.f; }
     int64_t pe = e0;   // next chunk to issue: block pe, columns from pj
     int pj = 0;
     auto issue = [&](int slot) {
@@ -479,11 +479,11 @@ __global__ void __launch_bounds__(8 * DC) k_bsr_tile128(BsrArgs a, const float *
 #pragma unroll 2
       for (int j = 0; j < nj; ++j) {
         const float4 o = *reinterpret_cast<const float4 *>(Os + j * DC);
-        float bv[4];
+        float bv[RI];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) bv[i] = Br[j * m + 32 * i];
+        for (int i = 0; i < RI; ++i) bv[i] = Br[j * m + 32 * i];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < RI; ++i) {
           part[4 * i + 0] += bv[i] * o.x;
           part[4 * i + 1] += bv[i] * o.y;
           part[4 * i + 2] += bv[i] * o.z;
@@ -495,7 +495,7 @@ __global__ void __launch_bounds__(8 * DC) k_bsr_tile128(BsrArgs a, const float *
         cj = 0;
         ++ce_;
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
+        for (int q = 0; q < NR; ++q) {
           const float y = sgn * part[q] - cmp[q];
           const float t = acc[q] + y;
           cmp[q] = (t - acc[q]) - y;
@@ -509,7 +509,7 @@ __global__ void __launch_bounds__(8 * DC) k_bsr_tile128(BsrArgs a, const float *
     __syncthreads();
     const int64_t orow = a.row_off[tau];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < RI; ++i) {
       if (rg + 32 * i >= m) continue;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
@@ -1113,10 +1113,10 @@ void launch_bsr(const BsrArgs &a, cudaStream_t s) {
   H2_CHECK_LAUNCH();
 }
 
-template <int DC>
-void launch_bsr_tile128(const BsrArgs &a, const float *tin, int64_t ldt, cudaStream_t s) {
-  const size_t bytes = sizeof(float) * 2 * (128 * 64 + 64 * DC);
-  auto kern = k_bsr_tile128<DC>;
+template <int DC, int RI, int JC>
+void launch_bsr_tile_big(const BsrArgs &a, const float *tin, int64_t ldt, cudaStream_t s) {
+  const size_t bytes = sizeof(float) * 2 * (32 * RI * JC + JC * DC);
+  auto kern = k_bsr_tile_big<DC, RI, JC>;
   set_smem(kern, bytes);
   kern<<<a.n_rows * a.seg, 8 * DC, bytes, s>>>(a, tin, ldt);
   count_launch();
@@ -1141,7 +1141,10 @@ void bsr_apply(bool fp64, const BsrArgs &a_in, int max_m, int max_cols, cudaStre
   // that its sums stay in a fixed order)
   BsrArgs a = a_in;
   a.seg = fp64 ? 1 : std::max(1, std::min(16, 4 * device_sm_count() / a.n_rows));
-  if (!fp64 && max_m <= 128 && a.col_hi > 0 && a.in_rows > 0) {
+  // register-tiled kernels: up to 128 rows at any width, 256 rows for up to 32
+  // columns (wider 256-row tiles would spill registers)
+  const bool tiled = max_m <= 128 || (max_m <= 256 && max_cols <= 32);
+  if (!fp64 && tiled && a.col_hi > 0 && a.in_rows > 0) {
     // register-tiled path on a row-major copy of the input columns [0, col_hi)
     const int64_t ldt = (a.col_hi + 3) / 4 * 4;
     DBuf<float> tin;
@@ -1151,11 +1154,14 @@ void bsr_apply(bool fp64, const BsrArgs &a_in, int max_m, int max_cols, cudaStre
                                                     a.in_rows, a.col_hi, tin.p, ldt);
     count_launch();
     H2_CHECK_LAUNCH();
-    if (max_m > 64) {
-      if (max_cols <= 16) launch_bsr_tile128<16>(a, tin.p, ldt, s);
-      else if (max_cols <= 32) launch_bsr_tile128<32>(a, tin.p, ldt, s);
-      else if (max_cols <= 64) launch_bsr_tile128<64>(a, tin.p, ldt, s);
-      else launch_bsr_tile128<80>(a, tin.p, ldt, s);
+    if (max_m > 128) {   // rows rg + 32 i, i < 8; 32-column chunks of the partners
+      if (max_cols <= 16) launch_bsr_tile_big<16, 8, 32>(a, tin.p, ldt, s);
+      else launch_bsr_tile_big<32, 8, 32>(a, tin.p, ldt, s);
+    } else if (max_m > 64) {   // rows rg + 32 i, i < 4; 64-column chunks
+      if (max_cols <= 16) launch_bsr_tile_big<16, 4, 64>(a, tin.p, ldt, s);
+      else if (max_cols <= 32) launch_bsr_tile_big<32, 4, 64>(a, tin.p, ldt, s);
+      else if (max_cols <= 64) launch_bsr_tile_big<64, 4, 64>(a, tin.p, ldt, s);
+      else launch_bsr_tile_big<80, 4, 64>(a, tin.p, ldt, s);
     } else if (max_cols <= 16) launch_bsr_tile<16>(a, tin.p, ldt, s);
     else if (max_cols <= 32) launch_bsr_tile<32>(a, tin.p, ldt, s);
     else if (max_cols <= 64) launch_bsr_tile<64>(a, tin.p, ldt, s);
