@@ -279,6 +279,15 @@ def test_ranks_match_dense_svd(tol):
     assert O.dense_rel_error(h, A) <= 10 * tol
 
 
+def test_helmholtz_ranks_match_dense_svd():
+    # the same rank pin for the oscillatory, sign-changing IE kernel cos(3r)/r
+    params = (3.0, 0.0)
+    X, om, t, lists, A, h = _build(2048, 3, O.K_HELMHOLTZ_IE, params, 1e-6, leaf=16, seed=6)
+    assert h.l_top >= 2
+    assert _svd_rank_violations(t, lists, h, O.K_HELMHOLTZ_IE, params) == []
+    assert O.dense_rel_error(h, A) <= 10 * 1e-6
+
+
 def test_sample_recurrence_exact_low_rank():
     # Y^l = W^l Y^{l-1} (Sec. III-A): with exact IDs (rank-10 kernel) the local
     # samples of child nu inside its parent equal the samples of the blocks
