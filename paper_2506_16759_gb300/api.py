@@ -159,6 +159,14 @@ class H2Matrix:
 
     @classmethod
     def build(cls, tree: ClusterTree, kernel, params, tol: float, stream=None, **kw):
+        lr = kw.get("lowrank")
+        if lr is not None:
+            # the library reads N x rank from each factor: check the shapes here
+            u, v = lr
+            n = tree.info.n
+            if u.dim() != 2 or tuple(u.shape) != tuple(v.shape) or u.shape[0] != n:
+                raise ValueError(f"low-rank factors must both be ({n}, rank), got "
+                                 f"{tuple(u.shape)} and {tuple(v.shape)}")
         o, keep = make_opts(**kw)
         p = _params(params)
         h = C.c_void_p()
