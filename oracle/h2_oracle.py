@@ -698,7 +698,8 @@ def h2_sampler(h: H2Oracle):
 def low_rank_update(tree: ClusterTree, entries, sampler, U: np.ndarray, V: np.ndarray) -> tuple:
     """Entry function and sampler of an operator plus the product U V^T (the
     update problem of Sec. V-A: an existing H2 matrix plus a rank-32 product;
-    U V^T is taken symmetric, like the operator).  `entries` is a kernel id
+    the symmetric construction needs U V^T symmetric, the non-symmetric one
+    takes any U, V).  `entries` is a kernel id
     with its parameters as a pair (kernel, params), or a callable on tree
     positions; `sampler` gives the operator's products in original order; U
     and V are (N, r) in original order."""

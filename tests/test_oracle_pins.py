@@ -611,3 +611,27 @@ def test_nonsym_build_of_the_transpose_is_the_transpose():
         assert np.array_equal(h.cols[tau].J, hT.rows[tau].J)
     M, MT = O.h2_matvec_nonsym(h, np.eye(n)), O.h2_matvec_nonsym(hT, np.eye(n))
     assert np.linalg.norm(MT - M.T) <= 1e-12 * np.linalg.norm(M)
+
+
+def test_nonsym_update_of_an_h2_matrix():
+    # the update use case with a non-symmetric product: H2(exp) + U V^T, U != V
+    # (LU-type updates); entries from the operand's representation plus the
+    # product's, samples of A and A^T from matvecs plus the product
+    n, tol = 1024, 1e-6
+    X = W.uniform_points(n, 2, 111)
+    t = O.build_cluster_tree(X, 16)
+    lists = O.dual_traversal(t, 0.7)
+    kp = (O.K_EXP, (0.2, 0.0))
+    K = O.dense_matrix(X, *kp)
+    op = O.build_h2(t, lists, *kp, 1e-8, W.gaussian_omega(n, 256, 112), O.dense_sampler(K))
+    rng = np.random.default_rng(113)
+    U = rng.standard_normal((n, 4)) / math.sqrt(n) * 0.05 * n
+    V = rng.standard_normal((n, 4)) / math.sqrt(n)
+    base_entries, base_sampler = O.h2_sum_operator([op])
+    entries, sampler = O.low_rank_update(t, base_entries, base_sampler, U, V)
+    _, sampler_t = O.low_rank_update(t, base_entries, base_sampler, V, U)   # A^T = H2 + V U^T
+    A = K + U @ V.T
+    h = O.build_h2_nonsym(t, lists, entries, tol, W.gaussian_omega(n, 256, 114),
+                          W.gaussian_omega(n, 256, 115), sampler, sampler_t)
+    assert h.converged
+    assert np.linalg.norm(O.h2_matvec_nonsym(h, np.eye(n)) - A) <= 10 * tol * np.linalg.norm(A)
