@@ -135,7 +135,13 @@ class ClusterTree:
         return self.depth - level + 1
 
     def Xt(self) -> np.ndarray:
-        return self.X[self.perm]
+        """Points in tree order (formed once: a per-block permutation would make
+        the construction quadratic in N)."""
+        xt = self.__dict__.get("_xt")
+        if xt is None:
+            xt = self.X[self.perm]
+            self.__dict__["_xt"] = xt
+        return xt
 
 
 def leaf_depth(n: int, leaf_size: int) -> int:
