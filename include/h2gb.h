@@ -313,12 +313,15 @@ h2_status h2_batched_row_id(int count, const int32_t *m, const int32_t *d, const
  *
  * Working copies of the panels that need a QR (m[i] > d[i]) go to one fixed
  * workspace compiled into the library: 2097152 doubles (16 MiB), present on
- * every device that loads the library until the process exits.  If the sum of
- * m[i]*d[i] over those panels exceeds it, the call returns H2_ERR_ARG and the
- * panels that did not fit get NaN.
+ * every device that loads the library until the process exits.  Its front
+ * holds a table of count + 1 panel offsets (rounded up to 32 doubles).  If the
+ * table and the sum of m[i]*d[i] over those panels exceed it, the call returns
+ * H2_ERR_ARG and the panels that did not fit get NaN.  A panel with m[i] < 0 or
+ * d[i] < 1 gets NaN and the call returns H2_ERR_ARG (checked on the device,
+ * since m and d are device arrays).
  * The first call on a device looks up the workspace's device address (once
- * per device, with that device current); make that first call before any
- * stream capture.  All calls share the one workspace and it keeps the last
+ * per device and CUDA context, with that device current); make that first
+ * call before any stream capture.  All calls share the one workspace and it keeps the last
  * call's contents: calls that overlap on the GPU (other streams, other host
  * threads) race with each other.  The call waits for its stream to finish
  * before it returns. */
@@ -342,6 +345,11 @@ void h2_trim_memory(void);
 /* CUDA kernels the library has launched from the calling host thread so far
  * (all entry points); a profiling aid. */
 int64_t h2_kernel_launches(void);
+
+/* Device blocks the library has requested from its allocator so far (all
+ * threads; every request counts, whether its cache or cudaMalloc served it).
+ * An entry point that allocates nothing leaves it unchanged. */
+int64_t h2_device_allocations(void);
 
 const char *h2_last_error(void);
 

@@ -6,6 +6,7 @@
 // only host decisions are the adaptive flag per round and the sizes of the
 // next level (ranks), each read with one small device-to-host copy.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -72,7 +73,10 @@ void free_all(Pool &pool) {
 }
 }  // namespace
 
+std::atomic<int64_t> g_alloc_requests{0};
+
 void *dev_alloc(size_t bytes) {
+  g_alloc_requests.fetch_add(1, std::memory_order_relaxed);
   int dev = 0;
   H2_CUDA(cudaGetDevice(&dev));
   const size_t b = bucket_of(bytes);
@@ -1511,6 +1515,10 @@ void h2_default_opts(h2_build_opts *o) {
 const char *h2_last_error(void) { return g_last_error.c_str(); }
 
 int64_t h2_kernel_launches(void) { return g_launches; }
+
+int64_t h2_device_allocations(void) {
+  return h2::g_alloc_requests.load(std::memory_order_relaxed);
+}
 
 void h2_trim_memory(void) { h2::dev_trim(); }
 

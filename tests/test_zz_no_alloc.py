@@ -35,11 +35,29 @@ def _static_call(panels):
     return st, out.cpu().numpy()
 
 
+def _raw_call(m, d, off, flat, n, out=None):
+    if out is None:
+        out = torch.full((n,), -1.0, dtype=torch.float64, device=DEV)
+    st = _lib.lib().h2_batched_qr_mindiag_static(
+        n, m.data_ptr(), d.data_ptr(), off.data_ptr(), flat.data_ptr(), out.data_ptr(),
+        torch.cuda.current_stream().cuda_stream)
+    return st, out.cpu().numpy()
+
+
 def test_static_workspace_matches_allocating_entry_point():
+    L = _lib.lib()
     for seed in (1, 2):                    # two calls in a row
         panels = _panels(seed)
-        st, got = _static_call(panels)
-        assert st == 0, _lib.lib().h2_last_error()
+        m, d, off, flat, _, _ = api._pack_panels([torch.from_numpy(p).to(DEV) for p in panels])
+        out = torch.full((len(panels),), -1.0, dtype=torch.float64, device=DEV)
+        torch.cuda.synchronize()
+        reserved, requests = torch.cuda.memory_reserved(DEV), L.h2_device_allocations()
+        st, got = _raw_call(m, d, off, flat, len(panels), out)
+        # the defining property: no device memory requested, by the library
+        # or through torch
+        assert L.h2_device_allocations() == requests
+        assert torch.cuda.memory_reserved(DEV) == reserved
+        assert st == 0, L.h2_last_error()
         want = api.batched_qr_mindiag([torch.from_numpy(p).to(DEV) for p in panels]).cpu().numpy()
         for g, w, p in zip(got, want, panels):
             if p.shape[0] <= p.shape[1]:
@@ -57,4 +75,25 @@ def test_static_workspace_rejects_oversize_requests():
     assert np.isnan(got).any()
     # the next call starts clean
     st, _ = _static_call(_panels(3))
+    assert st == 0
+
+
+def test_static_workspace_rejects_bad_shapes():
+    # d = 0 with m > 0, and a negative d ahead of a valid panel: both get NaN
+    # and the call reports an argument error; the valid panel is still right
+    rng = np.random.default_rng(4)
+    good = rng.standard_normal((50, 20))
+    want = api.batched_qr_mindiag([torch.from_numpy(good).to(DEV)]).cpu().numpy()[0]
+    for shapes in ([(10, 0)], [(10, -3), (50, 20)]):
+        ms = torch.tensor([a for a, _ in shapes], dtype=torch.int32, device=DEV)
+        ds = torch.tensor([b for _, b in shapes], dtype=torch.int32, device=DEV)
+        offs = torch.zeros(len(shapes), dtype=torch.int64, device=DEV)
+        flat = torch.from_numpy(good.T.reshape(-1).copy()).to(DEV)   # column-major 50 x 20
+        st, got = _raw_call(ms, ds, offs, flat, len(shapes))
+        assert st == -1
+        assert b"m < 0 or d < 1" in _lib.lib().h2_last_error()
+        assert np.isnan(got[0])
+        if len(shapes) == 2:
+            assert got[1] == pytest.approx(want, rel=1e-11)
+    st, _ = _static_call(_panels(5))        # and the next call starts clean
     assert st == 0
