@@ -329,6 +329,15 @@ h2_status h2_batched_qr_mindiag_static(int count, const int32_t *m, const int32_
                                        const int64_t *off, const double *panels,
                                        double *mindiag, h2_stream_t s);
 
+/* Measured throughput of one arithmetic pipe of the current device, for the
+ * roofline fractions: which = 0 FP64 FMA (TFLOP/s), 1 FP32 FMA (TFLOP/s),
+ * 2 exp2 on the special-function units (G operations/s), 3 dense tcgen05
+ * products of FP16 operands with FP32 accumulation (TFLOP/s), 4 the same with
+ * TF32 operands (TFLOP/s).  Each probe runs a fixed amount of independent work
+ * on every SM (tens of milliseconds in all) and reports the best of five
+ * timed launches.  Not part of the construction. */
+h2_status h2_measure_peak(int which, h2_stream_t stream, double *value);
+
 /* Failure-detection self-test of the tensor-core sketch: one small launch in
  * which the producer warp withholds the first tile, so the waits of the
  * other warps run out (0.2 s bound each), followed by a normal launch of the

@@ -67,6 +67,7 @@ SIGNATURES = {
     "h2_last_error": (C.c_char_p, []),
     "h2_kernel_launches": (C.c_int64, []),
     "h2_device_allocations": (C.c_int64, []),
+    "h2_measure_peak": (C.c_int, [C.c_int, C.c_void_p, C.POINTER(C.c_double)]),
     "h2_trim_memory": (None, []),
     "h2_selftest_wait_timeout": (C.c_int, [C.c_void_p]),
     "h2_build_cluster_tree": (i32, [vp, i64, i32, i32, dbl, vp, C.POINTER(vp)]),
