@@ -26,20 +26,14 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "H2 build time & points/s at tol, mixed vs FP64 on 1 GB300; % HBM/compute roofline"
-SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
-FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.55
-FP64_PEAK_TFLOPS = 1.25
-# The tensor-core sketch is bound by entry generation on the special-function
-# units: a Matern-3/2 entry takes two of their operations (square root and
-# exp2); 16 SFU lanes per SM (4 per sub-partition).
-SFU_LANES, SFU_OPS_PER_PAIR = 16, 2
-SFU_PEAK_GPAIRS = SMS * SFU_LANES * SM_MAX_MHZ * 1e6 / SFU_OPS_PER_PAIR / 1e9   # 2516.5
 WORKLOAD_DESC = ("c2: N=131072 uniform [0,1]^3, Matern-3/2 l=0.1 + 1e-4 nugget, leaf 64, "
-                 "eta 0.7, tol 1e-6, adaptive sampling up to 256 columns (schedule in config.schedule), "
+                 "eta 0.7, tol 1e-6, adaptive sampling up to 256 columns (schedule in the line's schedule key), "
                  "fused kernel-summation sketch")
 
 
@@ -48,39 +42,138 @@ def log(*a):
 
 
 # ---------------------------------------------------------------- CPU oracle leg
-def oracle_sample(n_sample: int) -> dict:
-    """Full oracle build of the same workload family at n_sample points.
-    Runs in a child process with single-threaded BLAS (cores = 1)."""
+# The oracle's build of the benchmark workload takes minutes on one core, so
+# it is timed on a bounded sample of that workload:
+#  * the sketch (most of the oracle's time): its direct kernel sums for a
+#    seeded sample of rows of the full 131072-point problem, over the column
+#    blocks of the oracle's sample schedule; every row costs the same, so the
+#    full sketch takes (N / rows) times as long;
+#  * the rest (tree, lists, near field, QR tests, IDs, couplings): full oracle
+#    builds of the same workload family at three smaller N (sketch excluded,
+#    the samples from the dense matrix), fitted as a*N^b and evaluated at N.
+# The sketch rows run once on one core and once spread over all host cores
+# (spawned worker processes, as the paper's OpenMP code spreads the sketch).
+FIT_SIZES = (4096, 8192, 16384)
+# Columns the construction of the full 131072-point workload samples with the
+# 32/+16 schedule: the first 32 and three rounds of 16, as its FP64 build (the
+# oracle's arithmetic, rank for rank) reports; smaller members of the family
+# stop earlier, so the sketch sample takes the full size's column blocks.
+FULL_D_FINAL = 80
+_W_STATE = {}
+
+
+def _worker_init(cmax):
+    from paper_2506_16759_gb300 import workloads as W
+    w = W.config("c2")
+    _W_STATE["X"] = w.points()
+    _W_STATE["om"] = w.omega(cmax)
+    _W_STATE["w"] = w
+
+
+def _worker_rows(task):
+    from oracle import h2_oracle as O
+    rows, blocks = task
+    X, om, w = _W_STATE["X"], _W_STATE["om"], _W_STATE["w"]
+    t0 = time.perf_counter()
+    for c0, c1 in blocks:
+        O.ksum_rows(X, w.kernel, w.params, np.ascontiguousarray(om[:, c0:c1]), rows, chunk=64)
+    return time.perf_counter() - t0
+
+
+def construction_fit(sizes=FIT_SIZES) -> dict:
+    """Oracle builds of the benchmark family at `sizes` (sketch excluded)."""
     from oracle import h2_oracle as O
     from paper_2506_16759_gb300 import workloads as W
-    w = W.scaled(W.config("c2"), n_sample)
-    X = w.points()
-    om = w.omega()
-    t0 = time.perf_counter()
-    t = O.build_cluster_tree(X, w.leaf_size)
-    lists = O.dual_traversal(t, w.eta)
-    t_tree = time.perf_counter() - t0
-    h = O.build_h2(t, lists, w.kernel, w.params, w.tol, om,
-                   O.ksum_sampler(X, w.kernel, w.params, 512), w.d0, w.d_inc, w.d_max)
-    return {"n": n_sample, "t_tree": t_tree, "t_sketch": h.timings["sketch_s"],
-            "t_construct": h.timings["construct_s"], "d_final": h.d_final}
+    pts = []
+    for n in sizes:
+        w = W.scaled(W.config("c2"), n)
+        X = w.points()
+        t0 = time.perf_counter()
+        t = O.build_cluster_tree(X, w.leaf_size)
+        lists = O.dual_traversal(t, w.eta)
+        t_tree = time.perf_counter() - t0
+        A = O.dense_matrix(X, w.kernel, w.params)
+        h = O.build_h2(t, lists, w.kernel, w.params, w.tol, w.omega(), O.dense_sampler(A),
+                       w.d0, w.d_inc, w.d_max)
+        del A
+        pts.append({"n": n, "s": t_tree + h.timings["construct_s"], "d_final": h.d_final})
+    ln = np.log([p["n"] for p in pts])
+    lt = np.log([p["s"] for p in pts])
+    b, a = np.polyfit(ln, lt, 1)
+    resid = float(np.max(np.abs(lt - (a + b * ln))))
+    return {"points": pts, "exponent": float(b), "log_coef": float(a),
+            "max_log_residual": resid, "d_final": pts[-1]["d_final"]}
 
 
-def run_oracle_child(n_sample: int) -> dict:
+def sketch_blocks(d_final, d0=32, d_inc=16):
+    return [(0, d0)] + [(c, c + d_inc) for c in range(d0, d_final, d_inc)]
+
+
+def sketch_sample(rows_n, d_final, pool=None, workers=1, seed=0) -> dict:
+    """Seconds for the oracle's sketch of `rows_n` sampled rows of the full
+    workload (serially, or split over `workers` pool processes)."""
+    from paper_2506_16759_gb300 import workloads as W
+    n = W.config("c2").n
+    rows = np.sort(np.random.default_rng(seed).choice(n, rows_n, replace=False))
+    blocks = sketch_blocks(d_final)
+    if pool is None:
+        _worker_init(blocks[-1][1])
+        t = _worker_rows((rows, blocks))
+    else:
+        parts = np.array_split(rows, workers)
+        t0 = time.perf_counter()
+        pool.map(_worker_rows, [(p, blocks) for p in parts])
+        t = time.perf_counter() - t0
+    return {"rows": rows_n, "s": t, "full_s": t * n / rows_n, "blocks": len(blocks),
+            "columns": blocks[-1][1]}
+
+
+def make_pool(d_final):
+    import multiprocessing as mp
+    workers = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    return ctx.Pool(workers, initializer=_worker_init, initargs=(sketch_blocks(d_final)[-1][1],)), \
+        workers
+
+
+def oracle_baseline(rows_serial: int, rows_parallel: int) -> dict:
+    """The CPU oracle's rate on the benchmark workload (runs in a child
+    process with single-threaded BLAS)."""
+    from paper_2506_16759_gb300 import workloads as W
+    n = W.config("c2").n
+    fit = construction_fit()
+    rest = math.exp(fit["log_coef"]) * n ** fit["exponent"]
+    ser = sketch_sample(rows_serial, FULL_D_FINAL)
+    pool, workers = make_pool(FULL_D_FINAL)
+    with pool:
+        pool.map(_worker_rows, [(np.arange(1), [(0, 1)])] * workers)   # workers loaded
+        par = sketch_sample(rows_parallel, FULL_D_FINAL, pool, workers)
+    return {"n": n, "fit": fit, "rest_s": rest, "serial": ser, "parallel": par,
+            "workers": workers,
+            "secs_1": ser["full_s"] + rest, "secs_p": par["full_s"] + rest}
+
+
+def run_oracle_child(*args) -> dict:
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample",
-                          str(n_sample)], capture_output=True, text=True, env=env, cwd=ROOT)
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), *args],
+                         capture_output=True, text=True, env=env, cwd=ROOT)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
-def scaled_oracle_rate(r: dict, n_full: int) -> tuple[float, float]:
-    """Oracle seconds for the full workload from a sample: the sketch scales as
-    N^2 (direct summation), tree and construction as N."""
-    f = n_full / r["n"]
-    secs = r["t_sketch"] * f * f + (r["t_construct"] + r["t_tree"]) * f
-    return n_full / secs, secs
+def describe_baseline(r: dict) -> str:
+    f = r["fit"]
+    pts = ", ".join(f"N={p['n']}: {p['s']:.2f}s" for p in f["points"])
+    return (f"sketch: the oracle's direct kernel sums for {r['parallel']['rows']} seeded rows of "
+            f"the full N={r['n']} problem over its {r['parallel']['blocks']} column blocks "
+            f"({r['parallel']['columns']} columns) on {r['workers']} processes "
+            f"({r['parallel']['s']:.2f}s; one core, {r['serial']['rows']} rows: "
+            f"{r['serial']['s']:.2f}s), scaled by N/rows; the rest of the build: oracle builds "
+            f"at {pts} (sketch excluded), fitted as a*N^b with b={f['exponent']:.3f} "
+            f"(max log residual {f['max_log_residual']:.3f}) -> {r['rest_s']:.1f}s at N; "
+            f"estimated build {r['secs_p']:.0f}s on {r['workers']} cores, "
+            f"{r['secs_1']:.0f}s on one")
 
 
 # ---------------------------------------------------------------- clocks
@@ -179,6 +272,256 @@ def job_throughput(world: int, n_per_rank: int, steps: int, max_total_ms: float)
 
 
 # ---------------------------------------------------------------- GPU arm
+PEAK_NAMES = ("fp64_tflops", "fp32_tflops", "sfu_ex2_gops", "f16_tc_tflops", "tf32_tc_tflops",
+              "sfu_sqrt_gops", "sfu_rsqrt_gops")
+
+
+def measure_peaks() -> dict:
+    """Measured pipe throughputs of this device (h2_measure_peak) plus the
+    measured HBM copy bandwidth and cuBLAS BF16 rate."""
+    import ctypes
+    import torch
+    from paper_2506_16759_gb300 import _lib
+    L = _lib.lib()
+    out = {}
+    for w, name in enumerate(PEAK_NAMES):
+        v = ctypes.c_double()
+        st = L.h2_measure_peak(w, torch.cuda.current_stream().cuda_stream, ctypes.byref(v))
+        out[name] = v.value if st == 0 else None
+    mp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(mp):
+        d = json.load(open(mp))
+        out["hbm_gbs"] = d.get("hbm_gbs")
+        out["bf16_tflops"] = d.get("bf16_tflops")
+        out["hbm_source"] = "MEASURED_PEAKS.json (STREAM-style copy)"
+    else:
+        out["hbm_gbs"], out["bf16_tflops"] = 6800.0, 1900.0
+        out["hbm_source"] = "fallback (no MEASURED_PEAKS.json)"
+    return out
+
+
+# Special-function operations per kernel entry in the tensor-core sketch:
+# square root and exp2 (exponential, Matern), exp2 (Gaussian), reciprocal
+# square root (Laplace, Helmholtz; its cosine is a polynomial).
+SFU_OPS = {0: ("sqrt", "ex2"), 1: ("sqrt", "ex2"), 2: ("ex2",), 3: ("rsqrt",), 6: ("rsqrt",)}
+
+
+def sfu_pair_peak(kid: int, peaks: dict):
+    """Entries per second (G) the special-function units allow: they share one
+    pipe, so the times of an entry's operations add."""
+    ops = SFU_OPS.get(kid)
+    if not ops or any(not peaks.get(f"sfu_{o}_gops") for o in ops):
+        return None, None
+    per = sum(1.0 / peaks[f"sfu_{o}_gops"] for o in ops)
+    src = " + ".join(f"1/{peaks[f'sfu_{o}_gops']:.0f} ({o})" for o in ops)
+    return 1.0 / per, f"1 / ({src}) G entries/s from the measured rates (h2_measure_peak)"
+
+
+def sketch_roofline(stats: list, kid: int, prec: str, peaks: dict, timed_alone: bool) -> dict:
+    """Roofline of the fused sketch over the launches of instrumented builds:
+    entries per second against the special-function-unit bound (mixed), or
+    FP64 flops against the measured FP64 FMA rate."""
+    ms = sum(s["ms_sketch_kernel"] for s in stats)
+    n = sum(s["sketch_launches"] for s in stats)
+    pairs = sum(s["sketch_pairs"] for s in stats)
+    flops = sum(s["sketch_flops"] for s in stats)
+    if ms <= 0:
+        return None
+    peak, src = sfu_pair_peak(kid, peaks)
+    if prec == "mixed" and peak:
+        achieved = pairs / (ms * 1e-3) / 1e9
+        return {"kernel": "k_ksum_tc (fused kernel summation: entries on the CUDA cores and "
+                          "special-function units, contracted on tcgen05 with two-part operands)",
+                "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s",
+                "frac": achieved / peak, "peak_source": src,
+                "algorithmic_tflops": flops / (ms * 1e-3) / 1e12, "launches": n,
+                "avg_launch_ms": ms / n if n else None}
+    achieved = flops / (ms * 1e-3) / 1e12
+    peak = peaks.get("fp64_tflops") if prec == "fp64" else peaks.get("fp32_tflops")
+    return {"kernel": "k_ksum64 (fused kernel summation, FP64)" if prec == "fp64" else
+            "k_ksum32 (fused kernel summation, FP32 CUDA cores)", "bound": "alu",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if peak else None,
+            "peak_source": "measured FMA rate (h2_measure_peak)",
+            "flops_per_pair": "2*columns + 10", "launches": n,
+            "avg_launch_ms": ms / n if n else None}
+
+
+def timed(fn, steps, flush):
+    """CUDA-event milliseconds of `steps` calls of fn() (L2 flushed before each)."""
+    import torch
+    out = []
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
+def extra_configs(dev, flush, peaks, names, fp64_steps) -> dict:
+    """The other workloads: mixed and FP64 build times, points/s, errors and
+    the roofline of each one's dominant kernel."""
+    import torch
+    from paper_2506_16759_gb300 import api
+    from paper_2506_16759_gb300 import workloads as W
+    res = {}
+
+    def probe_err(h, X, kid, params, n):
+        G = torch.from_numpy(W.gaussian_probe(n, 8, 3)).to(dev)
+        AG = api.ksum_sketch(X, kid, params, G, prec="fp64")
+        return float(torch.linalg.norm(h.matvec(G) - AG) / torch.linalg.norm(AG))
+
+    def run_single(name, w, sched, extra_kw=None, err_fn=None, roof_fn=None, tree=None):
+        X = torch.from_numpy(w.points()).to(dev)
+        kw = dict(extra_kw or {})
+        entry = {"n": w.n, "tol": w.tol}
+        for prec in ("mixed", "fp64"):
+            sc = sched if prec == "mixed" else {"d0": w.d0, "d_inc": w.d_inc}
+            holder = {}
+
+            def build(timing=False, seed=0):
+                tr = tree if tree is not None else api.ClusterTree(X, w.leaf_size, w.eta)
+                holder["h"] = api.H2Matrix.build(tr, w.kernel, w.params, w.tol, prec=prec,
+                                                 seed=seed, sketch=w.sketch, timing=timing,
+                                                 d0=sc["d0"], d_inc=sc["d_inc"], d_max=w.d_max,
+                                                 **kw)
+                holder["t"] = tr
+            steps = 3 if prec == "mixed" else fp64_steps
+            if steps <= 0:
+                continue
+            build(seed=90)
+            ms = statistics.mean(timed(lambda: build(seed=91), steps, flush))
+            flush.zero_()
+            build(timing=True, seed=92)
+            st = holder["h"].stats()
+            e = {"ms_per_build": ms, "points_per_s": w.n / (ms * 1e-3), "steps": steps,
+                 "schedule": sc, "d_final": st["d_final"], "rounds": st["rounds"],
+                 "rank_range": [st["rank_min"], st["rank_max"]],
+                 "memory_bytes": st["bytes_dense"] + st["bytes_coupling"] + st["bytes_basis"],
+                 "phases_ms": {p: st[f"ms_{p}"] for p in ("sketch", "nearfield", "qr", "id",
+                                                         "upsweep", "coupling", "bsr")}}
+            e["rel_error"] = err_fn(holder["h"], X) if err_fn else None
+            e["roofline"] = roof_fn(st, prec) if roof_fn else None
+            entry[prec] = e
+            holder.clear()
+        res[name] = entry
+
+    if "c1" in names:
+        w = W.config("c1")
+        Xh = w.points()
+        from oracle import h2_oracle as O   # noqa: F401  (not used: A comes from the library)
+        X = torch.from_numpy(Xh).to(dev)
+        idx = torch.arange(w.n, dtype=torch.int32, device=dev)
+        A = api.entry_block(X, w.kernel, w.params, idx, idx)
+
+        def dense_roof(st, prec):
+            cols = st["sketch_columns"]
+            flops = 2.0 * w.n * w.n * cols
+            ms = st["ms_sketch"]
+            pk = peaks.get("fp64_tflops")
+            a = flops / (ms * 1e-3) / 1e12 if ms > 0 else None
+            return {"kernel": "k_dense_gemm64 (dense sketch Y = A Omega, FP64)", "bound": "alu",
+                    "achieved": a, "peak": pk, "unit": "TFLOP/s",
+                    "frac": a / pk if a and pk else None,
+                    "note": "sketch phase time (includes the permutations of Omega and Y)"}
+
+        def dense_err(h, _X):
+            G = torch.from_numpy(W.gaussian_probe(w.n, 8, 3)).to(dev)
+            AG = A @ G
+            return float(torch.linalg.norm(h.matvec(G) - AG) / torch.linalg.norm(AG))
+        run_single("c1", w, {"d0": w.d0, "d_inc": w.d_inc}, {"dense_a": A}, dense_err,
+                   dense_roof)
+        del A
+    if "c3" in names:
+        w = W.config("c3")
+
+        def c3_roof(st, prec):
+            return sketch_roofline([st], w.kernel, prec, peaks, False)
+        run_single("c3", w, {"d0": 64, "d_inc": 32}, None,
+                   lambda h, X: probe_err(h, X, w.kernel, w.params, w.n), c3_roof)
+    if "c5" in names:
+        insts = W.c5_instances()
+        Xs = [torch.from_numpy(i.points()).to(dev) for i in insts]
+        ntot = sum(i.n for i in insts)
+        entry = {"instances": len(insts), "n_total": ntot, "tol": 1e-6}
+        for prec in ("mixed", "fp64"):
+            holder = {}
+            steps = 3 if prec == "mixed" else fp64_steps
+            if steps <= 0:
+                continue
+
+            def build(timing=False, seed=0):
+                trees = [api.ClusterTree(X, i.leaf_size, i.eta) for X, i in zip(Xs, insts)]
+                holder["h"] = api.H2Matrix.build_batched(
+                    trees, [i.kernel for i in insts], [i.params for i in insts],
+                    [i.tol for i in insts], prec=prec, seed=seed, timing=timing)
+            build(seed=80)
+            ms = statistics.mean(timed(lambda: build(seed=81), steps, flush))
+            flush.zero_()
+            build(timing=True, seed=82)
+            st = holder["h"].stats()
+            G = torch.from_numpy(W.gaussian_probe(ntot, 8, 3)).to(dev)
+            y = holder["h"].matvec(G)
+            errs, off = [], 0
+            for X, i in zip(Xs, insts):
+                AG = api.ksum_sketch(X, i.kernel, i.params, G[off:off + i.n], prec="fp64")
+                errs.append(float(torch.linalg.norm(y[off:off + i.n] - AG) / torch.linalg.norm(AG)))
+                off += i.n
+            entry[prec] = {"ms_per_build": ms, "points_per_s": ntot / (ms * 1e-3),
+                           "steps": steps, "max_rel_error": max(errs),
+                           "d_final": st["d_final"], "rank_range": [st["rank_min"], st["rank_max"]],
+                           "kernel_launches": st["kernel_launches"],
+                           "roofline": sketch_roofline([st], 0, prec, peaks, False),
+                           "step": "64 trees + one batched build (leaf 64, 32/+16 samples)"}
+            holder.clear()
+        res["c5"] = entry
+    if "c4" in names:
+        w = W.config("c4")
+        X = torch.from_numpy(w.points()).to(dev)
+        tree = api.ClusterTree(X, w.leaf_size, w.eta)
+        t0 = time.perf_counter()
+        ops = [api.H2Matrix.build(tree, k, p, w.extra["operand_tol"], prec="mixed", seed=3 + q)
+               for q, (k, p) in enumerate(w.extra["operands"])]
+        torch.cuda.synchronize()
+        op_s = time.perf_counter() - t0
+        op_bytes = 0
+        for o in ops:
+            so = o.stats()
+            op_bytes += so["bytes_dense"] + so["bytes_coupling"] + so["bytes_basis"]
+
+        def c4_err(h, _X):
+            G = torch.from_numpy(W.gaussian_probe(w.n, 8, 3)).to(dev)
+            AG = ops[0].matvec(G) + ops[1].matvec(G)
+            return float(torch.linalg.norm(h.matvec(G) - AG) / torch.linalg.norm(AG))
+
+        def c4_roof(st, prec):
+            calls = 1 + st["rounds"]
+            ms = st["ms_sketch"]
+            cols = st["sketch_columns"]
+            byts = op_bytes * calls + 2.0 * w.n * cols * 8 * len(ops)
+            a = byts / (ms * 1e-3) / 1e9 if ms > 0 else None
+            pk = peaks.get("hbm_gbs")
+            return {"kernel": "operand H2 matvecs (k_bsr_* block-sparse products, k_basis_* "
+                              "basis products)", "bound": "hbm", "achieved": a, "peak": pk,
+                    "unit": "GB/s", "frac": a / pk if a and pk else None,
+                    "traffic": None,
+                    "algorithmic_bytes": "operand blocks (D, B, U/E) once per sketch call + "
+                                         "x and y panels in FP64",
+                    "note": "sketch phase time: every operand matvec of the build"}
+        run_single("c4", w, {"d0": 80, "d_inc": 16}, {"operands": ops}, c4_err, c4_roof,
+                   tree=tree)
+        res["c4"]["operands"] = {"tol": w.extra["operand_tol"], "prec": "mixed",
+                                 "build_s": op_s, "bytes": op_bytes}
+        del ops
+    return res
+
+
 def main_gpu(args):
     import numpy as np
     import torch
@@ -205,18 +548,16 @@ def main_gpu(args):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
-            r = run_oracle_child(args.cpu_sample)
-            rate, secs = scaled_oracle_rate(r, W.config("c2").n)
-            cpu = {"value": rate, "unit": "points/s", "cores": 1, "kind": "oracle",
-                   "sample": (f"full oracle build of the same workload at N={r['n']} "
-                              f"(sketch {r['t_sketch']:.1f}s, construction "
-                              f"{r['t_construct']:.1f}s, tree {r['t_tree']:.1f}s, 1 thread); "
-                              f"scaled to N=131072 as sketch*(N/n)^2 + rest*(N/n): "
-                              f"{secs:.0f}s per build")}
+            r = run_oracle_child("--oracle-baseline", str(args.cpu_rows), str(args.cpu_rows_par))
+            n = r["n"]
+            cpu = {"value": n / r["secs_p"], "unit": "points/s", "cores": r["workers"],
+                   "kind": "oracle", "sample": describe_baseline(r),
+                   "single_core": {"value": n / r["secs_1"], "unit": "points/s", "cores": 1}}
         except Exception as e:  # the baseline must not sink the GPU line
-            cpu = {"value": None, "unit": "points/s", "cores": 1, "kind": "oracle",
+            cpu = {"value": None, "unit": "points/s", "cores": None, "kind": "oracle",
                    "sample": f"failed: {e}"}
 
+    peaks = measure_peaks() if rank == 0 else {}
     w = W.config("c2")
     X = torch.from_numpy(w.points()).to(dev)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
@@ -279,19 +620,6 @@ def main_gpu(args):
     value = job_throughput(world, w.n, args.steps, total_ms)
     log(f"[bench] {prec}: {ms_per_step:.1f} ms/step, {value:.3e} points/s")
 
-    # roofline of the dominant kernel (fused kernel summation)
-    ksum_ms = sum(s["ms_sketch_kernel"] for s in stats)
-    ksum_n = sum(s["sketch_launches"] for s in stats)
-    ksum_flops = sum(s["sketch_flops"] for s in stats)
-    ksum_pairs = sum(s["sketch_pairs"] for s in stats)
-    if prec == "mixed":
-        # entries generated per second against the special-function-unit bound
-        achieved = ksum_pairs / (ksum_ms * 1e-3) / 1e9 if ksum_ms > 0 else None
-        peak, r_unit = SFU_PEAK_GPAIRS, "Gpair/s"
-    else:
-        achieved = ksum_flops / (ksum_ms * 1e-3) / 1e12 if ksum_ms > 0 else None
-        peak, r_unit = FP64_PEAK_TFLOPS, "TFLOP/s"
-    ksum_tflops = ksum_flops / (ksum_ms * 1e-3) / 1e12 if ksum_ms > 0 else None
     phases = {p: statistics.mean(s[f"ms_{p}"] for s in stats)
               for p in ("sketch", "nearfield", "qr", "id", "upsweep", "coupling", "bsr", "total")}
     last = stats[-1]
@@ -301,20 +629,13 @@ def main_gpu(args):
     if rank == 0 and tuned is not None:
         base = {"d0": w.d0, "d_inc": w.d_inc, "prec": prec}
         step(500, prec, schedule=base)
-        tb = []
-        for k in range(3):
-            flush.zero_()
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record()
-            step(600 + k, prec, schedule=base)
-            e1.record()
-            torch.cuda.synchronize()
-            tb.append(e0.elapsed_time(e1))
+        tb = timed(lambda: step(600, prec, schedule=base), 3, flush)
         untuned = dict(base, ms_per_step=statistics.mean(tb),
                        value=w.n / (statistics.mean(tb) / 1e3))
     if rank == 0:
+        roof = sketch_roofline(stats, w.kernel, sched["prec"], peaks, False)
+        if roof is not None:
+            roof["traffic"] = profiled_traffic(prec)
         # accuracy: ||(A_H2 - A) G|| / ||A G|| with A G by FP64 direct summation
         _, h = step(7, prec, timing=False)
         G = torch.from_numpy(W.gaussian_probe(w.n, 8, 3)).to(dev)
@@ -325,32 +646,30 @@ def main_gpu(args):
         fp64 = None
         if args.fp64_steps > 0:
             step(2000, "fp64")
-            t64 = []
-            for k in range(args.fp64_steps):
-                flush.zero_()
-                torch.cuda.synchronize()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record()
-                _, h64 = step(3000 + k, "fp64")
-                e1.record()
-                torch.cuda.synchronize()
-                t64.append(e0.elapsed_time(e1))
+            holder = {}
+
+            def run64():
+                holder["h"] = step(3000, "fp64")[1]
+            t64 = timed(run64, args.fp64_steps, flush)
+            h64 = holder["h"]
             s64 = h64.stats()
             err64 = float(torch.linalg.norm(h64.matvec(G) - AG) / torch.linalg.norm(AG))
+            flush.zero_()
+            _, h64t = step(3100, "fp64", timing=True)
             fp64 = {"value": w.n / (statistics.mean(t64) / 1e3), "unit": "points/s",
                     "ms_per_step": statistics.mean(t64), "steps": len(t64), "warmup": 1,
                     "rel_error": err64, "d_final": s64["d_final"],
                     "rank_range": [s64["rank_min"], s64["rank_max"]],
-                    "sketch_kernel_tflops": (s64["sketch_flops"] / (s64["ms_sketch_kernel"] * 1e-3)
-                                             / 1e12 if s64["ms_sketch_kernel"] > 0 else None),
-                    "sketch_kernel_peak_tflops": FP64_PEAK_TFLOPS}
-            del h64
+                    "roofline": sketch_roofline([h64t.stats()], w.kernel, "fp64", peaks, False)}
+            del h64, h64t
+            holder.clear()
 
-        # end to end through the C ABI with host buffers
+        # end to end through the C ABI with host buffers: points in, the
+        # level-1 ranks and skeletons out (the H2 matrix itself stays on the
+        # device, where its matvec is used)
         Xh = torch.from_numpy(w.points()).pin_memory()
         e2e_t = []
-        for k in range(max(2, min(args.steps, 5))):
+        for k in range(args.steps):
             flush.zero_()
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -370,35 +689,27 @@ def main_gpu(args):
         bi = Xh.numel() * 8
         bo = int(ranks.nbytes + skel.nbytes)
 
-        traffic = profiled_traffic(prec)
+        extras = {}
+        if args.configs:
+            names = [c for c in args.configs.split(",") if c]
+            log(f"[bench] other workloads: {names}")
+            extras = extra_configs(dev, flush, peaks, names, args.fp64_steps)
+
         result = {
             "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if prec == "mixed" else "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_DESC, "prec": prec, "schedule": sched,
-                       "omega": "Philox4x32-10 on device",
-                       "l2": "flushed between timed steps (512 MiB write)",
-                       "step": "tree + lists + H2 build, device-resident points"},
-            "roofline": {"kernel": ("k_ksum_tc (fused kernel summation: entries generated on "
-                                    "the CUDA cores and special-function units, contracted on "
-                                    "tcgen05 with two-part FP16 operands)")
-                         if sched["prec"] == "mixed" else
-                         ("k_ksum32 (fused kernel summation, FP32 CUDA cores)"
-                          if sched["prec"] == "mixed_simt" else
-                          "k_ksum64 (fused kernel summation, FP64)"),
-                         "bound": "alu", "achieved": achieved, "peak": peak, "unit": r_unit,
-                         "frac": achieved / peak if achieved else None,
-                         "traffic": traffic,
-                         "peak_source": ("152 SMs x 16 SFU lanes x 2070 MHz / 2 SFU operations per "
-                                         "Matern entry (unit counts and max clock)"
-                                         if prec == "mixed" else "nominal GB300 FP64 1.25 TFLOP/s"),
-                         "algorithmic_tflops": ksum_tflops,
-                         "flops_per_pair": "2*columns + 10", "launches": ksum_n,
-                         "avg_launch_ms": ksum_ms / ksum_n if ksum_n else None},
+            "config": bench_config(),
+            "prec": prec, "schedule": sched,
+            "roofline": roof,
+            "peaks": peaks,
             "cpu_baseline": cpu,
             "e2e": {"value": w.n / (e2e_ms / 1e3), "unit": "points/s",
-                    "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": e2e_ms},
+                    "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": e2e_ms,
+                    "steps": len(e2e_t),
+                    "result": "level-1 ranks and skeleton indices read back; the H2 matrix "
+                              "stays on the device"},
             "gpu_launches": int(launches),
             "clocks": clk,
             "rel_error": err_mixed,
@@ -410,6 +721,7 @@ def main_gpu(args):
             "d_final": last["d_final"], "rounds": last["rounds"],
             "rank_range": [last["rank_min"], last["rank_max"]],
             "memory_bytes": last["bytes_dense"] + last["bytes_coupling"] + last["bytes_basis"],
+            "configs": extras,
         }
         print(json.dumps(result), flush=True)
     if world > 1:
@@ -418,39 +730,67 @@ def main_gpu(args):
     return result
 
 
+def bench_config() -> dict:
+    """The workload every arm of the benchmark measures (identical keys)."""
+    return {"workload": WORKLOAD_DESC,
+            "l2": "flushed between timed steps (512 MiB write)",
+            "step": "tree + lists + H2 build from device-resident points"}
+
+
 # ---------------------------------------------------------------- reference arm
 def main_reference(args):
-    """The CPU oracle timed on the host cores on a bounded sample of the same
-    workload, scaled to the full point count (rank 0 only)."""
+    """The CPU oracle on the host cores (rank 0 only).  Each step times the
+    oracle's sketch of sampled rows of the full workload on all cores and an
+    oracle build of the same family at N=8192 (sketch excluded), and scales
+    them to the full build: rows by N/rows, the build by (N/8192)^b with b
+    fitted in the warm-up from builds at three sizes."""
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
         return
-    from paper_2506_16759_gb300 import workloads as W
-    n_full = W.config("c2").n
-    for _ in range(args.warmup):
-        run_oracle_child(args.ref_sample)
-    secs = []
-    last = None
-    for _ in range(args.steps):
-        last = run_oracle_child(args.ref_sample)
-        secs.append(scaled_oracle_rate(last, n_full)[1])
-    mean = statistics.mean(secs)
-    value = n_full / mean
+    r = run_oracle_child("--oracle-reference", str(args.steps), str(max(args.warmup, 0)),
+                         str(args.ref_rows))
+    value = r["n"] / statistics.mean(r["secs"])
     line = {
         "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(r["wall"]) * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "impl": "reference",
-        "config": {"workload": WORKLOAD_DESC, "prec": "fp64"},
-        "cpu_baseline": {"value": value, "unit": "points/s", "cores": 1, "kind": "oracle",
-                         "sample": (f"each step a full oracle build at N={last['n']} of the same "
-                                    "workload, scaled to N=131072 as sketch*(N/n)^2 + "
-                                    "rest*(N/n); 1 thread")},
+        "config": bench_config(), "prec": "fp64",
+        "cpu_baseline": {"value": value, "unit": "points/s", "cores": r["workers"],
+                         "kind": "oracle",
+                         "sample": (f"each step: the oracle's sketch of {args.ref_rows} seeded "
+                                    f"rows of the full problem on {r['workers']} processes, "
+                                    "scaled by N/rows, plus an oracle build at N=8192 (sketch "
+                                    f"excluded) scaled by (N/8192)^{r['exponent']:.3f} (exponent "
+                                    "fitted in the warm-up at N=4096/8192/16384); ms_per_step is "
+                                    "the measured wall time of one such step, value the "
+                                    "estimated rate of the full build")},
         "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def oracle_reference_steps(steps: int, warmup: int, rows: int) -> dict:
+    """Child process of the reference arm."""
+    from paper_2506_16759_gb300 import workloads as W
+    n = W.config("c2").n
+    fit = construction_fit()
+    b = fit["exponent"]
+    pool, workers = make_pool(FULL_D_FINAL)
+    secs, wall = [], []
+    with pool:
+        pool.map(_worker_rows, [(np.arange(1), [(0, 1)])] * workers)
+        for k in range(max(warmup - 1, 0) + steps):
+            t0 = time.perf_counter()
+            sk = sketch_sample(rows, FULL_D_FINAL, pool, workers, seed=k)
+            c = construction_fit((8192,))
+            el = time.perf_counter() - t0
+            if k >= max(warmup - 1, 0):
+                secs.append(sk["full_s"] + c["points"][0]["s"] * (n / 8192) ** b)
+                wall.append(el)
+    return {"n": n, "secs": secs, "wall": wall, "workers": workers, "exponent": b}
 
 
 def main_kernel_only(args):
@@ -585,12 +925,20 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=1)
-    ap.add_argument("--cpu-sample", type=int, default=8192)
-    ap.add_argument("--ref-sample", type=int, default=4096)
+    ap.add_argument("--cpu-rows", type=int, default=64,
+                    help="sketch rows of the one-core oracle sample")
+    ap.add_argument("--cpu-rows-par", type=int, default=1024,
+                    help="sketch rows of the all-cores oracle sample")
+    ap.add_argument("--ref-rows", type=int, default=512,
+                    help="sketch rows per step of the reference arm")
+    ap.add_argument("--configs", default="c1,c3,c5,c4",
+                    help="other workloads reported beside the headline ('' = none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="time the workload's 32/+16 sample schedule instead of the tuned one")
-    ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-baseline", nargs=2, type=int, default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-reference", nargs=3, type=int, default=None,
+                    help=argparse.SUPPRESS)
     ap.add_argument("--kernel-only", default="", choices=["", "ksum", "build", "paper"],
                     help="time only the fused sketch, builds at --n points (for profiling), "
                          "or a paper kernel problem with the H2-matvec sampler")
@@ -601,8 +949,11 @@ def main():
     if args.kernel_only:
         main_kernel_only(args)
         return
-    if args.oracle_sample:
-        print(json.dumps(oracle_sample(args.oracle_sample)))
+    if args.oracle_baseline:
+        print(json.dumps(oracle_baseline(*args.oracle_baseline)))
+        return
+    if args.oracle_reference:
+        print(json.dumps(oracle_reference_steps(*args.oracle_reference)))
         return
     if args.impl == "reference":
         main_reference(args)

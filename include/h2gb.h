@@ -333,7 +333,8 @@ h2_status h2_batched_qr_mindiag_static(int count, const int32_t *m, const int32_
  * roofline fractions: which = 0 FP64 FMA (TFLOP/s), 1 FP32 FMA (TFLOP/s),
  * 2 exp2 on the special-function units (G operations/s), 3 dense tcgen05
  * products of FP16 operands with FP32 accumulation (TFLOP/s), 4 the same with
- * TF32 operands (TFLOP/s).  Each probe runs a fixed amount of independent work
+ * TF32 operands (TFLOP/s), 5 square root and 6 reciprocal square root on the
+ * special-function units (G operations/s).  Each probe runs a fixed amount of independent work
  * on every SM (tens of milliseconds in all) and reports the best of five
  * timed launches.  Not part of the construction. */
 h2_status h2_measure_peak(int which, h2_stream_t stream, double *value);

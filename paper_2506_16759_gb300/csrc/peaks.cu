@@ -35,14 +35,27 @@ __global__ void __launch_bounds__(256) k_fma_peak(int iters, T a, T b, T *sink) 
   if (s == (T)-12345.0) sink[threadIdx.x] = s;
 }
 
-// exp2 on the special-function units: x <- 2^-x stays in [0.5, 1].
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// One special-function operation per step and chain: OP 0 exp2 (x <- 2^-x
+// stays in [0.5, 1]), 1 square root and 2 reciprocal square root (x <-
+// op(x + 1) stays in [1, 2]).
+template <int OP>
 __global__ void __launch_bounds__(256) k_sfu_peak(int iters, float *sink) {
   float x[kChains];
 #pragma unroll
   for (int c = 0; c < kChains; ++c) x[c] = 0.5f + 0.01f * c;
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
-    for (int c = 0; c < kChains; ++c) x[c] = ex2_approx(-x[c]);
+    for (int c = 0; c < kChains; ++c) {
+      if constexpr (OP == 0) x[c] = ex2_approx(-x[c]);
+      else if constexpr (OP == 1) x[c] = sqrt_approx(x[c] + 1.f);
+      else x[c] = rsqrt_approx(x[c] + 1.f);
+    }
   }
   float s = 0.f;
 #pragma unroll
@@ -146,7 +159,7 @@ double best_ms(cudaStream_t s, int reps, F &&launch) {
 using namespace h2;
 
 extern "C" h2_status h2_measure_peak(int which, h2_stream_t stream, double *value) {
-  if (!value || which < 0 || which > 4) return fail(H2_ERR_ARG, "h2_measure_peak: bad arguments");
+  if (!value || which < 0 || which > 6) return fail(H2_ERR_ARG, "h2_measure_peak: bad arguments");
   try {
     cudaStream_t s = (cudaStream_t)stream;
     const int sms = device_sm_count();
@@ -166,12 +179,13 @@ extern "C" h2_status h2_measure_peak(int which, h2_stream_t stream, double *valu
       });
       const double flops = 2.0 * kChains * (double)iters * blocks * threads;
       *value = flops / (ms * 1e-3) / 1e12;   // TFLOP/s
-    } else if (which == 2) {   // exp2 operations per second
+    } else if (which == 2 || which >= 5) {   // special-function operations per second
       const int blocks = sms * 8, threads = 256, iters = 4096;
       DBuf<float> sink;
       sink.alloc(256);
+      auto kern = which == 2 ? k_sfu_peak<0> : (which == 5 ? k_sfu_peak<1> : k_sfu_peak<2>);
       double ms = best_ms(s, reps, [&]() {
-        k_sfu_peak<<<blocks, threads, 0, s>>>(iters, sink.p);
+        kern<<<blocks, threads, 0, s>>>(iters, sink.p);
         count_launch();
         H2_CHECK_LAUNCH();
       });

@@ -10,10 +10,10 @@ from paper_2506_16759_gb300 import _lib
 pytestmark = pytest.mark.gpu
 
 # which -> (low, high): FP64 and FP32 TFLOP/s, exp2 G op/s, FP16 and TF32
-# tensor TFLOP/s.  The bounds are generous brackets around GB300's unit
+# tensor TFLOP/s, square root and reciprocal square root G op/s.  The bounds are generous brackets around GB300's unit
 # counts and clocks, not targets.
 BOUNDS = {0: (0.2, 10.0), 1: (20.0, 150.0), 2: (500.0, 20000.0), 3: (300.0, 4000.0),
-          4: (150.0, 2500.0)}
+          4: (150.0, 2500.0), 5: (500.0, 20000.0), 6: (500.0, 20000.0)}
 
 
 @pytest.mark.parametrize("which", sorted(BOUNDS))
