@@ -192,7 +192,8 @@ void h2_tree_destroy(h2_tree *t);
  * unconverged, the row ID by column-pivoted QR of Y_loc^T/sqrt(d), the
  * shrink/upsweep of Y and Omega, and the couplings B = K(Itil_s, Itil_t).
  * Thresholds: nrmK = ||Y||_F/sqrt(d0), eps_abs = tol*nrmK,
- * eps_l = eps_abs/sqrt(l_top * n_l).
+ * eps_l = eps_abs/sqrt(2 * l_top * n_l) (a Frobenius budget over the levels,
+ * the nodes of a level and the row and column sides of each block).
  *
  * kernel_id/params/nparams: the entry evaluator (see h2_kernel).  tol >= 0.
  * Returns H2_ERR_NOT_CONVERGED (with *out valid) if d_max was reached.

@@ -26,8 +26,12 @@ listed in the design notes of the repository):
 * Boxes are tight; D(s) is the box diagonal; Dist(s,t) is the Euclidean gap
   between boxes; a pair is admissible iff Dist>0 and (D(s)+D(t))/2 <= eta Dist.
 * nrmK = ||Y||_F / sqrt(d0) from the first sketch; eps_abs = tol * nrmK;
-  per-level threshold eps_l = eps_abs / sqrt(l_top * n_l), a Frobenius budget
-  spread over the l_top compressed levels and the n_l nodes of level l.
+  per-level threshold eps_l = eps_abs / sqrt(2 * l_top * n_l), a Frobenius
+  budget spread over the l_top compressed levels, the n_l nodes of level l and
+  the two sides of every admissible block: the same bases act on rows and
+  columns, and A - P A P = (I - P) A + P A (I - P) splits into two parts that
+  are orthogonal in the Frobenius inner product (the "simple error
+  compensation" of Sec. V-B is left unspecified by the paper).
 * Convergence of node tau: m_tau <= d, or min_j |R_jj| <= eps_l where R is the
   triangular factor of an unpivoted Householder QR of Y_loc (m x d).
 * Row ID: column-pivoted Householder QR of A = Y_loc^T / sqrt(d) with column
@@ -505,7 +509,7 @@ class _Builder:
         below = None
         for level in range(1, self.l_top + 1):
             nodes = list(self.level_nodes(level))
-            eps_l = self.eps_abs / math.sqrt(self.l_top * len(nodes))
+            eps_l = self.eps_abs / math.sqrt(2 * self.l_top * len(nodes))
             self.eps_level[level] = eps_l
             local = self.local_samples(level, Yt if level == 1 else None,
                                        Ot if level == 1 else None, below)
@@ -917,7 +921,7 @@ class _NonSymBuilder:
         below = None
         for level in range(1, self.l_top + 1):
             nodes = list(self.level_nodes(level))
-            eps_l = self.eps_abs / math.sqrt(self.l_top * len(nodes))
+            eps_l = self.eps_abs / math.sqrt(2 * self.l_top * len(nodes))
             self.eps_level[level] = eps_l
             local = self.local_samples(level, S if level == 1 else None, below)
             for tau in nodes:

@@ -883,7 +883,8 @@ struct Builder {
       int lt = H->inst_ltop[i];
       if (l > lt) continue;
       double nl = std::ldexp(1.0, H->inst_depth[i] - l + 1);
-      L.h_eps[i] = eps_abs[i] / std::sqrt((double)lt * nl);
+      // Frobenius budget over levels, nodes and the two sides of a block
+      L.h_eps[i] = eps_abs[i] / std::sqrt(2.0 * lt * nl);
     }
     to_device(L.eps, L.h_eps, s);
   }

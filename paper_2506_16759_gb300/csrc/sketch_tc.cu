@@ -8,8 +8,11 @@
 // below FP32 rounding):
 //   TF32 mode: x = hi + lo, hi = rna_tf32(x), lo = rna_tf32(x - hi);
 //              Y = A_hi B_hi + A_hi B_lo + A_lo B_hi   (K = 8 per MMA).
-//   FP16 mode: x = h + 2^-11 s, h = rn_f16(x), s = rn_f16(2^11 (x - h));
-//              Y = A_h B_h + 2^-11 (A_h B_s + A_s B_h)  (K = 16 per MMA).
+//   FP16 mode: the entries are formed as x' = 2048 x; h' = rn_f16(x'),
+//              t = rn_f16(h' - x') (one mixed-precision subtraction of the
+//              packed h'); Omega as w = h_w + (w - h_w), its image holding
+//              h_w and rn_f16(h_w - w);
+//              Y = 2^-11 (A_h B_h - (A_h B_s + A_s B_h))  (K = 16 per MMA).
 // FP16 halves the MMA count per point; it is used when every entry is at
 // most 1 (exponential, Matern, Gaussian kernels) and |Omega| is bounded,
 // so no part leaves the FP16 range (tiny entries fall to subnormals with an
@@ -23,8 +26,10 @@
 // tiles of TJ points (32 in TF32 mode, 64 in FP16 mode: 128 bytes per row
 // either way).  The build stores, per padded point, its offset from its
 // leaf's reference point (FP32, already multiplied by the kernel's scale
-// factor sigma), and per leaf that reference (sigma * x_ref as FP32 hi/lo
-// parts).  Every sample call stores an "Omega image": per tile and column
+// factor sigma; per tile the x offsets of its points, then the y and the z
+// offsets, so that a thread loads its points four at a time and works on
+// them in packed pairs), and per leaf that reference (sigma * x_ref as FP32
+// hi/lo parts).  Every sample call stores an "Omega image": per tile and column
 // the TJ values' two parts in the 128-byte-swizzled K-major order the MMA
 // reads, so one bulk copy per part moves a tile's operand into shared
 // memory.  Padding rows are zero.
@@ -117,7 +122,9 @@ double tc_sigma(const KernelDesc &kd) {
 // Entry from the scaled row coordinates (rx, ry, rz) and a scaled point
 // offset p (the polynomial kernel: absolute coordinates).  `c` is the
 // Laplace factor 1/(4 pi), the Helmholtz wave number or the polynomial shift.
-template <int KID>
+// S (FP16 parts): the entry times 2048, the scale at which its two FP16
+// parts are formed (see split_parts).
+template <int KID, bool S = false>
 __device__ __forceinline__ float tc_entry(float rx, float ry, float rz, float4 p, float c, int pw) {
   if constexpr (KID == H2_K_POLY) {
     const float base = c + (rx * p.x + ry * p.y + rz * p.z);
@@ -128,7 +135,7 @@ __device__ __forceinline__ float tc_entry(float rx, float ry, float rz, float4 p
     const float dx = rx - p.x, dy = ry - p.y, dz = rz - p.z;
     const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
     if constexpr (KID == H2_K_GAUSS) {
-      return ex2_approx(-r2);
+      return S ? ex2_approx(-r2) * kS16 : ex2_approx(-r2);
     } else if constexpr (KID == H2_K_LAPLACE_IE) {
       return r2 > 0.f ? rsqrtf(r2) * c : 0.f;
     } else if constexpr (KID == H2_K_HELMHOLTZ_IE) {
@@ -138,8 +145,61 @@ __device__ __forceinline__ float tc_entry(float rx, float ry, float rz, float4 p
     } else {
       const float r = sqrt_approx(r2);
       const float e = ex2_approx(-r);
-      if constexpr (KID == H2_K_EXP) return e;
+      if constexpr (KID == H2_K_EXP) return S ? e * kS16 : e;
+      else if constexpr (S) return fmaf(r, kS16 * kLn2, kS16) * e;
       else return fmaf(r * kLn2, e, e);
+    }
+  }
+}
+
+// Packed pairs of FP32 values (f32x2 arithmetic: one instruction for two
+// lanes of work, same rounding as the scalar operations).
+__device__ __forceinline__ uint64_t f2(float a, float b) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2u(uint64_t v, float &a, float &b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
+// 2048 x for two entries of the exponential, Matern or Gaussian kernel at the
+// scaled offsets (dx, dy, dz) of two points from the row (packed pairs).
+template <int KID>
+__device__ __forceinline__ uint64_t tc_entry2_s(uint64_t rx, uint64_t ry, uint64_t rz, uint64_t px,
+                                                uint64_t py, uint64_t pz) {
+  const uint64_t dx = f2_sub(rx, px), dy = f2_sub(ry, py), dz = f2_sub(rz, pz);
+  const uint64_t r2 = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
+  const uint64_t s16 = f2(kS16, kS16);
+  if constexpr (KID == H2_K_GAUSS) {
+    float a, b;
+    f2u(r2, a, b);
+    return f2_mul(f2(ex2_approx(-a), ex2_approx(-b)), s16);
+  } else {
+    float a, b;
+    f2u(r2, a, b);
+    const float ra = sqrt_approx(a), rb = sqrt_approx(b);
+    const uint64_t e = f2(ex2_approx(-ra), ex2_approx(-rb));
+    if constexpr (KID == H2_K_EXP) {
+      return f2_mul(e, s16);
+    } else {
+      const uint64_t c1 = f2(kS16 * kLn2, kS16 * kLn2);
+      return f2_mul(f2_fma(f2(ra, rb), c1, s16), e);
     }
   }
 }
@@ -161,16 +221,28 @@ constexpr size_t tc_smem_bytes() {
 
 // The two parts of 8 (FP16 mode: 16) entries, packed as the TMEM columns of
 // one thread's lane.
+// FP16 mode: kv holds x' = 2048 x.  Part 1 is h' = rn_f16(x') (= 2048 h,
+// h = rn_f16(x)), part 2 is t = rn_f16(h' - x') (= -2048 (x - h), the scaled
+// residual with its sign flipped); h' - x' comes from one mixed-precision
+// subtraction of the packed part 1, so no part is unpacked.  The Omega image
+// carries (h_w, h_w - w) for each value w; the products then give
+// x w = 2^-11 (D_1 - D_2) with D_1 = h' h_w and D_2 = h' (h_w - w) + t h_w
+// (up to the product of the two residuals, below FP32 rounding).
 template <bool F16, int EPT>
 __device__ __forceinline__ void split_parts(const float *kv, uint32_t *p1, uint32_t *p2) {
   if constexpr (F16) {
 #pragma unroll
     for (int u = 0; u < EPT / 2; ++u) {
-      const __half2 h = __floats2half2_rn(kv[2 * u], kv[2 * u + 1]);
-      const float2 hf = __half22float2(h);
-      const __half2 r = __floats2half2_rn((kv[2 * u] - hf.x) * kS16, (kv[2 * u + 1] - hf.y) * kS16);
-      p1[u] = *reinterpret_cast<const uint32_t *>(&h);
-      p2[u] = *reinterpret_cast<const uint32_t *>(&r);
+      uint32_t h, r;
+      float t0, t1;
+      asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(kv[2 * u + 1]), "f"(kv[2 * u]));
+      asm("{\n.reg .b16 lo, hi;\nmov.b32 {lo, hi}, %2;\n"
+          "sub.f32.f16 %0, lo, %3;\nsub.f32.f16 %1, hi, %4;\n}\n"
+          : "=f"(t0), "=f"(t1)
+          : "r"(h), "f"(kv[2 * u]), "f"(kv[2 * u + 1]));
+      asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(t1), "f"(t0));
+      p1[u] = h;
+      p2[u] = r;
     }
   } else {
 #pragma unroll
@@ -209,7 +281,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_ksum_tc(TcArgs a) {
   // second product A_2 * B_1: TF32 adds it to the first half, FP16 to the
   // scaled second half
   constexpr uint32_t D2_OFF = F16 ? NCOL : 0;
-  constexpr float SCALE2 = F16 ? kInvS16 : 1.f;
   extern __shared__ unsigned char smem_dyn[];
   unsigned char *base = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
@@ -501,8 +572,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_ksum_tc(TcArgs a) {
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(saddr(&accempty[ac]));
+      if constexpr (F16) {
+        const uint64_t sc2 = f2(kInvS16, kInvS16);
 #pragma unroll
-      for (int c = 0; c < CPT; ++c) grp[c] += fmaf(w[c], SCALE2, v[c]);
+        for (int c = 0; c < CPT; c += 2) {
+          const uint64_t d = f2_sub(f2(v[c], v[c + 1]), f2(w[c], w[c + 1]));
+          f2u(f2_fma(d, sc2, f2(grp[c], grp[c + 1])), grp[c], grp[c + 1]);
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) grp[c] += v[c] + w[c];
+      }
       if ((j & 7) == 7) fold();   // plain sums over 8 steps, compensated across
     };
     int k = 0;
@@ -522,14 +602,35 @@ __global__ void __launch_bounds__(kThreads, 1) k_ksum_tc(TcArgs a) {
         if (live) {
           const float rx = rx0 + ctrl[sb].dx[h], ry = ry0 + ctrl[sb].dy[h],
                       rz = rz0 + ctrl[sb].dz[h];
-          const float4 *po = sOff + (sb * 2 + h) * TJ + EPT * q;
-          float kv[EPT];
+          // this thread's EPT points of the tile: x, y, z runs of the SoA tile
+          const float *pt = reinterpret_cast<const float *>(sOff + (sb * 2 + h) * TJ) + EPT * q;
+          float4 xv[EPT / 4], yv[EPT / 4], zv[EPT / 4];
 #pragma unroll
-          for (int u = 0; u < EPT; ++u) {
-            kv[u] = tc_entry<KID>(rx, ry, rz, po[u], kc, pw);
-            if constexpr ((KID == H2_K_LAPLACE_IE || KID == H2_K_HELMHOLTZ_IE) && !FAR) {
-              // the row's own point: the rounded offsets need not cancel exactly
-              if (ctrl[sb].j0[h] + EPT * q + u == g) kv[u] = 0.f;
+          for (int v4 = 0; v4 < EPT / 4; ++v4) {
+            xv[v4] = *reinterpret_cast<const float4 *>(pt + 4 * v4);
+            yv[v4] = *reinterpret_cast<const float4 *>(pt + TJ + 4 * v4);
+            zv[v4] = *reinterpret_cast<const float4 *>(pt + 2 * TJ + 4 * v4);
+          }
+          const float *xs = reinterpret_cast<const float *>(xv);
+          const float *ys = reinterpret_cast<const float *>(yv);
+          const float *zs = reinterpret_cast<const float *>(zv);
+          float kv[EPT];
+          if constexpr (F16) {
+            const uint64_t rx2 = f2(rx, rx), ry2 = f2(ry, ry), rz2 = f2(rz, rz);
+#pragma unroll
+            for (int u = 0; u < EPT; u += 2) {
+              const uint64_t e = tc_entry2_s<KID>(rx2, ry2, rz2, f2(xs[u], xs[u + 1]),
+                                                  f2(ys[u], ys[u + 1]), f2(zs[u], zs[u + 1]));
+              f2u(e, kv[u], kv[u + 1]);
+            }
+          } else {
+#pragma unroll
+            for (int u = 0; u < EPT; ++u) {
+              kv[u] = tc_entry<KID>(rx, ry, rz, make_float4(xs[u], ys[u], zs[u], 0.f), kc, pw);
+              if constexpr ((KID == H2_K_LAPLACE_IE || KID == H2_K_HELMHOLTZ_IE) && !FAR) {
+                // the row's own point: the rounded offsets need not cancel exactly
+                if (ctrl[sb].j0[h] + EPT * q + u == g) kv[u] = 0.f;
+              }
             }
           }
           split_parts<F16, EPT>(kv, p1, p2);
@@ -616,15 +717,21 @@ __global__ void k_tc_offsets(bool poly, int tj, int n_leaves, const int64_t *lea
     ref_lo[b] = make_float4((float)(sx - hx), (float)(sy - hy), (float)(sz - hz), 0.f);
   }
   const int np = (m + tj - 1) / tj * tj;
-  float4 *o = off + leaf_tile[b] * tj;
+  // per tile: x of its tj points, then y, then z, then tj zeros
+  float *o = reinterpret_cast<float *>(off + leaf_tile[b] * tj);
   for (int u = threadIdx.x; u < np; u += blockDim.x) {
+    float *t = o + (int64_t)(u / tj) * 4 * tj + u % tj;
     if (u < m) {
       const int64_t i = row + u;
-      o[u] = make_float4((float)((p.x[i] - x0) * sg), (float)((p.y[i] - y0) * sg),
-                         (float)((p.z[i] - z0) * sg), 0.f);
+      t[0] = (float)((p.x[i] - x0) * sg);
+      t[tj] = (float)((p.y[i] - y0) * sg);
+      t[2 * tj] = (float)((p.z[i] - z0) * sg);
     } else {
-      o[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      t[0] = 0.f;
+      t[tj] = 0.f;
+      t[2 * tj] = 0.f;
     }
+    t[3 * tj] = 0.f;
   }
 }
 
@@ -652,7 +759,7 @@ __global__ void k_tc_image(const float *om, int64_t ld, const int32_t *tile_leaf
     const int64_t dst = (T * img_nc + c) * TJ + (((k / E) ^ (c & 7)) * E + k % E);
     if constexpr (F16) {
       const __half h = __float2half_rn(v);
-      const __half r = __float2half_rn((v - __half2float(h)) * kS16);
+      const __half r = __float2half_rn(__half2float(h) - v);   // residual, sign flipped
       reinterpret_cast<__half *>(img_1)[dst] = h;
       reinterpret_cast<__half *>(img_2)[dst] = r;
     } else {

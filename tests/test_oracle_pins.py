@@ -630,6 +630,27 @@ def test_low_rank_update_operator():
     assert O.dense_rel_error(hk, full) <= 10 * 1e-6
 
 
+def test_update_problem_at_16384_within_tolerance():
+    # the paper's update problem (Sec. V-A) at N = 2^14: the covariance H2
+    # (exp(-r/0.2), 3D, built at 1e-7) plus a symmetric rank-32 product,
+    # recompressed at 1e-6; dense error against the exact sum within 10 tol
+    w = W.paper_problem("update", 16384)
+    X = w.points()
+    t = O.build_cluster_tree(X, w.leaf_size)
+    lists = O.dual_traversal(t, w.eta)
+    kp = w.extra["operands"][0]
+    A = O.dense_matrix(X, *kp)
+    op = O.build_h2(t, lists, *kp, w.extra["operand_tol"], W.gaussian_omega(w.n, 256, 101),
+                    O.dense_sampler(A))
+    U, V = W.low_rank_factors(w.n, w.extra["rank"], w.extra["lowrank_seed"],
+                              w.extra["lowrank_scale"])
+    entries, sampler = O.low_rank_update(t, *O.h2_sum_operator([op]), U, V)
+    h = O.build_h2(t, lists, entries, None, w.tol, W.gaussian_omega(w.n, 256, 102), sampler)
+    A += U @ V.T
+    assert h.l_top >= 3
+    assert O.dense_rel_error(h, A) <= 10 * w.tol
+
+
 # --- non-symmetric operators (separate row and column bases) -------------------
 
 
