@@ -571,7 +571,8 @@ def main_gpu(args):
         kw, ms = api.autotune(tree0, w.kernel, w.params, w.tol, prec=prec, d0=w.d0,
                               d_inc=w.d_inc, d_max=w.d_max, seed=99)
         del tree0
-        sched = {"d0": kw["d0"], "d_inc": kw["d_inc"], "prec": kw["prec"]}
+        sched = {k: kw[k] for k in ("d0", "d_inc", "prec", "bsr_engine", "tc_cols",
+                                    "ksum_split")}
         tuned = dict(sched, tuning_s=time.perf_counter() - t0, build_ms=ms)
         log(f"[bench] autotuned schedule {sched} ({ms:.1f} ms build)")
 
@@ -580,9 +581,10 @@ def main_gpu(args):
         if precision == "fp64":
             sc = {"d0": w.d0, "d_inc": w.d_inc, "prec": "fp64"}
         tree = api.ClusterTree(X, w.leaf_size, w.eta)
+        shapes = {k: sc[k] for k in ("bsr_engine", "tc_cols", "ksum_split") if k in sc}
         h = api.H2Matrix.build(tree, w.kernel, w.params, w.tol, prec=sc["prec"], seed=seed,
                                sketch="ksum", timing=timing, d0=sc["d0"], d_inc=sc["d_inc"],
-                               d_max=w.d_max)
+                               d_max=w.d_max, **shapes)
         return tree, h
 
     log(f"[bench] warmup {args.warmup} x {prec}")
@@ -679,7 +681,9 @@ def main_gpu(args):
             tree = api.ClusterTree(Xd, w.leaf_size, w.eta)
             h = api.H2Matrix.build(tree, w.kernel, w.params, w.tol, prec=sched["prec"], seed=k,
                                    sketch="ksum", d0=sched["d0"], d_inc=sched["d_inc"],
-                                   d_max=w.d_max)
+                                   d_max=w.d_max,
+                                   **{k2: sched[k2] for k2 in ("bsr_engine", "tc_cols",
+                                                               "ksum_split") if k2 in sched})
             ranks, skel, _, _ = h.export_level(1)       # device -> host read of the result
             e1.record()
             torch.cuda.synchronize()
@@ -817,14 +821,20 @@ def main_kernel_only(args):
             t0 = time.perf_counter()
             tree = api.ClusterTree(X, w.leaf_size, w.eta)
             h = api.H2Matrix.build(tree, w.kernel, w.params, w.tol, prec="mixed", seed=k,
-                                   sketch="ksum", d0=80, d_inc=16, d_max=w.d_max)
+                                   sketch="ksum", d0=80, d_inc=16, d_max=w.d_max,
+                                   bsr_engine=args.bsr_engine, timing=args.phases)
             torch.cuda.synchronize()
             if k >= args.warmup:
                 times.append((time.perf_counter() - t0) * 1e3)
             st = h.stats()
             del h, tree
-        print(json.dumps({"kernel_only": "build", "n": w.n, "ms": statistics.mean(times),
-                          "d_final": st["d_final"], "rank_max": st["rank_max"]}), flush=True)
+        out = {"kernel_only": "build", "n": w.n, "ms": statistics.mean(times),
+               "bsr_engine": args.bsr_engine, "d_final": st["d_final"],
+               "rank_max": st["rank_max"]}
+        if args.phases:
+            out["phases_ms"] = {p: st[f"ms_{p}"] for p in ("sketch", "nearfield", "qr", "id",
+                                                         "upsweep", "coupling", "bsr", "total")}
+        print(json.dumps(out), flush=True)
         return
     X = torch.from_numpy(w.points()).to(dev)
     om = torch.from_numpy(w.omega(32)).to(dev)
@@ -945,6 +955,11 @@ def main():
     ap.add_argument("--problem", default="helmholtz", choices=["exp3d", "helmholtz", "update"],
                     help="kernel problem for --kernel-only paper")
     ap.add_argument("--n", type=int, default=0, help="point count for --kernel-only build")
+    ap.add_argument("--bsr-engine", type=int, default=0, choices=[0, 1],
+                    help="--kernel-only build: block-sparse products on tensor cores (0) or "
+                         "CUDA cores (1)")
+    ap.add_argument("--phases", action="store_true",
+                    help="--kernel-only build: per-phase device times (synchronising timers)")
     args = ap.parse_args()
     if args.kernel_only:
         main_kernel_only(args)

@@ -131,6 +131,15 @@ typedef struct {
   const double *lowrank_u;
   const double *lowrank_v;
   int lowrank_rank;           /* 0 = none, at most 64 */
+  /* Launch shapes (mixed precision; 0 = the default), the knobs h2_autotune
+   * tunes: */
+  int bsr_engine;             /* block-sparse products: 0 tensor cores where the
+                                 blocks have at most 128 rows, 1 CUDA cores */
+  int tc_cols;                /* sample columns per tensor-core sketch launch:
+                                 0 = 80, or 64 or 32 */
+  int ksum_split;             /* far-only sketch: target work items per SM, each
+                                 a contiguous range of one row tile's partner
+                                 leaves (0 = 32; items run largest first) */
 } h2_build_opts;
 
 /* Fills opts with the workload defaults (32/16/256, FP64, Philox seed 0,
@@ -253,13 +262,15 @@ h2_status h2_export_level(const h2_matrix *h, int inst, int level, int32_t *rank
 
 void h2_matrix_destroy(h2_matrix *h);
 
-/* Autotuner: times full builds of `tree` with candidate sample schedules
- * (d0, d_inc in {32, 64, leaf size} x {16, 32}, d0 <= d_max) and, for mixed
- * precision, both sketch engines (tensor cores / CUDA cores), and writes the
- * fastest candidate that converged into *best (other fields copied from
- * *base).  best_ms receives its build time.  Every candidate is an ordinary
- * adaptive build at tolerance tol, so the choice changes speed, not the
- * accuracy target. */
+/* Autotuner: times full builds of `tree` and writes the fastest candidate
+ * that converged into *best (other fields copied from *base); best_ms
+ * receives its build time.  Stage 1 searches the sample schedule (d0, d_inc
+ * in {32, 64, 80, leaf size} x {16, 32}, d0 <= d_max) and, for mixed
+ * precision, both sketch engines (tensor cores / CUDA cores); later stages
+ * keep that choice and try, one knob at a time, the block-sparse engine, the
+ * sketch's columns per launch and its work split (h2_build_opts launch
+ * shapes).  Every candidate is an ordinary adaptive build at tolerance tol,
+ * so the choice changes speed, not the accuracy target. */
 h2_status h2_autotune(const h2_tree *tree, int kernel_id, const double *params, int nparams,
                       double tol, const h2_build_opts *base, h2_stream_t s, h2_build_opts *best,
                       double *best_ms);

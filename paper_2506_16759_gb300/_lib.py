@@ -31,7 +31,8 @@ class BuildOpts(C.Structure):
                 ("sampler", SAMPLER_FN), ("sampler_ctx", C.c_void_p),
                 ("operands", C.c_void_p), ("n_operands", C.c_int), ("timing", C.c_int),
                 ("ksum_tile", C.c_int), ("lowrank_u", C.c_void_p), ("lowrank_v", C.c_void_p),
-                ("lowrank_rank", C.c_int)]
+                ("lowrank_rank", C.c_int), ("bsr_engine", C.c_int), ("tc_cols", C.c_int),
+                ("ksum_split", C.c_int)]
 
 
 class TreeInfo(C.Structure):

@@ -108,7 +108,7 @@ class ClusterTree:
 
 def make_opts(d0=32, d_inc=16, d_max=256, prec="fp64", omega=None, seed=0, sketch="ksum",
               dense_a=None, timing=False, sampler=None, operands=None, ksum_tile=0,
-              lowrank=None):
+              lowrank=None, bsr_engine=0, tc_cols=0, ksum_split=0):
     o = BuildOpts()
     lib().h2_default_opts(C.byref(o))
     o.d0, o.d_inc, o.d_max = d0, d_inc, d_max
@@ -136,6 +136,7 @@ def make_opts(d0=32, d_inc=16, d_max=256, prec="fp64", omega=None, seed=0, sketc
         o.n_operands = len(operands)
     o.timing = 1 if timing else 0
     o.ksum_tile = ksum_tile
+    o.bsr_engine, o.tc_cols, o.ksum_split = bsr_engine, tc_cols, ksum_split
     if lowrank is not None:
         # (U, V): the operator gets the symmetric term U V^T
         u, v = (colmajor(x.to(torch.float64)) for x in lowrank)
@@ -223,8 +224,8 @@ class H2Matrix:
 
 
 def autotune(tree: ClusterTree, kernel, params, tol: float, stream=None, **kw) -> tuple:
-    """(best build keyword arguments, build ms) over the sample schedules and
-    sketch engines h2_autotune tries."""
+    """(best build keyword arguments, build ms) over the sample schedules,
+    sketch engines and launch shapes h2_autotune tries."""
     o, keep = make_opts(**kw)
     best = BuildOpts()
     ms = C.c_double()
@@ -233,7 +234,8 @@ def autotune(tree: ClusterTree, kernel, params, tol: float, stream=None, **kw) -
                             _stream(stream), C.byref(best), C.byref(ms)), "h2_autotune")
     inv = {v: k for k, v in PREC.items()}
     out = dict(kw)
-    out.update(d0=best.d0, d_inc=best.d_inc, prec=inv[best.prec])
+    out.update(d0=best.d0, d_inc=best.d_inc, prec=inv[best.prec], bsr_engine=best.bsr_engine,
+               tc_cols=best.tc_cols, ksum_split=best.ksum_split)
     return out, ms.value
 
 

@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "libh2gb.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
 SOURCES = ["tree.cu", "sketch.cu", "sketch_tc.cu", "construct.cu", "h2sum.cu", "api.cu",
-           "noalloc.cu", "lowrank.cu", "peaks.cu"]
+           "noalloc.cu", "lowrank.cu", "peaks.cu", "bsr_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -254,6 +254,7 @@ struct h2_matrix {
   int64_t D_size = 0;
   std::vector<int> dcur;
   bool converged = true;
+  int bsr_engine = 0;   // block-sparse engine of its products (h2_build_opts)
   h2_stats_t st{};
 };
 
@@ -570,7 +571,7 @@ struct Builder {
         std::vector<int> c0(insts.size());
         for (size_t q = 0; q < insts.size(); ++q) c0[q] = H->dcur[insts[q]] + done;
         KsumPlan plan = far ? plan_ksum_far(L.h_row, L.h_m, L.task_base, lcount, insts, c0, dc,
-                                            sm_count)
+                                            sm_count, false, o.ksum_split)
                             : plan_ksum(nn, bb, insts, c0, dc, fp64(), o.ksum_tile, sm_count);
         count_sketch(insts, far, dc);
         if (fp64()) {
@@ -667,9 +668,10 @@ struct Builder {
       tc_layout_build(H->kid, f16, L.h_row, L.h_m, L.h_inst, kds, L.row.p, L.m.p, p64(), tcl, s);
       tcl_ready = true;
     }
-    const int nchunks = (nc + kTcChunk - 1) / kTcChunk;
-    const int last = nc - kTcChunk * (nchunks - 1);
-    const int img_nc = kTcChunk * (nchunks - 1) + tc_chunk_ncol(last);
+    const int chunk = o.tc_cols > 0 ? o.tc_cols : kTcChunk;
+    const int nchunks = (nc + chunk - 1) / chunk;
+    const int last = nc - chunk * (nchunks - 1);
+    const int img_nc = chunk * (nchunks - 1) + tc_chunk_ncol(last);
     std::vector<int32_t> hc0(c0.begin(), c0.end());
     DBuf<int32_t> dc0;
     to_device(dc0, hc0, s);
@@ -682,13 +684,14 @@ struct Builder {
     for (int i = 0; i < H->count; ++i) lcount[i] = 1 << H->inst_depth[i];
     std::vector<int32_t> ul_leaf, ul_flags;
     DBuf<int32_t> d_ul_leaf, d_ul_flags;
-    for (int done = 0; done < nc; done += kTcChunk) {
-      const int w = std::min(kTcChunk, nc - done);
+    for (int done = 0; done < nc; done += chunk) {
+      const int w = std::min(chunk, nc - done);
       std::vector<int> cq(insts.size());
       for (size_t q = 0; q < insts.size(); ++q) cq[q] = c0[insts[q]] + done;
       KsumPlan plan;
       if (mode == 1) {
-        plan = plan_ksum_far(L.h_row, L.h_m, L.task_base, lcount, insts, cq, w, sm_count, true);
+        plan = plan_ksum_far(L.h_row, L.h_m, L.task_base, lcount, insts, cq, w, sm_count, true,
+                             o.ksum_split);
         count_sketch(insts, true, w);
       } else if (mode == 0) {
         plan = plan_ksum_tc_all(nn, bb, L.task_base, lcount, insts, cq, w, sm_count);
@@ -836,6 +839,7 @@ struct Builder {
     a.cols = cols();
     a.in_rows = L.M;
     a.col_hi = col_hi;
+    a.engine = o.bsr_engine;
     bsr_apply(fp64(), a, L.max_m, max_cols, s);
     timer.end(PH_BSR);
   }
@@ -870,6 +874,7 @@ struct Builder {
     a.cols = cols();
     a.in_rows = U.M;
     a.col_hi = col_hi;
+    a.engine = o.bsr_engine;
     bsr_apply(fp64(), a, L.max_k, max_cols, s);
     timer.end(PH_BSR);
   }
@@ -1327,6 +1332,10 @@ void validate_opts(const h2_build_opts &o) {
              "a low-rank term needs U and V");
   H2_REQUIRE(o.lowrank_rank == 0 || o.sketch != H2_SKETCH_KSUM,
              "a low-rank term needs a dense, callback or H2-matvec sketch");
+  H2_REQUIRE(o.bsr_engine == 0 || o.bsr_engine == 1, "bsr_engine must be 0 or 1");
+  H2_REQUIRE(o.tc_cols == 0 || o.tc_cols == 32 || o.tc_cols == 64 || o.tc_cols == 80,
+             "tc_cols must be 0, 32, 64 or 80");
+  H2_REQUIRE(o.ksum_split >= 0 && o.ksum_split <= 1024, "ksum_split must be in 0..1024");
 }
 
 template <typename F>
@@ -1380,6 +1389,7 @@ void matvec_impl(const h2_matrix *H, const double *x, double *y, int nrhs, cudaS
     a.ld_out = N;
     a.sign = 1.0;
     a.cols = cols;
+    a.engine = H->bsr_engine;
     bsr_apply(f64, a, L1.max_m, nrhs, s);
   }
   int levels = H->levels;
@@ -1423,6 +1433,7 @@ void matvec_impl(const h2_matrix *H, const double *x, double *y, int nrhs, cudaS
       a.ld_out = L.K;
       a.sign = 1.0;
       a.cols = cols;
+      a.engine = H->bsr_engine;
       bsr_apply(f64, a, L.max_k, nrhs, s);
     }
     // downsweep
@@ -1688,6 +1699,7 @@ h2_status h2_build_batched(const h2_tree *const *trees, int count, const int *ke
     H->count = count;
     H->fp64 = opts->prec == H2_PREC_FP64;
     H->tensor_sketch = opts->prec == H2_PREC_MIXED;
+    H->bsr_engine = opts->bsr_engine;
     H->kid = kernel_ids[0];
     Builder b(H.get(), trees, *opts, (cudaStream_t)s);
     h2_status st = b.run(kernel_ids, params, tols);
@@ -1774,6 +1786,26 @@ h2_status h2_autotune(const h2_tree *tree, int kernel_id, const double *params, 
     cudaEvent_t e0, e1;
     H2_CUDA(cudaEventCreate(&e0));
     H2_CUDA(cudaEventCreate(&e1));
+    // one timed build after a warm-up one; false if it did not converge
+    auto try_opts = [&](const h2_build_opts &o) {
+      for (int rep = 0; rep < 2; ++rep) {
+        h2_matrix *h = nullptr;
+        H2_CUDA(cudaEventRecord(e0, st));
+        h2_status r = h2_build(tree, kernel_id, params, nparams, tol, &o, s, &h);
+        H2_CUDA(cudaEventRecord(e1, st));
+        H2_CUDA(cudaEventSynchronize(e1));
+        h2_matrix_destroy(h);
+        if (r != H2_OK) return false;        // not converged (or failed): not a candidate
+        float ms = 0.f;
+        H2_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep == 1 && ms < best_t) {
+          best_t = ms;
+          choice = o;
+        }
+      }
+      return true;
+    };
+    // stage 1: sample schedule and sketch engine
     for (int pr : precs)
       for (auto [d0, inc] : sched) {
         h2_build_opts o = *base;
@@ -1781,22 +1813,31 @@ h2_status h2_autotune(const h2_tree *tree, int kernel_id, const double *params, 
         o.d_inc = inc;
         o.prec = pr;
         o.timing = 0;
-        for (int rep = 0; rep < 2; ++rep) {   // first run warms up
-          h2_matrix *h = nullptr;
-          H2_CUDA(cudaEventRecord(e0, st));
-          h2_status r = h2_build(tree, kernel_id, params, nparams, tol, &o, s, &h);
-          H2_CUDA(cudaEventRecord(e1, st));
-          H2_CUDA(cudaEventSynchronize(e1));
-          h2_matrix_destroy(h);
-          if (r != H2_OK) break;             // not converged (or failed): not a candidate
-          float ms = 0.f;
-          H2_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-          if (rep == 1 && ms < best_t) {
-            best_t = ms;
-            choice = o;
-          }
-        }
+        try_opts(o);
       }
+    // later stages (mixed precision): one launch-shape knob at a time, the
+    // best so far kept
+    if (best_t < 1e300 && choice.prec != H2_PREC_FP64) {
+      for (int eng : {0, 1}) {
+        h2_build_opts o = choice;
+        if (o.bsr_engine == eng) continue;
+        o.bsr_engine = eng;
+        try_opts(o);
+      }
+      if (choice.prec == H2_PREC_MIXED)
+        for (int cols : {80, 64, 32}) {
+          h2_build_opts o = choice;
+          if ((o.tc_cols == 0 ? 80 : o.tc_cols) == cols) continue;
+          o.tc_cols = cols;
+          try_opts(o);
+        }
+      for (int split : {32, 8, 16, 64}) {
+        h2_build_opts o = choice;
+        if ((o.ksum_split == 0 ? 32 : o.ksum_split) == split) continue;
+        o.ksum_split = split;
+        try_opts(o);
+      }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     H2_REQUIRE(best_t < 1e300, "no candidate schedule converged");

@@ -1136,6 +1136,14 @@ void launch_bsr_tile(const BsrArgs &a, const float *tin, int64_t ldt, cudaStream
 void bsr_apply(bool fp64, const BsrArgs &a_in, int max_m, int max_cols, cudaStream_t s) {
   if (a_in.n_rows == 0 || max_cols <= 0) return;
   H2_REQUIRE(max_m <= kMaxRows, "block rows above 256 are not supported");
+  if (!fp64 && max_m <= 128 && a_in.engine == 0) {
+    // tensor cores: one CTA per SM; a row task's blocks are split over
+    // several CTAs only where the row tasks would not fill the device twice
+    BsrArgs t = a_in;
+    const int chunks = std::max(1, (max_cols + 95) / 96);
+    t.seg = std::max(1, std::min(16, 2 * device_sm_count() / std::max(1, a_in.n_rows * chunks)));
+    if (bsr_apply_tc(t, max_m, max_cols, s)) return;
+  }
   // Levels with few row tasks split each CSR row over several CTAs (FP32:
   // their partial sums meet in atomic adds; FP64 keeps one CTA per row so
   // that its sums stay in a fixed order)

@@ -48,9 +48,13 @@ struct BsrArgs {
   int64_t in_rows;          // rows of the input panel (FP32 tiled path)
   int col_hi;               // max over instances of ce (0: use the row-block kernel)
   int seg = 1;              // CTAs per row task (set by bsr_apply; > 1: atomic adds)
+  int engine = 0;           // FP32: 0 tensor cores where blocks have <= 128 rows, 1 CUDA cores
 };
 // max_cols: the widest per-instance column range of this call.
 void bsr_apply(bool fp64, const BsrArgs &a, int max_m, int max_cols, cudaStream_t s);
+// FP32 blocks of at most 128 rows on the tensor cores (bsr_tc.cu); false if
+// the call is outside that range.
+bool bsr_apply_tc(const BsrArgs &a, int max_m, int max_cols, cudaStream_t s);
 
 // Leaf near field: every D_{t,b} = K(I_t, I_b) of the near list, stored at
 // doff (16-byte aligned offsets).

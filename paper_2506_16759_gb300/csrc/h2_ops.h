@@ -88,7 +88,7 @@ KsumPlan plan_ksum(const std::vector<int64_t> &inst_n, const std::vector<int64_t
 KsumPlan plan_ksum_far(const std::vector<int64_t> &leaf_row, const std::vector<int32_t> &leaf_m,
                        const std::vector<int> &leaf_base, const std::vector<int> &leaf_count,
                        const std::vector<int> &insts, const std::vector<int> &c0, int ncols,
-                       int sm_count, bool pair_leaves = false);
+                       int sm_count, bool pair_leaves = false, int split = 0);
 
 // Runs a plan (items/partials staged in `scratch`-owned buffers).  Returns the
 // number of kernel launches.  `work` must hold plan.n_parts*tile_rows*dc

@@ -494,14 +494,15 @@ KsumPlan plan_ksum(const std::vector<int64_t> &inst_n, const std::vector<int64_t
 KsumPlan plan_ksum_far(const std::vector<int64_t> &leaf_row, const std::vector<int32_t> &leaf_m,
                        const std::vector<int> &leaf_base, const std::vector<int> &leaf_count,
                        const std::vector<int> &insts, const std::vector<int> &c0, int ncols,
-                       int sm_count, bool pair_leaves) {
+                       int sm_count, bool pair_leaves, int split) {
   KsumPlan p;
   const int per = pair_leaves ? 2 : 1;
   p.tile_rows = 64 * per;
   p.dc = ncols;
   int64_t tiles = 0;
   for (int i : insts) tiles += (leaf_count[i] + per - 1) / per;
-  const int64_t target = (int64_t)sm_count * 8 * 4;
+  // work items in all: `split` per SM (32 by default)
+  const int64_t target = (int64_t)sm_count * (split > 0 ? split : 32);
   struct Tmp {
     int64_t work;
     KsumItem it;
