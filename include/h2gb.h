@@ -123,9 +123,9 @@ typedef struct {
   /* Optional low-rank term: the operator becomes (kernel or H2 sum) + U V^T,
    * the update problem of Sec. V-A (an H2 matrix plus a rank-r product).
    * U, V: device, N x lowrank_rank column-major with ld = N, original point
-   * order, FP64, read during the call only.  U V^T must be symmetric (the
-   * construction shares row and column bases), e.g. V = U S with S
-   * symmetric.  Needs a single instance and a sketch in original order
+   * order, FP64, read during the call only.  Unless nonsym = 1, U V^T must
+   * be symmetric (the symmetric construction shares row and column bases),
+   * e.g. V = U S with S symmetric.  Needs a single instance and a sketch in original order
    * (dense, callback or H2 sum): the library adds U (V^T Omega) to the
    * sampler's output and U(I,:) V(J,:)^T to every generated block. */
   const double *lowrank_u;
@@ -140,6 +140,23 @@ typedef struct {
   int ksum_split;             /* far-only sketch: target work items per SM, each
                                  a contiguous range of one row tile's partner
                                  leaves (0 = 32; items run largest first) */
+  /* Non-symmetric operators (Sec. II-A: admissible blocks U_s B_st V_t^T with
+   * separate row and column bases; Sec. III calls the change a direct
+   * modification of the symmetric algorithm).  nonsym = 1: the row side runs
+   * Algorithm 1 on Y = A Omega (row IDs, bases U), the column side on
+   * Z = A^T Psi (column IDs, bases V), level by level together; each side's
+   * far-field subtraction goes through the other side's bases, the couplings
+   * are A(row skeletons, column skeletons), and nrmK is taken from both
+   * sketches, sqrt((||Y||^2 + ||Z||^2) / (2 d0)).  A node is converged when
+   * both of its sides are.  Needs a single instance, a kernel (not H2_K_H2SUM)
+   * and a sketch in original order: dense (Z from the transpose of dense_a),
+   * callback (sampler_t gives A^T x) or H2 matvecs (symmetric operands); the
+   * low-rank term U V^T may then be non-symmetric. */
+  int nonsym;
+  const double *psi_stored;   /* omega_mode 1: the column side's samples,
+                                 device N x d_max like omega_stored */
+  h2_sampler_fn sampler_t;    /* nonsym + H2_SKETCH_CALLBACK: y = A^T x */
+  void *sampler_t_ctx;
 } h2_build_opts;
 
 /* Fills opts with the workload defaults (32/16/256, FP64, Philox seed 0,
@@ -259,6 +276,13 @@ h2_status h2_stats(const h2_matrix *h, h2_stats_t *st);
  * be NULL. */
 h2_status h2_export_level(const h2_matrix *h, int inst, int level, int32_t *ranks,
                           int32_t *skel, double *eps_l, int32_t *d_l);
+
+/* The column side of a non-symmetric build (h2_build_opts.nonsym = 1): ranks
+ * and column skeletons of one level, laid out as h2_export_level lays out the
+ * row side's (which h2_export_level returns for such a matrix).  H2_ERR_ARG
+ * for a symmetric build, whose rows and columns share one set of bases. */
+h2_status h2_export_col_level(const h2_matrix *h, int inst, int level, int32_t *ranks,
+                              int32_t *skel);
 
 void h2_matrix_destroy(h2_matrix *h);
 

@@ -32,7 +32,8 @@ class BuildOpts(C.Structure):
                 ("operands", C.c_void_p), ("n_operands", C.c_int), ("timing", C.c_int),
                 ("ksum_tile", C.c_int), ("lowrank_u", C.c_void_p), ("lowrank_v", C.c_void_p),
                 ("lowrank_rank", C.c_int), ("bsr_engine", C.c_int), ("tc_cols", C.c_int),
-                ("ksum_split", C.c_int)]
+                ("ksum_split", C.c_int), ("nonsym", C.c_int), ("psi_stored", C.c_void_p),
+                ("sampler_t", SAMPLER_FN), ("sampler_t_ctx", C.c_void_p)]
 
 
 class TreeInfo(C.Structure):
@@ -81,6 +82,7 @@ SIGNATURES = {
     "h2_matvec": (i32, [vp, vp, vp, i32, vp]),
     "h2_stats": (i32, [vp, C.POINTER(Stats)]),
     "h2_export_level": (i32, [vp, i32, i32, vp, vp, vp, vp]),
+    "h2_export_col_level": (i32, [vp, i32, i32, vp, vp]),
     "h2_matrix_destroy": (None, [vp]),
     "h2_autotune": (i32, [vp, i32, vp, i32, dbl, C.POINTER(BuildOpts), vp, C.POINTER(BuildOpts),
                           C.POINTER(dbl)]),

@@ -108,7 +108,8 @@ class ClusterTree:
 
 def make_opts(d0=32, d_inc=16, d_max=256, prec="fp64", omega=None, seed=0, sketch="ksum",
               dense_a=None, timing=False, sampler=None, operands=None, ksum_tile=0,
-              lowrank=None, bsr_engine=0, tc_cols=0, ksum_split=0):
+              lowrank=None, bsr_engine=0, tc_cols=0, ksum_split=0, nonsym=False, psi=None,
+              sampler_t=None):
     o = BuildOpts()
     lib().h2_default_opts(C.byref(o))
     o.d0, o.d_inc, o.d_max = d0, d_inc, d_max
@@ -137,6 +138,17 @@ def make_opts(d0=32, d_inc=16, d_max=256, prec="fp64", omega=None, seed=0, sketc
     o.timing = 1 if timing else 0
     o.ksum_tile = ksum_tile
     o.bsr_engine, o.tc_cols, o.ksum_split = bsr_engine, tc_cols, ksum_split
+    if nonsym:
+        # separate row and column bases: Psi (stored mode) and A^T x (callback)
+        o.nonsym = 1
+        if psi is not None:
+            ps = colmajor(psi)
+            keep.append(ps)
+            o.psi_stored = ps.data_ptr()
+        if sampler_t is not None:
+            cbt = _lib.SAMPLER_FN(sampler_t)
+            keep.append(cbt)
+            o.sampler_t = cbt
     if lowrank is not None:
         # (U, V): the operator gets the symmetric term U V^T
         u, v = (colmajor(x.to(torch.float64)) for x in lowrank)
@@ -202,6 +214,17 @@ class H2Matrix:
         st = Stats()
         check(lib().h2_stats(self.handle, C.byref(st)), "h2_stats")
         return {name: getattr(st, name) for name, _ in Stats._fields_}
+
+    def export_col_level(self, level: int, inst: int = 0):
+        """Column side of a non-symmetric build: (ranks, column skeletons as
+        original indices)."""
+        tree = self.trees[inst]
+        nl = 1 << (tree.info.depth - level + 1)
+        ranks = np.zeros(nl, dtype=np.int32)
+        skel = np.zeros(nl * 512, dtype=np.int32)
+        check(lib().h2_export_col_level(self.handle, inst, level, ranks.ctypes.data,
+                                        skel.ctypes.data), "h2_export_col_level")
+        return ranks, skel[:int(ranks.sum())]
 
     def export_level(self, level: int, inst: int = 0):
         """(ranks per cluster in heap order, skeleton original indices, eps_l, d_l)."""

@@ -255,6 +255,14 @@ struct h2_matrix {
   std::vector<int> dcur;
   bool converged = true;
   int bsr_engine = 0;   // block-sparse engine of its products (h2_build_opts)
+  // separate row and column bases (non-symmetric operator): lv holds the row
+  // side (U, row skeletons, couplings B), lvc the column side (V, column
+  // skeletons); the column side's construction-only blocks (D^T and B^T of
+  // its subtractions) are released after the build
+  bool nonsym = false;
+  std::vector<h2::LevelData> lvc;
+  h2::DBuf<double> Dt64;
+  h2::DBuf<float> Dt32;
   h2_stats_t st{};
 };
 
@@ -347,6 +355,7 @@ struct Builder {
   std::vector<double> tols;
   DBuf<int32_t> cb, ce;             // per-instance column range of the current pass
   DBuf<double> om_stage;            // FP64 staging of new Omega columns (mixed / callbacks)
+  DBuf<double> om_stage_c;          // the same for the column side's Psi
   DBuf<char> lr_ut, lr_vt;          // low-rank factors, tree-order rows (T)
   TcLayout tcl;                     // padded leaf layout of the tensor-core sketch (built once)
   bool tcl_ready = false;
@@ -373,7 +382,10 @@ struct Builder {
   void *Omp(LevelData &L) { return fp64() ? (void *)L.Om64.p : (void *)L.Om32.p; }
   void *Ep(LevelData &L) { return (void *)L.E.p; }
   void *Bp(LevelData &L) { return fp64() ? (void *)L.B64.p : (void *)L.B32.p; }
-  void *Dp() { return fp64() ? (void *)H->D64.p : (void *)H->D32.p; }
+  void *Dp() {   // the current side's near blocks: D, or D^T for the column side
+    if (sd == 1) return fp64() ? (void *)H->Dt64.p : (void *)H->Dt32.p;
+    return fp64() ? (void *)H->D64.p : (void *)H->D32.p;
+  }
 
   int max_cols = 0;
   int col_hi = 0;   // the highest column end over the instances
@@ -389,15 +401,48 @@ struct Builder {
   }
   InstCols cols() const { return InstCols{cb.p, ce.p}; }
 
-  void alloc_panels(LevelData &L) {
-    size_t sz = (size_t)std::max<int64_t>(L.M, 1) * o.d_max;
-    if (fp64()) {
-      L.Y64.alloc_zero(sz, s);
-      L.Om64.alloc_zero(sz, s);
-    } else {
-      L.Y32.alloc_zero(sz, s);
-      L.Om32.alloc_zero(sz, s);
+  // ---- sides.  sd = 0: the row side (the only one of a symmetric build);
+  // sd = 1: the column side of a non-symmetric build.  LV() is the current
+  // side's levels, LVO() the other side's (the same levels when symmetric).
+  int sd = 0;
+  int nsides() const { return H->nonsym ? 2 : 1; }
+  std::vector<LevelData> &LV() { return sd == 0 ? H->lv : H->lvc; }
+  std::vector<LevelData> &LVO() { return (H->nonsym && sd == 0) ? H->lvc : H->lv; }
+  template <typename F>
+  void each_side(F &&f) {
+    for (int q = 0; q < nsides(); ++q) {
+      sd = q;
+      f();
     }
+    sd = 0;
+  }
+  // low-rank factors in the current side's order: the column side samples and
+  // generates entries of A^T = ... + V U^T
+  const char *lr_rows() const { return sd == 0 ? lr_ut.p : lr_vt.p; }
+  const char *lr_cols() const { return sd == 0 ? lr_vt.p : lr_ut.p; }
+
+  // Y rows follow the side's own layout (M); Omega rows the other side's,
+  // whose bases sweep it up (Mo; the same layout when symmetric)
+  void alloc_panels(LevelData &L, int64_t Mo) {
+    size_t sy = (size_t)std::max<int64_t>(L.M, 1) * o.d_max;
+    size_t so = (size_t)std::max<int64_t>(Mo, 1) * o.d_max;
+    if (fp64()) {
+      L.Y64.alloc_zero(sy, s);
+      L.Om64.alloc_zero(so, s);
+    } else {
+      L.Y32.alloc_zero(sy, s);
+      L.Om32.alloc_zero(so, s);
+    }
+  }
+
+  // the column side's copy of a level's task list (geometry set separately)
+  void copy_tasks(LevelData &dst, const LevelData &src) {
+    dst.n = src.n;
+    dst.h_inst = src.h_inst;
+    dst.h_child0 = src.h_child0;
+    dst.task_base = src.task_base;
+    to_device(dst.inst, dst.h_inst, s);
+    if (!dst.h_child0.empty()) to_device(dst.child0, dst.h_child0, s);
   }
 
   // ---------------- setup ---------------------------------------------------
@@ -518,11 +563,27 @@ struct Builder {
     // 16 bytes of slack: block copies round up to whole 16-byte units
     if (fp64()) H->D64.alloc(H->D_size + 2);
     else H->D32.alloc(H->D_size + 4);
-    alloc_panels(L);
+    alloc_panels(L, L.M);
+    if (H->nonsym) {   // the column side's leaves: the same clusters and blocks D^T
+      LevelData &Lc = H->lvc[1];
+      copy_tasks(Lc, L);
+      Lc.h_row = L.h_row;
+      Lc.h_m = L.h_m;
+      Lc.M = L.M;
+      Lc.max_m = L.max_m;
+      to_device(Lc.row, Lc.h_row, s);
+      to_device(Lc.m, Lc.h_m, s);
+      if (fp64()) H->Dt64.alloc(H->D_size + 2);
+      else H->Dt32.alloc(H->D_size + 4);
+      alloc_panels(Lc, Lc.M);
+    }
   }
 
   void set_level_flags(int l) {
-    LevelData &L = H->lv[l];
+    each_side([&]() { set_level_flags_side(l); });
+  }
+  void set_level_flags_side(int l) {
+    LevelData &L = LV()[l];
     int C = H->count;
     L.h_active.assign(C, 0);
     L.h_active_next.assign(C, 0);
@@ -539,25 +600,39 @@ struct Builder {
   // panel (tree order), then Y = K Omega for the same columns.
   // Returns true when the new columns already hold Y_loc (far-only summation:
   // the leaf near field was never added, so it must not be subtracted).
-  bool sample(const std::vector<int> &insts, int nc, bool far_only = false) {
-    LevelData &L = H->lv[1];
-    int64_t N = H->n_total;
-    timer.begin(PH_SKETCH);
-    // Omega in FP64 (staging for mixed precision)
+  // New Omega columns [c0_i, c0_i + nc) of the listed instances for the
+  // current side (the column side draws Psi: its own stored matrix, or Philox
+  // with a seed of its own) into its level-1 panel, tree order.  Returns the
+  // FP64 tree-order copy (the panel itself in FP64, a staging panel in mixed
+  // precision).
+  double *draw_omega(const std::vector<int> &insts, int nc) {
+    LevelData &L = LV()[1];
+    const int64_t N = H->n_total;
+    DBuf<double> &stage = sd == 0 ? om_stage : om_stage_c;
     double *om64 = fp64() ? L.Om64.p : nullptr;
     if (!fp64()) {
-      if ((int64_t)om_stage.n < N * o.d_max) om_stage.alloc((size_t)N * o.d_max);
-      om64 = om_stage.p;
+      if ((int64_t)stage.n < N * o.d_max) stage.alloc((size_t)N * o.d_max);
+      om64 = stage.p;
     }
+    const double *stored = sd == 0 ? o.omega_stored : o.psi_stored;
+    const uint64_t seed = sd == 0 ? o.seed : o.seed ^ 0x9e3779b97f4a7c15ull;
     for (int i : insts) {
       int c0 = H->dcur[i];
       int64_t b = H->inst_base[i], n = H->inst_n[i];
       if (o.omega_mode == 1)
-        gather_rows64(o.omega_stored, N, H->orig_of_pos.p + b, n, c0, c0 + nc, om64 + b, N, s);
+        gather_rows64(stored, N, H->orig_of_pos.p + b, n, c0, c0 + nc, om64 + b, N, s);
       else
-        philox_gaussian64(om64 + b, N, H->orig_of_pos.p + b, n, c0, c0 + nc, o.seed, s);
+        philox_gaussian64(om64 + b, N, H->orig_of_pos.p + b, n, c0, c0 + nc, seed, s);
       if (!fp64()) convert_cols_to32(om64, N, b, n, c0, c0 + nc, L.Om32.p, s);
     }
+    return om64;
+  }
+
+  bool sample(const std::vector<int> &insts, int nc, bool far_only = false) {
+    LevelData &L = H->lv[1];
+    int64_t N = H->n_total;
+    timer.begin(PH_SKETCH);
+    double *om64 = draw_omega(insts, nc);
     bool far = far_only && o.sketch == H2_SKETCH_KSUM && L.max_m <= 64;
     if (o.sketch == H2_SKETCH_KSUM && H->tensor_sketch) {
       sample_tc(insts, nc, far);
@@ -587,48 +662,10 @@ struct Builder {
       // samplers working in original order: Omega_orig -> y_orig -> tree order
       H2_REQUIRE(H->count == 1 || o.sketch == H2_SKETCH_H2SUM,
                  "dense and callback sketches take a single instance");
-      int c0 = H->dcur[insts[0]];
-      DBuf<double> omo, yo;
-      omo.alloc((size_t)N * nc);
-      yo.alloc_zero((size_t)N * nc, s);
-      // om64 (tree order, columns c0..) -> original order
-      permute_out(true, om64 + (int64_t)c0 * N, N, H->orig_of_pos.p, N, nc, omo.p, N, s);
-      if (o.sketch == H2_SKETCH_DENSE) {
-        H2_REQUIRE(o.dense_a != nullptr, "dense sketch needs dense_a");
-        dense_gemm64(o.dense_a, N, N, omo.p, N, yo.p, N, nc, s);
-      } else if (o.sketch == H2_SKETCH_CALLBACK) {
-        H2_REQUIRE(o.sampler != nullptr, "callback sketch needs a sampler");
-        int rc = o.sampler(o.sampler_ctx, omo.p, yo.p, N, nc, N, (h2_stream_t)s);
-        if (rc != 0) throw Error{H2_ERR_SAMPLER, "sampler callback returned an error"};
-      } else {
-        H2_REQUIRE(o.operands != nullptr && o.n_operands > 0, "H2 sum needs operands");
-        DBuf<double> tmp;
-        tmp.alloc((size_t)N * nc);
-        for (int q = 0; q < o.n_operands; ++q) {
-          const h2_matrix *op = o.operands[q];
-          H2_REQUIRE(op && op->n_total == N, "operand size mismatch");
-          h2_status st = h2_matvec(op, omo.p, tmp.p, nc, (h2_stream_t)s);
-          if (st != H2_OK) throw Error{st, "operand matvec failed"};
-          add_into(yo.p, tmp.p, (int64_t)N * nc);
-        }
-      }
-      if (o.lowrank_rank > 0)
-        lowrank_sample(o.lowrank_u, o.lowrank_v, N, N, o.lowrank_rank, omo.p, N, nc, yo.p, N, s);
-      DBuf<int> bad;
-      bad.alloc_zero(1, s);
-      k_check_finite_cols<<<ceil_div(N, 256), 256, 0, s>>>(yo.p, N, N, 0, nc, bad.p);
-      count_launch();
-      H2_CHECK_LAUNCH();
-      if (to_host(bad.p, 1, s)[0]) throw Error{H2_ERR_INPUT, "sampler produced non-finite values"};
-      if (fp64()) {
-        permute_in(true, yo.p, N, H->orig_of_pos.p, N, nc, L.Y64.p + (int64_t)c0 * N, N, s);
-      } else {
-        DBuf<double> yt;
-        yt.alloc((size_t)N * nc);
-        permute_in(true, yo.p, N, H->orig_of_pos.p, N, nc, yt.p, N, s);
-        convert32(yt.p, (int64_t)N * nc, L.Y32.p + (int64_t)c0 * N, s);
-      }
-      H2_CUDA(cudaStreamSynchronize(s));
+      each_side([&]() {
+        double *om = sd == 0 ? om64 : draw_omega(insts, nc);
+        sample_orig(om, H->dcur[insts[0]], nc);
+      });
     }
     sketch_cols += nc;
     timer.end(PH_SKETCH);
@@ -636,6 +673,61 @@ struct Builder {
   }
 
   void add_into(double *y, const double *x, int64_t n);
+
+  // Y(:, c0 .. c0+nc) of the current side from an original-order sampler:
+  // A Omega for the row side, A^T Psi for the column side (om64: the side's
+  // FP64 tree-order sample panel, ld N).
+  void sample_orig(const double *om64, int c0, int nc) {
+    LevelData &L = LV()[1];
+    const int64_t N = H->n_total;
+    DBuf<double> omo, yo;
+    omo.alloc((size_t)N * nc);
+    yo.alloc_zero((size_t)N * nc, s);
+    permute_out(true, om64 + (int64_t)c0 * N, N, H->orig_of_pos.p, N, nc, omo.p, N, s);
+    if (o.sketch == H2_SKETCH_DENSE) {
+      H2_REQUIRE(o.dense_a != nullptr, "dense sketch needs dense_a");
+      dense_gemm64(o.dense_a, N, N, omo.p, N, yo.p, N, nc, s, sd == 1);
+    } else if (o.sketch == H2_SKETCH_CALLBACK) {
+      h2_sampler_fn f = sd == 0 ? o.sampler : o.sampler_t;
+      void *ctx = sd == 0 ? o.sampler_ctx : o.sampler_t_ctx;
+      H2_REQUIRE(f != nullptr, sd == 0 ? "callback sketch needs a sampler"
+                                       : "a non-symmetric callback sketch needs sampler_t");
+      int rc = f(ctx, omo.p, yo.p, N, nc, N, (h2_stream_t)s);
+      if (rc != 0) throw Error{H2_ERR_SAMPLER, "sampler callback returned an error"};
+    } else {
+      // the operands are symmetric H2 matrices: the same products for A^T
+      H2_REQUIRE(o.operands != nullptr && o.n_operands > 0, "H2 sum needs operands");
+      DBuf<double> tmp;
+      tmp.alloc((size_t)N * nc);
+      for (int q = 0; q < o.n_operands; ++q) {
+        const h2_matrix *op = o.operands[q];
+        H2_REQUIRE(op && op->n_total == N, "operand size mismatch");
+        h2_status st = h2_matvec(op, omo.p, tmp.p, nc, (h2_stream_t)s);
+        if (st != H2_OK) throw Error{st, "operand matvec failed"};
+        add_into(yo.p, tmp.p, (int64_t)N * nc);
+      }
+    }
+    if (o.lowrank_rank > 0) {   // + U (V^T om), or V (U^T om) for A^T
+      const double *u = sd == 0 ? o.lowrank_u : o.lowrank_v;
+      const double *v = sd == 0 ? o.lowrank_v : o.lowrank_u;
+      lowrank_sample(u, v, N, N, o.lowrank_rank, omo.p, N, nc, yo.p, N, s);
+    }
+    DBuf<int> bad;
+    bad.alloc_zero(1, s);
+    k_check_finite_cols<<<ceil_div(N, 256), 256, 0, s>>>(yo.p, N, N, 0, nc, bad.p);
+    count_launch();
+    H2_CHECK_LAUNCH();
+    if (to_host(bad.p, 1, s)[0]) throw Error{H2_ERR_INPUT, "sampler produced non-finite values"};
+    if (fp64()) {
+      permute_in(true, yo.p, N, H->orig_of_pos.p, N, nc, L.Y64.p + (int64_t)c0 * N, N, s);
+    } else {
+      DBuf<double> yt;
+      yt.alloc((size_t)N * nc);
+      permute_in(true, yo.p, N, H->orig_of_pos.p, N, nc, yt.p, N, s);
+      convert32(yt.p, (int64_t)N * nc, L.Y32.p + (int64_t)c0 * N, s);
+    }
+    H2_CUDA(cudaStreamSynchronize(s));
+  }
 
   void count_sketch(const std::vector<int> &insts, bool far, int dc) {
     for (int i : insts) {
@@ -779,11 +871,18 @@ struct Builder {
     g.n_rows = L.n;
     g.ptr = H->near_ptr.p;
     dense_blocks_gen(H->kid, fp64(), g, s);
-    lowrank_near();
+    if (H->nonsym) {   // D^T(t, b) = D(b, t)^T: the kernel part is symmetric
+      const size_t es = fp64() ? 8 : 4;
+      H2_CUDA(cudaMemcpyAsync(fp64() ? (void *)H->Dt64.p : (void *)H->Dt32.p, Dp(),
+                              (size_t)H->D_size * es, cudaMemcpyDeviceToDevice, s));
+    }
+    each_side([&]() { lowrank_near(); });
     timer.end(PH_NEAR);
     std::vector<int32_t> b(C, 0), e(C, o.d0);
     set_cols(b, e);
-    if (far) {
+    if (H->nonsym) {
+      each_side([&]() { near_bsr(Yp(LV()[1]), -1.0); });
+    } else if (far) {
       P.alloc_zero((size_t)H->n_total * o.d0 * (fp64() ? 8 : 4), s);
       if (H->tensor_sketch) {
         // D Omega of the first columns from the generated entries of the near
@@ -802,23 +901,26 @@ struct Builder {
   }
 
   // The low-rank term's share of the near blocks D and of level l's couplings.
+  // (the current side's: U V^T for the row side, V U^T for the column side)
   void lowrank_near() {
     if (o.lowrank_rank == 0) return;
-    LevelData &L = H->lv[1];
+    LevelData &L = LV()[1];
     lowrank_blocks(fp64(), false, L.n, H->near_ptr.p, H->near_idx.p, H->doff.p, L.m.p, L.row.p,
-                   nullptr, nullptr, lr_ut.p, lr_vt.p, o.lowrank_rank, Dp(), s);
+                   nullptr, nullptr, lr_rows(), lr_cols(), o.lowrank_rank, Dp(), s);
   }
   void lowrank_couplings(int l) {
     if (o.lowrank_rank == 0) return;
-    LevelData &L = H->lv[l];
+    LevelData &L = LV()[l], &LO = LVO()[l];
+    const bool ns = H->nonsym;
     lowrank_blocks(fp64(), true, L.n, L.far_ptr.p, L.far_idx.p, L.boff.p, L.k.p, nullptr,
-                   L.krow.p, L.skel.p, lr_ut.p, lr_vt.p, o.lowrank_rank, Bp(L), s);
+                   L.krow.p, L.skel.p, lr_rows(), lr_cols(), o.lowrank_rank, Bp(L), s,
+                   ns ? LO.k.p : nullptr, ns ? LO.krow.p : nullptr, ns ? LO.skel.p : nullptr);
   }
 
   // out(cols) += sign * D Om1(cols) over the leaf tasks, columns from cb/ce
   // (out: an N-row panel, by default the level-1 Y panel with sign -1).
   void near_bsr(void *out = nullptr, double sign = -1.0) {
-    LevelData &L = H->lv[1];
+    LevelData &L = LV()[1];
     timer.begin(PH_BSR);
     BsrArgs a{};
     a.n_rows = L.n;
@@ -846,12 +948,15 @@ struct Builder {
 
   // Level l -> level l+1 panels for the current columns: skeleton rows of Y,
   // E^T Omega, then the far-field subtraction with the level-l couplings.
+  // Omega of a side sweeps up through the other side's bases (its rows follow
+  // the other side's layout; the same bases when symmetric).
   void transfer_up(int l) {
-    LevelData &L = H->lv[l], &U = H->lv[l + 1];
+    LevelData &L = LV()[l], &U = LV()[l + 1];
+    LevelData &LO = LVO()[l], &UO = LVO()[l + 1];
     timer.begin(PH_UP);
     gather_skeleton_rows(fp64(), L.dev(), Yp(L), L.M, Yp(U), U.M, cols(), L.active_next.p, s);
-    basis_t_apply(fp64(), L.dev(), Ep(L), Omp(L), L.M, Omp(U), U.M, cols(), L.active_next.p,
-                  L.max_m, L.max_k, s);
+    basis_t_apply(fp64(), LO.dev(), Ep(LO), Omp(L), LO.M, Omp(U), UO.M, cols(),
+                  LO.active_next.p, LO.max_m, LO.max_k, s);
     timer.end(PH_UP);
     if (L.far_nnz == 0) return;
     timer.begin(PH_BSR);
@@ -860,28 +965,28 @@ struct Builder {
     a.row_inst = L.inst.p;
     a.row_m = L.k.p;
     a.row_off = L.krow.p;
-    a.col_m = L.k.p;
-    a.col_off = L.krow.p;
+    a.col_m = LO.k.p;
+    a.col_off = LO.krow.p;
     a.ptr = L.far_ptr.p;
     a.idx = L.far_idx.p;
     a.boff = L.boff.p;
     a.blocks = Bp(L);
     a.in = Omp(U);
-    a.ld_in = U.M;
+    a.ld_in = UO.M;
     a.out = Yp(U);
     a.ld_out = U.M;
     a.sign = -1.0;
     a.cols = cols();
-    a.in_rows = U.M;
+    a.in_rows = UO.M;
     a.col_hi = col_hi;
     a.engine = o.bsr_engine;
-    bsr_apply(fp64(), a, L.max_k, max_cols, s);
+    bsr_apply(fp64(), a, std::max(L.max_k, LO.max_k), max_cols, s);
     timer.end(PH_BSR);
   }
 
   // ---------------- per-level steps -----------------------------------------
   void level_thresholds(int l, const std::vector<double> &eps_abs) {
-    LevelData &L = H->lv[l];
+    LevelData &L = LV()[l];
     int C = H->count;
     L.h_eps.assign(C, 0.0);
     for (int i = 0; i < C; ++i) {
@@ -919,7 +1024,7 @@ struct Builder {
   }
 
   void qr_round(int l, DBuf<int32_t> &unconv) {
-    LevelData &L = H->lv[l];
+    LevelData &L = LV()[l];
     DBuf<int64_t> ws_off;
     DBuf<double> ws;
     size_t smem = plan_workspace(L, 200 * 1024, 0, ws_off, ws, true);
@@ -947,15 +1052,18 @@ struct Builder {
   void run_level(int l, const std::vector<double> &eps_abs) {
     LevelData &L = H->lv[l];
     int C = H->count;
-    level_thresholds(l, eps_abs);
-    L.conv.alloc_zero(L.n, s);
+    each_side([&]() {
+      level_thresholds(l, eps_abs);
+      LV()[l].conv.alloc_zero(LV()[l].n, s);
+    });
     DBuf<int32_t> unconv;
     unconv.alloc(C);
     // adaptive sampling (Sec. III-B); d_inc = 0 is the fixed-sample
-    // construction (no convergence test, every cluster compressed from d0)
+    // construction (no convergence test, every cluster compressed from d0).
+    // A node of a non-symmetric build waits for both of its sides.
     for (; o.d_inc > 0;) {
       H2_CUDA(cudaMemsetAsync(unconv.p, 0, C * sizeof(int32_t), s));
-      qr_round(l, unconv);
+      each_side([&]() { qr_round(l, unconv); });
       std::vector<int32_t> hu = to_host(unconv.p, C, s);
       std::vector<int> need;
       for (int i = 0; i < C; ++i) {
@@ -973,15 +1081,24 @@ struct Builder {
       std::vector<int32_t> b(C, 0), e(C, 0);
       for (int i : need) { b[i] = H->dcur[i]; e[i] = H->dcur[i] + o.d_inc; }
       set_cols(b, e);
-      if (!far) near_bsr();
-      for (int lp = 1; lp < l; ++lp) transfer_up(lp);
+      if (!far) each_side([&]() { near_bsr(); });
+      for (int lp = 1; lp < l; ++lp) each_side([&]() { transfer_up(lp); });
       for (int i : need) H->dcur[i] += o.d_inc;
     }
-    L.d_at_id.assign(H->dcur.begin(), H->dcur.end());
-    // row ID of every cluster (batchedID)
+    // row ID (column ID for the column side) of every cluster (batchedID)
     DBuf<int32_t> dcur;
     std::vector<int32_t> hd(H->dcur.begin(), H->dcur.end());
     to_device(dcur, hd, s);
+    each_side([&]() {
+      LV()[l].d_at_id.assign(H->dcur.begin(), H->dcur.end());
+      id_level(l, dcur);
+    });
+    // couplings of this level (both sides' skeletons are known now)
+    each_side([&]() { couplings_level(l); });
+  }
+
+  void id_level(int l, const DBuf<int32_t> &dcur) {
+    LevelData &L = LV()[l];
     {
       DBuf<int64_t> cap;
       cap.alloc(L.n);
@@ -1007,7 +1124,7 @@ struct Builder {
     a.dcur = dcur.p;
     a.eps = L.eps.p;
     a.active = L.active.p;
-    a.ibar = l == 1 ? nullptr : H->lv[l - 1].skel.p;
+    a.ibar = l == 1 ? nullptr : LV()[l - 1].skel.p;
     a.k_out = L.k.p;
     a.J_tmp = L.Jtmp.p;
     a.skel_tmp = L.skeltmp.p;
@@ -1026,12 +1143,19 @@ struct Builder {
     L.J.alloc(std::max<int64_t>(L.K, 1));
     L.skel.alloc(std::max<int64_t>(L.K, 1));
     compact_skeletons(L.dev(), L.Jtmp.p, L.skeltmp.p, L.J.p, L.skel.p, s);
-    // couplings B = K(Itil_s, Itil_t) for the far list of this level
+  }
+
+  // couplings B(s, t) = A(Itil_s, Itil_t) for the far list of level l: the
+  // current side's skeletons on the rows, the other side's on the columns
+  // (the column side's blocks are those of A^T, for its own subtractions)
+  void couplings_level(int l) {
+    LevelData &L = LV()[l], &LO = LVO()[l];
+    const bool ns = H->nonsym;
     build_far_list(l);
     if (L.far_nnz > 0) {
       DBuf<int64_t> sz;
       sz.alloc(L.far_nnz);
-      block_sizes(L.far_nnz, L.far_erow.p, L.far_idx.p, L.k.p, L.k.p, fp64() ? 2 : 4, sz.p, s);
+      block_sizes(L.far_nnz, L.far_erow.p, L.far_idx.p, L.k.p, LO.k.p, fp64() ? 2 : 4, sz.p, s);
       L.boff.alloc(L.far_nnz + 1);
       scan_exclusive(sz.p, L.boff.p, L.far_nnz, s);
       L.B_size = to_host(L.boff.p + L.far_nnz, 1, s)[0];
@@ -1041,22 +1165,27 @@ struct Builder {
         sum_couplings(l);
         lowrank_couplings(l);
       } else {
-      CouplingArgs ca{};
-      ca.nnz = L.far_nnz;
-      ca.erow = L.far_erow.p;
-      ca.idx = L.far_idx.p;
-      ca.boff = L.boff.p;
-      ca.t = L.dev();
-      ca.skel = L.skel.p;
-      ca.inst = H->inst_dev.p;
-      ca.p64 = p64();
-      ca.p32 = p32();
-      ca.B = Bp(L);
-      ca.ptr = L.far_ptr.p;
-      timer.begin(PH_COUP);
-      coupling_gen(H->kid, fp64(), ca, s);
-      lowrank_couplings(l);
-      timer.end(PH_COUP);
+        CouplingArgs ca{};
+        ca.nnz = L.far_nnz;
+        ca.erow = L.far_erow.p;
+        ca.idx = L.far_idx.p;
+        ca.boff = L.boff.p;
+        ca.t = L.dev();
+        ca.skel = L.skel.p;
+        ca.inst = H->inst_dev.p;
+        ca.p64 = p64();
+        ca.p32 = p32();
+        ca.B = Bp(L);
+        ca.ptr = L.far_ptr.p;
+        if (ns) {
+          ca.col_k = LO.k.p;
+          ca.col_krow = LO.krow.p;
+          ca.col_skel = LO.skel.p;
+        }
+        timer.begin(PH_COUP);
+        coupling_gen(H->kid, fp64(), ca, s);
+        lowrank_couplings(l);
+        timer.end(PH_COUP);
       }
     } else if (is_sum()) {
       sum_g(l);   // later levels need this level's G even without couplings here
@@ -1120,7 +1249,7 @@ struct Builder {
   }
 
   void build_far_list(int l) {
-    LevelData &L = H->lv[l];
+    LevelData &L = LV()[l];
     int C = H->count;
     int64_t nnz = 0;
     for (int i = 0; i < C; ++i)
@@ -1169,23 +1298,28 @@ struct Builder {
       }
       U.n += nl;
     }
-    U.M = L.K;
     to_device(U.inst, U.h_inst, s);
     to_device(U.child0, U.h_child0, s);
-    U.row.alloc(std::max(U.n, 1));
-    U.m.alloc(std::max(U.n, 1));
-    inner_tasks(U.n, U.child0.p, L.krow.p, L.k.p, U.row.p, U.m.p, s);
-    U.h_m = to_host(U.m.p, U.n, s);
-    U.h_row = to_host(U.row.p, U.n, s);
-    U.max_m = U.h_m.empty() ? 0 : *std::max_element(U.h_m.begin(), U.h_m.end());
-    alloc_panels(U);
+    if (H->nonsym) copy_tasks(H->lvc[l + 1], U);
+    // each side's geometry from its own children's ranks
+    each_side([&]() {
+      LevelData &Ls = LV()[l], &Us = LV()[l + 1];
+      Us.M = Ls.K;
+      Us.row.alloc(std::max(Us.n, 1));
+      Us.m.alloc(std::max(Us.n, 1));
+      inner_tasks(Us.n, Us.child0.p, Ls.krow.p, Ls.k.p, Us.row.p, Us.m.p, s);
+      Us.h_m = to_host(Us.m.p, Us.n, s);
+      Us.h_row = to_host(Us.row.p, Us.n, s);
+      Us.max_m = Us.h_m.empty() ? 0 : *std::max_element(Us.h_m.begin(), Us.h_m.end());
+    });
+    each_side([&]() { alloc_panels(LV()[l + 1], LVO()[l].K); });
     set_level_flags(l + 1);
     // panels for all current columns, then subtract the level-l couplings
     std::vector<int32_t> b(C, 0), e(C, 0);
     for (int i = 0; i < C; ++i)
       if (L.h_active_next[i]) e[i] = H->dcur[i];
     set_cols(b, e);
-    transfer_up(l);
+    each_side([&]() { transfer_up(l); });
   }
 
   KernelTimer ktimer;
@@ -1203,6 +1337,7 @@ struct Builder {
     timer.begin(PH_TOTAL);
     setup_instances(kids, params);
     H->lv.resize(std::max(H->levels, 1) + 2);
+    if (H->nonsym) H->lvc.resize(H->lv.size());
     setup_leaves();
     set_level_flags(1);
     if (o.lowrank_rank > 0) {
@@ -1231,6 +1366,12 @@ struct Builder {
     if (far)
       instance_sumsq(Yp(H->lv[1]), P.p, fp64(), H->n_total, ib.p, in_.p, C, o.d0, ss.p, s);
     std::vector<double> hs = to_host(ss.p, C, s), eps_abs(C);
+    if (H->nonsym) {
+      // ||A||_F from both sketches: the same thresholds for A and A^T
+      instance_sumsq(Yp(H->lvc[1]), nullptr, fp64(), H->n_total, ib.p, in_.p, C, o.d0, ss.p, s);
+      std::vector<double> hz = to_host(ss.p, C, s);
+      for (int i = 0; i < C; ++i) hs[i] = 0.5 * (hs[i] + hz[i]);
+    }
     for (int i = 0; i < C; ++i) {
       if (!std::isfinite(hs[i])) throw Error{H2_ERR_INPUT, "sketch is not finite"};
       double nrmK = std::sqrt(hs[i] / o.d0);
@@ -1245,12 +1386,20 @@ struct Builder {
     }
     timer.end(PH_TOTAL);
     H2_CUDA(cudaStreamSynchronize(s));
-    // release build-time panels
-    for (auto &L : H->lv) {
-      L.Y64.release(); L.Om64.release(); L.Y32.release(); L.Om32.release();
-      L.Jtmp.release(); L.skeltmp.release(); L.conv.release();
+    // release build-time panels (and the column side's blocks of A^T)
+    for (auto *lvs : {&H->lv, &H->lvc})
+      for (auto &L : *lvs) {
+        L.Y64.release(); L.Om64.release(); L.Y32.release(); L.Om32.release();
+        L.Jtmp.release(); L.skeltmp.release(); L.conv.release();
+      }
+    for (auto &L : H->lvc) {
+      L.B64.release();
+      L.B32.release();
     }
+    H->Dt64.release();
+    H->Dt32.release();
     om_stage.release();
+    om_stage_c.release();
     fill_stats(launches0);
     H->converged = not_conv.empty();
     return H->converged ? H2_OK : H2_ERR_NOT_CONVERGED;
@@ -1268,18 +1417,19 @@ struct Builder {
     st.rank_min = 1 << 30;
     st.rank_max = 0;
     int64_t bb = 0, bu = 0;
-    for (int l = 1; l <= H->levels; ++l) {
-      LevelData &L = H->lv[l];
-      for (int t = 0; t < L.n; ++t) {
-        if (!L.h_active[L.h_inst[t]]) continue;
-        st.rank_min = std::min(st.rank_min, L.h_k[t]);
-        st.rank_max = std::max(st.rank_max, L.h_k[t]);
+    for (int q = 0; q < nsides(); ++q)   // ranks and bases of both sides
+      for (int l = 1; l <= H->levels; ++l) {
+        LevelData &L = q == 0 ? H->lv[l] : H->lvc[l];
+        for (int t = 0; t < L.n; ++t) {
+          if (!L.h_active[L.h_inst[t]]) continue;
+          st.rank_min = std::min(st.rank_min, L.h_k[t]);
+          st.rank_max = std::max(st.rank_max, L.h_k[t]);
+        }
+        if (q == 0) bb += L.B_size;
+        int64_t used = 0;
+        for (int t = 0; t < L.n; ++t) used += (int64_t)L.h_m[t] * L.h_k[t];
+        bu += used;
       }
-      bb += L.B_size;
-      int64_t used = 0;
-      for (int t = 0; t < L.n; ++t) used += (int64_t)L.h_m[t] * L.h_k[t];
-      bu += used;
-    }
     if (st.rank_min > st.rank_max) st.rank_min = 0;
     size_t es = fp64() ? 8 : 4;
     st.bytes_dense = H->D_size * es;
@@ -1336,6 +1486,15 @@ void validate_opts(const h2_build_opts &o) {
   H2_REQUIRE(o.tc_cols == 0 || o.tc_cols == 32 || o.tc_cols == 64 || o.tc_cols == 80,
              "tc_cols must be 0, 32, 64 or 80");
   H2_REQUIRE(o.ksum_split >= 0 && o.ksum_split <= 1024, "ksum_split must be in 0..1024");
+  H2_REQUIRE(o.nonsym == 0 || o.nonsym == 1, "nonsym must be 0 or 1");
+  if (o.nonsym) {
+    H2_REQUIRE(o.sketch != H2_SKETCH_KSUM,
+               "a non-symmetric build needs a dense, callback or H2-matvec sketch");
+    H2_REQUIRE(o.omega_mode == 0 || o.psi_stored != nullptr,
+               "stored Omega mode of a non-symmetric build needs psi_stored");
+    H2_REQUIRE(o.sketch != H2_SKETCH_CALLBACK || o.sampler_t != nullptr,
+               "a non-symmetric callback sketch needs sampler_t");
+  }
 }
 
 template <typename F>
@@ -1394,47 +1553,48 @@ void matvec_impl(const h2_matrix *H, const double *x, double *y, int nrhs, cudaS
   }
   int levels = H->levels;
   if (levels > 0) {
+    // x^ rides the column bases V up (U when symmetric), y^ the row bases U down
+    const std::vector<LevelData> &CV = H->nonsym ? H->lvc : H->lv;
     std::vector<DBuf<char>> xh(levels + 1), yh(levels + 1);
     for (int l = 1; l <= levels; ++l) {
-      const LevelData &L = H->lv[l];
-      xh[l].alloc((size_t)std::max<int64_t>(L.K, 1) * nrhs * es);
-      yh[l].alloc_zero((size_t)std::max<int64_t>(L.K, 1) * nrhs * es, s);
+      xh[l].alloc((size_t)std::max<int64_t>(CV[l].K, 1) * nrhs * es);
+      yh[l].alloc_zero((size_t)std::max<int64_t>(H->lv[l].K, 1) * nrhs * es, s);
     }
     // upsweep
     for (int l = 1; l <= levels; ++l) {
-      const LevelData &L = H->lv[l];
+      const LevelData &L = CV[l];
       const void *E = (const void *)L.E.p;
       if (l == 1)
         basis_t_apply(f64, L.dev(), E, xt.p, N, xh[1].p, L.K, cols, L.active.p, L.max_m, L.max_k, s);
       else
-        basis_t_apply(f64, L.dev(), E, xh[l - 1].p, H->lv[l - 1].K, xh[l].p, L.K, cols,
+        basis_t_apply(f64, L.dev(), E, xh[l - 1].p, CV[l - 1].K, xh[l].p, L.K, cols,
                       L.active.p, L.max_m, L.max_k, s);
     }
     // couplings
     for (int l = 1; l <= levels; ++l) {
-      const LevelData &L = H->lv[l];
+      const LevelData &L = H->lv[l], &LC = CV[l];
       if (L.far_nnz == 0) continue;
       BsrArgs a{};
       a.n_rows = L.n;
       a.row_inst = L.inst.p;
       a.row_m = L.k.p;
       a.row_off = L.krow.p;
-      a.col_m = L.k.p;
-      a.col_off = L.krow.p;
+      a.col_m = LC.k.p;
+      a.col_off = LC.krow.p;
       a.ptr = L.far_ptr.p;
       a.idx = L.far_idx.p;
       a.boff = L.boff.p;
       a.blocks = f64 ? (const void *)L.B64.p : (const void *)L.B32.p;
       a.in = xh[l].p;
-      a.ld_in = L.K;
-      a.in_rows = L.K;
+      a.ld_in = LC.K;
+      a.in_rows = LC.K;
       a.col_hi = nrhs;
       a.out = yh[l].p;
       a.ld_out = L.K;
       a.sign = 1.0;
       a.cols = cols;
       a.engine = H->bsr_engine;
-      bsr_apply(f64, a, L.max_k, nrhs, s);
+      bsr_apply(f64, a, std::max(L.max_k, LC.max_k), nrhs, s);
     }
     // downsweep
     for (int l = levels; l >= 1; --l) {
@@ -1679,6 +1839,8 @@ h2_status h2_build_batched(const h2_tree *const *trees, int count, const int *ke
       H2_REQUIRE(tols[i] >= 0 && std::isfinite(tols[i]), "tol must be finite and >= 0");
     }
     H2_REQUIRE(opts->lowrank_rank == 0 || count == 1, "a low-rank term needs a single instance");
+    H2_REQUIRE(!opts->nonsym || (count == 1 && kernel_ids[0] != H2_K_H2SUM),
+               "a non-symmetric build takes a single instance of a kernel operator");
     if (kernel_ids[0] == H2_K_H2SUM) {
       H2_REQUIRE(count == 1, "an H2 sum is built as a single instance");
       H2_REQUIRE(opts->operands && opts->n_operands >= 1, "an H2 sum needs operands");
@@ -1687,6 +1849,7 @@ h2_status h2_build_batched(const h2_tree *const *trees, int count, const int *ke
       for (int q = 0; q < opts->n_operands; ++q) {
         const h2_matrix *op = opts->operands[q];
         H2_REQUIRE(op != nullptr && op->count == 1, "operands must be single-instance H2 matrices");
+        H2_REQUIRE(!op->nonsym, "operands of an H2 sum must be symmetric H2 matrices");
         H2_REQUIRE(op->n_total == t->n && op->inst_depth[0] == t->depth &&
                        op->inst_ltop[0] == t->l_top && op->near_nnz == t->near_nnz,
                    "operands must be built on the same cluster tree and partition");
@@ -1700,6 +1863,7 @@ h2_status h2_build_batched(const h2_tree *const *trees, int count, const int *ke
     H->fp64 = opts->prec == H2_PREC_FP64;
     H->tensor_sketch = opts->prec == H2_PREC_MIXED;
     H->bsr_engine = opts->bsr_engine;
+    H->nonsym = opts->nonsym != 0;
     H->kid = kernel_ids[0];
     Builder b(H.get(), trees, *opts, (cudaStream_t)s);
     h2_status st = b.run(kernel_ids, params, tols);
@@ -1739,13 +1903,15 @@ h2_status h2_stats(const h2_matrix *h, h2_stats_t *st) {
   });
 }
 
-h2_status h2_export_level(const h2_matrix *h, int inst, int level, int32_t *ranks, int32_t *skel,
-                          double *eps_l, int32_t *d_l) {
+namespace {
+h2_status export_side(const h2_matrix *h, bool col_side, int inst, int level, int32_t *ranks,
+                      int32_t *skel, double *eps_l, int32_t *d_l) {
   return guarded([&]() -> h2_status {
     H2_REQUIRE(h && ranks, "NULL argument");
+    H2_REQUIRE(!col_side || h->nonsym, "the matrix has one set of bases (a symmetric build)");
     H2_REQUIRE(inst >= 0 && inst < h->count, "instance out of range");
     H2_REQUIRE(level >= 1 && level <= h->inst_ltop[inst], "level not compressed");
-    const LevelData &L = h->lv[level];
+    const LevelData &L = col_side ? h->lvc[level] : h->lv[level];
     int base = L.task_base[inst];
     int nl = 1 << (h->inst_depth[inst] - level + 1);
     std::vector<int64_t> krow = to_host(L.krow.p, L.n + 1, 0);
@@ -1763,6 +1929,17 @@ h2_status h2_export_level(const h2_matrix *h, int inst, int level, int32_t *rank
     if (d_l) *d_l = L.d_at_id[inst];
     return H2_OK;
   });
+}
+}  // namespace
+
+h2_status h2_export_level(const h2_matrix *h, int inst, int level, int32_t *ranks, int32_t *skel,
+                          double *eps_l, int32_t *d_l) {
+  return export_side(h, false, inst, level, ranks, skel, eps_l, d_l);
+}
+
+h2_status h2_export_col_level(const h2_matrix *h, int inst, int level, int32_t *ranks,
+                              int32_t *skel) {
+  return export_side(h, true, inst, level, ranks, skel, nullptr, nullptr);
 }
 
 h2_status h2_autotune(const h2_tree *tree, int kernel_id, const double *params, int nparams,

@@ -12,13 +12,12 @@
 // CTA = one row task (at most 128 rows: the MMA's M, padding rows zero) x one
 // chunk of NCOL columns, 10 warps with fixed roles:
 //   warp 0      producer: per step (one 32-wide K chunk of one partner block)
-//               one bulk copy of the partner's input slice from an "input
-//               image" into a shared-memory ring;
+//               bulk copies of the partner's input slice (from an "input
+//               image") and of the chunk's columns of the block (contiguous
+//               in the column-major block) into a shared-memory ring;
 //   warp 1      one thread issues the MMAs of a step and commits them;
-//   warps 2-5   stage the block: thread = block row, 32 values of the chunk
-//               (coalesced across the warp), split into TF32 parts and
-//               stored into TMEM (operand A; the block never passes through
-//               shared memory), loads of the next step in flight meanwhile;
+//   warps 2-5   move the chunk into TMEM (operand A): thread = block row, 32
+//               values read from shared memory, split into TF32 parts;
 //   warps 6-9   read every partner's product back from TMEM (two
 //               accumulators, so the next partner's products proceed), plain
 //               sums over eight partners, compensated sums across in shared

@@ -948,7 +948,9 @@ __global__ void __launch_bounds__(256) k_gen_rows(int n_rows, const int64_t *ptr
                                                   const int32_t *rows_of, const int64_t *row0,
                                                   const int64_t *krow, const int32_t *skel,
                                                   const int32_t *tinst, const InstDev *inst,
-                                                  Points64 p64, Points32 p32, void *out_) {
+                                                  Points64 p64, Points32 p32, void *out_,
+                                                  const int32_t *cols_of, const int64_t *ckrow,
+                                                  const int32_t *cskel) {
   constexpr int NC = PtsOf<T>::NC;
   constexpr int NS = (NC * (int)sizeof(T) + 15) / 16 * 16 / (int)sizeof(T);   // 16-byte rows
   __shared__ __align__(16) T sa[kMaxRows * NS], sb[2][kMaxRows * NS];
@@ -965,6 +967,12 @@ __global__ void __launch_bounds__(256) k_gen_rows(int n_rows, const int64_t *ptr
   auto gpos = [&](int task, int i) -> int64_t {
     return SKEL ? (int64_t)skel[krow[task] + i] : row0[task] + i;
   };
+  // partners: the column side's skeletons where given (separate row and
+  // column bases), else the rows' own
+  auto gpos_c = [&](int task, int j) -> int64_t {
+    return SKEL && cskel ? (int64_t)cskel[ckrow[task] + j] : gpos(task, j);
+  };
+  auto width = [&](int task) { return cols_of ? cols_of[task] : rows_of[task]; };
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     const int64_t g = gpos(tr, i);
     ga[i] = g;
@@ -973,9 +981,9 @@ __global__ void __launch_bounds__(256) k_gen_rows(int n_rows, const int64_t *ptr
   // partner points of entry e into buffer slot
   auto load_partner = [&](int64_t e, int slot) {
     const int tc = idx[e];
-    const int mb = rows_of[tc];
+    const int mb = width(tc);
     for (int j = threadIdx.x; j < mb; j += blockDim.x) {
-      const int64_t g = gpos(tc, j);
+      const int64_t g = gpos_c(tc, j);
       gb[slot][j] = g;
       PtsOf<T>::load(p64, p32, g, sb[slot] + j * NS);
     }
@@ -989,7 +997,7 @@ __global__ void __launch_bounds__(256) k_gen_rows(int n_rows, const int64_t *ptr
   for (int64_t e = e0; e < e1; ++e) {
     const int slot = (int)((e - e0) & 1);
     if (e + 1 < e1) load_partner(e + 1, slot ^ 1);   // overlaps the evaluation below
-    const int mb = rows_of[idx[e]];
+    const int mb = width(idx[e]);
     T *blk = out + off[e];
     const T *pb = sb[slot];
     const int64_t *gbs = gb[slot];
@@ -1092,11 +1100,11 @@ void dense_blocks_gen(int kid, bool fp64, const DgenArgs &a, cudaStream_t s) {
     if (fp64)
       k_gen_rows<KID, double, false><<<a.n_rows, 256, 0, s>>>(
           a.n_rows, a.ptr, a.idx, a.doff, a.m, a.row, nullptr, nullptr, a.tinst, a.inst, a.p64,
-          a.p32, a.D);
+          a.p32, a.D, nullptr, nullptr, nullptr);
     else
       k_gen_rows<KID, float, false><<<a.n_rows, 256, 0, s>>>(
           a.n_rows, a.ptr, a.idx, a.doff, a.m, a.row, nullptr, nullptr, a.tinst, a.inst, a.p64,
-          a.p32, a.D);
+          a.p32, a.D, nullptr, nullptr, nullptr);
     count_launch();
     H2_CHECK_LAUNCH();
   });
@@ -1308,11 +1316,11 @@ void coupling_gen(int kid, bool fp64, const CouplingArgs &a, cudaStream_t s) {
     if (fp64)
       k_gen_rows<KID, double, true><<<a.t.n, 256, 0, s>>>(
           a.t.n, a.ptr, a.idx, a.boff, a.t.k, nullptr, a.t.krow, a.skel, a.t.inst, a.inst, a.p64,
-          a.p32, a.B);
+          a.p32, a.B, a.col_k, a.col_krow, a.col_skel);
     else
       k_gen_rows<KID, float, true><<<a.t.n, 256, 0, s>>>(
           a.t.n, a.ptr, a.idx, a.boff, a.t.k, nullptr, a.t.krow, a.skel, a.t.inst, a.inst, a.p64,
-          a.p32, a.B);
+          a.p32, a.B, a.col_k, a.col_krow, a.col_skel);
     count_launch();
     H2_CHECK_LAUNCH();
   });

@@ -145,6 +145,11 @@ struct CouplingArgs {
   Points32 p32;
   void *B;
   const int64_t *ptr;       // far CSR over the level's tasks (t.n rows)
+  // column tasks' ranks, skeleton offsets and skeletons when they differ from
+  // the rows' (separate row and column bases); NULL = the rows'
+  const int32_t *col_k = nullptr;
+  const int64_t *col_krow = nullptr;
+  const int32_t *col_skel = nullptr;
 };
 void coupling_gen(int kid, bool fp64, const CouplingArgs &a, cudaStream_t s);
 
@@ -218,9 +223,12 @@ void lowrank_sample(const double *U, const double *V, int64_t ld, int64_t n, int
                     cudaStream_t s);
 // Every block e of the CSR (rows n_rows tasks) += U(rows) V(cols)^T, the rows
 // of a task being its points (row0) or its skeleton points (skel at krow).
+// cols_of / ckrow / cskel: the column tasks' ranks and skeletons when they
+// differ from the rows' (separate row and column bases); NULL = the rows'.
 void lowrank_blocks(bool fp64, bool skel_rows, int n_rows, const int64_t *ptr, const int32_t *idx,
                     const int64_t *off, const int32_t *rows_of, const int64_t *row0,
                     const int64_t *krow, const int32_t *skel, const void *Ut, const void *Vt,
-                    int r, void *out, cudaStream_t s);
+                    int r, void *out, cudaStream_t s, const int32_t *cols_of = nullptr,
+                    const int64_t *ckrow = nullptr, const int32_t *cskel = nullptr);
 
 }  // namespace h2

@@ -192,7 +192,7 @@ void convert_cols_to32(const double *src, int64_t ld, int64_t row0, int64_t n, i
 
 // Dense GEMM Y[:, c] = A Om[:, c] (FP64), all column-major.
 void dense_gemm64(const double *a, int64_t lda, int64_t n, const double *om, int64_t ldo,
-                  double *y, int64_t ldy, int d, cudaStream_t s);
+                  double *y, int64_t ldy, int d, cudaStream_t s, bool trans = false);
 // Entries K(rows, cols) into out (nr x nc, ld nr).
 void entry_block64(int kid, const KernelDesc &kd, Points64 pts, const int32_t *rows, int64_t nr,
                    const int32_t *cols, int64_t nc, double *out, cudaStream_t s);

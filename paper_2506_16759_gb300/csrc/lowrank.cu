@@ -114,7 +114,9 @@ __global__ void __launch_bounds__(256) k_lr_blocks(int n_rows, const int64_t *pt
                                                    const int32_t *idx, const int64_t *off,
                                                    const int32_t *rows_of, const int64_t *row0,
                                                    const int64_t *krow, const int32_t *skel,
-                                                   const T *Ut, const T *Vt, int r, T *out) {
+                                                   const int32_t *cols_of, const int64_t *ckrow,
+                                                   const int32_t *cskel, const T *Ut, const T *Vt,
+                                                   int r, T *out) {
   extern __shared__ __align__(16) unsigned char lr_smem[];
   const int rs = r + 1;                       // padded row of a staged factor
   T *sU = reinterpret_cast<T *>(lr_smem);     // [64][rs]
@@ -127,10 +129,15 @@ __global__ void __launch_bounds__(256) k_lr_blocks(int n_rows, const int64_t *pt
   auto gpos = [&](int task, int i) -> int64_t {
     return SKEL ? (int64_t)skel[krow[task] + i] : row0[task] + i;
   };
+  // columns: the column side's skeletons where given (separate row and
+  // column bases), else the rows' own
+  auto gpos_c = [&](int task, int j) -> int64_t {
+    return SKEL && cskel ? (int64_t)cskel[ckrow[task] + j] : gpos(task, j);
+  };
   const int ii = threadIdx.x & 63, jg = threadIdx.x >> 6;
   for (int64_t e = e0; e < e1; ++e) {
     const int tc = idx[e];
-    const int mb = rows_of[tc];
+    const int mb = cols_of ? cols_of[tc] : rows_of[tc];
     T *blk = out + off[e];
     for (int i0 = 0; i0 < m; i0 += 64) {
       const int mi = min(64, m - i0);
@@ -139,7 +146,7 @@ __global__ void __launch_bounds__(256) k_lr_blocks(int n_rows, const int64_t *pt
         for (int u = threadIdx.x; u < 64 * r; u += blockDim.x) {
           const int a = u / r, k = u % r;
           sU[a * rs + k] = a < mi ? Ut[gpos(tr, i0 + a) * r + k] : T(0);
-          sV[a * rs + k] = a < mj ? Vt[gpos(tc, j0 + a) * r + k] : T(0);
+          sV[a * rs + k] = a < mj ? Vt[gpos_c(tc, j0 + a) * r + k] : T(0);
         }
         __syncthreads();
         if (ii < mi) {
@@ -196,7 +203,8 @@ void lowrank_sample(const double *U, const double *V, int64_t ld, int64_t n, int
 void lowrank_blocks(bool fp64, bool skel_rows, int n_rows, const int64_t *ptr, const int32_t *idx,
                     const int64_t *off, const int32_t *rows_of, const int64_t *row0,
                     const int64_t *krow, const int32_t *skel, const void *Ut, const void *Vt,
-                    int r, void *out, cudaStream_t s) {
+                    int r, void *out, cudaStream_t s, const int32_t *cols_of,
+                    const int64_t *ckrow, const int32_t *cskel) {
   if (n_rows == 0 || r == 0) return;
   H2_REQUIRE(r <= kLrMaxRank, "low-rank term of rank above 64");
   auto go = [&](auto T0, auto S0) {
@@ -206,8 +214,8 @@ void lowrank_blocks(bool fp64, bool skel_rows, int n_rows, const int64_t *ptr, c
     auto kern = k_lr_blocks<T, SK>;
     if (bytes > 48 * 1024)
       H2_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-    kern<<<n_rows, 256, bytes, s>>>(n_rows, ptr, idx, off, rows_of, row0, krow, skel,
-                                    (const T *)Ut, (const T *)Vt, r, (T *)out);
+    kern<<<n_rows, 256, bytes, s>>>(n_rows, ptr, idx, off, rows_of, row0, krow, skel, cols_of,
+                                    ckrow, cskel, (const T *)Ut, (const T *)Vt, r, (T *)out);
   };
   if (fp64) {
     if (skel_rows) go(double{}, std::true_type{});

@@ -303,9 +303,11 @@ __global__ void k_split32(const double *x, const double *y, const double *z, int
 }
 
 // Dense FP64 GEMM tile: 64 rows x 32 columns per CTA, k-steps of 32.
+// trans: C = A^T B (the transpose of a caller's operator, for the column
+// sketch of a non-symmetric construction).
 __global__ void __launch_bounds__(256) k_dense_gemm64(const double *A, int64_t lda, int64_t n,
                                                       const double *B, int64_t ldb, double *C,
-                                                      int64_t ldc, int d) {
+                                                      int64_t ldc, int d, bool trans) {
   __shared__ double sa[32][65];
   __shared__ double sb[32][33];
   int64_t r0 = blockIdx.x * 64;
@@ -314,10 +316,18 @@ __global__ void __launch_bounds__(256) k_dense_gemm64(const double *A, int64_t l
   int tc = threadIdx.x / 64;   // column group (8 columns each)
   double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (int64_t k0 = 0; k0 < n; k0 += 32) {
-    for (int q = threadIdx.x; q < 64 * 32; q += 256) {
-      int r = q % 64, k = q / 64;
-      int64_t gr = r0 + r, gk = k0 + k;
-      sa[k][r] = (gr < n && gk < n) ? A[gr + gk * lda] : 0.0;
+    if (!trans) {
+      for (int q = threadIdx.x; q < 64 * 32; q += 256) {
+        int r = q % 64, k = q / 64;
+        int64_t gr = r0 + r, gk = k0 + k;
+        sa[k][r] = (gr < n && gk < n) ? A[gr + gk * lda] : 0.0;
+      }
+    } else {   // consecutive threads read consecutive k of one column of A
+      for (int q = threadIdx.x; q < 64 * 32; q += 256) {
+        int k = q % 32, r = q / 32;
+        int64_t gr = r0 + r, gk = k0 + k;
+        sa[k][r] = (gr < n && gk < n) ? A[gk + gr * lda] : 0.0;
+      }
     }
     for (int q = threadIdx.x; q < 32 * 32; q += 256) {
       int k = q % 32, c = q / 32;
@@ -722,10 +732,10 @@ void convert_cols_to32(const double *src, int64_t ld, int64_t row0, int64_t n, i
 }
 
 void dense_gemm64(const double *a, int64_t lda, int64_t n, const double *om, int64_t ldo,
-                  double *y, int64_t ldy, int d, cudaStream_t s) {
+                  double *y, int64_t ldy, int d, cudaStream_t s, bool trans) {
   if (n == 0 || d == 0) return;
   dim3 grid(ceil_div(n, 64), ceil_div(d, 32));
-  k_dense_gemm64<<<grid, 256, 0, s>>>(a, lda, n, om, ldo, y, ldy, d);
+  k_dense_gemm64<<<grid, 256, 0, s>>>(a, lda, n, om, ldo, y, ldy, d, trans);
   count_launch();
   H2_CHECK_LAUNCH();
 }
