@@ -59,6 +59,8 @@ FIT_SIZES = (4096, 8192, 16384)
 # oracle's arithmetic, rank for rank) reports; smaller members of the family
 # stop earlier, so the sketch sample takes the full size's column blocks.
 FULL_D_FINAL = 80
+# launch-shape build options the autotuner picks (passed through to every build)
+SHAPE_KEYS = ("bsr_engine", "tc_cols", "ksum_split", "queue_order")
 _W_STATE = {}
 
 
@@ -572,7 +574,7 @@ def main_gpu(args):
                               d_inc=w.d_inc, d_max=w.d_max, seed=99)
         del tree0
         sched = {k: kw[k] for k in ("d0", "d_inc", "prec", "bsr_engine", "tc_cols",
-                                    "ksum_split")}
+                                    "ksum_split", "queue_order")}
         tuned = dict(sched, tuning_s=time.perf_counter() - t0, build_ms=ms)
         log(f"[bench] autotuned schedule {sched} ({ms:.1f} ms build)")
 
@@ -581,7 +583,7 @@ def main_gpu(args):
         if precision == "fp64":
             sc = {"d0": w.d0, "d_inc": w.d_inc, "prec": "fp64"}
         tree = api.ClusterTree(X, w.leaf_size, w.eta)
-        shapes = {k: sc[k] for k in ("bsr_engine", "tc_cols", "ksum_split") if k in sc}
+        shapes = {k: sc[k] for k in SHAPE_KEYS if k in sc}
         h = api.H2Matrix.build(tree, w.kernel, w.params, w.tol, prec=sc["prec"], seed=seed,
                                sketch="ksum", timing=timing, d0=sc["d0"], d_inc=sc["d_inc"],
                                d_max=w.d_max, **shapes)
@@ -682,8 +684,7 @@ def main_gpu(args):
             h = api.H2Matrix.build(tree, w.kernel, w.params, w.tol, prec=sched["prec"], seed=k,
                                    sketch="ksum", d0=sched["d0"], d_inc=sched["d_inc"],
                                    d_max=w.d_max,
-                                   **{k2: sched[k2] for k2 in ("bsr_engine", "tc_cols",
-                                                               "ksum_split") if k2 in sched})
+                                   **{k2: sched[k2] for k2 in SHAPE_KEYS if k2 in sched})
             ranks, skel, _, _ = h.export_level(1)       # device -> host read of the result
             e1.record()
             torch.cuda.synchronize()
@@ -812,6 +813,9 @@ def main_kernel_only(args):
     if args.kernel_only == "paper":
         main_paper_problem(args, dev)
         return
+    if args.kernel_only == "matvec":
+        main_matvec(args, dev)
+        return
     if args.kernel_only == "build":
         w = W.scaled(w, args.n or w.n)
         X = torch.from_numpy(w.points()).to(dev)
@@ -853,6 +857,53 @@ def main_kernel_only(args):
     ms = statistics.mean(times)
     print(json.dumps({"kernel_only": "ksum", "prec": args.prec, "n": w.n, "columns": 32,
                       "ms": ms, "tflops": flops / (ms * 1e-3) / 1e12}), flush=True)
+
+
+def main_matvec(args, dev):
+    """The H2 matrix-vector product on its own: the first operand of the
+    H2-sum workload (exp(-r/0.1) on 2^18 uniform points in [0,1]^3, built in
+    mixed precision at tol 1e-8) applied to 16 and 80 Gaussian columns.  The
+    product reads every stored block once (near-field D, couplings B, bases
+    E), so its roofline is HBM bandwidth over the operand's bytes."""
+    import torch
+
+    from paper_2506_16759_gb300 import api
+    from paper_2506_16759_gb300 import workloads as W
+    w = W.config("c4")
+    if args.n:
+        w = W.scaled(w, args.n)
+    kop, pop = w.extra["operands"][0]
+    X = torch.from_numpy(w.points()).to(dev)
+    tree = api.ClusterTree(X, w.leaf_size, w.eta)
+    op = api.H2Matrix.build(tree, kop, pop, w.extra["operand_tol"], prec="mixed", seed=3)
+    st = op.stats()
+    op_bytes = st["bytes_dense"] + st["bytes_coupling"] + st["bytes_basis"]
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    out = {"kernel_only": "matvec", "n": w.n, "operand_tol": w.extra["operand_tol"],
+           "operand_bytes": op_bytes, "rank_max": st["rank_max"], "columns": {}}
+    mp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm = json.load(open(mp)).get("hbm_gbs") if os.path.exists(mp) else 6800.0
+    out["hbm_peak_gbs"] = hbm
+    for cols in (16, 80):
+        G = torch.from_numpy(W.gaussian_probe(w.n, cols, 0)).to(dev)
+        for _ in range(args.warmup):
+            op.matvec(G)
+        times = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            op.matvec(G)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        ms = statistics.mean(times)
+        gbs = (op_bytes + 2.0 * w.n * cols * 8) / (ms * 1e-3) / 1e9
+        out["columns"][str(cols)] = {"ms": ms, "gb_per_s": gbs,
+                                     "hbm_frac": gbs / hbm if hbm else None}
+    print(json.dumps(out), flush=True)
 
 
 def main_paper_problem(args, dev):
@@ -949,7 +1000,7 @@ def main():
     ap.add_argument("--oracle-baseline", nargs=2, type=int, default=None, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-reference", nargs=3, type=int, default=None,
                     help=argparse.SUPPRESS)
-    ap.add_argument("--kernel-only", default="", choices=["", "ksum", "build", "paper"],
+    ap.add_argument("--kernel-only", default="", choices=["", "ksum", "build", "paper", "matvec"],
                     help="time only the fused sketch, builds at --n points (for profiling), "
                          "or a paper kernel problem with the H2-matvec sampler")
     ap.add_argument("--problem", default="helmholtz", choices=["exp3d", "helmholtz", "update"],

@@ -134,7 +134,7 @@ typedef struct {
   /* Launch shapes (mixed precision; 0 = the default), the knobs h2_autotune
    * tunes: */
   int bsr_engine;             /* block-sparse products: 0 tensor cores where the
-                                 blocks have at most 128 rows, 1 CUDA cores */
+                                 blocks have at most 256 rows, 1 CUDA cores */
   int tc_cols;                /* sample columns per tensor-core sketch launch:
                                  0 = 80, or 64 or 32 */
   int ksum_split;             /* far-only sketch: target work items per SM, each
@@ -157,6 +157,11 @@ typedef struct {
                                  device N x d_max like omega_stored */
   h2_sampler_fn sampler_t;    /* nonsym + H2_SKETCH_CALLBACK: y = A^T x */
   void *sampler_t_ctx;
+  int queue_order;            /* order of the per-cluster QR tests and IDs: 0 one
+                                 CTA per cluster in tree order; 1 a work queue
+                                 over a device-filling grid, largest estimated
+                                 cost first (m d^2 for the test, d m min(m, d)
+                                 for the ID).  Results do not depend on it. */
 } h2_build_opts;
 
 /* Fills opts with the workload defaults (32/16/256, FP64, Philox seed 0,

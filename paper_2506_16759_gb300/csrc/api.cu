@@ -1023,6 +1023,25 @@ struct Builder {
     return need_smem;
   }
 
+  // Work queue of a level's QR tests (id = false) or IDs (id = true) when
+  // queue_order = 1: tasks by decreasing estimated cost (the Householder
+  // test of an m x d panel ~ m d^2; the pivoted QR of a d x m panel ~
+  // d m min(m, d)), ties in tree order.
+  void make_queue(const LevelData &L, bool id, DBuf<int32_t> &queue, DBuf<int32_t> &next) {
+    if (o.queue_order != 1 || L.n < 2) return;
+    std::vector<double> cost(L.n);
+    for (int t = 0; t < L.n; ++t) {
+      const double m = L.h_m[t], d = H->dcur[L.h_inst[t]];
+      cost[t] = id ? d * m * std::min(m, d) : m * d * d;
+    }
+    std::vector<int32_t> order(L.n);
+    for (int t = 0; t < L.n; ++t) order[t] = t;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t x, int32_t y) { return cost[x] > cost[y]; });
+    to_device(queue, order, s);
+    next.alloc(1);
+  }
+
   void qr_round(int l, DBuf<int32_t> &unconv) {
     LevelData &L = LV()[l];
     DBuf<int64_t> ws_off;
@@ -1043,6 +1062,10 @@ struct Builder {
     a.ws = ws.p;
     a.ws_off = ws_off.p;
     a.mindiag = nullptr;
+    DBuf<int32_t> queue, next;
+    make_queue(L, false, queue, next);
+    a.queue = queue.p;
+    a.next = next.p;
     timer.begin(PH_QR);
     qr_test(fp64(), a, smem, *std::max_element(hd.begin(), hd.end()), s);
     timer.end(PH_QR);
@@ -1132,6 +1155,10 @@ struct Builder {
     a.E = L.E.p;
     a.ws = ws.p;
     a.ws_off = ws_off.p;
+    DBuf<int32_t> queue, next;
+    make_queue(L, true, queue, next);
+    a.queue = queue.p;
+    a.next = next.p;
     timer.begin(PH_ID);
     row_id(fp64(), a, smem, L.max_m, s);
     timer.end(PH_ID);
@@ -1487,6 +1514,7 @@ void validate_opts(const h2_build_opts &o) {
              "tc_cols must be 0, 32, 64 or 80");
   H2_REQUIRE(o.ksum_split >= 0 && o.ksum_split <= 1024, "ksum_split must be in 0..1024");
   H2_REQUIRE(o.nonsym == 0 || o.nonsym == 1, "nonsym must be 0 or 1");
+  H2_REQUIRE(o.queue_order == 0 || o.queue_order == 1, "queue_order must be 0 or 1");
   if (o.nonsym) {
     H2_REQUIRE(o.sketch != H2_SKETCH_KSUM,
                "a non-symmetric build needs a dense, callback or H2-matvec sketch");
@@ -2014,6 +2042,12 @@ h2_status h2_autotune(const h2_tree *tree, int kernel_id, const double *params, 
         o.ksum_split = split;
         try_opts(o);
       }
+    }
+    // last stage (any precision): the order of the per-cluster factorizations
+    if (best_t < 1e300) {
+      h2_build_opts o = choice;
+      o.queue_order = 1 - o.queue_order;
+      try_opts(o);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

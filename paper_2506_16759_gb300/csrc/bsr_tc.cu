@@ -9,15 +9,18 @@
 // an input slice is formed from three part products, A_hi [B_hi | B_lo] and
 // A_lo B_hi, into one TMEM accumulator (D = D[0:N) + D[N:2N)).
 //
-// CTA = one row task (at most 128 rows: the MMA's M, padding rows zero) x one
+// CTA = one 128-row half of a row task (the MMA's M, padding rows zero; row
+// tasks of up to MR = 128 or 256 rows, so one or two CTAs per task) x one
 // chunk of NCOL columns, 10 warps with fixed roles:
 //   warp 0      producer: per step (one 32-wide K chunk of one partner block)
 //               bulk copies of the partner's input slice (from an "input
 //               image") and of the chunk's columns of the block (contiguous
-//               in the column-major block) into a shared-memory ring;
+//               in the column-major block, all of its rows: both halves read
+//               the same copy pattern) into a shared-memory ring;
 //   warp 1      one thread issues the MMAs of a step and commits them;
-//   warps 2-5   move the chunk into TMEM (operand A): thread = block row, 32
-//               values read from shared memory, split into TF32 parts;
+//   warps 2-5   move the half's rows of the chunk into TMEM (operand A):
+//               thread = block row, 32 values read from shared memory, split
+//               into TF32 parts;
 //   warps 6-9   read every partner's product back from TMEM (two
 //               accumulators, so the next partner's products proceed), plain
 //               sums over eight partners, compensated sums across in shared
@@ -29,6 +32,7 @@
 // Every mbarrier wait is bounded; a timeout raises the error flag, which the
 // launcher turns into H2_ERR_TIMEOUT.
 #include <algorithm>
+#include <type_traits>
 
 #include "h2_level.h"
 #include "h2_types.h"
@@ -39,11 +43,15 @@ namespace {
 
 constexpr int kKc = 32;                 // K values per chunk: one 128-byte TF32 row
 constexpr int kSA = 2, kR = 4;          // A stages (TMEM), step barriers (>= every stage count)
-constexpr uint32_t kSlotA = 128 * kKc * 4;   // one block chunk: up to 128 rows x 32 columns
+// one block chunk: up to MR rows x 32 columns
+template <int MR>
+__host__ __device__ constexpr uint32_t slot_a() {
+  return MR * kKc * 4;
+}
 // shared-memory stages (input slice + block chunk) for NCOL columns
-template <int NCOL>
+template <int NCOL, int MR>
 struct TcStages {
-  static constexpr int SB = NCOL >= 64 ? 3 : 4;
+  static constexpr int SB = MR == 128 ? (NCOL >= 64 ? 3 : 4) : (NCOL >= 80 ? 2 : 3);
 };
 // A row's partner metadata (column task, block width, block offset) is read
 // once into shared memory for its first kMeta partners.
@@ -111,13 +119,13 @@ __global__ void k_bsr_tc_image(BsrArgs a, int kcmax, int64_t W, float *img) {
   }
 }
 
-template <int NCOL>
-constexpr size_t tc_bsr_smem() {
-  return 1024 + (size_t)TcStages<NCOL>::SB * (2 * NCOL * 128 + kSlotA) +
+template <int NCOL, int MR>
+__host__ __device__ constexpr size_t tc_bsr_smem() {
+  return 1024 + (size_t)TcStages<NCOL, MR>::SB * (2 * NCOL * 128 + slot_a<MR>()) +
          (size_t)2 * NCOL * 128 * sizeof(float) + (size_t)kMeta * 16;
 }
 
-template <int NCOL>
+template <int NCOL, int MR>
 __global__ void __launch_bounds__(kThreadsTc, 1) k_bsr_tc(TcBsrArgs ta) {
   const BsrArgs &a = ta.a;
   constexpr uint32_t STAGE_B = 2 * NCOL * 128;        // hi rows then lo rows
@@ -128,8 +136,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_bsr_tc(TcBsrArgs ta) {
   static_assert(NCOL % 16 == 0, "MMA N");
   constexpr uint32_t IDESC2 = idesc_mma(false, 128, 2 * NCOL);
   constexpr uint32_t IDESC1 = idesc_mma(false, 128, NCOL);
-  constexpr int kSB = TcStages<NCOL>::SB;
+  constexpr int kSB = TcStages<NCOL, MR>::SB;
+  constexpr uint32_t kSlotA = slot_a<MR>();
+  constexpr int kHalves = MR / 128;
   static_assert(kR >= kSB && kR >= kSA, "step barriers");
+  static_assert(tc_bsr_smem<NCOL, MR>() <= 227 * 1024, "shared memory");
   extern __shared__ unsigned char smem_dyn[];
   unsigned char *base = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
@@ -146,16 +157,20 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_bsr_tc(TcBsrArgs ta) {
 
   const int seg = a.seg;
   const int part = blockIdx.x % seg;
-  const int rest = blockIdx.x / seg;
+  int rest = blockIdx.x / seg;
+  const int half = rest % kHalves;
+  rest /= kHalves;
   const int chunk = rest % ta.nchunk;
   const int tau = rest / ta.nchunk;
-  const int m = a.row_m[tau];
+  const int m = a.row_m[tau];        // rows of the task (the blocks' leading dimension)
+  const int hr0 = half * 128;        // first row of this CTA's half
+  const int mh = min(128, m - hr0);  // rows of the half (<= 0: nothing to do)
   const int inst = a.row_inst[tau];
   const int cb = a.cols.cb[inst], ce = a.cols.ce[inst];
   const int c0 = cb + chunk * NCOL;
   const int64_t r0 = a.ptr[tau], rn = a.ptr[tau + 1] - r0;
   const int64_t e0 = r0 + rn * part / seg, e1 = r0 + rn * (part + 1) / seg;
-  if (m == 0 || c0 >= ce || e0 == e1) return;   // uniform over the CTA
+  if (mh <= 0 || c0 >= ce || e0 == e1) return;   // uniform over the CTA
   const int ncol = min(NCOL, ce - c0);
 
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -279,8 +294,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_bsr_tc(TcBsrArgs ta) {
   } else if (warp < 6) {
     // ------------------------------------------------------------ block staging
     const int quad = warp & 3;
-    const int i = quad * 32 + lane;   // block row of this thread
-    const bool rowok = i < m;
+    const int i = quad * 32 + lane;   // row of this thread in the half
+    const bool rowok = i < mh;
     const uint32_t lane_addr = (uint32_t)(quad * 32) << 16;
     int64_t s = 0;
     bool alive = s_abort == 0;
@@ -301,7 +316,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_bsr_tc(TcBsrArgs ta) {
         uint32_t hv[kKc], lv[kKc];
 #pragma unroll
         for (int j = 0; j < kKc; ++j) {
-          const float v = (rowok && j < nc) ? slot[j * m + i] : 0.f;
+          const float v = (rowok && j < nc) ? slot[j * m + hr0 + i] : 0.f;
           const float h = tf32_rna(v);
           hv[j] = __float_as_uint(h);
           lv[j] = __float_as_uint(v - h);
@@ -368,10 +383,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_bsr_tc(TcBsrArgs ta) {
       if (p % kGroup == 0) fold();
     }
     fold();
-    if (alive && i < m) {
+    if (alive && i < mh) {
       float *out = reinterpret_cast<float *>(a.out);
       const float sgn = (float)a.sign;
-      const int64_t orow = a.row_off[tau] + i;
+      const int64_t orow = a.row_off[tau] + hr0 + i;
       for (int c = 0; c < ncol; ++c) {
         float *op = out + orow + (int64_t)(c0 + c) * a.ld_out;
         const float v = sgn * sAcc[c * 128 + i];
@@ -396,10 +411,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_bsr_tc(TcBsrArgs ta) {
                  "n"(TCOLS));
 }
 
-template <int NCOL>
+template <int NCOL, int MR>
 void launch_bsr_tc(const TcBsrArgs &ta, int64_t ctas, cudaStream_t s) {
-  auto kern = k_bsr_tc<NCOL>;
-  const size_t bytes = tc_bsr_smem<NCOL>();
+  auto kern = k_bsr_tc<NCOL, MR>;
+  const size_t bytes = tc_bsr_smem<NCOL, MR>();
   H2_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   kern<<<(unsigned)ctas, kThreadsTc, bytes, s>>>(ta);
   count_launch();
@@ -409,7 +424,7 @@ void launch_bsr_tc(const TcBsrArgs &ta, int64_t ctas, cudaStream_t s) {
 }  // namespace
 
 bool bsr_apply_tc(const BsrArgs &a, int max_m, int max_cols, cudaStream_t s) {
-  if (max_m <= 0 || max_m > 128 || max_cols <= 0 || a.col_hi <= 0 || a.n_rows <= 0) return false;
+  if (max_m <= 0 || max_m > 256 || max_cols <= 0 || a.col_hi <= 0 || a.n_rows <= 0) return false;
   const int ncol = max_cols <= 16 ? 16 : (max_cols <= 32 ? 32 : (max_cols <= 64 ? 64
                                                                  : (max_cols <= 80 ? 80 : 96)));
   TcBsrArgs ta{};
@@ -433,14 +448,20 @@ bool bsr_apply_tc(const BsrArgs &a, int max_m, int max_cols, cudaStream_t s) {
                                                                             img.p);
   count_launch();
   H2_CHECK_LAUNCH();
-  const int64_t ctas = (int64_t)a.n_rows * ta.nchunk * a.seg;
-  switch (ncol) {
-    case 16: launch_bsr_tc<16>(ta, ctas, s); break;
-    case 32: launch_bsr_tc<32>(ta, ctas, s); break;
-    case 64: launch_bsr_tc<64>(ta, ctas, s); break;
-    case 80: launch_bsr_tc<80>(ta, ctas, s); break;
-    default: launch_bsr_tc<96>(ta, ctas, s); break;
-  }
+  const int halves = max_m > 128 ? 2 : 1;
+  const int64_t ctas = (int64_t)a.n_rows * halves * ta.nchunk * a.seg;
+  auto go = [&](auto mr) {
+    constexpr int MR = decltype(mr)::value;
+    switch (ncol) {
+      case 16: launch_bsr_tc<16, MR>(ta, ctas, s); break;
+      case 32: launch_bsr_tc<32, MR>(ta, ctas, s); break;
+      case 64: launch_bsr_tc<64, MR>(ta, ctas, s); break;
+      case 80: launch_bsr_tc<80, MR>(ta, ctas, s); break;
+      default: launch_bsr_tc<96, MR>(ta, ctas, s); break;
+    }
+  };
+  if (halves == 1) go(std::integral_constant<int, 128>{});
+  else go(std::integral_constant<int, 256>{});
   if (to_host(err.p, 1, s)[0] != 0)
     throw Error{H2_ERR_TIMEOUT, "tensor-core block-sparse product: a bounded wait ran out"};
   return true;

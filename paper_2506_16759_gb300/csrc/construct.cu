@@ -547,17 +547,31 @@ __global__ void k_transpose_panel(const float *in, int64_t ld, int64_t n, int nc
 }
 
 // ----------------------------------------------------------------------------
+// Task scheduling of the per-cluster factorizations.  Without a queue each
+// CTA takes one task (task = blockIdx.x, or queue[blockIdx.x]).  With one, a
+// grid of as many CTAs as fit on the device at once takes tasks in queue
+// order from a device counter, one at a time, so that an ordering by cost
+// (largest first) evens out the CTAs' loads.
+// ----------------------------------------------------------------------------
+// The CTA's next position in the queue (>= n: none left); s_j is a shared
+// slot that carries thread 0's draw to the CTA.
+__device__ __forceinline__ int take_task(int32_t *next, int *s_j, bool first, int n) {
+  if (!next) return first ? (int)blockIdx.x : n;
+  __syncthreads();   // the previous task is done with shared memory
+  if (threadIdx.x == 0) *s_j = atomicAdd(next, 1);
+  __syncthreads();
+  return *s_j;
+}
+
+// ----------------------------------------------------------------------------
 // QR convergence test (FP64 Householder, one CTA per cluster).
 // ----------------------------------------------------------------------------
 template <typename T, int NT>
-__global__ void __launch_bounds__(NT) k_qr_test(QrArgs a) {
+__device__ __forceinline__ void qr_task(const QrArgs &a, int tau, unsigned char *smem_raw, double *nrm2) {
   // One thread per column of Y_loc (m x d), stored row-major in shared
   // memory (a thread's column is read with unit stride across the warp).
   // Each column's trailing norm for the next step is summed while the column
   // is updated, so a step needs no block reduction.
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double nrm2[kMaxCols];
-  int tau = blockIdx.x;
   int inst = a.t.inst[tau];
   if (!a.active[inst] || a.conv[tau]) return;
   int m = a.t.m[tau];
@@ -624,21 +638,27 @@ __global__ void __launch_bounds__(NT) k_qr_test(QrArgs a) {
   }
 }
 
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_qr_test(QrArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double nrm2[kMaxCols];
+  __shared__ int s_j;
+  const int n = a.t.n;
+  for (int j = take_task(a.next, &s_j, true, n); j < n; j = take_task(a.next, &s_j, false, n))
+    qr_task<T, NT>(a, a.queue ? a.queue[j] : j, smem_raw, nrm2);
+}
+
 // ----------------------------------------------------------------------------
 // Row ID by column-pivoted Householder QR of A = Y_loc^T / sqrt(d), d x m.
 // ----------------------------------------------------------------------------
 template <typename T, int NT>
-__global__ void __launch_bounds__(NT) k_row_id(IdArgs a) {
+__device__ __forceinline__ void id_task(const IdArgs &a, int tau, unsigned char *smem_raw, double *red,
+                        double *redv, int *redi) {
   // One thread per column (a point of the cluster) of A = Y_loc^T / sqrt(d),
   // d x m, stored row-major in shared memory; each column's trailing norm for
   // the next step is recomputed while the column is updated (FP64 panels) or
   // downdated (FP32 panels).
   constexpr bool DOWNDATE = sizeof(T) == 4;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[33];
-  __shared__ double redv[33];
-  __shared__ int redi[33];
-  int tau = blockIdx.x;
   int inst = a.t.inst[tau];
   int m = a.t.m[tau];
   int64_t row = a.t.row[tau];
@@ -784,6 +804,18 @@ __global__ void __launch_bounds__(NT) k_row_id(IdArgs a) {
     E[piv[k + rr] + (int64_t)ap * m] = A[(int64_t)sig[ap] * m + (k + rr)];
   }
   if (threadIdx.x == 0) a.k_out[tau] = k;
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_row_id(IdArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[33];
+  __shared__ double redv[33];
+  __shared__ int redi[33];
+  __shared__ int s_j;
+  const int n = a.t.n;
+  for (int j = take_task(a.next, &s_j, true, n); j < n; j = take_task(a.next, &s_j, false, n))
+    id_task<T, NT>(a, a.queue ? a.queue[j] : j, smem_raw, red, redv, redi);
 }
 
 __global__ void k_compact(TasksDev t, const int32_t *J_tmp, const int32_t *skel_tmp, int32_t *J,
@@ -935,6 +967,125 @@ __global__ void __launch_bounds__(256) k_basis_n32(TasksDev t, const double *E, 
       out[row + i + (int64_t)(c0 + c) * ld_out] += s0 + s1;
     }
   }
+}
+
+// Tiled FP32 forms of the two products for clusters whose whole basis does
+// not fit in shared memory (large leaves, high ranks).  A cluster's outputs
+// are cut into 64 x 32 tiles (64 basis columns or rows by 32 right-hand
+// sides) spread over gridDim.y CTAs; each tile streams the contracted index
+// through shared memory in chunks of 32, so the shared footprint (13 KB) does
+// not depend on the cluster.  Thread t owns tile row t % 64 and columns
+// t / 64 + 4 r (r < 8), so one staged basis value feeds 8 accumulators and the
+// right-hand-side values are warp broadcasts.
+constexpr int kTileR = 64, kTileC = 32, kTileK = 32;
+
+// out(krow+a, c) = sum_i E(i,a) in(row+i, c)
+__global__ void __launch_bounds__(256) k_basis_t32_tiled(TasksDev t, const double *E,
+                                                         const float *in, int64_t ld_in,
+                                                         float *out, int64_t ld_out, InstCols cols,
+                                                         const int32_t *active) {
+  __shared__ float sE[kTileR * (kTileK + 1)];   // E(i0+ii, a0+aa) at aa*(K+1) + ii
+  __shared__ float sX[kTileC * (kTileK + 1)];   // in(row+i0+ii, c0+c) at c*(K+1) + ii
+  const int tau = blockIdx.x;
+  const int inst = t.inst[tau];
+  if (active && !active[inst]) return;
+  const int k = t.k[tau], m = t.m[tau];
+  const int cb = cols.cb[inst], ce = cols.ce[inst];
+  if (k == 0 || ce <= cb) return;
+  const int64_t row = t.row[tau], kr = t.krow[tau];
+  const double *Et = E + t.eoff[tau];
+  const int na_t = (k + kTileR - 1) / kTileR, nc_t = (ce - cb + kTileC - 1) / kTileC;
+  const int tid = threadIdx.x, aa = tid % kTileR, cq = tid / kTileR;
+  for (int w = blockIdx.y; w < na_t * nc_t; w += gridDim.y) {
+    const int a0 = (w % na_t) * kTileR, c0 = cb + (w / na_t) * kTileC;
+    const int na = min(kTileR, k - a0), nc = min(kTileC, ce - c0);
+    float acc[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) acc[r] = 0.f;
+    for (int i0 = 0; i0 < m; i0 += kTileK) {
+      const int mi = min(kTileK, m - i0);
+      __syncthreads();
+      for (int q = tid; q < kTileR * kTileK; q += 256) {
+        const int a = q / kTileK, ii = q % kTileK;
+        sE[a * (kTileK + 1) + ii] =
+            (a < na && ii < mi) ? (float)Et[(int64_t)(a0 + a) * m + i0 + ii] : 0.f;
+      }
+      for (int q = tid; q < kTileC * kTileK; q += 256) {
+        const int c = q / kTileK, ii = q % kTileK;
+        sX[c * (kTileK + 1) + ii] =
+            (c < nc && ii < mi) ? in[row + i0 + ii + (int64_t)(c0 + c) * ld_in] : 0.f;
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int ii = 0; ii < kTileK; ++ii) {
+        const float e = sE[aa * (kTileK + 1) + ii];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) acc[r] = fmaf(e, sX[(cq + 4 * r) * (kTileK + 1) + ii], acc[r]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int c = cq + 4 * r;
+      if (aa < na && c < nc) out[kr + a0 + aa + (int64_t)(c0 + c) * ld_out] = acc[r];
+    }
+  }
+}
+
+// out(row+i, c) += sum_a E(i,a) in(krow+a, c)
+__global__ void __launch_bounds__(256) k_basis_n32_tiled(TasksDev t, const double *E,
+                                                         const float *in, int64_t ld_in,
+                                                         float *out, int64_t ld_out,
+                                                         InstCols cols) {
+  __shared__ float sE[kTileK * kTileR];         // E(i0+ii, a0+aa) at aa*R + ii
+  __shared__ float sY[kTileC * (kTileK + 1)];   // in(krow+a0+aa, c0+c) at c*(K+1) + aa
+  const int tau = blockIdx.x;
+  const int inst = t.inst[tau];
+  const int k = t.k[tau], m = t.m[tau];
+  const int cb = cols.cb[inst], ce = cols.ce[inst];
+  if (k == 0 || ce <= cb) return;
+  const int64_t row = t.row[tau], kr = t.krow[tau];
+  const double *Et = E + t.eoff[tau];
+  const int ni_t = (m + kTileR - 1) / kTileR, nc_t = (ce - cb + kTileC - 1) / kTileC;
+  const int tid = threadIdx.x, ii = tid % kTileR, cq = tid / kTileR;
+  for (int w = blockIdx.y; w < ni_t * nc_t; w += gridDim.y) {
+    const int i0 = (w % ni_t) * kTileR, c0 = cb + (w / ni_t) * kTileC;
+    const int mi = min(kTileR, m - i0), nc = min(kTileC, ce - c0);
+    float acc[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) acc[r] = 0.f;
+    for (int a0 = 0; a0 < k; a0 += kTileK) {
+      const int na = min(kTileK, k - a0);
+      __syncthreads();
+      for (int q = tid; q < kTileK * kTileR; q += 256) {
+        const int a = q / kTileR, i = q % kTileR;
+        sE[q] = (a < na && i < mi) ? (float)Et[(int64_t)(a0 + a) * m + i0 + i] : 0.f;
+      }
+      for (int q = tid; q < kTileC * kTileK; q += 256) {
+        const int c = q / kTileK, a = q % kTileK;
+        sY[c * (kTileK + 1) + a] =
+            (c < nc && a < na) ? in[kr + a0 + a + (int64_t)(c0 + c) * ld_in] : 0.f;
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int a = 0; a < kTileK; ++a) {
+        const float e = sE[a * kTileR + ii];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) acc[r] = fmaf(e, sY[(cq + 4 * r) * (kTileK + 1) + a], acc[r]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int c = cq + 4 * r;
+      if (ii < mi && c < nc) out[row + i0 + ii + (int64_t)(c0 + c) * ld_out] += acc[r];
+    }
+  }
+}
+
+// CTAs per cluster for the tiled products: enough to cover the device twice
+// when the level has few clusters, one when it has many.
+int tiled_split(int n_tasks) {
+  const int want = (2 * device_sm_count() + n_tasks - 1) / n_tasks;
+  return want < 1 ? 1 : (want > 16 ? 16 : want);
 }
 
 // One CTA per row task: its points (the leaf's, or its skeleton points) are
@@ -1144,11 +1295,12 @@ void launch_bsr_tile(const BsrArgs &a, const float *tin, int64_t ldt, cudaStream
 void bsr_apply(bool fp64, const BsrArgs &a_in, int max_m, int max_cols, cudaStream_t s) {
   if (a_in.n_rows == 0 || max_cols <= 0) return;
   H2_REQUIRE(max_m <= kMaxRows, "block rows above 256 are not supported");
-  if (!fp64 && max_m <= 128 && a_in.engine == 0) {
-    // tensor cores: one CTA per SM; a row task's blocks are split over
-    // several CTAs only where the row tasks would not fill the device twice
+  if (!fp64 && max_m <= 256 && a_in.engine == 0) {
+    // tensor cores: one CTA per SM and 128-row half of a task; a row task's
+    // blocks are split over several CTAs only where the row tasks would not
+    // fill the device twice
     BsrArgs t = a_in;
-    const int chunks = std::max(1, (max_cols + 95) / 96);
+    const int chunks = std::max(1, (max_cols + 95) / 96) * (max_m > 128 ? 2 : 1);
     t.seg = std::max(1, std::min(16, 2 * device_sm_count() / std::max(1, a_in.n_rows * chunks)));
     if (bsr_apply_tc(t, max_m, max_cols, s)) return;
   }
@@ -1215,7 +1367,15 @@ template <template <typename, int> class K, typename A>
 void launch_width(bool fp64, int width, const A &a, int n, size_t bytes, cudaStream_t s) {
   auto go = [&](auto kern, int nt) {
     set_smem(kern, bytes);
-    kern<<<n, nt, bytes, s>>>(a);
+    int grid = n;
+    if (a.next) {
+      // work queue: as many CTAs as are resident at once, at most one per task
+      int per_sm = 0;
+      H2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, bytes));
+      grid = std::min(n, std::max(1, per_sm) * device_sm_count());
+      H2_CUDA(cudaMemsetAsync(a.next, 0, sizeof(int32_t), s));
+    }
+    kern<<<grid, nt, bytes, s>>>(a);
   };
   const int w = width <= 0 ? 256 : width;
   if (fp64) {
@@ -1274,15 +1434,16 @@ void basis_t_apply(bool fp64, const TasksDev &t, const void *E, const void *in, 
                                                   ld_in, (double *)out, ld_out, cols, active);
   else {
     // staged basis (k x m) and 64 input columns (64 x m), FP32; clusters too
-    // large for shared memory take the FP64-accumulating kernel
+    // large for shared memory take the tiled kernel
     const size_t bytes = sizeof(float) * (size_t)(max_k * max_m + 64 * max_m);
     if (bytes <= 200 * 1024) {
       set_smem(k_basis_t32, bytes);
       k_basis_t32<<<t.n, 256, bytes, s>>>(t, (const double *)E, (const float *)in, ld_in,
                                           (float *)out, ld_out, cols, active);
     } else {
-      k_basis_t<float, double><<<t.n, 256, 0, s>>>(t, (const double *)E, (const float *)in,
-                                                  ld_in, (float *)out, ld_out, cols, active);
+      const dim3 grid(t.n, tiled_split(t.n));
+      k_basis_t32_tiled<<<grid, 256, 0, s>>>(t, (const double *)E, (const float *)in, ld_in,
+                                             (float *)out, ld_out, cols, active);
     }
   }
   count_launch();
@@ -1301,9 +1462,11 @@ void basis_n_apply(bool fp64, const TasksDev &t, const void *E, const void *in, 
     set_smem(k_basis_n32, bytes);
     k_basis_n32<<<t.n, 256, bytes, s>>>(t, (const double *)E, (const float *)in, ld_in,
                                         (float *)out, ld_out, cols);
-  } else
-    k_basis_n<float, double><<<t.n, 256, 0, s>>>(t, (const double *)E, (const float *)in, ld_in,
-                                                (float *)out, ld_out, cols);
+  } else {
+    const dim3 grid(t.n, tiled_split(t.n));
+    k_basis_n32_tiled<<<grid, 256, 0, s>>>(t, (const double *)E, (const float *)in, ld_in,
+                                           (float *)out, ld_out, cols);
+  }
   count_launch();
   H2_CHECK_LAUNCH();
 }

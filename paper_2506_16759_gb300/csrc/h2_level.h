@@ -48,11 +48,11 @@ struct BsrArgs {
   int64_t in_rows;          // rows of the input panel (FP32 tiled path)
   int col_hi;               // max over instances of ce (0: use the row-block kernel)
   int seg = 1;              // CTAs per row task (set by bsr_apply; > 1: atomic adds)
-  int engine = 0;           // FP32: 0 tensor cores where blocks have <= 128 rows, 1 CUDA cores
+  int engine = 0;           // FP32: 0 tensor cores where blocks have <= 256 rows, 1 CUDA cores
 };
 // max_cols: the widest per-instance column range of this call.
 void bsr_apply(bool fp64, const BsrArgs &a, int max_m, int max_cols, cudaStream_t s);
-// FP32 blocks of at most 128 rows on the tensor cores (bsr_tc.cu); false if
+// FP32 blocks of at most 256 rows on the tensor cores (bsr_tc.cu); false if
 // the call is outside that range.
 bool bsr_apply_tc(const BsrArgs &a, int max_m, int max_cols, cudaStream_t s);
 
@@ -88,6 +88,10 @@ struct QrArgs {
   double *ws;               // global workspace for panels too large for smem
   const int64_t *ws_off;    // per task offset into ws, -1 = shared memory
   double *mindiag;          // optional per task output (may be NULL)
+  // work queue (both NULL: one CTA per task in task order): the order in which
+  // the tasks are taken, and a device counter the launcher zeroes
+  const int32_t *queue = nullptr;
+  int32_t *next = nullptr;
 };
 // width: the widest cluster of the call (threads = columns), 0 = 256 threads.
 void qr_test(bool fp64, const QrArgs &a, size_t smem_bytes, int width, cudaStream_t s);
@@ -109,6 +113,8 @@ struct IdArgs {
   double *ws;
   const int64_t *ws_off;
   int mcap;                 // rows the per-cluster index arrays hold (>= every m, <= 512)
+  const int32_t *queue = nullptr;   // work queue, as in QrArgs
+  int32_t *next = nullptr;
 };
 void row_id(bool fp64, const IdArgs &a, size_t smem_bytes, int width, cudaStream_t s);
 // Shared memory the ID kernel needs besides the d x m panel (clusters of at

@@ -521,9 +521,10 @@ def test_large_build_matches_oracle():
 
 def test_leaf256_fixed_sample_matches_oracle():
     # leaves of 256 points, compressed from 256 fixed samples (Table I's
-    # largest setting): blocks of up to 256 rows in the near field and the
-    # block-sparse kernels for them (256-row register tiles in the mixed
-    # matvec, the general kernel in the build)
+    # largest setting): blocks of up to 256 rows in the near field (mixed
+    # precision: the tensor-core block-sparse kernel in two 128-row halves,
+    # in the build and in the matvec) and leaf bases too large to stage
+    # whole (the tiled basis products)
     n, dim, kernel, params, tol, leaf = 8192, 3, W.K_MATERN32, (0.1, 1e-4), 1e-6, 256
     X, om, t, lists, ho = oracle_build(n, dim, kernel, params, tol, leaf, 0.7, 52, d0=256,
                                        d_inc=0)
@@ -573,3 +574,28 @@ def test_batched_instances_match_oracle_per_instance():
             yo = O.h2_matvec(ho, G[off:off + n])
             assert np.linalg.norm(yb[off:off + n] - yo) <= bar * np.linalg.norm(yo), (prec, i)
             off += n
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_work_queue_order_gives_the_same_build(prec):
+    # the QR tests and IDs taken from a work queue, largest first, write the
+    # same per-cluster results as one CTA per cluster.  FP64 builds are
+    # deterministic and agree bit for bit (ranks, skeletons, matvec); mixed
+    # builds sum some block-sparse partial products in atomic adds, so there
+    # the two matvecs agree to the mixed-precision bar
+    n, dim, kernel, params, tol, leaf = 20000, 3, W.K_MATERN32, (0.1, 1e-4), 1e-6, 64
+    X = W.uniform_points(n, dim, 53)
+    om = W.gaussian_omega(n, 256, 54)
+    _, h0 = gpu_build(X, om, kernel, params, tol, leaf, 0.7, prec=prec, queue_order=0)
+    tree, h1 = gpu_build(X, om, kernel, params, tol, leaf, 0.7, prec=prec, queue_order=1)
+    assert h0.stats()["rounds"] >= 1
+    G = gpu(W.gaussian_probe(n, 4, 9))
+    y0, y1 = h0.matvec(G), h1.matvec(G)
+    if prec == "fp64":
+        for level in range(1, tree.info.l_top + 1):
+            r0, s0, _, d0 = h0.export_level(level)
+            r1, s1, _, d1 = h1.export_level(level)
+            assert np.array_equal(r0, r1) and np.array_equal(s0, s1) and d0 == d1
+        assert torch.equal(y0, y1)
+    else:
+        assert float(torch.linalg.norm(y0 - y1) / torch.linalg.norm(y0)) <= 1e-5
