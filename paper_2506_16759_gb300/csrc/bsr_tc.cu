@@ -21,8 +21,8 @@
 //   warps 2-5   move the half's rows of the chunk into TMEM (operand A):
 //               thread = block row, 32 values read from shared memory, split
 //               into TF32 parts;
-//   warps 6-9   read every partner's product back from TMEM (two
-//               accumulators, so the next partner's products proceed), plain
+//   warps 6-9   read every partner's product back from TMEM (two or four
+//               accumulators, so the next partners' products proceed), plain
 //               sums over eight partners, compensated sums across in shared
 //               memory, then the compensated update of the output rows.
 // The input image is built per call: per column task and 32-wide K chunk,
@@ -42,16 +42,27 @@ namespace h2 {
 namespace {
 
 constexpr int kKc = 32;                 // K values per chunk: one 128-byte TF32 row
-constexpr int kSA = 2, kR = 4;          // A stages (TMEM), step barriers (>= every stage count)
+constexpr int kR = 4;                   // step barriers (>= every stage count)
 // one block chunk: up to MR rows x 32 columns
 template <int MR>
 __host__ __device__ constexpr uint32_t slot_a() {
   return MR * kKc * 4;
 }
-// shared-memory stages (input slice + block chunk) for NCOL columns
+// Per-shape resources.  TWO: two CTAs per SM (16 columns, 128 rows: the
+// narrow products of the adaptive rounds and of matvecs, whose time goes into
+// streaming blocks, so two independent pipelines per SM), each with half of
+// the TMEM.  SB: shared-memory stages (input slice + block chunk).  ACC:
+// accumulators (partners in flight between the MMAs and the read-back).  SA:
+// A stages in TMEM (steps the staging warps may run ahead of the MMAs).
 template <int NCOL, int MR>
 struct TcStages {
+  static constexpr bool TWO = NCOL == 16 && MR == 128;
   static constexpr int SB = MR == 128 ? (NCOL >= 64 ? 3 : 4) : (NCOL >= 80 ? 2 : 3);
+  static constexpr int TMEM_BUDGET = TWO ? 256 : 512;
+  static constexpr int ACC = 4 * 2 * NCOL + 2 * 64 <= TMEM_BUDGET ? 4 : 2;
+  static constexpr int SA = ACC * 2 * NCOL + 4 * 64 <= TMEM_BUDGET ? 4 : 2;
+  static constexpr int USED = ACC * 2 * NCOL + SA * 64;
+  static constexpr int TCOLS = USED <= 128 ? 128 : (USED <= 256 ? 256 : 512);
 };
 // A row's partner metadata (column task, block width, block offset) is read
 // once into shared memory for its first kMeta partners.
@@ -126,13 +137,16 @@ __host__ __device__ constexpr size_t tc_bsr_smem() {
 }
 
 template <int NCOL, int MR>
-__global__ void __launch_bounds__(kThreadsTc, 1) k_bsr_tc(TcBsrArgs ta) {
+__global__ void __launch_bounds__(kThreadsTc, TcStages<NCOL, MR>::TWO ? 2 : 1)
+    k_bsr_tc(TcBsrArgs ta) {
   const BsrArgs &a = ta.a;
   constexpr uint32_t STAGE_B = 2 * NCOL * 128;        // hi rows then lo rows
   constexpr uint32_t ACC_N = 2 * NCOL;
-  constexpr uint32_t A_COL0 = 2 * ACC_N;              // two accumulators first
-  constexpr uint32_t TCOLS = A_COL0 + kSA * 64 <= 256 ? 256 : 512;
-  static_assert(A_COL0 + kSA * 64 <= 512, "TMEM columns");
+  constexpr int kSA = TcStages<NCOL, MR>::SA;
+  constexpr int kAcc = TcStages<NCOL, MR>::ACC;
+  constexpr uint32_t A_COL0 = kAcc * ACC_N;           // the accumulators first
+  constexpr uint32_t TCOLS = TcStages<NCOL, MR>::TCOLS;
+  static_assert(A_COL0 + kSA * 64 <= TCOLS && TCOLS <= 512, "TMEM columns");
   static_assert(NCOL % 16 == 0, "MMA N");
   constexpr uint32_t IDESC2 = idesc_mma(false, 128, 2 * NCOL);
   constexpr uint32_t IDESC1 = idesc_mma(false, 128, NCOL);
@@ -140,7 +154,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_bsr_tc(TcBsrArgs ta) {
   constexpr uint32_t kSlotA = slot_a<MR>();
   constexpr int kHalves = MR / 128;
   static_assert(kR >= kSB && kR >= kSA, "step barriers");
-  static_assert(tc_bsr_smem<NCOL, MR>() <= 227 * 1024, "shared memory");
+  static_assert(tc_bsr_smem<NCOL, MR>() * (TcStages<NCOL, MR>::TWO ? 2 : 1) <= 226 * 1024,
+                "shared memory");
   extern __shared__ unsigned char smem_dyn[];
   unsigned char *base = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
@@ -151,7 +166,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_bsr_tc(TcBsrArgs ta) {
   int64_t *mBoff = reinterpret_cast<int64_t *>(sCmp + NCOL * 128);     // [kMeta]
   int32_t *mB = reinterpret_cast<int32_t *>(mBoff + kMeta);            // [kMeta]
   int32_t *mKb = mB + kMeta;                                           // [kMeta]
-  __shared__ uint64_t bfull[kSB], afull[kSA], stepdone[kR], accfull[2], accempty[2];
+  __shared__ uint64_t bfull[kSB], afull[kSA], stepdone[kR], accfull[kAcc], accempty[kAcc];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_abort;
 
@@ -195,7 +210,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_bsr_tc(TcBsrArgs ta) {
     for (int i = 0; i < kSB; ++i) mbar_init(saddr(&bfull[i]), 1);
     for (int i = 0; i < kSA; ++i) mbar_init(saddr(&afull[i]), 4);
     for (int i = 0; i < kR; ++i) mbar_init(saddr(&stepdone[i]), 1);
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kAcc; ++i) {
       mbar_init(saddr(&accfull[i]), 1);
       mbar_init(saddr(&accempty[i]), 4);
     }
@@ -259,8 +274,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_bsr_tc(TcBsrArgs ta) {
       for (int64_t e = e0; e < e1 && ok; ++e) {
         const int nkc = (meta_kb(e) + kKc - 1) / kKc;
         if (nkc == 0) continue;
-        const int ac = (int)(p & 1);
-        if (p >= 2 && !mbar_wait(saddr(&accempty[ac]), (uint32_t)(((p >> 1) - 1) & 1), &s_abort)) {
+        const int ac = (int)(p % kAcc);
+        if (p >= kAcc &&
+            !mbar_wait(saddr(&accempty[ac]), (uint32_t)(((p / kAcc) - 1) & 1), &s_abort)) {
           ok = false;
           break;
         }
@@ -358,9 +374,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_bsr_tc(TcBsrArgs ta) {
     bool alive = s_abort == 0;
     for (int64_t e = e0; e < e1 && alive; ++e) {
       if (meta_kb(e) == 0) continue;
-      const int ac = (int)(p & 1);
+      const int ac = (int)(p % kAcc);
       if (!__all_sync(0xffffffffu,
-                      mbar_wait(saddr(&accfull[ac]), (uint32_t)((p >> 1) & 1), &s_abort))) {
+                      mbar_wait(saddr(&accfull[ac]), (uint32_t)((p / kAcc) & 1), &s_abort))) {
         alive = false;
         if (lane == 0) abort_cta();
         break;
@@ -416,6 +432,8 @@ void launch_bsr_tc(const TcBsrArgs &ta, int64_t ctas, cudaStream_t s) {
   auto kern = k_bsr_tc<NCOL, MR>;
   const size_t bytes = tc_bsr_smem<NCOL, MR>();
   H2_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  if (TcStages<NCOL, MR>::TWO)   // room for two CTAs per SM
+    H2_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   kern<<<(unsigned)ctas, kThreadsTc, bytes, s>>>(ta);
   count_launch();
   H2_CHECK_LAUNCH();

@@ -866,49 +866,6 @@ __global__ void k_basis_t(TasksDev t, const TE *E, const T *in, int64_t ld_in, T
   }
 }
 
-// FP32 panels (mixed precision): the cluster's basis (converted to FP32) and
-// its input rows are staged in shared memory, each output is an FP32 dot
-// product over the cluster's rows.  The identity rows of the basis (its
-// skeleton rows) contribute exact products, so the rounding is that of the
-// m - k interpolated rows.  Column chunks of 64.
-__global__ void __launch_bounds__(256) k_basis_t32(TasksDev t, const double *E, const float *in,
-                                                   int64_t ld_in, float *out, int64_t ld_out,
-                                                   InstCols cols, const int32_t *active) {
-  extern __shared__ __align__(16) float sm[];
-  const int tau = blockIdx.x;
-  const int inst = t.inst[tau];
-  if (active && !active[inst]) return;
-  const int k = t.k[tau], m = t.m[tau];
-  const int cb = cols.cb[inst], ce = cols.ce[inst];
-  if (k == 0 || ce <= cb) return;
-  const int64_t row = t.row[tau], kr = t.krow[tau];
-  const double *Et = E + t.eoff[tau];
-  float *sE = sm;                          // [k][m] (basis column a contiguous)
-  float *sX = sm + (size_t)k * m;          // [64][m] (input column c contiguous)
-  for (int q = threadIdx.x; q < m * k; q += blockDim.x) sE[q] = (float)Et[q];
-  for (int c0 = cb; c0 < ce; c0 += 64) {
-    const int nc = min(64, ce - c0);
-    __syncthreads();
-    for (int q = threadIdx.x; q < m * nc; q += blockDim.x) {
-      const int i = q % m, c = q / m;
-      sX[c * m + i] = in[row + i + (int64_t)(c0 + c) * ld_in];
-    }
-    __syncthreads();
-    for (int q = threadIdx.x; q < k * nc; q += blockDim.x) {
-      const int a = q % k, c = q / k;
-      const float *ea = sE + a * m, *xc = sX + c * m;
-      float s0 = 0.f, s1 = 0.f;
-      int i = 0;
-      for (; i + 1 < m; i += 2) {
-        s0 = fmaf(ea[i], xc[i], s0);
-        s1 = fmaf(ea[i + 1], xc[i + 1], s1);
-      }
-      if (i < m) s0 = fmaf(ea[i], xc[i], s0);
-      out[kr + a + (int64_t)(c0 + c) * ld_out] = s0 + s1;
-    }
-  }
-}
-
 // out(row+i, c) += sum_a E(i,a) in(krow+a, c)
 template <typename T, typename TE>
 __global__ void k_basis_n(TasksDev t, const TE *E, const T *in, int64_t ld_in, T *out,
@@ -929,63 +886,25 @@ __global__ void k_basis_n(TasksDev t, const TE *E, const T *in, int64_t ld_in, T
   }
 }
 
-// FP32 downsweep (mixed precision): out(row+i, c) += sum_a E(i,a) in(krow+a, c)
-// with the cluster's basis (converted to FP32, column a contiguous) and 64
-// columns of its skeleton-row inputs staged in shared memory.
-__global__ void __launch_bounds__(256) k_basis_n32(TasksDev t, const double *E, const float *in,
-                                                   int64_t ld_in, float *out, int64_t ld_out,
-                                                   InstCols cols) {
-  extern __shared__ __align__(16) float sm[];
-  const int tau = blockIdx.x;
-  const int inst = t.inst[tau];
-  const int k = t.k[tau], m = t.m[tau];
-  const int cb = cols.cb[inst], ce = cols.ce[inst];
-  if (k == 0 || ce <= cb) return;
-  const int64_t row = t.row[tau], kr = t.krow[tau];
-  const double *Et = E + t.eoff[tau];
-  float *sE = sm;                          // [k][m]: E(i, a) at a * m + i
-  float *sY = sm + (size_t)k * m;          // [64][k]: in(krow + a, c) at c * k + a
-  for (int q = threadIdx.x; q < m * k; q += blockDim.x) sE[q] = (float)Et[q];
-  for (int c0 = cb; c0 < ce; c0 += 64) {
-    const int nc = min(64, ce - c0);
-    __syncthreads();
-    for (int q = threadIdx.x; q < k * nc; q += blockDim.x) {
-      const int a = q % k, c = q / k;
-      sY[c * k + a] = in[kr + a + (int64_t)(c0 + c) * ld_in];
-    }
-    __syncthreads();
-    for (int q = threadIdx.x; q < m * nc; q += blockDim.x) {
-      const int i = q % m, c = q / m;
-      const float *yc = sY + c * k;
-      float s0 = 0.f, s1 = 0.f;
-      int a = 0;
-      for (; a + 1 < k; a += 2) {
-        s0 = fmaf(sE[a * m + i], yc[a], s0);
-        s1 = fmaf(sE[(a + 1) * m + i], yc[a + 1], s1);
-      }
-      if (a < k) s0 = fmaf(sE[a * m + i], yc[a], s0);
-      out[row + i + (int64_t)(c0 + c) * ld_out] += s0 + s1;
-    }
-  }
-}
-
-// Tiled FP32 forms of the two products for clusters whose whole basis does
-// not fit in shared memory (large leaves, high ranks).  A cluster's outputs
-// are cut into 64 x 32 tiles (64 basis columns or rows by 32 right-hand
-// sides) spread over gridDim.y CTAs; each tile streams the contracted index
-// through shared memory in chunks of 32, so the shared footprint (13 KB) does
-// not depend on the cluster.  Thread t owns tile row t % 64 and columns
-// t / 64 + 4 r (r < 8), so one staged basis value feeds 8 accumulators and the
-// right-hand-side values are warp broadcasts.
+// FP32 forms of the two basis products (mixed precision).  A cluster's
+// outputs are cut into 64 x 32 tiles (64 basis columns or rows by 32
+// right-hand sides) spread over gridDim.y CTAs; each tile streams the
+// contracted index through shared memory in chunks of 32, so the shared
+// footprint (13 KB) does not depend on the cluster.  Thread t owns tile row
+// t % 64 and the 8 consecutive columns 8 (t / 64) .. 8 (t / 64) + 7: per
+// contracted index it reads one basis value (rows at an odd stride, so a
+// warp's 32 reads hit 32 banks) and its 8 right-hand-side values as two
+// 16-byte broadcasts (the warp shares t / 64), then does 8 FMAs.
 constexpr int kTileR = 64, kTileC = 32, kTileK = 32;
+constexpr int kTileXS = kTileC + 4;   // row stride of the staged right-hand sides (16-byte rows)
 
 // out(krow+a, c) = sum_i E(i,a) in(row+i, c)
 __global__ void __launch_bounds__(256) k_basis_t32_tiled(TasksDev t, const double *E,
                                                          const float *in, int64_t ld_in,
                                                          float *out, int64_t ld_out, InstCols cols,
                                                          const int32_t *active) {
-  __shared__ float sE[kTileR * (kTileK + 1)];   // E(i0+ii, a0+aa) at aa*(K+1) + ii
-  __shared__ float sX[kTileC * (kTileK + 1)];   // in(row+i0+ii, c0+c) at c*(K+1) + ii
+  __shared__ float sE[kTileR * (kTileK + 1)];              // E(i0+ii, a0+aa) at aa*(K+1) + ii
+  __shared__ __align__(16) float sX[kTileK * kTileXS];     // in(row+i0+ii, c0+c) at ii*XS + c
   const int tau = blockIdx.x;
   const int inst = t.inst[tau];
   if (active && !active[inst]) return;
@@ -995,7 +914,7 @@ __global__ void __launch_bounds__(256) k_basis_t32_tiled(TasksDev t, const doubl
   const int64_t row = t.row[tau], kr = t.krow[tau];
   const double *Et = E + t.eoff[tau];
   const int na_t = (k + kTileR - 1) / kTileR, nc_t = (ce - cb + kTileC - 1) / kTileC;
-  const int tid = threadIdx.x, aa = tid % kTileR, cq = tid / kTileR;
+  const int tid = threadIdx.x, aa = tid % kTileR, cq = (tid / kTileR) * 8;
   for (int w = blockIdx.y; w < na_t * nc_t; w += gridDim.y) {
     const int a0 = (w % na_t) * kTileR, c0 = cb + (w / na_t) * kTileC;
     const int na = min(kTileR, k - a0), nc = min(kTileC, ce - c0);
@@ -1012,21 +931,29 @@ __global__ void __launch_bounds__(256) k_basis_t32_tiled(TasksDev t, const doubl
       }
       for (int q = tid; q < kTileC * kTileK; q += 256) {
         const int c = q / kTileK, ii = q % kTileK;
-        sX[c * (kTileK + 1) + ii] =
+        sX[ii * kTileXS + c] =
             (c < nc && ii < mi) ? in[row + i0 + ii + (int64_t)(c0 + c) * ld_in] : 0.f;
       }
       __syncthreads();
 #pragma unroll 4
       for (int ii = 0; ii < kTileK; ++ii) {
         const float e = sE[aa * (kTileK + 1) + ii];
-#pragma unroll
-        for (int r = 0; r < 8; ++r) acc[r] = fmaf(e, sX[(cq + 4 * r) * (kTileK + 1) + ii], acc[r]);
+        const float4 x0 = *reinterpret_cast<const float4 *>(sX + ii * kTileXS + cq);
+        const float4 x1 = *reinterpret_cast<const float4 *>(sX + ii * kTileXS + cq + 4);
+        acc[0] = fmaf(e, x0.x, acc[0]);
+        acc[1] = fmaf(e, x0.y, acc[1]);
+        acc[2] = fmaf(e, x0.z, acc[2]);
+        acc[3] = fmaf(e, x0.w, acc[3]);
+        acc[4] = fmaf(e, x1.x, acc[4]);
+        acc[5] = fmaf(e, x1.y, acc[5]);
+        acc[6] = fmaf(e, x1.z, acc[6]);
+        acc[7] = fmaf(e, x1.w, acc[7]);
       }
     }
+    if (aa < na) {
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int c = cq + 4 * r;
-      if (aa < na && c < nc) out[kr + a0 + aa + (int64_t)(c0 + c) * ld_out] = acc[r];
+      for (int r = 0; r < 8; ++r)
+        if (cq + r < nc) out[kr + a0 + aa + (int64_t)(c0 + cq + r) * ld_out] = acc[r];
     }
   }
 }
@@ -1036,8 +963,8 @@ __global__ void __launch_bounds__(256) k_basis_n32_tiled(TasksDev t, const doubl
                                                          const float *in, int64_t ld_in,
                                                          float *out, int64_t ld_out,
                                                          InstCols cols) {
-  __shared__ float sE[kTileK * kTileR];         // E(i0+ii, a0+aa) at aa*R + ii
-  __shared__ float sY[kTileC * (kTileK + 1)];   // in(krow+a0+aa, c0+c) at c*(K+1) + aa
+  __shared__ float sE[kTileK * kTileR];                    // E(i0+ii, a0+aa) at aa*R + ii
+  __shared__ __align__(16) float sY[kTileK * kTileXS];     // in(krow+a0+aa, c0+c) at aa*XS + c
   const int tau = blockIdx.x;
   const int inst = t.inst[tau];
   const int k = t.k[tau], m = t.m[tau];
@@ -1046,7 +973,7 @@ __global__ void __launch_bounds__(256) k_basis_n32_tiled(TasksDev t, const doubl
   const int64_t row = t.row[tau], kr = t.krow[tau];
   const double *Et = E + t.eoff[tau];
   const int ni_t = (m + kTileR - 1) / kTileR, nc_t = (ce - cb + kTileC - 1) / kTileC;
-  const int tid = threadIdx.x, ii = tid % kTileR, cq = tid / kTileR;
+  const int tid = threadIdx.x, ii = tid % kTileR, cq = (tid / kTileR) * 8;
   for (int w = blockIdx.y; w < ni_t * nc_t; w += gridDim.y) {
     const int i0 = (w % ni_t) * kTileR, c0 = cb + (w / ni_t) * kTileC;
     const int mi = min(kTileR, m - i0), nc = min(kTileC, ce - c0);
@@ -1062,21 +989,29 @@ __global__ void __launch_bounds__(256) k_basis_n32_tiled(TasksDev t, const doubl
       }
       for (int q = tid; q < kTileC * kTileK; q += 256) {
         const int c = q / kTileK, a = q % kTileK;
-        sY[c * (kTileK + 1) + a] =
+        sY[a * kTileXS + c] =
             (c < nc && a < na) ? in[kr + a0 + a + (int64_t)(c0 + c) * ld_in] : 0.f;
       }
       __syncthreads();
 #pragma unroll 4
       for (int a = 0; a < kTileK; ++a) {
         const float e = sE[a * kTileR + ii];
-#pragma unroll
-        for (int r = 0; r < 8; ++r) acc[r] = fmaf(e, sY[(cq + 4 * r) * (kTileK + 1) + a], acc[r]);
+        const float4 y0 = *reinterpret_cast<const float4 *>(sY + a * kTileXS + cq);
+        const float4 y1 = *reinterpret_cast<const float4 *>(sY + a * kTileXS + cq + 4);
+        acc[0] = fmaf(e, y0.x, acc[0]);
+        acc[1] = fmaf(e, y0.y, acc[1]);
+        acc[2] = fmaf(e, y0.z, acc[2]);
+        acc[3] = fmaf(e, y0.w, acc[3]);
+        acc[4] = fmaf(e, y1.x, acc[4]);
+        acc[5] = fmaf(e, y1.y, acc[5]);
+        acc[6] = fmaf(e, y1.z, acc[6]);
+        acc[7] = fmaf(e, y1.w, acc[7]);
       }
     }
+    if (ii < mi) {
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int c = cq + 4 * r;
-      if (ii < mi && c < nc) out[row + i0 + ii + (int64_t)(c0 + c) * ld_out] += acc[r];
+      for (int r = 0; r < 8; ++r)
+        if (cq + r < nc) out[row + i0 + ii + (int64_t)(c0 + cq + r) * ld_out] += acc[r];
     }
   }
 }
@@ -1428,23 +1363,16 @@ void gather_skeleton_rows(bool fp64, const TasksDev &t, const void *Y, int64_t l
 void basis_t_apply(bool fp64, const TasksDev &t, const void *E, const void *in, int64_t ld_in,
                    void *out, int64_t ld_out, InstCols cols, const int32_t *active, int max_m,
                    int max_k, cudaStream_t s) {
+  (void)max_m;
+  (void)max_k;
   if (t.n == 0) return;
-  if (fp64)
+  if (fp64) {
     k_basis_t<double, double><<<t.n, 256, 0, s>>>(t, (const double *)E, (const double *)in,
                                                   ld_in, (double *)out, ld_out, cols, active);
-  else {
-    // staged basis (k x m) and 64 input columns (64 x m), FP32; clusters too
-    // large for shared memory take the tiled kernel
-    const size_t bytes = sizeof(float) * (size_t)(max_k * max_m + 64 * max_m);
-    if (bytes <= 200 * 1024) {
-      set_smem(k_basis_t32, bytes);
-      k_basis_t32<<<t.n, 256, bytes, s>>>(t, (const double *)E, (const float *)in, ld_in,
-                                          (float *)out, ld_out, cols, active);
-    } else {
-      const dim3 grid(t.n, tiled_split(t.n));
-      k_basis_t32_tiled<<<grid, 256, 0, s>>>(t, (const double *)E, (const float *)in, ld_in,
-                                             (float *)out, ld_out, cols, active);
-    }
+  } else {
+    const dim3 grid(t.n, tiled_split(t.n));
+    k_basis_t32_tiled<<<grid, 256, 0, s>>>(t, (const double *)E, (const float *)in, ld_in,
+                                           (float *)out, ld_out, cols, active);
   }
   count_launch();
   H2_CHECK_LAUNCH();
@@ -1453,15 +1381,12 @@ void basis_t_apply(bool fp64, const TasksDev &t, const void *E, const void *in, 
 void basis_n_apply(bool fp64, const TasksDev &t, const void *E, const void *in, int64_t ld_in,
                    void *out, int64_t ld_out, InstCols cols, int max_m, int max_k,
                    cudaStream_t s) {
+  (void)max_m;
+  (void)max_k;
   if (t.n == 0) return;
-  const size_t bytes = sizeof(float) * (size_t)(max_k * max_m + 64 * max_k);
-  if (fp64)
+  if (fp64) {
     k_basis_n<double, double><<<t.n, 256, 0, s>>>(t, (const double *)E, (const double *)in,
                                                   ld_in, (double *)out, ld_out, cols);
-  else if (bytes <= 200 * 1024) {
-    set_smem(k_basis_n32, bytes);
-    k_basis_n32<<<t.n, 256, bytes, s>>>(t, (const double *)E, (const float *)in, ld_in,
-                                        (float *)out, ld_out, cols);
   } else {
     const dim3 grid(t.n, tiled_split(t.n));
     k_basis_n32_tiled<<<grid, 256, 0, s>>>(t, (const double *)E, (const float *)in, ld_in,

@@ -129,7 +129,8 @@ void compact_skeletons(const TasksDev &t, const int32_t *J_tmp, const int32_t *s
 void gather_skeleton_rows(bool fp64, const TasksDev &t, const void *Y, int64_t ld, void *Ynext,
                           int64_t ldn, InstCols cols, const int32_t *active, cudaStream_t s);
 // out(krow+a, c) = sum_i E(i,a) in(row+i, c)       (E^T products: upsweep)
-// E is FP64 in both modes; the sums accumulate in FP64.
+// E is FP64 in both modes: FP64 sums, or (mixed precision) converted to FP32
+// on load with FP32 sums.
 void basis_t_apply(bool fp64, const TasksDev &t, const void *E, const void *in, int64_t ld_in,
                    void *out, int64_t ld_out, InstCols cols, const int32_t *active, int max_m,
                    int max_k, cudaStream_t s);
