@@ -547,6 +547,66 @@ __global__ void k_transpose_panel(const float *in, int64_t ld, int64_t n, int nc
 }
 
 // ----------------------------------------------------------------------------
+// Double-float arithmetic for the mixed-precision QR test and ID.  A value is
+// an unevaluated sum hi + lo of two FP32 numbers with |lo| <= ulp(hi) / 2,
+// about 48 significant bits.  Sums and products are formed with the
+// error-free transformations of Knuth (two-sum: a + b = s + e exactly) and
+// of the fused multiply-add (a b = p + fma(a, b, -p) exactly), Dekker's
+// double-length arithmetic.  GB300 issues FP32 at about 75 times its FP64
+// rate, so the 12-15 FP32 operations of one double-float multiply-add cost a
+// fraction of one FP64 one.  The explicit-rounding intrinsics keep the
+// compiler from fusing the steps.  The products drop lo * lo (below 2^-48
+// relative), and sums renormalise once (their error is below 2^-46 of the
+// operands' magnitude, the backward error Householder QR needs).
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ void df_two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// (s, e) with |e| small against |s| -> normalised pair
+__device__ __forceinline__ float2 df_norm(float s, float e) {
+  const float h = __fadd_rn(s, e);
+  return make_float2(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+__device__ __forceinline__ float2 df_from(double v) {
+  const float h = __double2float_rn(v);
+  return make_float2(h, __double2float_rn(v - (double)h));
+}
+__device__ __forceinline__ double df_val(float2 a) { return (double)a.x + (double)a.y; }
+// running sum of products: s + c with c the accumulated rounding errors
+struct DfAcc {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add_prod(float2 a, float2 b) {
+    const float p = __fmul_rn(a.x, b.x);
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, e);
+    e = fmaf(a.y, b.x, e);
+    float t;
+    df_two_sum(s, p, s, t);
+    c = __fadd_rn(c, __fadd_rn(t, e));
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  return df_norm(p, e);
+}
+// a - w v
+__device__ __forceinline__ float2 df_sub_prod(float2 a, float2 w, float2 v) {
+  const float p = __fmul_rn(w.x, v.x);
+  float e = fmaf(w.x, v.x, -p);
+  e = fmaf(w.x, v.y, e);
+  e = fmaf(w.y, v.x, e);
+  float h, t;
+  df_two_sum(a.x, -p, h, t);
+  return df_norm(h, __fadd_rn(t, __fsub_rn(a.y, e)));
+}
+
+// ----------------------------------------------------------------------------
 // Task scheduling of the per-cluster factorizations.  Without a queue each
 // CTA takes one task (task = blockIdx.x, or queue[blockIdx.x]).  With one, a
 // grid of as many CTAs as fit on the device at once takes tasks in queue
@@ -638,14 +698,92 @@ __device__ __forceinline__ void qr_task(const QrArgs &a, int tau, unsigned char 
   }
 }
 
+// The same test on FP32 panels (mixed precision) in double-float arithmetic:
+// the panel and its Householder updates as hi/lo pairs (8 bytes, like FP64),
+// the scalars of a step (norm, alpha, beta, w) in FP64.
+template <int NT>
+__device__ __forceinline__ void qr_task_df(const QrArgs &a, int tau, unsigned char *smem_raw,
+                                           double *nrm2) {
+  const int inst = a.t.inst[tau];
+  if (!a.active[inst] || a.conv[tau]) return;
+  const int m = a.t.m[tau];
+  const int d = a.dcur[inst];
+  if (m <= d) {
+    if (threadIdx.x == 0) {
+      a.conv[tau] = 1;
+      if (a.mindiag) a.mindiag[tau] = 0.0;
+    }
+    return;
+  }
+  float2 *A = reinterpret_cast<float2 *>(a.ws_off && a.ws_off[tau] >= 0
+                                             ? a.ws + a.ws_off[tau]
+                                             : reinterpret_cast<double *>(smem_raw));
+  const float *Y = reinterpret_cast<const float *>(a.Y);
+  const int64_t row = a.t.row[tau];
+  for (int64_t q = threadIdx.x; q < (int64_t)m * d; q += NT) {
+    const int i = (int)(q % m), c = (int)(q / m);
+    A[(int64_t)i * d + c] = make_float2(Y[row + i + (int64_t)c * a.ld], 0.f);
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < d; c += NT) {
+    DfAcc s2;
+    for (int i = 0; i < m; ++i) {
+      const float2 x = A[(int64_t)i * d + c];
+      s2.add_prod(x, x);
+    }
+    nrm2[c] = s2.value();
+  }
+  __syncthreads();
+  const double eps = a.eps[inst];
+  double minr = INFINITY;
+  for (int j = 0; j < d; ++j) {
+    const double nrm = sqrt(nrm2[j]);
+    minr = fmin(minr, nrm);
+    if (minr <= eps && !a.mindiag) break;
+    if (nrm == 0.0) continue;
+    const double x0 = df_val(A[(int64_t)j * d + j]);
+    const double alpha = x0 != 0.0 ? -copysign(nrm, x0) : -nrm;
+    const double beta = 1.0 / (nrm * (nrm + fabs(x0)));
+    __syncthreads();
+    if (threadIdx.x == 0) A[(int64_t)j * d + j] = df_from(x0 - alpha);   // v_j
+    __syncthreads();
+    for (int c = j + 1 + threadIdx.x; c < d; c += NT) {
+      DfAcc w0, w1;
+      int i = j;
+      for (; i + 1 < m; i += 2) {
+        w0.add_prod(A[(int64_t)i * d + j], A[(int64_t)i * d + c]);
+        w1.add_prod(A[(int64_t)(i + 1) * d + j], A[(int64_t)(i + 1) * d + c]);
+      }
+      if (i < m) w0.add_prod(A[(int64_t)i * d + j], A[(int64_t)i * d + c]);
+      const float2 w = df_from((w0.value() + w1.value()) * beta);
+      A[(int64_t)j * d + c] = df_sub_prod(A[(int64_t)j * d + c], w, A[(int64_t)j * d + j]);
+      DfAcc s2;
+      for (int r = j + 1; r < m; ++r) {
+        const float2 x = df_sub_prod(A[(int64_t)r * d + c], w, A[(int64_t)r * d + j]);
+        A[(int64_t)r * d + c] = x;
+        s2.add_prod(x, x);
+      }
+      nrm2[c] = s2.value();
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (a.mindiag) a.mindiag[tau] = minr;
+    if (minr <= eps) a.conv[tau] = 1;
+    else atomicAdd(&a.unconv[inst], 1);
+  }
+}
+
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) k_qr_test(QrArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double nrm2[kMaxCols];
   __shared__ int s_j;
   const int n = a.t.n;
-  for (int j = take_task(a.next, &s_j, true, n); j < n; j = take_task(a.next, &s_j, false, n))
-    qr_task<T, NT>(a, a.queue ? a.queue[j] : j, smem_raw, nrm2);
+  for (int j = take_task(a.next, &s_j, true, n); j < n; j = take_task(a.next, &s_j, false, n)) {
+    if constexpr (sizeof(T) == 4) qr_task_df<NT>(a, a.queue ? a.queue[j] : j, smem_raw, nrm2);
+    else qr_task<T, NT>(a, a.queue ? a.queue[j] : j, smem_raw, nrm2);
+  }
 }
 
 // ----------------------------------------------------------------------------
@@ -806,6 +944,155 @@ __device__ __forceinline__ void id_task(const IdArgs &a, int tau, unsigned char 
   if (threadIdx.x == 0) a.k_out[tau] = k;
 }
 
+// The row ID of an FP32 panel (mixed precision) in double-float arithmetic:
+// the panel, its Householder updates and the back substitution as hi/lo
+// pairs; norms, pivots, thresholds and the scalars of a step in FP64.  The
+// pivot is the largest squared trailing norm (the same order as the norm).
+template <int NT>
+__device__ __forceinline__ void id_task_df(const IdArgs &a, int tau, unsigned char *smem_raw,
+                                           double *red, double *redv, int *redi) {
+  const int inst = a.t.inst[tau];
+  const int m = a.t.m[tau];
+  const int64_t row = a.t.row[tau];
+  if (!a.active[inst] || m == 0) {
+    if (threadIdx.x == 0) a.k_out[tau] = 0;
+    return;
+  }
+  const int d = a.dcur[inst];
+  // shared layout: norms[m] (double), piv[m], rank[m], sig[m] (int), then A
+  double *nrm2 = reinterpret_cast<double *>(smem_raw);
+  int *piv = reinterpret_cast<int *>(nrm2 + a.mcap);
+  int *rnk = piv + a.mcap;
+  int *sig = rnk + a.mcap;
+  float2 *A = reinterpret_cast<float2 *>(a.ws_off && a.ws_off[tau] >= 0
+                                             ? a.ws + a.ws_off[tau]
+                                             : reinterpret_cast<double *>(sig + a.mcap));
+  const float *Y = reinterpret_cast<const float *>(a.Y);
+  const double rsd = 1.0 / sqrt((double)d);
+  for (int64_t q = threadIdx.x; q < (int64_t)m * d; q += NT) {
+    const int i = (int)(q % m), c = (int)(q / m);
+    A[(int64_t)c * m + i] = df_from((double)Y[row + i + (int64_t)c * a.ld] * rsd);   // A(c, i)
+  }
+  for (int i = threadIdx.x; i < m; i += NT) piv[i] = i;
+  __syncthreads();
+  for (int c = threadIdx.x; c < m; c += NT) {
+    DfAcc s2;
+    for (int r = 0; r < d; ++r) {
+      const float2 x = A[(int64_t)r * m + c];
+      s2.add_prod(x, x);
+    }
+    nrm2[c] = s2.value();
+  }
+  __syncthreads();
+  const double eps2 = a.eps[inst] * a.eps[inst];
+  const int kmax = min(d, m);
+  int k = 0;
+  while (k < kmax) {
+    double tot = 0.0, best = -1.0;
+    int bi = 0x7fffffff;
+    for (int c = k + threadIdx.x; c < m; c += NT) {
+      const double nv = nrm2[c];
+      tot += nv;
+      if (nv > best) { best = nv; bi = c; }
+    }
+    tot = block_sum(tot, red);
+    if (tot <= eps2) break;
+    const int p = block_argmax(best, bi, redv, redi);
+    if (p < k || p >= m) break;  // no finite pivot left
+    const double nk = sqrt(nrm2[p]);
+    __syncthreads();
+    if (p != k) {
+      for (int r = threadIdx.x; r < d; r += NT) {
+        const float2 t0 = A[(int64_t)r * m + k];
+        A[(int64_t)r * m + k] = A[(int64_t)r * m + p];
+        A[(int64_t)r * m + p] = t0;
+      }
+      if (threadIdx.x == 0) {
+        const int t1 = piv[k]; piv[k] = piv[p]; piv[p] = t1;
+        const double t2 = nrm2[k]; nrm2[k] = nrm2[p]; nrm2[p] = t2;
+      }
+    }
+    __syncthreads();
+    const double x0 = df_val(A[(int64_t)k * m + k]);
+    const double alpha = x0 != 0.0 ? -copysign(nk, x0) : -nk;
+    const double beta = nk > 0.0 ? 1.0 / (nk * (nk + fabs(x0))) : 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0) A[(int64_t)k * m + k] = df_from(x0 - alpha);   // v_k
+    __syncthreads();
+    for (int c = k + 1 + threadIdx.x; c < m; c += NT) {
+      DfAcc w0, w1, w2, w3;
+      int r = k;
+      for (; r + 3 < d; r += 4) {
+        w0.add_prod(A[(int64_t)r * m + k], A[(int64_t)r * m + c]);
+        w1.add_prod(A[(int64_t)(r + 1) * m + k], A[(int64_t)(r + 1) * m + c]);
+        w2.add_prod(A[(int64_t)(r + 2) * m + k], A[(int64_t)(r + 2) * m + c]);
+        w3.add_prod(A[(int64_t)(r + 3) * m + k], A[(int64_t)(r + 3) * m + c]);
+      }
+      for (; r < d; ++r) w0.add_prod(A[(int64_t)r * m + k], A[(int64_t)r * m + c]);
+      const float2 w =
+          df_from(((w0.value() + w1.value()) + (w2.value() + w3.value())) * beta);
+      const float2 rkc = df_sub_prod(A[(int64_t)k * m + c], w, A[(int64_t)k * m + k]);
+      A[(int64_t)k * m + c] = rkc;
+      // trailing norm downdated, |A(k+1:, c)|^2 = |A(k:, c)|^2 - R(k, c)^2,
+      // and recomputed after a cancellation of four digits
+      const double rk = df_val(rkc);
+      const double down = nrm2[c] - rk * rk;
+      if (down > 1e-4 * nrm2[c]) {
+        for (int q = k + 1; q < d; ++q)
+          A[(int64_t)q * m + c] = df_sub_prod(A[(int64_t)q * m + c], w, A[(int64_t)q * m + k]);
+        nrm2[c] = down;
+      } else {
+        DfAcc s2;
+        for (int q = k + 1; q < d; ++q) {
+          const float2 x = df_sub_prod(A[(int64_t)q * m + c], w, A[(int64_t)q * m + k]);
+          A[(int64_t)q * m + c] = x;
+          s2.add_prod(x, x);
+        }
+        nrm2[c] = s2.value();
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) A[(int64_t)k * m + k] = df_from(alpha);
+    __syncthreads();
+    ++k;
+  }
+  // T = R11^{-1} R12 by back substitution, written over R12 (one thread per
+  // column); the reciprocals of R's diagonal go where the norms were
+  __syncthreads();
+  float2 *rinv = reinterpret_cast<float2 *>(nrm2);
+  for (int i = threadIdx.x; i < k; i += NT) rinv[i] = df_from(1.0 / df_val(A[(int64_t)i * m + i]));
+  __syncthreads();
+  for (int c = k + threadIdx.x; c < m; c += NT) {
+    for (int i = k - 1; i >= 0; --i) {
+      float2 t = A[(int64_t)i * m + c];
+      for (int j = i + 1; j < k; ++j) t = df_sub_prod(t, A[(int64_t)i * m + j], A[(int64_t)j * m + c]);
+      A[(int64_t)i * m + c] = df_mul(t, rinv[i]);
+    }
+  }
+  // sorted skeleton order
+  for (int q = threadIdx.x; q < k; q += NT) {
+    int r = 0;
+    for (int b = 0; b < k; ++b) r += piv[b] < piv[q];
+    rnk[q] = r;
+    sig[r] = q;
+  }
+  __syncthreads();
+  double *E = a.E + a.eoff[tau];
+  for (int64_t q = threadIdx.x; q < (int64_t)m * k; q += NT) E[q] = 0.0;
+  __syncthreads();
+  for (int q = threadIdx.x; q < k; q += NT) {
+    const int jr = piv[sig[q]];
+    E[jr + (int64_t)q * m] = 1.0;
+    a.J_tmp[row + q] = jr;
+    a.skel_tmp[row + q] = a.ibar ? a.ibar[row + jr] : (int32_t)(row + jr);
+  }
+  for (int64_t q = threadIdx.x; q < (int64_t)(m - k) * k; q += NT) {
+    const int rr = (int)(q % (m - k)), ap = (int)(q / (m - k));
+    E[piv[k + rr] + (int64_t)ap * m] = df_val(A[(int64_t)sig[ap] * m + (k + rr)]);
+  }
+  if (threadIdx.x == 0) a.k_out[tau] = k;
+}
+
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) k_row_id(IdArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -814,8 +1101,12 @@ __global__ void __launch_bounds__(NT) k_row_id(IdArgs a) {
   __shared__ int redi[33];
   __shared__ int s_j;
   const int n = a.t.n;
-  for (int j = take_task(a.next, &s_j, true, n); j < n; j = take_task(a.next, &s_j, false, n))
-    id_task<T, NT>(a, a.queue ? a.queue[j] : j, smem_raw, red, redv, redi);
+  for (int j = take_task(a.next, &s_j, true, n); j < n; j = take_task(a.next, &s_j, false, n)) {
+    if constexpr (sizeof(T) == 4)
+      id_task_df<NT>(a, a.queue ? a.queue[j] : j, smem_raw, red, redv, redi);
+    else
+      id_task<T, NT>(a, a.queue ? a.queue[j] : j, smem_raw, red, redv, redi);
+  }
 }
 
 __global__ void k_compact(TasksDev t, const int32_t *J_tmp, const int32_t *skel_tmp, int32_t *J,
