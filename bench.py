@@ -60,7 +60,7 @@ FIT_SIZES = (4096, 8192, 16384)
 # stop earlier, so the sketch sample takes the full size's column blocks.
 FULL_D_FINAL = 80
 # launch-shape build options the autotuner picks (passed through to every build)
-SHAPE_KEYS = ("bsr_engine", "tc_cols", "ksum_split", "queue_order")
+SHAPE_KEYS = ("bsr_engine", "tc_cols", "ksum_split", "queue_order", "sum_engine")
 _W_STATE = {}
 
 
@@ -516,8 +516,9 @@ def extra_configs(dev, flush, peaks, names, fp64_steps) -> dict:
                     "algorithmic_bytes": "operand blocks (D, B, U/E) once per sketch call + "
                                          "x and y panels in FP64",
                     "note": "sketch phase time: every operand matvec of the build"}
-        run_single("c4", w, {"d0": 80, "d_inc": 16}, {"operands": ops}, c4_err, c4_roof,
-                   tree=tree)
+        # mixed builds take the tensor-core couplings (sum_engine 1)
+        run_single("c4", w, {"d0": 80, "d_inc": 16}, {"operands": ops, "sum_engine": 1}, c4_err,
+                   c4_roof, tree=tree)
         res["c4"]["operands"] = {"tol": w.extra["operand_tol"], "prec": "mixed",
                                  "build_s": op_s, "bytes": op_bytes}
         del ops

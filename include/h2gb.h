@@ -162,6 +162,15 @@ typedef struct {
                                  over a device-filling grid, largest estimated
                                  cost first (m d^2 for the test, d m min(m, d)
                                  for the ID).  Results do not depend on it. */
+  int sum_engine;             /* couplings of an H2 sum (H2_K_H2SUM), mixed
+                                 precision: 0 CUDA cores (FP32 products with
+                                 compensated sums), 1 tensor cores (two-part
+                                 TF32, accumulated in tensor memory: faster,
+                                 but the accumulator adds a few units of 1e-7
+                                 relative error, which can cost adaptive
+                                 rounds on problems whose blocks are large
+                                 against eps_l); falls back to 0 for target
+                                 ranks above 96 */
 } h2_build_opts;
 
 /* Fills opts with the workload defaults (32/16/256, FP64, Philox seed 0,

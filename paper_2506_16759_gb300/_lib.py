@@ -34,7 +34,7 @@ class BuildOpts(C.Structure):
                 ("lowrank_rank", C.c_int), ("bsr_engine", C.c_int), ("tc_cols", C.c_int),
                 ("ksum_split", C.c_int), ("nonsym", C.c_int), ("psi_stored", C.c_void_p),
                 ("sampler_t", SAMPLER_FN), ("sampler_t_ctx", C.c_void_p),
-                ("queue_order", C.c_int)]
+                ("queue_order", C.c_int), ("sum_engine", C.c_int)]
 
 
 class TreeInfo(C.Structure):

@@ -109,7 +109,7 @@ class ClusterTree:
 def make_opts(d0=32, d_inc=16, d_max=256, prec="fp64", omega=None, seed=0, sketch="ksum",
               dense_a=None, timing=False, sampler=None, operands=None, ksum_tile=0,
               lowrank=None, bsr_engine=0, tc_cols=0, ksum_split=0, nonsym=False, psi=None,
-              sampler_t=None, queue_order=0):
+              sampler_t=None, queue_order=0, sum_engine=0):
     o = BuildOpts()
     lib().h2_default_opts(C.byref(o))
     o.d0, o.d_inc, o.d_max = d0, d_inc, d_max
@@ -139,6 +139,7 @@ def make_opts(d0=32, d_inc=16, d_max=256, prec="fp64", omega=None, seed=0, sketc
     o.ksum_tile = ksum_tile
     o.bsr_engine, o.tc_cols, o.ksum_split = bsr_engine, tc_cols, ksum_split
     o.queue_order = queue_order
+    o.sum_engine = sum_engine
     if nonsym:
         # separate row and column bases: Psi (stored mode) and A^T x (callback)
         o.nonsym = 1
@@ -259,7 +260,8 @@ def autotune(tree: ClusterTree, kernel, params, tol: float, stream=None, **kw) -
     inv = {v: k for k, v in PREC.items()}
     out = dict(kw)
     out.update(d0=best.d0, d_inc=best.d_inc, prec=inv[best.prec], bsr_engine=best.bsr_engine,
-               tc_cols=best.tc_cols, ksum_split=best.ksum_split, queue_order=best.queue_order)
+               tc_cols=best.tc_cols, ksum_split=best.ksum_split, queue_order=best.queue_order,
+               sum_engine=best.sum_engine)
     return out, ms.value
 
 

@@ -1270,7 +1270,7 @@ struct Builder {
     a.B = Bp(L);
     a.ops = dops.p;
     a.nops = o.n_operands;
-    h2sum_couplings(fp64(), a, max_kop, L.max_k, s);
+    h2sum_couplings(fp64(), a, max_kop, L.max_k, o.sum_engine, s);
     H2_CUDA(cudaStreamSynchronize(s));
     timer.end(PH_COUP);
   }
@@ -1515,6 +1515,7 @@ void validate_opts(const h2_build_opts &o) {
   H2_REQUIRE(o.ksum_split >= 0 && o.ksum_split <= 1024, "ksum_split must be in 0..1024");
   H2_REQUIRE(o.nonsym == 0 || o.nonsym == 1, "nonsym must be 0 or 1");
   H2_REQUIRE(o.queue_order == 0 || o.queue_order == 1, "queue_order must be 0 or 1");
+  H2_REQUIRE(o.sum_engine == 0 || o.sum_engine == 1, "sum_engine must be 0 or 1");
   if (o.nonsym) {
     H2_REQUIRE(o.sketch != H2_SKETCH_KSUM,
                "a non-symmetric build needs a dense, callback or H2-matvec sketch");
@@ -2042,6 +2043,12 @@ h2_status h2_autotune(const h2_tree *tree, int kernel_id, const double *params, 
         o.ksum_split = split;
         try_opts(o);
       }
+    }
+    // H2 sums in mixed precision: the couplings' engine
+    if (best_t < 1e300 && choice.prec != H2_PREC_FP64 && kernel_id == H2_K_H2SUM) {
+      h2_build_opts o = choice;
+      o.sum_engine = 1 - o.sum_engine;
+      try_opts(o);
     }
     // last stage (any precision): the order of the per-cluster factorizations
     if (best_t < 1e300) {

@@ -606,6 +606,14 @@ __device__ __forceinline__ float2 df_sub_prod(float2 a, float2 w, float2 v) {
   return df_norm(h, __fadd_rn(t, __fsub_rn(a.y, e)));
 }
 
+// Sum over a group of TPC consecutive lanes (mask: the group's lanes).
+template <int TPC>
+__device__ __forceinline__ double group_sum(double v, unsigned mask) {
+  if constexpr (TPC >= 2) v += __shfl_xor_sync(mask, v, 1);
+  if constexpr (TPC >= 4) v += __shfl_xor_sync(mask, v, 2);
+  return v;
+}
+
 // ----------------------------------------------------------------------------
 // Task scheduling of the per-cluster factorizations.  Without a queue each
 // CTA takes one task (task = blockIdx.x, or queue[blockIdx.x]).  With one, a
@@ -700,10 +708,13 @@ __device__ __forceinline__ void qr_task(const QrArgs &a, int tau, unsigned char 
 
 // The same test on FP32 panels (mixed precision) in double-float arithmetic:
 // the panel and its Householder updates as hi/lo pairs (8 bytes, like FP64),
-// the scalars of a step (norm, alpha, beta, w) in FP64.
+// the scalars of a step (norm, alpha, beta, w) in FP64.  In clusters wider
+// than 128 four threads share a column (rows interleaved); their partial dot
+// products and norms meet in shuffles within the 4-lane group.
 template <int NT>
 __device__ __forceinline__ void qr_task_df(const QrArgs &a, int tau, unsigned char *smem_raw,
                                            double *nrm2) {
+  constexpr int kTpc = NT >= 512 ? 4 : 1, kSlots = NT / kTpc;
   const int inst = a.t.inst[tau];
   if (!a.active[inst] || a.conv[tau]) return;
   const int m = a.t.m[tau];
@@ -720,18 +731,22 @@ __device__ __forceinline__ void qr_task_df(const QrArgs &a, int tau, unsigned ch
                                              : reinterpret_cast<double *>(smem_raw));
   const float *Y = reinterpret_cast<const float *>(a.Y);
   const int64_t row = a.t.row[tau];
+  const int slot = threadIdx.x / kTpc, sub = threadIdx.x % kTpc;
+  const unsigned gmask = kTpc == 4 ? 0xFu << (threadIdx.x & 28) : 1u << (threadIdx.x & 31);
+
   for (int64_t q = threadIdx.x; q < (int64_t)m * d; q += NT) {
     const int i = (int)(q % m), c = (int)(q / m);
     A[(int64_t)i * d + c] = make_float2(Y[row + i + (int64_t)c * a.ld], 0.f);
   }
   __syncthreads();
-  for (int c = threadIdx.x; c < d; c += NT) {
+  for (int c = slot; c < d; c += kSlots) {
     DfAcc s2;
-    for (int i = 0; i < m; ++i) {
+    for (int i = sub; i < m; i += kTpc) {
       const float2 x = A[(int64_t)i * d + c];
       s2.add_prod(x, x);
     }
-    nrm2[c] = s2.value();
+    const double v = group_sum<kTpc>(s2.value(), gmask);
+    if (sub == 0) nrm2[c] = v;
   }
   __syncthreads();
   const double eps = a.eps[inst];
@@ -747,23 +762,24 @@ __device__ __forceinline__ void qr_task_df(const QrArgs &a, int tau, unsigned ch
     __syncthreads();
     if (threadIdx.x == 0) A[(int64_t)j * d + j] = df_from(x0 - alpha);   // v_j
     __syncthreads();
-    for (int c = j + 1 + threadIdx.x; c < d; c += NT) {
+    // the group's rows: j + sub, j + sub + 4, ... (row j, the pivot row, is sub 0's)
+    for (int c = j + 1 + slot; c < d; c += kSlots) {
       DfAcc w0, w1;
-      int i = j;
-      for (; i + 1 < m; i += 2) {
+      int i = j + sub;
+      for (; i + kTpc < m; i += 2 * kTpc) {
         w0.add_prod(A[(int64_t)i * d + j], A[(int64_t)i * d + c]);
-        w1.add_prod(A[(int64_t)(i + 1) * d + j], A[(int64_t)(i + 1) * d + c]);
+        w1.add_prod(A[(int64_t)(i + kTpc) * d + j], A[(int64_t)(i + kTpc) * d + c]);
       }
       if (i < m) w0.add_prod(A[(int64_t)i * d + j], A[(int64_t)i * d + c]);
-      const float2 w = df_from((w0.value() + w1.value()) * beta);
-      A[(int64_t)j * d + c] = df_sub_prod(A[(int64_t)j * d + c], w, A[(int64_t)j * d + j]);
+      const float2 w = df_from(group_sum<kTpc>(w0.value() + w1.value(), gmask) * beta);
       DfAcc s2;
-      for (int r = j + 1; r < m; ++r) {
+      for (int r = j + sub; r < m; r += kTpc) {
         const float2 x = df_sub_prod(A[(int64_t)r * d + c], w, A[(int64_t)r * d + j]);
         A[(int64_t)r * d + c] = x;
-        s2.add_prod(x, x);
+        if (r > j) s2.add_prod(x, x);
       }
-      nrm2[c] = s2.value();
+      const double v = group_sum<kTpc>(s2.value(), gmask);
+      if (sub == 0) nrm2[c] = v;
     }
     __syncthreads();
   }
@@ -948,9 +964,16 @@ __device__ __forceinline__ void id_task(const IdArgs &a, int tau, unsigned char 
 // the panel, its Householder updates and the back substitution as hi/lo
 // pairs; norms, pivots, thresholds and the scalars of a step in FP64.  The
 // pivot is the largest squared trailing norm (the same order as the norm).
+// In clusters wider than 128 four threads share a column in the updates
+// (rows interleaved, partial sums meeting in shuffles within the 4-lane
+// group).
 template <int NT>
 __device__ __forceinline__ void id_task_df(const IdArgs &a, int tau, unsigned char *smem_raw,
                                            double *red, double *redv, int *redi) {
+  constexpr int kTpc = NT >= 512 ? 4 : 1, kSlots = NT / kTpc;
+  const int slot = threadIdx.x / kTpc, sub = threadIdx.x % kTpc;
+  const unsigned gmask = kTpc == 4 ? 0xFu << (threadIdx.x & 28) : 1u << (threadIdx.x & 31);
+
   const int inst = a.t.inst[tau];
   const int m = a.t.m[tau];
   const int64_t row = a.t.row[tau];
@@ -975,13 +998,14 @@ __device__ __forceinline__ void id_task_df(const IdArgs &a, int tau, unsigned ch
   }
   for (int i = threadIdx.x; i < m; i += NT) piv[i] = i;
   __syncthreads();
-  for (int c = threadIdx.x; c < m; c += NT) {
+  for (int c = slot; c < m; c += kSlots) {
     DfAcc s2;
-    for (int r = 0; r < d; ++r) {
+    for (int r = sub; r < d; r += kTpc) {
       const float2 x = A[(int64_t)r * m + c];
       s2.add_prod(x, x);
     }
-    nrm2[c] = s2.value();
+    const double v = group_sum<kTpc>(s2.value(), gmask);
+    if (sub == 0) nrm2[c] = v;
   }
   __syncthreads();
   const double eps2 = a.eps[inst] * a.eps[inst];
@@ -1019,36 +1043,36 @@ __device__ __forceinline__ void id_task_df(const IdArgs &a, int tau, unsigned ch
     __syncthreads();
     if (threadIdx.x == 0) A[(int64_t)k * m + k] = df_from(x0 - alpha);   // v_k
     __syncthreads();
-    for (int c = k + 1 + threadIdx.x; c < m; c += NT) {
-      DfAcc w0, w1, w2, w3;
-      int r = k;
-      for (; r + 3 < d; r += 4) {
+    for (int c = k + 1 + slot; c < m; c += kSlots) {
+      const double nc2 = nrm2[c];
+      DfAcc w0, w1;
+      int r = k + sub;
+      for (; r + kTpc < d; r += 2 * kTpc) {
         w0.add_prod(A[(int64_t)r * m + k], A[(int64_t)r * m + c]);
-        w1.add_prod(A[(int64_t)(r + 1) * m + k], A[(int64_t)(r + 1) * m + c]);
-        w2.add_prod(A[(int64_t)(r + 2) * m + k], A[(int64_t)(r + 2) * m + c]);
-        w3.add_prod(A[(int64_t)(r + 3) * m + k], A[(int64_t)(r + 3) * m + c]);
+        w1.add_prod(A[(int64_t)(r + kTpc) * m + k], A[(int64_t)(r + kTpc) * m + c]);
       }
-      for (; r < d; ++r) w0.add_prod(A[(int64_t)r * m + k], A[(int64_t)r * m + c]);
-      const float2 w =
-          df_from(((w0.value() + w1.value()) + (w2.value() + w3.value())) * beta);
+      if (r < d) w0.add_prod(A[(int64_t)r * m + k], A[(int64_t)r * m + c]);
+      const float2 w = df_from(group_sum<kTpc>(w0.value() + w1.value(), gmask) * beta);
       const float2 rkc = df_sub_prod(A[(int64_t)k * m + c], w, A[(int64_t)k * m + k]);
-      A[(int64_t)k * m + c] = rkc;
+      __syncwarp(gmask);   // the group has read row k before it changes
+      if (sub == 0) A[(int64_t)k * m + c] = rkc;
       // trailing norm downdated, |A(k+1:, c)|^2 = |A(k:, c)|^2 - R(k, c)^2,
       // and recomputed after a cancellation of four digits
       const double rk = df_val(rkc);
-      const double down = nrm2[c] - rk * rk;
-      if (down > 1e-4 * nrm2[c]) {
-        for (int q = k + 1; q < d; ++q)
+      const double down = nc2 - rk * rk;
+      if (down > 1e-4 * nc2) {
+        for (int q = k + 1 + sub; q < d; q += kTpc)
           A[(int64_t)q * m + c] = df_sub_prod(A[(int64_t)q * m + c], w, A[(int64_t)q * m + k]);
-        nrm2[c] = down;
+        if (sub == 0) nrm2[c] = down;
       } else {
         DfAcc s2;
-        for (int q = k + 1; q < d; ++q) {
+        for (int q = k + 1 + sub; q < d; q += kTpc) {
           const float2 x = df_sub_prod(A[(int64_t)q * m + c], w, A[(int64_t)q * m + k]);
           A[(int64_t)q * m + c] = x;
           s2.add_prod(x, x);
         }
-        nrm2[c] = s2.value();
+        const double v = group_sum<kTpc>(s2.value(), gmask);
+        if (sub == 0) nrm2[c] = v;
       }
     }
     __syncthreads();
@@ -1062,11 +1086,14 @@ __device__ __forceinline__ void id_task_df(const IdArgs &a, int tau, unsigned ch
   float2 *rinv = reinterpret_cast<float2 *>(nrm2);
   for (int i = threadIdx.x; i < k; i += NT) rinv[i] = df_from(1.0 / df_val(A[(int64_t)i * m + i]));
   __syncthreads();
-  for (int c = k + threadIdx.x; c < m; c += NT) {
-    for (int i = k - 1; i >= 0; --i) {
-      float2 t = A[(int64_t)i * m + c];
-      for (int j = i + 1; j < k; ++j) t = df_sub_prod(t, A[(int64_t)i * m + j], A[(int64_t)j * m + c]);
-      A[(int64_t)i * m + c] = df_mul(t, rinv[i]);
+  if (sub == 0) {
+    for (int c = k + slot; c < m; c += kSlots) {
+      for (int i = k - 1; i >= 0; --i) {
+        float2 t = A[(int64_t)i * m + c];
+        for (int j = i + 1; j < k; ++j)
+          t = df_sub_prod(t, A[(int64_t)i * m + j], A[(int64_t)j * m + c]);
+        A[(int64_t)i * m + c] = df_mul(t, rinv[i]);
+      }
     }
   }
   // sorted skeleton order
@@ -1577,7 +1604,7 @@ void bsr_apply(bool fp64, const BsrArgs &a_in, int max_m, int max_cols, cudaStre
 }
 
 // CTA width for clusters of up to `width` columns (64, 128 or 256 threads).
-template <template <typename, int> class K, typename A>
+template <template <typename, int> class K, int MUL, typename A>
 void launch_width(bool fp64, int width, const A &a, int n, size_t bytes, cudaStream_t s);
 
 template <typename T, int NT>
@@ -1589,7 +1616,9 @@ struct IdKern {
   static constexpr auto f = k_row_id<T, NT>;
 };
 
-template <template <typename, int> class K, typename A>
+// FP32 panels (double-float kernels) of clusters wider than 128 run MUL
+// threads per column.
+template <template <typename, int> class K, int MUL, typename A>
 void launch_width(bool fp64, int width, const A &a, int n, size_t bytes, cudaStream_t s) {
   auto go = [&](auto kern, int nt) {
     set_smem(kern, bytes);
@@ -1611,7 +1640,7 @@ void launch_width(bool fp64, int width, const A &a, int n, size_t bytes, cudaStr
   } else {
     if (w <= 64) go(K<float, 64>::f, 64);
     else if (w <= 128) go(K<float, 128>::f, 128);
-    else go(K<float, 256>::f, 256);
+    else go(K<float, 256 * MUL>::f, 256 * MUL);
   }
   count_launch();
   H2_CHECK_LAUNCH();
@@ -1619,7 +1648,7 @@ void launch_width(bool fp64, int width, const A &a, int n, size_t bytes, cudaStr
 
 void qr_test(bool fp64, const QrArgs &a, size_t smem_bytes, int width, cudaStream_t s) {
   if (a.t.n == 0) return;
-  launch_width<QrKern>(fp64, width, a, a.t.n, smem_bytes, s);
+  launch_width<QrKern, 4>(fp64, width, a, a.t.n, smem_bytes, s);
 }
 
 size_t row_id_fixed_smem(int mcap) { return (size_t)mcap * (sizeof(double) + 3 * sizeof(int)); }
@@ -1627,7 +1656,7 @@ size_t row_id_fixed_smem(int mcap) { return (size_t)mcap * (sizeof(double) + 3 *
 void row_id(bool fp64, const IdArgs &a, size_t smem_bytes, int width, cudaStream_t s) {
   if (a.t.n == 0) return;
   H2_REQUIRE(a.mcap >= 8 && a.mcap % 8 == 0 && a.mcap <= kMaxIdRows, "row ID capacity");
-  launch_width<IdKern>(fp64, width, a, a.t.n, smem_bytes + row_id_fixed_smem(a.mcap), s);
+  launch_width<IdKern, 4>(fp64, width, a, a.t.n, smem_bytes + row_id_fixed_smem(a.mcap), s);
 }
 
 void compact_skeletons(const TasksDev &t, const int32_t *J_tmp, const int32_t *skel_tmp,

@@ -214,7 +214,9 @@ void h2sum_g_inner(const TasksDev &t, const int32_t *child0, const int32_t *kt_c
                    const int32_t *kop_child, const int64_t *goff_child, const double *Gchild,
                    const int32_t *kop, const int32_t *mop, const int64_t *eoff_op,
                    const double *Eop, const int64_t *goff, double *G, cudaStream_t s);
-void h2sum_couplings(bool fp64, const SumCouplingArgs &a, int max_kop, int max_kt, cudaStream_t s);
+// engine (mixed precision): 0 CUDA cores, 1 tensor cores where target ranks are <= 96.
+void h2sum_couplings(bool fp64, const SumCouplingArgs &a, int max_kop, int max_kt, int engine,
+                     cudaStream_t s);
 void h2sum_dense(bool fp64, int64_t nnz, const int32_t *erow, const int32_t *idx, const int32_t *m,
                  const int64_t *doff, void *D, const double *const *Dop, const float *const *Dop32,
                  const int64_t *const *doff_op, int nops, cudaStream_t s);

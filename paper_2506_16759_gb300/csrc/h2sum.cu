@@ -16,6 +16,7 @@
 
 #include "h2_level.h"
 #include "h2_types.h"
+#include "tc_ptx.cuh"
 
 namespace h2 {
 namespace {
@@ -244,6 +245,222 @@ __global__ void __launch_bounds__(256, 2) k_b_h2sum32(SumCouplingArgs a) {
   }
 }
 
+// Mixed-precision couplings of an H2 sum on the tensor cores (tcgen05,
+// FP32 values carried as two TF32 parts, three part products per K step
+// into an FP32 accumulator in tensor memory).  One CTA of 8 warps per far
+// block (s, t); per operand and per 128-row tile p0.. of the operand's rank
+// at s:
+//   step 1  T = B_op(s,t)(p0.., :) G_op,t^T  (M = 128 rows p, N = k_t padded
+//           to np, K = the operand's rank at t in chunks of 32): the block's
+//           chunk goes into TMEM as operand A (thread = row p, 16 of the 32
+//           columns per warp), G_op,t's chunk into a 128-byte-swizzled K-major
+//           image in shared memory (operand B);
+//   step 2  C += G_op,s(:, p0..) T  (M = 128 rows r of the target rank k_s,
+//           N = np, K = the tile's rows p): T is read back from TMEM and
+//           written as four K chunks of B images, G_op,s's columns go into
+//           TMEM as operand A.
+// C stays in TMEM across operands and is stored once.  Every product is
+// waited for before its operands are overwritten (no pipelining: the
+// kernel's time is the blocks' streaming and these round trips).  Target
+// ranks up to 96 (k_s and k_t), operand ranks of any size.  Tensor memory:
+// T and C (np columns each) and one A stage (64 columns), 256 columns, so two
+// CTAs fit an SM.  Waits are bounded; a timeout sets *err.
+constexpr int kHsMaxN = 96;
+
+__device__ __forceinline__ int hs_sw(int row, int j) {   // element (row, j) of a swizzled image
+  return row * 32 + (((j >> 2) ^ (row & 7)) << 2) + (j & 3);
+}
+__device__ __forceinline__ void hs_split(float v, uint32_t &h, uint32_t &l) {
+  const float hh = tf32_rna(v);
+  h = __float_as_uint(hh);
+  l = __float_as_uint(v - hh);
+}
+
+__global__ void __launch_bounds__(256, 2) k_b_h2sum_tc(SumCouplingArgs a, int np, int *err) {
+  extern __shared__ unsigned char hs_dyn[];
+  float *img = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(hs_dyn) + 1023) &
+                                         ~uintptr_t(1023));   // [4][2][np][32]
+  __shared__ uint64_t done;
+  __shared__ uint32_t tmem_base;
+  const int64_t e = blockIdx.x;
+  const int s = a.erow[e], tt = a.idx[e];
+  const int ks = a.t.k[s], kt = a.t.k[tt];
+  if (ks == 0 || kt == 0) return;   // uniform over the CTA
+  float *out = reinterpret_cast<float *>(a.B) + a.boff[e];
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int quad = warp & 3, half = warp >> 2;
+  if (t == 0) {
+    mbar_init(saddr(&done), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     saddr(&tmem_base)),
+                 "n"(256));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tb = tmem_base;
+  const uint32_t t_col = tb, c_col = tb + np, a_col = tb + 2 * np;
+  const uint32_t lane_addr = (uint32_t)(quad * 32) << 16;
+  const uint32_t idesc = idesc_mma(false, 128, np);
+  uint32_t phase = 0;
+  bool ok = true, c_started = false;
+
+  // operand A (16 of the chunk's 32 columns of this thread's row) into TMEM
+  auto stage_a = [&](const float *v) {
+    uint32_t hv[16], lv[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) hs_split(v[j], hv[j], lv[j]);
+    const uint32_t at = a_col + lane_addr + 16 * half;
+    tmem_st8(at, hv);
+    tmem_st8(at + 8, hv + 8);
+    tmem_st8(at + 32, lv);
+    tmem_st8(at + 40, lv + 8);
+    tmem_st_wait();
+  };
+  // D (+)= A * B with B = the image at bimg (hi rows, then lo rows), then
+  // every thread waits for the products; false (everywhere) on a timeout.
+  // `prefetch` runs between the issue and the wait (the next chunk's loads).
+  auto product = [&](uint32_t d, const float *bimg, bool acc, auto &&prefetch) -> bool {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (t == 0) {
+      const uint32_t h = saddr(bimg), l = h + (uint32_t)np * 128;
+#pragma unroll
+      for (int k8 = 0; k8 < 4; ++k8) {
+        mma_ts<false>(d, a_col + k8 * 8, desc_sw128(h + k8 * 32), idesc, (acc || k8) ? 1u : 0u);
+        mma_ts<false>(d, a_col + k8 * 8, desc_sw128(l + k8 * 32), idesc, 1u);
+        mma_ts<false>(d, a_col + 32 + k8 * 8, desc_sw128(h + k8 * 32), idesc, 1u);
+      }
+      mma_commit(saddr(&done));
+    }
+    prefetch();
+    const bool w = mbar_wait(saddr(&done), phase);
+    phase ^= 1u;
+    fence_after();
+    return __syncthreads_and(w ? 1 : 0) != 0;
+  };
+
+  for (int o = 0; o < a.nops && ok; ++o) {
+    const SumOperand &op = a.ops[o];
+    const int kos = op.k[s], kot = op.k[tt];
+    if (kos == 0 || kot == 0) continue;
+    const double *Gs = op.G + op.goff[s];
+    const double *Gt = op.G + op.goff[tt];
+    const double *Bo = op.B ? op.B + op.boff[e] : nullptr;
+    const float *Bo32 = op.B32 ? op.B32 + op.boff[e] : nullptr;
+    for (int p0 = 0; p0 < kos && ok; p0 += 128) {
+      const int mp = min(128, kos - p0);
+      // ---- step 1: T = B_op(p0.., :) G_t^T.  This thread's share of a chunk:
+      // 16 values of block row p (A) and up to 12 values of G_t's image
+      // (element q = t + 256 u: image row q % np, column q / np); the next
+      // chunk's share is loaded while the current chunk's products run.
+      const int p = p0 + quad * 32 + lane;
+      float bv[16], gv[12];
+      auto load1 = [&](int c0) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int c = c0 + 16 * half + j;
+          float x = 0.f;
+          if (p < kos && c < kot) {
+            const int64_t i = p + (int64_t)c * kos;
+            x = Bo ? (float)Bo[i] : Bo32[i];
+          }
+          bv[j] = x;
+        }
+#pragma unroll
+        for (int u = 0; u < 12; ++u) {
+          const int q = t + 256 * u;
+          const int b = q % np, j = q / np;
+          gv[u] = (q < np * 32 && b < kt && c0 + j < kot) ? (float)Gt[b + (int64_t)(c0 + j) * kt]
+                                                           : 0.f;
+        }
+      };
+      load1(0);
+      for (int c0 = 0; c0 < kot && ok; c0 += 32) {
+        stage_a(bv);
+#pragma unroll
+        for (int u = 0; u < 12; ++u) {
+          const int q = t + 256 * u;
+          if (q < np * 32) {
+            const int b = q % np, j = q / np;
+            const float h = tf32_rna(gv[u]);
+            img[hs_sw(b, j)] = h;
+            img[np * 32 + hs_sw(b, j)] = gv[u] - h;
+          }
+        }
+        ok = product(t_col, img, c0 > 0, [&]() {
+          if (c0 + 32 < kot) load1(c0 + 32);
+        });
+      }
+      if (!ok) break;
+      // ---- T rows p0 + 32 w .. (warp quadrant w) -> the B image of step-2 chunk w
+      const int nch = (mp + 31) / 32;
+      if (quad < nch) {   // uniform per warp
+        float *hi = img + quad * (np * 64), *lo = hi + np * 32;
+        for (int b0 = 8 * half; b0 < np; b0 += 16) {
+          float v[8];
+          tmem_ld<8>(t_col + lane_addr + b0, v);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const float h = tf32_rna(v[u]);
+            hi[hs_sw(b0 + u, lane)] = h;
+            lo[hs_sw(b0 + u, lane)] = v[u] - h;
+          }
+        }
+      }
+      // ---- step 2: C += G_s(:, p0..) T (the next chunk of G_s loaded while
+      // the current products run)
+      const int r = quad * 32 + lane;
+      auto load2 = [&](int ch) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int pp = p0 + ch * 32 + 16 * half + j;
+          bv[j] = (r < ks && pp < kos) ? (float)Gs[r + (int64_t)pp * ks] : 0.f;
+        }
+      };
+      load2(0);
+      for (int ch = 0; ch < nch && ok; ++ch) {
+        stage_a(bv);
+        ok = product(c_col, img + ch * (np * 64), c_started || ch > 0, [&]() {
+          if (ch + 1 < nch) load2(ch + 1);
+        });
+        c_started = true;
+      }
+    }
+  }
+  if (ok) {
+    const int r = quad * 32 + lane;
+    for (int b0 = 8 * half; b0 < np; b0 += 16) {
+      float v[8];
+      if (c_started) {
+        tmem_ld<8>(c_col + lane_addr + b0, v);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = 0.f;
+      }
+      if (r < ks) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (b0 + u < kt) out[r + (int64_t)(b0 + u) * ks] = v[u];
+      }
+    }
+  } else if (t == 0) {
+    atomicExch(err, 1);
+    mbar_wait(saddr(&done), phase ^ 1u);   // once more before the memory is released
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tb), "n"(256));
+}
+
 template <typename T>
 __global__ void k_d_h2sum(int64_t nnz, const int32_t *erow, const int32_t *idx, const int32_t *m,
                           const int64_t *doff, T *D, const double *const *Dop,
@@ -280,10 +497,25 @@ void h2sum_g_inner(const TasksDev &t, const int32_t *child0, const int32_t *kt_c
   H2_CHECK_LAUNCH();
 }
 
-void h2sum_couplings(bool fp64, const SumCouplingArgs &a, int max_kop, int max_kt, cudaStream_t s) {
+void h2sum_couplings(bool fp64, const SumCouplingArgs &a, int max_kop, int max_kt, int engine,
+                     cudaStream_t s) {
   if (a.nnz == 0) return;
   H2_REQUIRE(a.nnz < (1ll << 31), "too many coupling blocks");
   const size_t bytes = sizeof(double) * (size_t)std::max(max_kop, 1) * std::max(max_kt, 1);
+  if (!fp64 && engine == 1 && max_kt <= kHsMaxN) {
+    const int np = std::max(16, (max_kt + 15) / 16 * 16);
+    const size_t smem = (size_t)np * 1024 + 1024;
+    H2_CUDA(cudaFuncSetAttribute(k_b_h2sum_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    DBuf<int> err;
+    err.alloc_zero(1, s);
+    k_b_h2sum_tc<<<(int)a.nnz, 256, smem, s>>>(a, np, err.p);
+    count_launch();
+    H2_CHECK_LAUNCH();
+    if (to_host(err.p, 1, s)[0] != 0)
+      throw Error{H2_ERR_TIMEOUT, "tensor-core H2-sum couplings: a bounded wait ran out"};
+    return;
+  }
   if (!fp64 && max_kop <= kB32MaxKop) {
     H2_CUDA(cudaFuncSetAttribute(k_b_h2sum32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kB32Smem));

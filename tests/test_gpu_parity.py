@@ -333,13 +333,15 @@ def test_h2sum_build_matches_oracle():
     ops_g = [api.H2Matrix.build(tree, k, p, 1e-8, omega=gpu(om)) for (k, p), om in zip(kps, oms)]
     A = O.dense_matrix(X, *kps[0]) + O.dense_matrix(X, *kps[1])
     G = W.gaussian_probe(n, 4, 5)
-    for prec, bar in (("fp64", 1e-10), ("mixed", 1e-5)):
+    # mixed precision: couplings on the CUDA cores (sum_engine 0) and on the
+    # tensor cores (sum_engine 1)
+    for prec, bar, eng in (("fp64", 1e-10, 0), ("mixed", 1e-5, 0), ("mixed", 1e-5, 1)):
         h = api.H2Matrix.build(tree, "h2sum", (), 1e-6, omega=gpu(oms[2]), sketch="h2sum",
-                               operands=ops_g, prec=prec)
+                               operands=ops_g, prec=prec, sum_engine=eng)
         if prec == "fp64":
             check_same_skeletons(h, t, ho)
         rel, y, _ = matvec_rel(h, ho, n, seed=5)
-        assert rel <= bar
+        assert rel <= bar, (prec, eng)
         assert np.linalg.norm(y - A @ G) <= 10 * 1e-6 * np.linalg.norm(A @ G)
 
 
@@ -371,11 +373,11 @@ def test_h2sum_with_mixed_precision_operands():
     A = O.dense_matrix(X, *kps[0]) + O.dense_matrix(X, *kps[1])
     G = W.gaussian_probe(n, 4, 5)
     AG = A @ G
-    for prec in ("fp64", "mixed"):
+    for prec, eng in (("fp64", 0), ("mixed", 0), ("mixed", 1)):
         h = api.H2Matrix.build(tree, "h2sum", (), 1e-6, sketch="h2sum", operands=ops, prec=prec,
-                               seed=9)
+                               seed=9, sum_engine=eng)
         y = h.matvec(gpu(G)).cpu().numpy()
-        assert np.linalg.norm(y - AG) <= 10 * 1e-6 * np.linalg.norm(AG)
+        assert np.linalg.norm(y - AG) <= 10 * 1e-6 * np.linalg.norm(AG), (prec, eng)
 
 
 @pytest.mark.parametrize("kernel,params", [(W.K_HELMHOLTZ_IE, (3.0, 0.0)), (W.K_EXP, (0.2, 0.0))])
