@@ -227,7 +227,8 @@ class ClockSampler:
 
 def source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("sketch.cu", "sketch_tc.cu", "h2_internal.cuh", "h2_ops.h"):
+    # the sources the tensor-core sketch kernel is compiled from
+    for f in ("sketch_tc.cu", "tc_ptx.cuh", "h2_internal.cuh", "h2_types.h", "h2_ops.h"):
         h.update(open(os.path.join(ROOT, "paper_2506_16759_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -803,8 +804,10 @@ def main_kernel_only(args):
     """Small processes for ncu captures.  "ksum": only the fused sketch of the
     benchmark workload (N=131072, 32 columns, all points, same launch plan as
     inside a build).  "build": whole builds of the same workload family at
-    --n points with the 80/+16 mixed schedule (its first k_ksum_tc launch is
-    the 80-column far-only sketch)."""
+    --n points with the 80/+16 mixed schedule and the work-queue order (the
+    tuned choice on this workload; its first k_ksum_tc launch is the
+    80-column far-only sketch).  "paper": a Sec. V-A problem.  "matvec": the
+    H2 matvec of a 1e-8 operand."""
     import torch
 
     from paper_2506_16759_gb300 import api
@@ -827,7 +830,8 @@ def main_kernel_only(args):
             tree = api.ClusterTree(X, w.leaf_size, w.eta)
             h = api.H2Matrix.build(tree, w.kernel, w.params, w.tol, prec="mixed", seed=k,
                                    sketch="ksum", d0=80, d_inc=16, d_max=w.d_max,
-                                   bsr_engine=args.bsr_engine, timing=args.phases)
+                                   bsr_engine=args.bsr_engine, queue_order=1,
+                                   timing=args.phases)
             torch.cuda.synchronize()
             if k >= args.warmup:
                 times.append((time.perf_counter() - t0) * 1e3)

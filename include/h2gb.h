@@ -106,7 +106,9 @@ typedef struct {
                           its d0 samples (the non-adaptive construction) */
   int d_max;           /* sample budget (256) */
   int prec;            /* h2_prec */
-  int omega_mode;      /* 0: Gaussian Omega from Philox4x32-10 (seed);
+  int omega_mode;      /* 0: Gaussian Omega from Philox4x32-10 (seed) and the
+                          Box-Muller transform (FP64 builds: in FP64 on 53-bit
+                          uniforms; mixed precision: in FP32 on 24-bit ones);
                           1: stored Omega (omega_stored) */
   uint64_t seed;
   const double *omega_stored; /* device, N_total x d_max, column-major with

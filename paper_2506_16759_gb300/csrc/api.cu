@@ -622,7 +622,7 @@ struct Builder {
       if (o.omega_mode == 1)
         gather_rows64(stored, N, H->orig_of_pos.p + b, n, c0, c0 + nc, om64 + b, N, s);
       else
-        philox_gaussian64(om64 + b, N, H->orig_of_pos.p + b, n, c0, c0 + nc, seed, s);
+        philox_gaussian64(om64 + b, N, H->orig_of_pos.p + b, n, c0, c0 + nc, seed, !fp64(), s);
       if (!fp64()) convert_cols_to32(om64, N, b, n, c0, c0 + nc, L.Om32.p, s);
     }
     return om64;

@@ -181,9 +181,10 @@ KsumPlan plan_ksum_tc_all(const std::vector<int64_t> &inst_n, const std::vector<
 
 // Gaussian sample columns for rows in tree order: om[pos + c*ld] for
 // c in [c0, c1), drawn from Philox4x32-10 keyed by (seed) at counter
-// (original index of pos, column).  T = double or float.
+// (original index of pos, column pair), Box-Muller in FP64 (53-bit
+// uniforms) or, with f32_math, in FP32 (24-bit uniforms).
 void philox_gaussian64(double *om, int64_t ld, const int32_t *orig_of_pos, int64_t n, int c0,
-                       int c1, uint64_t seed, cudaStream_t s);
+                       int c1, uint64_t seed, bool f32_math, cudaStream_t s);
 // Stored Omega (original order, ld_src) gathered into tree order.
 void gather_rows64(const double *src, int64_t ld_src, const int32_t *orig_of_pos, int64_t n,
                    int c0, int c1, double *dst, int64_t ld_dst, cudaStream_t s);

@@ -256,6 +256,10 @@ __device__ __forceinline__ void philox4x32_10(uint32_t ctr[4], uint32_t k0, uint
   }
 }
 
+// F32: the Box-Muller transform of 24-bit uniforms in FP32 arithmetic (the
+// mixed-precision builds consume FP32 samples; GB300's FP64 logarithm and
+// sine are slow), else of 53-bit uniforms in FP64.
+template <bool F32>
 __global__ void k_philox_gauss(double *om, int64_t ld, const int32_t *orig, int64_t n, int c0,
                                int c1, uint64_t seed) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -264,15 +268,28 @@ __global__ void k_philox_gauss(double *om, int64_t ld, const int32_t *orig, int6
   for (int c = c0 & ~1; c < c1; c += 2) {
     uint32_t ctr[4] = {oi, (uint32_t)(c >> 1), 0x48324742u, 0u};
     philox4x32_10(ctr, (uint32_t)seed, (uint32_t)(seed >> 32));
-    uint64_t a = ((uint64_t)ctr[0] << 32 | ctr[1]) >> 11;
-    uint64_t b = ((uint64_t)ctr[2] << 32 | ctr[3]) >> 11;
-    double u1 = ((double)a + 0.5) * 0x1.0p-53;
-    double u2 = ((double)b + 0.5) * 0x1.0p-53;
-    double rad = sqrt(-2.0 * log(u1));
-    double sn, cs;
-    sincospi(2.0 * u2, &sn, &cs);
-    if (c >= c0) om[i + (int64_t)c * ld] = rad * cs;
-    if (c + 1 < c1) om[i + (int64_t)(c + 1) * ld] = rad * sn;
+    double z0, z1;
+    if constexpr (F32) {
+      const float u1 = ((float)(ctr[0] >> 8) + 0.5f) * 0x1.0p-24f;
+      const float u2 = ((float)(ctr[2] >> 8) + 0.5f) * 0x1.0p-24f;
+      const float rad = sqrtf(-2.0f * logf(u1));
+      float sn, cs;
+      sincospif(2.0f * u2, &sn, &cs);
+      z0 = (double)(rad * cs);
+      z1 = (double)(rad * sn);
+    } else {
+      uint64_t a = ((uint64_t)ctr[0] << 32 | ctr[1]) >> 11;
+      uint64_t b = ((uint64_t)ctr[2] << 32 | ctr[3]) >> 11;
+      double u1 = ((double)a + 0.5) * 0x1.0p-53;
+      double u2 = ((double)b + 0.5) * 0x1.0p-53;
+      double rad = sqrt(-2.0 * log(u1));
+      double sn, cs;
+      sincospi(2.0 * u2, &sn, &cs);
+      z0 = rad * cs;
+      z1 = rad * sn;
+    }
+    if (c >= c0) om[i + (int64_t)c * ld] = z0;
+    if (c + 1 < c1) om[i + (int64_t)(c + 1) * ld] = z1;
   }
 }
 
@@ -708,9 +725,12 @@ void run_ksum64(int kid, const KsumPlan &plan, const KsumArgs64 &a, cudaStream_t
 }
 
 void philox_gaussian64(double *om, int64_t ld, const int32_t *orig_of_pos, int64_t n, int c0,
-                       int c1, uint64_t seed, cudaStream_t s) {
+                       int c1, uint64_t seed, bool f32_math, cudaStream_t s) {
   if (n == 0 || c1 <= c0) return;
-  k_philox_gauss<<<ceil_div(n, 256), 256, 0, s>>>(om, ld, orig_of_pos, n, c0, c1, seed);
+  if (f32_math)
+    k_philox_gauss<true><<<ceil_div(n, 256), 256, 0, s>>>(om, ld, orig_of_pos, n, c0, c1, seed);
+  else
+    k_philox_gauss<false><<<ceil_div(n, 256), 256, 0, s>>>(om, ld, orig_of_pos, n, c0, c1, seed);
   count_launch();
   H2_CHECK_LAUNCH();
 }
