@@ -1395,25 +1395,37 @@ __global__ void __launch_bounds__(256) k_gen_rows(int n_rows, const int64_t *ptr
   load_partner(e0, 0);
   __syncthreads();
   T *out = reinterpret_cast<T *>(out_);
-  // thread = row i (of 64 at a time) x every 4th column j: a warp shares j,
-  // so the partner point is a broadcast read and the stores are coalesced
-  const int ig = threadIdx.x & 63, jg = threadIdx.x >> 6;
+  // thread = row i (of RG = 32 or 64 at a time, whichever covers m with fewer
+  // idle lanes) x every (256 / RG)-th column j: a warp shares j, so the
+  // partner point is a broadcast read and the stores are coalesced
+  const int rg = m <= 32 ? 32 : 64, cg = 256 / rg;
+  const int ig = threadIdx.x % rg, jg = threadIdx.x / rg;
   for (int64_t e = e0; e < e1; ++e) {
     const int slot = (int)((e - e0) & 1);
     if (e + 1 < e1) load_partner(e + 1, slot ^ 1);   // overlaps the evaluation below
-    const int mb = width(idx[e]);
+    const int tc = idx[e];
+    const int mb = width(tc);
+    // only a leaf's block with itself holds coincident points (the diagonal)
+    const bool self = !SKEL && tc == tr;
     T *blk = out + off[e];
     const T *pb = sb[slot];
     const int64_t *gbs = gb[slot];
-    for (int i = ig; i < m; i += 64) {
+    for (int i = ig; i < m; i += rg) {
       T pa[NS];
 #pragma unroll
       for (int c = 0; c < NS; ++c) pa[c] = sa[i * NS + c];
-      const int64_t gi = ga[i];
-      for (int j = jg; j < mb; j += 4) {
-        const T gm = PtsOf<T>::template geom<KID>(pa, pb + j * NS);
-        blk[i + (int64_t)j * m] =
-            gi == gbs[j] ? kdiag<KID, T>(gm, scale, pw, diag) : kval<KID, T>(gm, scale, pw);
+      T *bp = blk + i + (int64_t)jg * m;
+      const int64_t bstep = (int64_t)cg * m;
+      if (self) {
+        const int64_t gi = ga[i];
+        for (int j = jg; j < mb; j += cg, bp += bstep) {
+          const T gm = PtsOf<T>::template geom<KID>(pa, pb + j * NS);
+          *bp = gi == gbs[j] ? kdiag<KID, T>(gm, scale, pw, diag) : kval<KID, T>(gm, scale, pw);
+        }
+      } else {
+#pragma unroll 2
+        for (int j = jg; j < mb; j += cg, bp += bstep)
+          *bp = kval<KID, T>(PtsOf<T>::template geom<KID>(pa, pb + j * NS), scale, pw);
       }
     }
     __syncthreads();
