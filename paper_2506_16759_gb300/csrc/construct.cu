@@ -606,6 +606,40 @@ __device__ __forceinline__ float2 df_sub_prod(float2 a, float2 w, float2 v) {
   return df_norm(h, __fadd_rn(t, __fsub_rn(a.y, e)));
 }
 
+// The sum of tot and the argmax of (best, bi) over the CTA in one pass
+// (lowest index on ties); every thread gets both.  Two barriers: the caller
+// keeps a barrier between two calls.
+__device__ void block_sum_argmax(double &tot, double &best, int &bi, double *sh, double *shv,
+                                 int *shi) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+  }
+  if (lane == 0) { sh[warp] = tot; shv[warp] = best; shi[warp] = bi; }
+  __syncthreads();
+  if (warp == 0) {
+    double t = lane < nw ? sh[lane] : 0.0;
+    double w = lane < nw ? shv[lane] : -1.0;
+    int wi = lane < nw ? shi[lane] : 0x7fffffff;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      t += __shfl_xor_sync(0xffffffffu, t, o);
+      const double ov = __shfl_xor_sync(0xffffffffu, w, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, wi, o);
+      if (ov > w || (ov == w && oi < wi)) { w = ov; wi = oi; }
+    }
+    if (lane == 0) { sh[32] = t; shv[32] = w; shi[32] = wi; }
+  }
+  __syncthreads();
+  tot = sh[32];
+  best = shv[32];
+  bi = shi[32];
+}
+
 // Sum over a group of TPC consecutive lanes (mask: the group's lanes).
 template <int TPC>
 __device__ __forceinline__ double group_sum(double v, unsigned mask) {
@@ -759,13 +793,17 @@ __device__ __forceinline__ void qr_task_df(const QrArgs &a, int tau, unsigned ch
     const double x0 = df_val(A[(int64_t)j * d + j]);
     const double alpha = x0 != 0.0 ? -copysign(nrm, x0) : -nrm;
     const double beta = 1.0 / (nrm * (nrm + fabs(x0)));
-    __syncthreads();
-    if (threadIdx.x == 0) A[(int64_t)j * d + j] = df_from(x0 - alpha);   // v_j
-    __syncthreads();
+    // the reflector's first entry stays in registers (A(j, j) itself is never
+    // read again), so the step needs no barrier before its updates
+    const float2 vj = df_from(x0 - alpha);
     // the group's rows: j + sub, j + sub + 4, ... (row j, the pivot row, is sub 0's)
     for (int c = j + 1 + slot; c < d; c += kSlots) {
       DfAcc w0, w1;
       int i = j + sub;
+      if (sub == 0) {
+        w0.add_prod(vj, A[(int64_t)j * d + c]);
+        i += kTpc;
+      }
       for (; i + kTpc < m; i += 2 * kTpc) {
         w0.add_prod(A[(int64_t)i * d + j], A[(int64_t)i * d + c]);
         w1.add_prod(A[(int64_t)(i + kTpc) * d + j], A[(int64_t)(i + kTpc) * d + c]);
@@ -773,10 +811,15 @@ __device__ __forceinline__ void qr_task_df(const QrArgs &a, int tau, unsigned ch
       if (i < m) w0.add_prod(A[(int64_t)i * d + j], A[(int64_t)i * d + c]);
       const float2 w = df_from(group_sum<kTpc>(w0.value() + w1.value(), gmask) * beta);
       DfAcc s2;
-      for (int r = j + sub; r < m; r += kTpc) {
+      int r = j + sub;
+      if (sub == 0) {
+        A[(int64_t)j * d + c] = df_sub_prod(A[(int64_t)j * d + c], w, vj);
+        r += kTpc;
+      }
+      for (; r < m; r += kTpc) {
         const float2 x = df_sub_prod(A[(int64_t)r * d + c], w, A[(int64_t)r * d + j]);
         A[(int64_t)r * d + c] = x;
-        if (r > j) s2.add_prod(x, x);
+        s2.add_prod(x, x);
       }
       const double v = group_sum<kTpc>(s2.value(), gmask);
       if (sub == 0) nrm2[c] = v;
@@ -1019,9 +1062,9 @@ __device__ __forceinline__ void id_task_df(const IdArgs &a, int tau, unsigned ch
       tot += nv;
       if (nv > best) { best = nv; bi = c; }
     }
-    tot = block_sum(tot, red);
+    block_sum_argmax(tot, best, bi, red, redv, redi);
     if (tot <= eps2) break;
-    const int p = block_argmax(best, bi, redv, redi);
+    const int p = bi;
     if (p < k || p >= m) break;  // no finite pivot left
     const double nk = sqrt(nrm2[p]);
     __syncthreads();
@@ -1040,20 +1083,24 @@ __device__ __forceinline__ void id_task_df(const IdArgs &a, int tau, unsigned ch
     const double x0 = df_val(A[(int64_t)k * m + k]);
     const double alpha = x0 != 0.0 ? -copysign(nk, x0) : -nk;
     const double beta = nk > 0.0 ? 1.0 / (nk * (nk + fabs(x0))) : 0.0;
-    __syncthreads();
-    if (threadIdx.x == 0) A[(int64_t)k * m + k] = df_from(x0 - alpha);   // v_k
-    __syncthreads();
+    // the reflector's first entry stays in registers; A(k, k) receives R's
+    // diagonal after the updates
+    const float2 vk = df_from(x0 - alpha);
     for (int c = k + 1 + slot; c < m; c += kSlots) {
       const double nc2 = nrm2[c];
       DfAcc w0, w1;
       int r = k + sub;
+      if (sub == 0) {
+        w0.add_prod(vk, A[(int64_t)k * m + c]);
+        r += kTpc;
+      }
       for (; r + kTpc < d; r += 2 * kTpc) {
         w0.add_prod(A[(int64_t)r * m + k], A[(int64_t)r * m + c]);
         w1.add_prod(A[(int64_t)(r + kTpc) * m + k], A[(int64_t)(r + kTpc) * m + c]);
       }
       if (r < d) w0.add_prod(A[(int64_t)r * m + k], A[(int64_t)r * m + c]);
       const float2 w = df_from(group_sum<kTpc>(w0.value() + w1.value(), gmask) * beta);
-      const float2 rkc = df_sub_prod(A[(int64_t)k * m + c], w, A[(int64_t)k * m + k]);
+      const float2 rkc = df_sub_prod(A[(int64_t)k * m + c], w, vk);
       __syncwarp(gmask);   // the group has read row k before it changes
       if (sub == 0) A[(int64_t)k * m + c] = rkc;
       // trailing norm downdated, |A(k+1:, c)|^2 = |A(k:, c)|^2 - R(k, c)^2,
@@ -1076,8 +1123,8 @@ __device__ __forceinline__ void id_task_df(const IdArgs &a, int tau, unsigned ch
       }
     }
     __syncthreads();
+    // column k is not read again before the next barrier
     if (threadIdx.x == 0) A[(int64_t)k * m + k] = df_from(alpha);
-    __syncthreads();
     ++k;
   }
   // T = R11^{-1} R12 by back substitution, written over R12 (one thread per
