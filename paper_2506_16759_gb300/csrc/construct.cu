@@ -587,7 +587,20 @@ struct DfAcc {
     c = __fadd_rn(c, __fadd_rn(t, e));
   }
   __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+  // s and c as one normalised pair; exact even where the sum cancelled below
+  // its rounding errors (|c| > |s|)
+  __device__ __forceinline__ float2 pair() const {
+    float h, l;
+    df_two_sum(s, c, h, l);
+    return make_float2(h, l);
+  }
 };
+// a + b (the error of the low parts' sum is below 2^-46 of |a| + |b|)
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  float s, e;
+  df_two_sum(a.x, b.x, s, e);
+  return df_norm(s, __fadd_rn(e, __fadd_rn(a.y, b.y)));
+}
 __device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
   const float p = __fmul_rn(a.x, b.x);
   float e = fmaf(a.x, b.x, -p);
@@ -645,6 +658,15 @@ template <int TPC>
 __device__ __forceinline__ double group_sum(double v, unsigned mask) {
   if constexpr (TPC >= 2) v += __shfl_xor_sync(mask, v, 1);
   if constexpr (TPC >= 4) v += __shfl_xor_sync(mask, v, 2);
+  return v;
+}
+// The same for double-float pairs (FP32 arithmetic only).
+template <int TPC>
+__device__ __forceinline__ float2 group_sum_df(float2 v, unsigned mask) {
+  if constexpr (TPC >= 2)
+    v = df_add(v, make_float2(__shfl_xor_sync(mask, v.x, 1), __shfl_xor_sync(mask, v.y, 1)));
+  if constexpr (TPC >= 4)
+    v = df_add(v, make_float2(__shfl_xor_sync(mask, v.x, 2), __shfl_xor_sync(mask, v.y, 2)));
   return v;
 }
 
@@ -794,8 +816,9 @@ __device__ __forceinline__ void qr_task_df(const QrArgs &a, int tau, unsigned ch
     const double alpha = x0 != 0.0 ? -copysign(nrm, x0) : -nrm;
     const double beta = 1.0 / (nrm * (nrm + fabs(x0)));
     // the reflector's first entry stays in registers (A(j, j) itself is never
-    // read again), so the step needs no barrier before its updates
-    const float2 vj = df_from(x0 - alpha);
+    // read again), so the step needs no barrier before its updates; the
+    // per-column scalars of the step stay in FP32 pairs (the FP64 pipe is slow)
+    const float2 vj = df_from(x0 - alpha), beta2 = df_from(beta);
     // the group's rows: j + sub, j + sub + 4, ... (row j, the pivot row, is sub 0's)
     for (int c = j + 1 + slot; c < d; c += kSlots) {
       DfAcc w0, w1;
@@ -809,7 +832,8 @@ __device__ __forceinline__ void qr_task_df(const QrArgs &a, int tau, unsigned ch
         w1.add_prod(A[(int64_t)(i + kTpc) * d + j], A[(int64_t)(i + kTpc) * d + c]);
       }
       if (i < m) w0.add_prod(A[(int64_t)i * d + j], A[(int64_t)i * d + c]);
-      const float2 w = df_from(group_sum<kTpc>(w0.value() + w1.value(), gmask) * beta);
+      const float2 w =
+          df_mul(group_sum_df<kTpc>(df_add(w0.pair(), w1.pair()), gmask), beta2);
       DfAcc s2;
       int r = j + sub;
       if (sub == 0) {
@@ -1084,8 +1108,8 @@ __device__ __forceinline__ void id_task_df(const IdArgs &a, int tau, unsigned ch
     const double alpha = x0 != 0.0 ? -copysign(nk, x0) : -nk;
     const double beta = nk > 0.0 ? 1.0 / (nk * (nk + fabs(x0))) : 0.0;
     // the reflector's first entry stays in registers; A(k, k) receives R's
-    // diagonal after the updates
-    const float2 vk = df_from(x0 - alpha);
+    // diagonal after the updates.  The per-column scalars stay in FP32 pairs.
+    const float2 vk = df_from(x0 - alpha), beta2 = df_from(beta);
     for (int c = k + 1 + slot; c < m; c += kSlots) {
       const double nc2 = nrm2[c];
       DfAcc w0, w1;
@@ -1099,7 +1123,8 @@ __device__ __forceinline__ void id_task_df(const IdArgs &a, int tau, unsigned ch
         w1.add_prod(A[(int64_t)(r + kTpc) * m + k], A[(int64_t)(r + kTpc) * m + c]);
       }
       if (r < d) w0.add_prod(A[(int64_t)r * m + k], A[(int64_t)r * m + c]);
-      const float2 w = df_from(group_sum<kTpc>(w0.value() + w1.value(), gmask) * beta);
+      const float2 w =
+          df_mul(group_sum_df<kTpc>(df_add(w0.pair(), w1.pair()), gmask), beta2);
       const float2 rkc = df_sub_prod(A[(int64_t)k * m + c], w, vk);
       __syncwarp(gmask);   // the group has read row k before it changes
       if (sub == 0) A[(int64_t)k * m + c] = rkc;
