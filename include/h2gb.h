@@ -372,11 +372,11 @@ h2_status h2_batched_row_id(int count, const int32_t *m, const int32_t *d, const
  * d[i] < 1 gets NaN and the call returns H2_ERR_ARG (checked on the device,
  * since m and d are device arrays).
  * The first call on a device looks up the workspace's device address (once
- * per device and CUDA context, with that device current); make that first
- * call before any stream capture.  All calls share the one workspace and it keeps the last
- * call's contents: calls that overlap on the GPU (other streams, other host
- * threads) race with each other.  The call waits for its stream to finish
- * before it returns. */
+ * per device and CUDA context, with that device current).  All calls share
+ * the one workspace and it keeps the last call's contents: calls that overlap
+ * on the GPU (other streams, other host threads) race with each other.  The
+ * call reads its status flag back and waits for its stream to finish before
+ * it returns, so it cannot be recorded into a CUDA graph (stream capture). */
 h2_status h2_batched_qr_mindiag_static(int count, const int32_t *m, const int32_t *d,
                                        const int64_t *off, const double *panels,
                                        double *mindiag, h2_stream_t s);
