@@ -764,13 +764,13 @@ __device__ __forceinline__ void qr_task(const QrArgs &a, int tau, unsigned char 
 
 // The same test on FP32 panels (mixed precision) in double-float arithmetic:
 // the panel and its Householder updates as hi/lo pairs (8 bytes, like FP64),
-// the scalars of a step (norm, alpha, beta, w) in FP64.  In clusters wider
-// than 128 four threads share a column (rows interleaved); their partial dot
-// products and norms meet in shuffles within the 4-lane group.
+// the scalars of a step (norm, alpha, beta, w) in FP64.  Two (clusters of 65
+// to 128 columns) or four (wider) threads share a column, rows interleaved;
+// their partial dot products and norms meet in shuffles within the group.
 template <int NT>
 __device__ __forceinline__ void qr_task_df(const QrArgs &a, int tau, unsigned char *smem_raw,
                                            double *nrm2) {
-  constexpr int kTpc = NT >= 512 ? 4 : 1, kSlots = NT / kTpc;
+  constexpr int kTpc = NT >= 512 ? 4 : (NT >= 256 ? 2 : 1), kSlots = NT / kTpc;
   const int inst = a.t.inst[tau];
   if (!a.active[inst] || a.conv[tau]) return;
   const int m = a.t.m[tau];
@@ -788,7 +788,9 @@ __device__ __forceinline__ void qr_task_df(const QrArgs &a, int tau, unsigned ch
   const float *Y = reinterpret_cast<const float *>(a.Y);
   const int64_t row = a.t.row[tau];
   const int slot = threadIdx.x / kTpc, sub = threadIdx.x % kTpc;
-  const unsigned gmask = kTpc == 4 ? 0xFu << (threadIdx.x & 28) : 1u << (threadIdx.x & 31);
+  const unsigned gmask = kTpc == 4   ? 0xFu << (threadIdx.x & 28)
+                         : kTpc == 2 ? 0x3u << (threadIdx.x & 30)
+                                     : 1u << (threadIdx.x & 31);
 
   for (int64_t q = threadIdx.x; q < (int64_t)m * d; q += NT) {
     const int i = (int)(q % m), c = (int)(q / m);
@@ -1037,9 +1039,11 @@ __device__ __forceinline__ void id_task(const IdArgs &a, int tau, unsigned char 
 template <int NT>
 __device__ __forceinline__ void id_task_df(const IdArgs &a, int tau, unsigned char *smem_raw,
                                            double *red, double *redv, int *redi) {
-  constexpr int kTpc = NT >= 512 ? 4 : 1, kSlots = NT / kTpc;
+  constexpr int kTpc = NT >= 512 ? 4 : (NT >= 256 ? 2 : 1), kSlots = NT / kTpc;
   const int slot = threadIdx.x / kTpc, sub = threadIdx.x % kTpc;
-  const unsigned gmask = kTpc == 4 ? 0xFu << (threadIdx.x & 28) : 1u << (threadIdx.x & 31);
+  const unsigned gmask = kTpc == 4   ? 0xFu << (threadIdx.x & 28)
+                         : kTpc == 2 ? 0x3u << (threadIdx.x & 30)
+                                     : 1u << (threadIdx.x & 31);
 
   const int inst = a.t.inst[tau];
   const int m = a.t.m[tau];
@@ -1688,7 +1692,7 @@ void bsr_apply(bool fp64, const BsrArgs &a_in, int max_m, int max_cols, cudaStre
 }
 
 // CTA width for clusters of up to `width` columns (64, 128 or 256 threads).
-template <template <typename, int> class K, int MUL, typename A>
+template <template <typename, int> class K, int MUL128, int MUL256, typename A>
 void launch_width(bool fp64, int width, const A &a, int n, size_t bytes, cudaStream_t s);
 
 template <typename T, int NT>
@@ -1700,9 +1704,9 @@ struct IdKern {
   static constexpr auto f = k_row_id<T, NT>;
 };
 
-// FP32 panels (double-float kernels) of clusters wider than 128 run MUL
-// threads per column.
-template <template <typename, int> class K, int MUL, typename A>
+// FP32 panels (double-float kernels) run MUL128 threads per column in
+// clusters of 65 to 128 columns and MUL256 in wider ones.
+template <template <typename, int> class K, int MUL128, int MUL256, typename A>
 void launch_width(bool fp64, int width, const A &a, int n, size_t bytes, cudaStream_t s) {
   auto go = [&](auto kern, int nt) {
     set_smem(kern, bytes);
@@ -1723,8 +1727,8 @@ void launch_width(bool fp64, int width, const A &a, int n, size_t bytes, cudaStr
     else go(K<double, 256>::f, 256);
   } else {
     if (w <= 64) go(K<float, 64>::f, 64);
-    else if (w <= 128) go(K<float, 128>::f, 128);
-    else go(K<float, 256 * MUL>::f, 256 * MUL);
+    else if (w <= 128) go(K<float, 128 * MUL128>::f, 128 * MUL128);
+    else go(K<float, 256 * MUL256>::f, 256 * MUL256);
   }
   count_launch();
   H2_CHECK_LAUNCH();
@@ -1732,7 +1736,7 @@ void launch_width(bool fp64, int width, const A &a, int n, size_t bytes, cudaStr
 
 void qr_test(bool fp64, const QrArgs &a, size_t smem_bytes, int width, cudaStream_t s) {
   if (a.t.n == 0) return;
-  launch_width<QrKern, 4>(fp64, width, a, a.t.n, smem_bytes, s);
+  launch_width<QrKern, 2, 4>(fp64, width, a, a.t.n, smem_bytes, s);
 }
 
 size_t row_id_fixed_smem(int mcap) { return (size_t)mcap * (sizeof(double) + 3 * sizeof(int)); }
@@ -1740,7 +1744,7 @@ size_t row_id_fixed_smem(int mcap) { return (size_t)mcap * (sizeof(double) + 3 *
 void row_id(bool fp64, const IdArgs &a, size_t smem_bytes, int width, cudaStream_t s) {
   if (a.t.n == 0) return;
   H2_REQUIRE(a.mcap >= 8 && a.mcap % 8 == 0 && a.mcap <= kMaxIdRows, "row ID capacity");
-  launch_width<IdKern, 4>(fp64, width, a, a.t.n, smem_bytes + row_id_fixed_smem(a.mcap), s);
+  launch_width<IdKern, 1, 4>(fp64, width, a, a.t.n, smem_bytes + row_id_fixed_smem(a.mcap), s);
 }
 
 void compact_skeletons(const TasksDev &t, const int32_t *J_tmp, const int32_t *skel_tmp,

@@ -396,16 +396,20 @@ __global__ void k_to64(const float *src, int64_t n, double *dst) {
 template <typename T>
 __global__ void k_sumsq_partial(const T *panel, const T *panel2, int64_t ld, const int64_t *base,
                                 const int64_t *nn, int d, double *part) {
-  int inst = blockIdx.y;
-  int64_t b = base[inst], n = nn[inst];
-  int64_t total = n * d;
+  // thread = rows r (grid stride) x every column: no index division, loads
+  // coalesced along the rows
+  const int inst = blockIdx.y;
+  const int64_t b = base[inst], n = nn[inst];
   double s = 0.0;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t r = e % n, c = e / n;
-    double v = (double)panel[b + r + c * ld];
-    if (panel2) v += (double)panel2[b + r + c * ld];
-    s += v * v;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const T *p1 = panel + b + r;
+    const T *p2 = panel2 ? panel2 + b + r : nullptr;
+    for (int c = 0; c < d; ++c) {
+      double v = (double)p1[(int64_t)c * ld];
+      if (p2) v += (double)p2[(int64_t)c * ld];
+      s += v * v;
+    }
   }
   __shared__ double sh[256];
   sh[threadIdx.x] = s;
@@ -797,7 +801,8 @@ void convert_to64(const float *src, int64_t n, double *dst, cudaStream_t s) {
 void instance_sumsq(const void *panel, const void *panel2, bool fp64, int64_t ld,
                     const int64_t *inst_base, const int64_t *inst_n, int count, int d,
                     double *out, cudaStream_t s) {
-  const int nb = 64;
+  // about two CTAs per SM over all instances
+  const int nb = std::max(4, std::min(256, 2 * device_sm_count() / std::max(count, 1)));
   DBuf<double> part;
   part.alloc((size_t)nb * count);
   dim3 grid(nb, count);
