@@ -52,16 +52,41 @@ __global__ void k_iota(int32_t *p, int64_t n) {
   if (i < n) p[i] = (int32_t)i;
 }
 
+// Box of a node from its coordinate minima a and maxima c; the extent
+// argmax (lowest dimension on ties) gives its split dimension.
+__device__ void box_finish(int node, const double *a, const double *c, double *lo, double *hi,
+                           int n_nodes_total, int *split_dim) {
+  double ext[3];
+  for (int k = 0; k < 3; ++k) {
+    lo[k * n_nodes_total + node] = a[k];
+    hi[k * n_nodes_total + node] = c[k];
+    ext[k] = __dsub_rn(c[k], a[k]);
+  }
+  int s = 0;
+  for (int k = 1; k < 3; ++k)
+    if (ext[k] > ext[s]) s = k;
+  split_dim[node] = s;
+}
+
 // Tight box of each node of one depth over its points (in the current
-// order `cur`); the extent argmax (lowest dimension on ties) gives its split
-// dimension.  One CTA per node.
+// order `cur`).  CTA (node, part) takes the part-th of gridDim.y slices of
+// the node's points; with one slice it writes the box, else its partial
+// minima and maxima go to part[] for k_node_boxes_final (the top levels have
+// too few nodes to fill the device with one CTA each).
 __global__ void k_node_boxes(const double *__restrict__ x, const double *__restrict__ y,
                              const double *__restrict__ z, const int32_t *__restrict__ cur,
                              const int64_t *__restrict__ begin, const int64_t *__restrict__ end,
                              int first_node, double *lo, double *hi, int n_nodes_total,
-                             int *split_dim) {
+                             int *split_dim, double *part) {
   int node = first_node + blockIdx.x;
+  const int nsplit = gridDim.y;
   int64_t b = begin[node], e = end[node];
+  if (nsplit > 1) {
+    const int64_t chunk = (e - b + nsplit - 1) / nsplit;
+    const int64_t pb = b + blockIdx.y * chunk;
+    e = pb + chunk < e ? pb + chunk : e;
+    b = pb;
+  }
   double mn[3] = {INFINITY, INFINITY, INFINITY};
   double mx[3] = {-INFINITY, -INFINITY, -INFINITY};
   for (int64_t p = b + threadIdx.x; p < e; p += blockDim.x) {
@@ -86,19 +111,32 @@ __global__ void k_node_boxes(const double *__restrict__ x, const double *__restr
   __syncthreads();
   if (threadIdx.x == 0) {
     int nw = blockDim.x / 32;
-    double ext[3];
+    double a[3], c[3];
     for (int k = 0; k < 3; ++k) {
-      double a = smn[k][0], c = smx[k][0];
-      for (int w = 1; w < nw; ++w) { a = fmin(a, smn[k][w]); c = fmax(c, smx[k][w]); }
-      lo[k * n_nodes_total + node] = a;
-      hi[k * n_nodes_total + node] = c;
-      ext[k] = __dsub_rn(c, a);
+      a[k] = smn[k][0];
+      c[k] = smx[k][0];
+      for (int w = 1; w < nw; ++w) { a[k] = fmin(a[k], smn[k][w]); c[k] = fmax(c[k], smx[k][w]); }
     }
-    int s = 0;
-    for (int k = 1; k < 3; ++k)
-      if (ext[k] > ext[s]) s = k;
-    split_dim[node] = s;
+    if (nsplit == 1) {
+      box_finish(node, a, c, lo, hi, n_nodes_total, split_dim);
+    } else {
+      double *pp = part + ((int64_t)blockIdx.x * nsplit + blockIdx.y) * 6;
+      for (int k = 0; k < 3; ++k) { pp[k] = a[k]; pp[3 + k] = c[k]; }
+    }
   }
+}
+
+// The boxes of nodes split over several CTAs: minima and maxima of the parts.
+__global__ void k_node_boxes_final(int n_at, int nsplit, int first_node, const double *part,
+                                   double *lo, double *hi, int n_nodes_total, int *split_dim) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_at) return;
+  double a[3] = {INFINITY, INFINITY, INFINITY}, c[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int q = 0; q < nsplit; ++q) {
+    const double *pp = part + ((int64_t)i * nsplit + q) * 6;
+    for (int k = 0; k < 3; ++k) { a[k] = fmin(a[k], pp[k]); c[k] = fmax(c[k], pp[3 + k]); }
+  }
+  box_finish(first_node + i, a, c, lo, hi, n_nodes_total, split_dim);
 }
 
 // Sort keys of every node of one depth, each segment padded to P slots.
@@ -484,14 +522,33 @@ void build_tree(const double *pts, int64_t n, int dim, int leaf, double eta, cud
   DBuf<int> split;
   split.alloc(n_nodes);
   DBuf<SortItem> items;
+  DBuf<double> box_part;   // partial boxes of nodes split over several CTAs
+  const int sms = device_sm_count();
 
   for (int k = 0; k <= L; ++k) {
     int first = (1 << k) - 1;
     int n_at = 1 << k;
-    k_node_boxes<<<n_at, 256, 0, s>>>(ox.p, oy.p, oz.p, t->perm.p, t->begin.p, t->end.p, first,
-                                      t->lo.p, t->hi.p, n_nodes, split.p);
-    count_launch();
-    H2_CHECK_LAUNCH();
+    {
+      // nodes of the top levels are split over several CTAs (slices of at
+      // least 1024 points) so that the level fills the device
+      const int64_t seg = (n + n_at - 1) / n_at;
+      int nsplit = n_at >= 2 * sms ? 1 : (2 * sms + n_at - 1) / n_at;
+      nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(nsplit, seg / 1024));
+      if (nsplit > 1 && (int64_t)box_part.n < (int64_t)n_at * nsplit * 6)
+        box_part.alloc((size_t)n_at * nsplit * 6);
+      k_node_boxes<<<dim3(n_at, nsplit), 256, 0, s>>>(ox.p, oy.p, oz.p, t->perm.p, t->begin.p,
+                                                      t->end.p, first, t->lo.p, t->hi.p, n_nodes,
+                                                      split.p, box_part.p);
+      count_launch();
+      H2_CHECK_LAUNCH();
+      if (nsplit > 1) {
+        k_node_boxes_final<<<ceil_div(n_at, 128), 128, 0, s>>>(n_at, nsplit, first, box_part.p,
+                                                                t->lo.p, t->hi.p, n_nodes,
+                                                                split.p);
+        count_launch();
+        H2_CHECK_LAUNCH();
+      }
+    }
     if (k == L) break;
     int64_t maxseg = (n + n_at - 1) / n_at;
     int64_t P = next_pow2(maxseg);
