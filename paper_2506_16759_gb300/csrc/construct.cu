@@ -1539,12 +1539,16 @@ __global__ void k_basis_capacity(int n, const int32_t *m, const int32_t *inst,
 __global__ void k_map_csr(const int64_t *ptr, const int32_t *idx, int nrows, int first_node,
                           int task_base, int64_t nnz_base, int64_t *ptr_out, int32_t *idx_out,
                           int32_t *erow_out, int write_last) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  // one warp per row: its entries are copied by the 32 lanes (coalesced)
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   if (r >= nrows) return;
-  int64_t b = ptr[r], e = ptr[r + 1];
-  ptr_out[task_base + r] = nnz_base + b;
-  if (write_last && r == nrows - 1) ptr_out[task_base + nrows] = nnz_base + e;
-  for (int64_t q = b; q < e; ++q) {
+  const int64_t b = ptr[r], e = ptr[r + 1];
+  if (lane == 0) {
+    ptr_out[task_base + r] = nnz_base + b;
+    if (write_last && r == nrows - 1) ptr_out[task_base + nrows] = nnz_base + e;
+  }
+  for (int64_t q = b + lane; q < e; q += 32) {
     idx_out[nnz_base + q] = task_base + (idx[q] - first_node);
     if (erow_out) erow_out[nnz_base + q] = task_base + r;
   }
@@ -1850,8 +1854,8 @@ void map_csr(const int64_t *ptr, const int32_t *idx, int nrows, int first_node, 
              int64_t nnz_base, int64_t *ptr_out, int32_t *idx_out, int32_t *erow_out,
              bool write_last, cudaStream_t s) {
   if (nrows == 0) return;
-  k_map_csr<<<ceil_div(nrows, 128), 128, 0, s>>>(ptr, idx, nrows, first_node, task_base, nnz_base,
-                                                 ptr_out, idx_out, erow_out, write_last ? 1 : 0);
+  k_map_csr<<<ceil_div(nrows, 4), 128, 0, s>>>(ptr, idx, nrows, first_node, task_base, nnz_base,
+                                               ptr_out, idx_out, erow_out, write_last ? 1 : 0);
   count_launch();
   H2_CHECK_LAUNCH();
 }

@@ -171,7 +171,8 @@ __global__ void k_bitonic_global(SortItem *items, int64_t total, int64_t P, int6
                                  int64_t stride) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   // thread t handles the pair whose lower index has bit `stride` clear
-  int64_t i = ((t / stride) * 2 * stride) + (t % stride);
+  // (stride is a power of two: the index is t with a zero bit inserted)
+  int64_t i = ((t & ~(stride - 1)) << 1) | (t & (stride - 1));
   int64_t j = i + stride;
   if (j >= total) return;
   bool up = ((i & (P - 1)) & size) == 0;
@@ -197,9 +198,9 @@ __global__ void __launch_bounds__(kSortTile / 2) k_bitonic_smem(SortItem *items,
     int64_t s0 = size / 2;
     if (s0 > kSortTile / 2) s0 = kSortTile / 2;
     for (int64_t stride = s0; stride > 0; stride >>= 1) {
-      int t = threadIdx.x;
-      int i = (int)(((t / stride) * 2 * stride) + (t % stride));
-      int j = i + (int)stride;
+      const int t = threadIdx.x, st = (int)stride;   // a power of two
+      const int i = ((t & ~(st - 1)) << 1) | (t & (st - 1));
+      const int j = i + st;
       int64_t gi = base + i;
       bool up = ((gi & (P - 1)) & size) == 0;
       SortItem a = sh[i], b = sh[j];
