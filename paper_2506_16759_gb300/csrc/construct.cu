@@ -1116,19 +1116,24 @@ __device__ __forceinline__ void id_task_df(const IdArgs &a, int tau, unsigned ch
     const float2 vk = df_from(x0 - alpha), beta2 = df_from(beta);
     for (int c = k + 1 + slot; c < m; c += kSlots) {
       const double nc2 = nrm2[c];
-      DfAcc w0, w1;
+      // four running sums (independent dependency chains)
+      DfAcc w0, w1, w2, w3;
       int r = k + sub;
       if (sub == 0) {
         w0.add_prod(vk, A[(int64_t)k * m + c]);
         r += kTpc;
       }
-      for (; r + kTpc < d; r += 2 * kTpc) {
+      for (; r + 3 * kTpc < d; r += 4 * kTpc) {
         w0.add_prod(A[(int64_t)r * m + k], A[(int64_t)r * m + c]);
         w1.add_prod(A[(int64_t)(r + kTpc) * m + k], A[(int64_t)(r + kTpc) * m + c]);
+        w2.add_prod(A[(int64_t)(r + 2 * kTpc) * m + k], A[(int64_t)(r + 2 * kTpc) * m + c]);
+        w3.add_prod(A[(int64_t)(r + 3 * kTpc) * m + k], A[(int64_t)(r + 3 * kTpc) * m + c]);
       }
-      if (r < d) w0.add_prod(A[(int64_t)r * m + k], A[(int64_t)r * m + c]);
-      const float2 w =
-          df_mul(group_sum_df<kTpc>(df_add(w0.pair(), w1.pair()), gmask), beta2);
+      for (; r < d; r += kTpc) w0.add_prod(A[(int64_t)r * m + k], A[(int64_t)r * m + c]);
+      const float2 w = df_mul(
+          group_sum_df<kTpc>(df_add(df_add(w0.pair(), w1.pair()), df_add(w2.pair(), w3.pair())),
+                             gmask),
+          beta2);
       const float2 rkc = df_sub_prod(A[(int64_t)k * m + c], w, vk);
       __syncwarp(gmask);   // the group has read row k before it changes
       if (sub == 0) A[(int64_t)k * m + c] = rkc;
