@@ -823,31 +823,46 @@ __device__ __forceinline__ void qr_task_df(const QrArgs &a, int tau, unsigned ch
     const float2 vj = df_from(x0 - alpha), beta2 = df_from(beta);
     // the group's rows: j + sub, j + sub + 4, ... (row j, the pivot row, is sub 0's)
     for (int c = j + 1 + slot; c < d; c += kSlots) {
-      DfAcc w0, w1;
+      // independent dependency chains: four running sums for the dot
+      // product, two for the trailing norm
+      DfAcc w0, w1, w2, w3;
       int i = j + sub;
       if (sub == 0) {
         w0.add_prod(vj, A[(int64_t)j * d + c]);
         i += kTpc;
       }
-      for (; i + kTpc < m; i += 2 * kTpc) {
+      for (; i + 3 * kTpc < m; i += 4 * kTpc) {
         w0.add_prod(A[(int64_t)i * d + j], A[(int64_t)i * d + c]);
         w1.add_prod(A[(int64_t)(i + kTpc) * d + j], A[(int64_t)(i + kTpc) * d + c]);
+        w2.add_prod(A[(int64_t)(i + 2 * kTpc) * d + j], A[(int64_t)(i + 2 * kTpc) * d + c]);
+        w3.add_prod(A[(int64_t)(i + 3 * kTpc) * d + j], A[(int64_t)(i + 3 * kTpc) * d + c]);
       }
-      if (i < m) w0.add_prod(A[(int64_t)i * d + j], A[(int64_t)i * d + c]);
-      const float2 w =
-          df_mul(group_sum_df<kTpc>(df_add(w0.pair(), w1.pair()), gmask), beta2);
-      DfAcc s2;
+      for (; i < m; i += kTpc) w0.add_prod(A[(int64_t)i * d + j], A[(int64_t)i * d + c]);
+      const float2 w = df_mul(
+          group_sum_df<kTpc>(df_add(df_add(w0.pair(), w1.pair()), df_add(w2.pair(), w3.pair())),
+                             gmask),
+          beta2);
+      DfAcc s2, s3;
       int r = j + sub;
       if (sub == 0) {
         A[(int64_t)j * d + c] = df_sub_prod(A[(int64_t)j * d + c], w, vj);
         r += kTpc;
       }
-      for (; r < m; r += kTpc) {
+      for (; r + kTpc < m; r += 2 * kTpc) {
+        const float2 x = df_sub_prod(A[(int64_t)r * d + c], w, A[(int64_t)r * d + j]);
+        const float2 y =
+            df_sub_prod(A[(int64_t)(r + kTpc) * d + c], w, A[(int64_t)(r + kTpc) * d + j]);
+        A[(int64_t)r * d + c] = x;
+        A[(int64_t)(r + kTpc) * d + c] = y;
+        s2.add_prod(x, x);
+        s3.add_prod(y, y);
+      }
+      if (r < m) {
         const float2 x = df_sub_prod(A[(int64_t)r * d + c], w, A[(int64_t)r * d + j]);
         A[(int64_t)r * d + c] = x;
         s2.add_prod(x, x);
       }
-      const double v = group_sum<kTpc>(s2.value(), gmask);
+      const double v = group_sum<kTpc>(s2.value() + s3.value(), gmask);
       if (sub == 0) nrm2[c] = v;
     }
     __syncthreads();
