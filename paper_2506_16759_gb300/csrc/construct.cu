@@ -1519,7 +1519,7 @@ __global__ void __launch_bounds__(256) k_gen_rows(int n_rows, const int64_t *ptr
           *bp = gi == gbs[j] ? kdiag<KID, T>(gm, scale, pw, diag) : kval<KID, T>(gm, scale, pw);
         }
       } else {
-#pragma unroll 2
+#pragma unroll 4
         for (int j = jg; j < mb; j += cg, bp += bstep)
           *bp = kval<KID, T>(PtsOf<T>::template geom<KID>(pa, pb + j * NS), scale, pw);
       }
