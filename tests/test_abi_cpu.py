@@ -60,6 +60,20 @@ def test_structs_match_c_layout(built_lib):
     assert ctypes.sizeof(_lib.BuildOpts) % 8 == 0
 
 
+def test_options_struct_has_the_c_size(built_lib):
+    # h2_default_opts clears sizeof(h2_build_opts) bytes: on a buffer filled
+    # with a pattern it must clear exactly the binding's struct (a longer C
+    # struct would write past it, a shorter one would leave its tail)
+    n = ctypes.sizeof(_lib.BuildOpts)
+    buf = (ctypes.c_ubyte * (n + 64))(*([0xAB] * (n + 64)))
+    _lib.lib().h2_default_opts(ctypes.cast(buf, ctypes.POINTER(_lib.BuildOpts)))
+    assert all(b == 0xAB for b in buf[n:]), "the C struct is longer than the binding's"
+    o = _lib.BuildOpts.from_buffer(buf)
+    assert o.sum_engine == 0 and o.queue_order == 0 and o.nonsym == 0
+    tail = bytes(buf[n - 8:n])
+    assert tail != bytes([0xAB] * 8), "the C struct is shorter than the binding's"
+
+
 def test_library_targets_sm103a():
     # the build compiles and links every translation unit for sm_103a only
     from paper_2506_16759_gb300 import build
